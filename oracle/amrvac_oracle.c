@@ -1,0 +1,963 @@
+/*
+ * FP64 CPU oracle for the ideal-MHD + glm block update (MPI-AMRVAC 3.0,
+ * Keppens et al. 2023).  TEST INFRASTRUCTURE ONLY: used by the tests, by the
+ * smoke check and by the benchmark's CPU-baseline leg; never by the GPU library.
+ *
+ * Build: gcc -O2 -ffp-contract=off -fPIC -shared (no FMA contraction, IEEE
+ * division and square root), see oracle/__init__.py.
+ *
+ * Readings where the paper names a method without printing it (each one is a
+ * published method the paper cites, restated here from its definition):
+ *  - equations: ideal MHD in conservative form with magnetic pressure B^2/2,
+ *    plus the mixed glm field psi of Dedner et al. 2002 (Sect. 3.2, Table of
+ *    monopole control, option `glm`); psi enters only through the interface
+ *    solve and an exponential damping after each Euler sub-step; no
+ *    non-conservative sources.
+ *  - reconstruction on primitive variables (Sect. 3, "usually on the primitive
+ *    variables") with the `minmod`, `vanleer` and `koren` limiters of the
+ *    limiter table (orders 2, 2, 3; two ghost cells).
+ *  - a face whose reconstructed density or pressure is not positive falls back
+ *    to first order (cell values) on both sides (Sect. 7.4 mentions checks on
+ *    reconstructions; the fallback form is our reading).
+ *  - HLL (Harten 1983) with Davis speed bounds; HLLD (Miyoshi & Kusano 2005)
+ *    with outer speeds min/max(u) -/+ max(c_f) and a degeneracy threshold.
+ *  - SSPRK(2,2) and SSPRK(3,3) in Shu-Osher form (Gottlieb 2005, Sect. 3).
+ *  - CFL: dt = C / max over cells of sum_d (|v_d| + c_f,d)/dx_d, from U^n,
+ *    global per instance, no subcycling; c_h = max (|v_d| + c_f,d).
+ *  - AMR ghost values (the paper gives no operators): same level -> copy;
+ *    finer -> mean of the 2^d children; coarser -> coarse value plus
+ *    minmod-limited slopes times +-1/4 coarse cell, on conserved variables.
+ *    Requires full 2:1 balance (checked at creation).  No refluxing.
+ *  - outflow boundary: a ghost takes the value of the nearest in-domain cell of
+ *    its own level (zero gradient, Sect. 3.1.1 and Sect. 3.2.1).
+ */
+#include "amrvac_oracle.h"
+
+#include <math.h>
+#include <pthread.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define NV ORC_NVAR
+#define NG 2
+enum { RHO = 0, MX = 1, MY = 2, MZ = 3, EN = 4, BXV = 5, BYV = 6, BZV = 7, PSI = 8 };
+enum { ST_OK = 0, ST_SMALL = 4 };
+
+typedef struct {
+  int inst, level, idx[3];
+} blockinfo;
+
+struct orc_mesh {
+  orc_config cfg;
+  int ninst;
+  orc_instance* inst;
+  int nblocks;
+  blockinfo* blk;
+  int ncell;
+  int nthreads;
+  /* hash map (inst, level, i, j, k) -> leaf block id (>= 0) or -1 (refined) */
+  size_t hcap;
+  uint64_t* hkey;
+  int* hval;
+  unsigned char* hused;
+};
+
+/* ------------------------------------------------------------------------ */
+/* block map                                                                 */
+/* ------------------------------------------------------------------------ */
+
+static uint64_t mkkey(int inst, int L, long i, long j, long k) {
+  return ((uint64_t)inst << 43) | ((uint64_t)L << 39) | ((uint64_t)i << 26) |
+         ((uint64_t)j << 13) | (uint64_t)k;
+}
+
+static size_t hslot(const orc_mesh* m, uint64_t key) {
+  uint64_t h = key * 0x9E3779B97F4A7C15ull;
+  return (size_t)(h >> 17) & (m->hcap - 1);
+}
+
+/* returns >= 0 leaf id, -1 refined, -2 nothing at this level */
+static int hget(const orc_mesh* m, uint64_t key) {
+  size_t s = hslot(m, key);
+  while (m->hused[s]) {
+    if (m->hkey[s] == key) return m->hval[s];
+    s = (s + 1) & (m->hcap - 1);
+  }
+  return -2;
+}
+
+/* insert; returns the previous value (-2 if absent) */
+static int hput(orc_mesh* m, uint64_t key, int val) {
+  size_t s = hslot(m, key);
+  while (m->hused[s]) {
+    if (m->hkey[s] == key) {
+      int old = m->hval[s];
+      m->hval[s] = val;
+      return old;
+    }
+    s = (s + 1) & (m->hcap - 1);
+  }
+  m->hused[s] = 1;
+  m->hkey[s] = key;
+  m->hval[s] = val;
+  return -2;
+}
+
+static long cells_at_level(const orc_mesh* m, int inst, int L, int d) {
+  return (long)m->inst[inst].base[d] * m->cfg.nx[d] << L;
+}
+
+static long blocks_at_level(const orc_mesh* m, int inst, int L, int d) {
+  if (d >= m->cfg.ndim) return 1;
+  return (long)m->inst[inst].base[d] << L;
+}
+
+/* ------------------------------------------------------------------------ */
+/* pointwise physics                                                         */
+/* ------------------------------------------------------------------------ */
+
+void orc_cons_to_prim(double gamma, const double* u, double* w) {
+  double rho = u[RHO];
+  double vx = u[MX] / rho, vy = u[MY] / rho, vz = u[MZ] / rho;
+  double ke = 0.5 * (u[MX] * vx + u[MY] * vy + u[MZ] * vz);
+  double me = 0.5 * (u[BXV] * u[BXV] + u[BYV] * u[BYV] + u[BZV] * u[BZV]);
+  w[RHO] = rho;
+  w[1] = vx;
+  w[2] = vy;
+  w[3] = vz;
+  w[4] = (gamma - 1.0) * (u[EN] - ke - me);
+  w[5] = u[BXV];
+  w[6] = u[BYV];
+  w[7] = u[BZV];
+  w[8] = u[PSI];
+}
+
+void orc_prim_to_cons(double gamma, const double* w, double* u) {
+  double rho = w[0];
+  u[RHO] = rho;
+  u[MX] = rho * w[1];
+  u[MY] = rho * w[2];
+  u[MZ] = rho * w[3];
+  u[EN] = w[4] / (gamma - 1.0) + 0.5 * rho * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]) +
+          0.5 * (w[5] * w[5] + w[6] * w[6] + w[7] * w[7]);
+  u[BXV] = w[5];
+  u[BYV] = w[6];
+  u[BZV] = w[7];
+  u[PSI] = w[8];
+}
+
+/* fast magnetosonic speed along dir, cancellation-free form
+ * c_f^2 = (a^2 + b^2 + sqrt((a^2 - b^2)^2 + 4 a^2 b_t^2)) / 2 */
+double orc_fast_speed(double gamma, const double* w, int dir) {
+  int t1 = (dir + 1) % 3, t2 = (dir + 2) % 3;
+  double rho = w[0];
+  double a2 = gamma * w[4] / rho;
+  double bn = w[5 + dir], b1 = w[5 + t1], b2t = w[5 + t2];
+  double bt2 = (b1 * b1 + b2t * b2t) / rho;
+  double b2 = (bn * bn + b1 * b1 + b2t * b2t) / rho;
+  double dd = a2 - b2;
+  double cf2 = 0.5 * (a2 + b2 + sqrt(dd * dd + 4.0 * a2 * bt2));
+  return sqrt(cf2);
+}
+
+/* ------------------------------------------------------------------------ */
+/* limiters (limiter table of Sect. 3.1.1)                                   */
+/* ------------------------------------------------------------------------ */
+
+static double sgn(double x) { return (x > 0.0) - (x < 0.0); }
+static double dmin(double a, double b) { return a < b ? a : b; }
+static double dmax(double a, double b) { return a > b ? a : b; }
+
+static double minmod2(double a, double b) {
+  if (a * b > 0.0) return sgn(a) * dmin(fabs(a), fabs(b));
+  return 0.0;
+}
+
+/* left state at the right face (i+1/2) of the cell with values (a, b, c) */
+static double recon_plus(int lim, double a, double b, double c) {
+  double dm = b - a, dp = c - b;
+  if (!(dm * dp > 0.0)) return b;
+  switch (lim) {
+    case 0: return b + 0.5 * minmod2(dm, dp);
+    case 1: return b + 0.5 * (2.0 * dm * dp / (dm + dp));
+    default: {
+      /* Koren: phi(r) = max(0, min(2r, (2+r)/3, 2)) with r = dm/dp, times dp */
+      double am = fabs(dm), ap = fabs(dp);
+      double lim3 = dmin(dmin(2.0 * am, (am + 2.0 * ap) / 3.0), 2.0 * ap);
+      return b + 0.5 * sgn(dp) * lim3;
+    }
+  }
+}
+
+/* right state at the left face (i-1/2) of the cell with values (a, b, c) */
+static double recon_minus(int lim, double a, double b, double c) {
+  double dm = b - a, dp = c - b;
+  if (!(dm * dp > 0.0)) return b;
+  switch (lim) {
+    case 0: return b - 0.5 * minmod2(dm, dp);
+    case 1: return b - 0.5 * (2.0 * dm * dp / (dm + dp));
+    default: {
+      double am = fabs(dm), ap = fabs(dp);
+      double lim3 = dmin(dmin(2.0 * ap, (ap + 2.0 * am) / 3.0), 2.0 * am);
+      return b - 0.5 * sgn(dm) * lim3;
+    }
+  }
+}
+
+void orc_reconstruct(int limiter, const double* w, int n, double* wl, double* wr) {
+  for (int i = 1; i + 1 < n; i++) {
+    wl[i] = recon_plus(limiter, w[i - 1], w[i], w[i + 1]);
+    wr[i] = recon_minus(limiter, w[i - 1], w[i], w[i + 1]);
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Riemann solvers in the face frame: x = face normal                        */
+/* local prim q = (rho, u, v, w, p, Bx, By, Bz);  local cons U, flux F.      */
+/* ------------------------------------------------------------------------ */
+
+static void local_cons_flux(double g, const double* q, double bx, double* U, double* F,
+                            double* pt_out) {
+  double rho = q[0], u = q[1], v = q[2], w = q[3], p = q[4], by = q[6], bz = q[7];
+  double b2 = bx * bx + by * by + bz * bz;
+  double pt = p + 0.5 * b2;
+  double e = p / (g - 1.0) + 0.5 * rho * (u * u + v * v + w * w) + 0.5 * b2;
+  double vb = u * bx + v * by + w * bz;
+  U[0] = rho;
+  U[1] = rho * u;
+  U[2] = rho * v;
+  U[3] = rho * w;
+  U[4] = e;
+  U[5] = bx;
+  U[6] = by;
+  U[7] = bz;
+  F[0] = rho * u;
+  F[1] = rho * u * u + pt - bx * bx;
+  F[2] = rho * u * v - bx * by;
+  F[3] = rho * u * w - bx * bz;
+  F[4] = (e + pt) * u - bx * vb;
+  F[5] = 0.0;
+  F[6] = by * u - bx * v;
+  F[7] = bz * u - bx * w;
+  *pt_out = pt;
+}
+
+static double local_fast(double g, const double* q, double bx) {
+  double rho = q[0];
+  double a2 = g * q[4] / rho;
+  double bt2 = (q[6] * q[6] + q[7] * q[7]) / rho;
+  double b2 = (bx * bx + q[6] * q[6] + q[7] * q[7]) / rho;
+  double dd = a2 - b2;
+  return sqrt(0.5 * (a2 + b2 + sqrt(dd * dd + 4.0 * a2 * bt2)));
+}
+
+/* HLL, Harten, Lax & van Leer 1983 */
+static void hll_local(double g, const double* ql, const double* qr, double bx, double* f) {
+  double UL[8], UR[8], FL[8], FR[8], ptl, ptr;
+  local_cons_flux(g, ql, bx, UL, FL, &ptl);
+  local_cons_flux(g, qr, bx, UR, FR, &ptr);
+  double cfl = local_fast(g, ql, bx), cfr = local_fast(g, qr, bx);
+  double sl = dmin(ql[1] - cfl, qr[1] - cfr);
+  double sr = dmax(ql[1] + cfl, qr[1] + cfr);
+  for (int c = 0; c < 8; c++) {
+    if (sl >= 0.0) f[c] = FL[c];
+    else if (sr <= 0.0) f[c] = FR[c];
+    else f[c] = (sr * FL[c] - sl * FR[c] + sl * sr * (UR[c] - UL[c])) / (sr - sl);
+  }
+}
+
+/* one side of the HLLD single-star state, Miyoshi & Kusano 2005 */
+typedef struct {
+  double rs, vs, ws, bys, bzs, es;
+} star_t;
+
+static star_t hlld_star(double g, const double* q, const double* U, double pt, double s,
+                        double sm, double pts, double bx) {
+  (void)g;
+  star_t r;
+  double rho = q[0], u = q[1], v = q[2], w = q[3], by = q[6], bz = q[7];
+  double su = s - u;
+  r.rs = rho * su / (s - sm);
+  double big = rho * su * (s - sm);
+  double den = big - bx * bx;
+  double scale = dmax(fabs(big), bx * bx);
+  if (fabs(den) <= 1e-8 * scale) {
+    r.vs = v;
+    r.ws = w;
+    r.bys = by;
+    r.bzs = bz;
+  } else {
+    double tv = bx * (sm - u) / den;
+    double tb = (rho * su * su - bx * bx) / den;
+    r.vs = v - by * tv;
+    r.ws = w - bz * tv;
+    r.bys = by * tb;
+    r.bzs = bz * tb;
+  }
+  double vb = u * bx + v * by + w * bz;
+  double vbs = sm * bx + r.vs * r.bys + r.ws * r.bzs;
+  r.es = (su * U[4] - pt * u + pts * sm + bx * (vb - vbs)) / (s - sm);
+  return r;
+}
+
+static void hlld_local(double g, const double* ql, const double* qr, double bx, double* f) {
+  double UL[8], UR[8], FL[8], FR[8], ptl, ptr;
+  local_cons_flux(g, ql, bx, UL, FL, &ptl);
+  local_cons_flux(g, qr, bx, UR, FR, &ptr);
+  double cfl = local_fast(g, ql, bx), cfr = local_fast(g, qr, bx);
+  double ul = ql[1], ur = qr[1];
+  double cmax = dmax(cfl, cfr);
+  double sl = dmin(ul, ur) - cmax;
+  double sr = dmax(ul, ur) + cmax;
+  if (sl > 0.0) {
+    for (int c = 0; c < 8; c++) f[c] = FL[c];
+    return;
+  }
+  if (sr < 0.0) {
+    for (int c = 0; c < 8; c++) f[c] = FR[c];
+    return;
+  }
+  double rl = ql[0], rr = qr[0];
+  double sul = sl - ul, sur = sr - ur;
+  double den = sur * rr - sul * rl;
+  double sm = (sur * rr * ur - sul * rl * ul - ptr + ptl) / den;
+  double pts = (sur * rr * ptl - sul * rl * ptr + rl * rr * sur * sul * (ur - ul)) / den;
+  star_t L = hlld_star(g, ql, UL, ptl, sl, sm, pts, bx);
+  star_t R = hlld_star(g, qr, UR, ptr, sr, sm, pts, bx);
+  double sqrl = sqrt(L.rs), sqrr = sqrt(R.rs);
+  double ssl = sm - fabs(bx) / sqrl, ssr = sm + fabs(bx) / sqrr;
+  double sb = sgn(bx);
+  double ssum = sqrl + sqrr;
+  double vss = (sqrl * L.vs + sqrr * R.vs + (R.bys - L.bys) * sb) / ssum;
+  double wss = (sqrl * L.ws + sqrr * R.ws + (R.bzs - L.bzs) * sb) / ssum;
+  double byss = (sqrl * R.bys + sqrr * L.bys + sqrl * sqrr * (R.vs - L.vs) * sb) / ssum;
+  double bzss = (sqrl * R.bzs + sqrr * L.bzs + sqrl * sqrr * (R.ws - L.ws) * sb) / ssum;
+  double vbss = sm * bx + vss * byss + wss * bzss;
+  double essl = L.es - sqrl * (sm * bx + L.vs * L.bys + L.ws * L.bzs - vbss) * sb;
+  double essr = R.es + sqrr * (sm * bx + R.vs * R.bys + R.ws * R.bzs - vbss) * sb;
+
+  /* star and double-star conserved states */
+  double USL[8] = {L.rs, L.rs * sm, L.rs * L.vs, L.rs * L.ws, L.es, bx, L.bys, L.bzs};
+  double USR[8] = {R.rs, R.rs * sm, R.rs * R.vs, R.rs * R.ws, R.es, bx, R.bys, R.bzs};
+  double USSL[8] = {L.rs, L.rs * sm, L.rs * vss, L.rs * wss, essl, bx, byss, bzss};
+  double USSR[8] = {R.rs, R.rs * sm, R.rs * vss, R.rs * wss, essr, bx, byss, bzss};
+  for (int c = 0; c < 8; c++) {
+    double fsl = FL[c] + sl * (USL[c] - UL[c]);
+    double fsr = FR[c] + sr * (USR[c] - UR[c]);
+    if (ssl >= 0.0) f[c] = fsl;
+    else if (sm >= 0.0) f[c] = fsl + ssl * (USSL[c] - USL[c]);
+    else if (ssr >= 0.0) f[c] = fsr + ssr * (USSR[c] - USR[c]);
+    else f[c] = fsr;
+  }
+}
+
+/* Face flux along dir from primitive states wl, wr (global frame, 9 entries).
+ * glm: B_n* and psi* from the (B_n, psi) subsystem (Dedner 2002), then the MHD
+ * flux with B_n = B_n* on both sides; F(B_n) = psi*, F(psi) = c_h^2 B_n*.
+ * Without glm: B_n = mean of the two sides, F(B_n) = F(psi) = 0. */
+void orc_face_flux(int flux, int glm, double gamma, double ch, int dir, const double* wl,
+                   const double* wr, double* f) {
+  int t1 = (dir + 1) % 3, t2 = (dir + 2) % 3;
+  double bnl = wl[5 + dir], bnr = wr[5 + dir];
+  double bns, psis;
+  if (glm) {
+    bns = 0.5 * (bnl + bnr) - (wr[8] - wl[8]) / (2.0 * ch);
+    psis = 0.5 * (wl[8] + wr[8]) - 0.5 * ch * (bnr - bnl);
+  } else {
+    bns = 0.5 * (bnl + bnr);
+    psis = 0.0;
+  }
+  double ql[8] = {wl[0], wl[1 + dir], wl[1 + t1], wl[1 + t2], wl[4], bns, wl[5 + t1], wl[5 + t2]};
+  double qr[8] = {wr[0], wr[1 + dir], wr[1 + t1], wr[1 + t2], wr[4], bns, wr[5 + t1], wr[5 + t2]};
+  double fl[8];
+  if (flux == 0) hll_local(gamma, ql, qr, bns, fl);
+  else hlld_local(gamma, ql, qr, bns, fl);
+  f[RHO] = fl[0];
+  f[MX + dir] = fl[1];
+  f[MX + t1] = fl[2];
+  f[MX + t2] = fl[3];
+  f[EN] = fl[4];
+  f[BXV + dir] = glm ? psis : 0.0;
+  f[BXV + t1] = fl[6];
+  f[BXV + t2] = fl[7];
+  f[PSI] = glm ? ch * ch * bns : 0.0;
+}
+
+void orc_stage_coeffs(int time, int k, double* a, double* b) {
+  if (k == 0) {
+    *a = 0.0;
+    *b = 1.0;
+  } else if (time == 0) {
+    *a = 0.5;
+    *b = 0.5;
+  } else if (k == 1) {
+    *a = 0.75;
+    *b = 0.25;
+  } else {
+    *a = 1.0 / 3.0;
+    *b = 2.0 / 3.0;
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* ghost values                                                              */
+/* ------------------------------------------------------------------------ */
+
+static int is_active(const orc_mesh* m, int d) { return d < m->cfg.ndim; }
+
+/* Conserved value of the level-L cell p of instance inst (p may lie outside
+ * the domain).  Recursive definition of the AMR ghost value. */
+static void value_at(const orc_mesh* m, const double* U, int inst, int L, const long* pin,
+                     double* out) {
+  long p[3] = {pin[0], pin[1], pin[2]};
+  for (int d = 0; d < 3; d++) {
+    if (!is_active(m, d)) {
+      p[d] = 0;
+      continue;
+    }
+    long N = cells_at_level(m, inst, L, d);
+    if (p[d] < 0 || p[d] >= N) {
+      if (m->cfg.bc[d][p[d] < 0 ? 0 : 1] == 0) {
+        p[d] = ((p[d] % N) + N) % N;
+      } else {
+        p[d] = p[d] < 0 ? 0 : N - 1;
+      }
+    }
+  }
+  long bp[3], c[3];
+  for (int d = 0; d < 3; d++) {
+    bp[d] = p[d] / m->cfg.nx[d];
+    c[d] = p[d] - bp[d] * m->cfg.nx[d];
+  }
+  int r = hget(m, mkkey(inst, L, bp[0], bp[1], bp[2]));
+  if (r >= 0) {
+    long cell = (c[2] * m->cfg.nx[1] + c[1]) * m->cfg.nx[0] + c[0];
+    for (int v = 0; v < NV; v++)
+      out[v] = U[((size_t)v * m->nblocks + r) * m->ncell + cell];
+    return;
+  }
+  if (r == -1) {
+    /* finer: mean of the 2^d children, children loop z, y, x (x fastest) */
+    double sum[NV] = {0};
+    int nchild = 0;
+    for (int oz = 0; oz < (is_active(m, 2) ? 2 : 1); oz++)
+      for (int oy = 0; oy < (is_active(m, 1) ? 2 : 1); oy++)
+        for (int ox = 0; ox < 2; ox++) {
+          long q[3] = {2 * p[0] + ox, is_active(m, 1) ? 2 * p[1] + oy : 0,
+                       is_active(m, 2) ? 2 * p[2] + oz : 0};
+          double tmp[NV];
+          value_at(m, U, inst, L + 1, q, tmp);
+          for (int v = 0; v < NV; v++) sum[v] += tmp[v];
+          nchild++;
+        }
+    for (int v = 0; v < NV; v++) out[v] = sum[v] * (1.0 / nchild);
+    return;
+  }
+  /* coarser: prolongation from the parent-level cell q = floor(p/2) */
+  long q[3], o[3];
+  for (int d = 0; d < 3; d++) {
+    q[d] = is_active(m, d) ? p[d] / 2 : 0;
+    o[d] = p[d] - 2 * q[d];
+  }
+  double uc[NV];
+  value_at(m, U, inst, L - 1, q, uc);
+  for (int v = 0; v < NV; v++) out[v] = uc[v];
+  for (int d = 0; d < 3; d++) {
+    if (!is_active(m, d)) continue;
+    long qm[3] = {q[0], q[1], q[2]}, qp[3] = {q[0], q[1], q[2]};
+    qm[d] -= 1;
+    qp[d] += 1;
+    double um[NV], up[NV];
+    value_at(m, U, inst, L - 1, qm, um);
+    value_at(m, U, inst, L - 1, qp, up);
+    double wgt = o[d] == 0 ? -0.25 : 0.25;
+    for (int v = 0; v < NV; v++) out[v] = out[v] + wgt * minmod2(uc[v] - um[v], up[v] - uc[v]);
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* mesh construction                                                         */
+/* ------------------------------------------------------------------------ */
+
+void orc_destroy(orc_mesh* m) {
+  if (!m) return;
+  free(m->inst);
+  free(m->blk);
+  free(m->hkey);
+  free(m->hval);
+  free(m->hused);
+  free(m);
+}
+
+void orc_set_threads(orc_mesh* m, int n) { m->nthreads = n < 1 ? 1 : n; }
+
+orc_mesh* orc_create(const orc_config* cfg, int ninst, const orc_instance* inst, int nblocks,
+                     const int32_t* meta, char* err, int errlen) {
+#define FAIL(...)                                   \
+  do {                                              \
+    if (err) snprintf(err, (size_t)errlen, __VA_ARGS__); \
+    orc_destroy(m);                                 \
+    return NULL;                                    \
+  } while (0)
+  orc_mesh* m = (orc_mesh*)calloc(1, sizeof(orc_mesh));
+  if (!m) return NULL;
+  m->cfg = *cfg;
+  m->ninst = ninst;
+  m->nblocks = nblocks;
+  m->nthreads = 1;
+  if (cfg->ndim < 1 || cfg->ndim > 3) FAIL("ndim must be 1..3");
+  for (int d = 0; d < 3; d++) {
+    if (d >= cfg->ndim) m->cfg.nx[d] = 1;
+    else if (cfg->nx[d] < NG) FAIL("block must have at least 2 cells per active dim");
+  }
+  m->ncell = m->cfg.nx[0] * m->cfg.nx[1] * m->cfg.nx[2];
+  m->inst = (orc_instance*)malloc(sizeof(orc_instance) * (size_t)ninst);
+  m->blk = (blockinfo*)malloc(sizeof(blockinfo) * (size_t)(nblocks > 0 ? nblocks : 1));
+  memcpy(m->inst, inst, sizeof(orc_instance) * (size_t)ninst);
+  for (int q = 0; q < ninst; q++)
+    for (int d = cfg->ndim; d < 3; d++) m->inst[q].base[d] = 1;
+  int maxlev = 0;
+  for (int b = 0; b < nblocks; b++) {
+    const int32_t* r = meta + 5 * b;
+    m->blk[b].inst = r[0];
+    m->blk[b].level = r[1];
+    for (int d = 0; d < 3; d++) m->blk[b].idx[d] = d < cfg->ndim ? r[2 + d] : 0;
+    if (r[0] < 0 || r[0] >= ninst) FAIL("block %d: bad instance", b);
+    if (r[1] < 0 || r[1] > 15) FAIL("block %d: bad level", b);
+    for (int d = 0; d < cfg->ndim; d++)
+      if (r[2 + d] < 0 || r[2 + d] >= blocks_at_level(m, r[0], r[1], d) || r[2 + d] >= 8192)
+        FAIL("block %d: index out of range", b);
+    if (r[1] > maxlev) maxlev = r[1];
+  }
+  size_t cap = 16;
+  while (cap < (size_t)4 * (size_t)(nblocks + 1) * (size_t)(maxlev + 1)) cap <<= 1;
+  m->hcap = cap;
+  m->hkey = (uint64_t*)calloc(cap, sizeof(uint64_t));
+  m->hval = (int*)calloc(cap, sizeof(int));
+  m->hused = (unsigned char*)calloc(cap, 1);
+  for (int b = 0; b < nblocks; b++) {
+    blockinfo* B = &m->blk[b];
+    if (hput(m, mkkey(B->inst, B->level, B->idx[0], B->idx[1], B->idx[2]), b) != -2)
+      FAIL("block %d duplicates another block", b);
+  }
+  for (int b = 0; b < nblocks; b++) {
+    blockinfo* B = &m->blk[b];
+    long p[3] = {B->idx[0], B->idx[1], B->idx[2]};
+    for (int L = B->level - 1; L >= 0; L--) {
+      for (int d = 0; d < 3; d++) p[d] /= 2;
+      int old = hget(m, mkkey(B->inst, L, p[0], p[1], p[2]));
+      if (old >= 0) FAIL("block %d overlaps block %d", b, old);
+      hput(m, mkkey(B->inst, L, p[0], p[1], p[2]), -1);
+    }
+  }
+  /* coverage: every level-0 position is a leaf or refined; every refined
+   * position has all children present */
+  for (int q = 0; q < ninst; q++) {
+    for (long k = 0; k < blocks_at_level(m, q, 0, 2); k++)
+      for (long j = 0; j < blocks_at_level(m, q, 0, 1); j++)
+        for (long i = 0; i < blocks_at_level(m, q, 0, 0); i++)
+          if (hget(m, mkkey(q, 0, i, j, k)) == -2) FAIL("instance %d: hole at level 0", q);
+  }
+  for (size_t s = 0; s < m->hcap; s++) {
+    if (!m->hused[s] || m->hval[s] != -1) continue;
+    uint64_t key = m->hkey[s];
+    int q = (int)(key >> 43), L = (int)((key >> 39) & 15);
+    long i = (long)((key >> 26) & 8191), j = (long)((key >> 13) & 8191), k = (long)(key & 8191);
+    for (int oz = 0; oz < (cfg->ndim > 2 ? 2 : 1); oz++)
+      for (int oy = 0; oy < (cfg->ndim > 1 ? 2 : 1); oy++)
+        for (int ox = 0; ox < 2; ox++)
+          if (hget(m, mkkey(q, L + 1, 2 * i + ox, 2 * j + oy, 2 * k + oz)) == -2)
+            FAIL("instance %d: hole below level %d", q, L);
+  }
+  /* full 2:1 balance: the leaf covering any neighbour position of a leaf at
+   * level L is at level >= L-1 */
+  for (int b = 0; b < nblocks; b++) {
+    blockinfo* B = &m->blk[b];
+    int lo[3], hi[3];
+    for (int d = 0; d < 3; d++) {
+      lo[d] = d < cfg->ndim ? -1 : 0;
+      hi[d] = d < cfg->ndim ? 1 : 0;
+    }
+    for (int dz = lo[2]; dz <= hi[2]; dz++)
+      for (int dy = lo[1]; dy <= hi[1]; dy++)
+        for (int dx = lo[0]; dx <= hi[0]; dx++) {
+          if (!dx && !dy && !dz) continue;
+          long p[3] = {B->idx[0] + dx, B->idx[1] + dy, B->idx[2] + dz};
+          int out = 0;
+          for (int d = 0; d < cfg->ndim; d++) {
+            long N = blocks_at_level(m, B->inst, B->level, d);
+            if (p[d] < 0 || p[d] >= N) {
+              if (cfg->bc[d][p[d] < 0 ? 0 : 1] == 0) p[d] = ((p[d] % N) + N) % N;
+              else out = 1;
+            }
+          }
+          if (out) continue;
+          int L = B->level;
+          int r = hget(m, mkkey(B->inst, L, p[0], p[1], p[2]));
+          while (r == -2 && L > 0) {
+            L--;
+            for (int d = 0; d < 3; d++) p[d] /= 2;
+            r = hget(m, mkkey(B->inst, L, p[0], p[1], p[2]));
+          }
+          if (r == -2) FAIL("block %d: neighbour not covered", b);
+          if (L < B->level - 1) FAIL("block %d (level %d) touches level %d: not 2:1", b, B->level, L);
+        }
+  }
+  return m;
+#undef FAIL
+}
+
+/* ------------------------------------------------------------------------ */
+/* block operations                                                          */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  int P[3];   /* padded extents */
+  int g[3];   /* ghost width per dim (2 active, 0 inactive) */
+  size_t np;  /* padded cells */
+} padinfo;
+
+static padinfo pad_of(const orc_mesh* m) {
+  padinfo p;
+  p.np = 1;
+  for (int d = 0; d < 3; d++) {
+    p.g[d] = is_active(m, d) ? NG : 0;
+    p.P[d] = m->cfg.nx[d] + 2 * p.g[d];
+    p.np *= (size_t)p.P[d];
+  }
+  return p;
+}
+
+static size_t pidx(const padinfo* pi, int i, int j, int k) {
+  return ((size_t)(k + pi->g[2]) * pi->P[1] + (size_t)(j + pi->g[1])) * pi->P[0] +
+         (size_t)(i + pi->g[0]);
+}
+
+static void cell_dx(const orc_mesh* m, int inst, int L, double* dx) {
+  for (int d = 0; d < 3; d++) {
+    if (!is_active(m, d)) dx[d] = 1.0;
+    else dx[d] = (m->inst[inst].xmax[d] - m->inst[inst].xmin[d]) / (double)cells_at_level(m, inst, L, d);
+  }
+}
+
+/* conserved values of block b on its padded box (interior + face slabs);
+ * cons[v * np + pidx] */
+static void gather_padded(const orc_mesh* m, const double* U, int b, double* cons) {
+  padinfo pi = pad_of(m);
+  const blockinfo* B = &m->blk[b];
+  const int* nx = m->cfg.nx;
+  memset(cons, 0, sizeof(double) * NV * pi.np);
+  for (int k = -pi.g[2]; k < nx[2] + pi.g[2]; k++)
+    for (int j = -pi.g[1]; j < nx[1] + pi.g[1]; j++)
+      for (int i = -pi.g[0]; i < nx[0] + pi.g[0]; i++) {
+        int outside = (i < 0 || i >= nx[0]) + (j < 0 || j >= nx[1]) + (k < 0 || k >= nx[2]);
+        if (outside > 1) continue;
+        double u[NV];
+        if (!outside) {
+          size_t cell = ((size_t)k * nx[1] + j) * nx[0] + i;
+          for (int v = 0; v < NV; v++) u[v] = U[((size_t)v * m->nblocks + b) * m->ncell + cell];
+        } else {
+          long p[3] = {(long)B->idx[0] * nx[0] + i, (long)B->idx[1] * nx[1] + j,
+                       (long)B->idx[2] * nx[2] + k};
+          value_at(m, U, B->inst, B->level, p, u);
+        }
+        size_t pc = pidx(&pi, i, j, k);
+        for (int v = 0; v < NV; v++) cons[v * pi.np + pc] = u[v];
+      }
+}
+
+int orc_fill_ghosts(const orc_mesh* m, const double* U, double* padded) {
+  padinfo pi = pad_of(m);
+  double* tmp = (double*)malloc(sizeof(double) * NV * pi.np);
+  for (int b = 0; b < m->nblocks; b++) {
+    gather_padded(m, U, b, tmp);
+    for (int v = 0; v < NV; v++)
+      memcpy(padded + ((size_t)v * m->nblocks + b) * pi.np, tmp + v * pi.np,
+             sizeof(double) * pi.np);
+  }
+  free(tmp);
+  return 0;
+}
+
+static int small_values(const orc_mesh* m, const double* w) {
+  if (!m->cfg.check_small_values) return 0;
+  return !(w[0] > m->cfg.small_density) || !(w[4] > m->cfg.small_pressure);
+}
+
+/* One stage on one block.  scratch: cons/prim padded (NV*np each) + fluxes. */
+static int block_stage(const orc_mesh* m, int b, int k, const double* dtv, const double* chv,
+                       const double* U0, const double* Uk, double* out, double* scratch) {
+  padinfo pi = pad_of(m);
+  const blockinfo* B = &m->blk[b];
+  const int* nx = m->cfg.nx;
+  const double gamma = m->inst[B->inst].gamma;
+  const double dt = dtv[B->inst], ch = chv[B->inst];
+  const size_t nvb = (size_t)m->nblocks * m->ncell;
+  int status = ST_OK;
+
+  if (dt == 0.0) {
+    for (int v = 0; v < NV; v++)
+      for (int c = 0; c < m->ncell; c++) {
+        size_t at = (size_t)v * nvb + (size_t)b * m->ncell + c;
+        out[at] = Uk[at];
+      }
+    return ST_OK;
+  }
+
+  double* cons = scratch;
+  double* W = scratch + NV * pi.np;
+  double* F[3];
+  size_t nf[3];
+  double* fp = W + NV * pi.np;
+  for (int d = 0; d < 3; d++) {
+    nf[d] = (size_t)(nx[0] + (d == 0)) * (nx[1] + (d == 1)) * (nx[2] + (d == 2));
+    F[d] = fp;
+    fp += NV * nf[d];
+  }
+
+  /* 1. ghost fill + conserved -> primitive on interior and face slabs */
+  gather_padded(m, Uk, b, cons);
+  for (int kk = -pi.g[2]; kk < nx[2] + pi.g[2]; kk++)
+    for (int j = -pi.g[1]; j < nx[1] + pi.g[1]; j++)
+      for (int i = -pi.g[0]; i < nx[0] + pi.g[0]; i++) {
+        int outside = (i < 0 || i >= nx[0]) + (j < 0 || j >= nx[1]) + (kk < 0 || kk >= nx[2]);
+        if (outside > 1) continue;
+        size_t pc = pidx(&pi, i, j, kk);
+        double u[NV], w[NV];
+        for (int v = 0; v < NV; v++) u[v] = cons[v * pi.np + pc];
+        orc_cons_to_prim(gamma, u, w);
+        if (small_values(m, w)) status = ST_SMALL;
+        for (int v = 0; v < NV; v++) W[v * pi.np + pc] = w[v];
+      }
+
+  /* 2. faces: reconstruction, positivity fallback, glm + Riemann flux */
+  for (int d = 0; d < m->cfg.ndim; d++) {
+    int ext[3] = {nx[0], nx[1], nx[2]};
+    ext[d] += 1;
+    for (int kk = 0; kk < ext[2]; kk++)
+      for (int j = 0; j < ext[1]; j++)
+        for (int i = 0; i < ext[0]; i++) {
+          /* face between cell (f-1) and cell f along d, f = (i,j,k)[d] */
+          int c[3] = {i, j, kk};
+          double wl[NV], wr[NV], w1[NV], w0[NV];
+          for (int v = 0; v < NV; v++) {
+            double s[4];
+            for (int t = 0; t < 4; t++) {
+              int cc[3] = {c[0], c[1], c[2]};
+              cc[d] += t - 2;
+              s[t] = W[v * pi.np + pidx(&pi, cc[0], cc[1], cc[2])];
+            }
+            wl[v] = recon_plus(m->cfg.limiter, s[0], s[1], s[2]);
+            wr[v] = recon_minus(m->cfg.limiter, s[1], s[2], s[3]);
+            w0[v] = s[1];
+            w1[v] = s[2];
+          }
+          if (!(wl[0] > 0.0) || !(wl[4] > 0.0) || !(wr[0] > 0.0) || !(wr[4] > 0.0)) {
+            for (int v = 0; v < NV; v++) {
+              wl[v] = w0[v];
+              wr[v] = w1[v];
+            }
+          }
+          double f[NV];
+          orc_face_flux(m->cfg.flux, m->cfg.glm, gamma, ch, d, wl, wr, f);
+          size_t fi = ((size_t)kk * ext[1] + j) * ext[0] + i;
+          for (int v = 0; v < NV; v++) F[d][v * nf[d] + fi] = f[v];
+        }
+  }
+
+  /* 3. update: Euler sub-step, psi damping, convex combination */
+  double dx[3];
+  cell_dx(m, B->inst, B->level, dx);
+  double dxmin = dx[0];
+  for (int d = 1; d < m->cfg.ndim; d++) dxmin = dmin(dxmin, dx[d]);
+  double damp = m->cfg.glm ? exp(-m->cfg.glm_alpha * ch * dt / dxmin) : 1.0;
+  double a, bb;
+  orc_stage_coeffs(m->cfg.time, k, &a, &bb);
+  for (int kk = 0; kk < nx[2]; kk++)
+    for (int j = 0; j < nx[1]; j++)
+      for (int i = 0; i < nx[0]; i++) {
+        size_t cell = ((size_t)kk * nx[1] + j) * nx[0] + i;
+        for (int v = 0; v < NV; v++) {
+          double acc = 0.0;
+          for (int d = 0; d < m->cfg.ndim; d++) {
+            int ext[3] = {nx[0], nx[1], nx[2]};
+            ext[d] += 1;
+            int cm[3] = {i, j, kk}, cp[3] = {i, j, kk};
+            cp[d] += 1;
+            size_t fm = ((size_t)cm[2] * ext[1] + cm[1]) * ext[0] + cm[0];
+            size_t fq = ((size_t)cp[2] * ext[1] + cp[1]) * ext[0] + cp[0];
+            acc += (F[d][v * nf[d] + fq] - F[d][v * nf[d] + fm]) / dx[d];
+          }
+          size_t at = (size_t)v * nvb + (size_t)b * m->ncell + cell;
+          double ut = Uk[at] - dt * acc;
+          if (v == PSI) ut = ut * damp;
+          out[at] = (k == 0) ? ut : a * U0[at] + bb * ut;
+        }
+      }
+  return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* threading over blocks                                                     */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  const orc_mesh* m;
+  int k;
+  const double *dt, *ch, *U0, *Uk;
+  double* out;
+  const int32_t* list;
+  int n, t, nt;
+  int status;
+} stage_job;
+
+static size_t scratch_doubles(const orc_mesh* m) {
+  padinfo pi = pad_of(m);
+  size_t s = 2 * NV * pi.np;
+  for (int d = 0; d < 3; d++)
+    s += NV * (size_t)(m->cfg.nx[0] + (d == 0)) * (m->cfg.nx[1] + (d == 1)) * (m->cfg.nx[2] + (d == 2));
+  return s;
+}
+
+static void* stage_worker(void* arg) {
+  stage_job* J = (stage_job*)arg;
+  double* scratch = (double*)malloc(sizeof(double) * scratch_doubles(J->m));
+  J->status = ST_OK;
+  for (int q = J->t; q < J->n; q += J->nt) {
+    int b = J->list ? J->list[q] : q;
+    int s = block_stage(J->m, b, J->k, J->dt, J->ch, J->U0, J->Uk, J->out, scratch);
+    if (s) J->status = s;
+  }
+  free(scratch);
+  return NULL;
+}
+
+int orc_stage(const orc_mesh* m, int k, const double* dt, const double* ch, const double* U0,
+              const double* Uk, double* out, const int32_t* sub, int nsub) {
+  int n = sub ? nsub : m->nblocks;
+  int nt = m->nthreads;
+  if (nt > n) nt = n > 0 ? n : 1;
+  stage_job* jobs = (stage_job*)calloc((size_t)nt, sizeof(stage_job));
+  pthread_t* th = (pthread_t*)calloc((size_t)nt, sizeof(pthread_t));
+  for (int t = 0; t < nt; t++) {
+    stage_job J = {m, k, dt, ch, U0, Uk, out, sub, n, t, nt, 0};
+    jobs[t] = J;
+    if (nt > 1) pthread_create(&th[t], NULL, stage_worker, &jobs[t]);
+    else stage_worker(&jobs[t]);
+  }
+  int status = ST_OK;
+  for (int t = 0; t < nt; t++) {
+    if (nt > 1) pthread_join(th[t], NULL);
+    if (jobs[t].status) status = jobs[t].status;
+  }
+  free(jobs);
+  free(th);
+  return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* CFL time step, sums, runs                                                 */
+/* ------------------------------------------------------------------------ */
+
+int orc_cfl(const orc_mesh* m, const double* U, const double* t, const double* t_end,
+            double* dt, double* ch) {
+  const size_t nvb = (size_t)m->nblocks * m->ncell;
+  double* smax = (double*)calloc((size_t)m->ninst, sizeof(double));
+  for (int q = 0; q < m->ninst; q++) ch[q] = 0.0;
+  for (int b = 0; b < m->nblocks; b++) {
+    const blockinfo* B = &m->blk[b];
+    double dx[3];
+    cell_dx(m, B->inst, B->level, dx);
+    double g = m->inst[B->inst].gamma;
+    for (int c = 0; c < m->ncell; c++) {
+      double u[NV], w[NV];
+      for (int v = 0; v < NV; v++) u[v] = U[(size_t)v * nvb + (size_t)b * m->ncell + c];
+      orc_cons_to_prim(g, u, w);
+      double s = 0.0;
+      for (int d = 0; d < m->cfg.ndim; d++) {
+        double sp = fabs(w[1 + d]) + orc_fast_speed(g, w, d);
+        s += sp / dx[d];
+        if (sp > ch[B->inst]) ch[B->inst] = sp;
+      }
+      if (s > smax[B->inst]) smax[B->inst] = s;
+    }
+  }
+  for (int q = 0; q < m->ninst; q++) {
+    double d = m->cfg.courant / smax[q];
+    double left = t_end[q] - t[q];
+    if (left <= 0.0) d = 0.0;
+    else if (d >= left) d = left;
+    dt[q] = d;
+  }
+  free(smax);
+  return 0;
+}
+
+void orc_sums(const orc_mesh* m, const double* U, double* sums) {
+  const size_t nvb = (size_t)m->nblocks * m->ncell;
+  memset(sums, 0, sizeof(double) * NV * (size_t)m->ninst);
+  for (int b = 0; b < m->nblocks; b++) {
+    const blockinfo* B = &m->blk[b];
+    double dx[3];
+    cell_dx(m, B->inst, B->level, dx);
+    double dv = dx[0];
+    for (int d = 1; d < m->cfg.ndim; d++) dv *= dx[d];
+    for (int v = 0; v < NV; v++) {
+      double s = 0.0;
+      for (int c = 0; c < m->ncell; c++) s += U[(size_t)v * nvb + (size_t)b * m->ncell + c];
+      sums[B->inst * NV + v] += s * dv;
+    }
+  }
+}
+
+int orc_run(orc_mesh* m, double* U, double* t, const double* t_end, int maxsteps,
+            double fixed_dt, int* nsteps_done) {
+  const size_t n = (size_t)NV * m->nblocks * m->ncell;
+  double* A = (double*)malloc(sizeof(double) * n);
+  double* Bf = (double*)malloc(sizeof(double) * n);
+  double* dt = (double*)malloc(sizeof(double) * (size_t)m->ninst);
+  double* ch = (double*)malloc(sizeof(double) * (size_t)m->ninst);
+  int status = ST_OK, s = 0;
+  for (; s < maxsteps; s++) {
+    orc_cfl(m, U, t, t_end, dt, ch);
+    if (fixed_dt > 0.0)
+      for (int q = 0; q < m->ninst; q++) {
+        double left = t_end[q] - t[q];
+        dt[q] = left <= 0.0 ? 0.0 : (fixed_dt >= left ? left : fixed_dt);
+      }
+    int any = 0;
+    for (int q = 0; q < m->ninst; q++) any |= dt[q] > 0.0;
+    if (!any) break;
+    int st;
+    if (m->cfg.time == 0) {
+      st = orc_stage(m, 0, dt, ch, U, U, A, NULL, 0);
+      if (st) status = st;
+      st = orc_stage(m, 1, dt, ch, U, A, Bf, NULL, 0);
+      if (st) status = st;
+      memcpy(U, Bf, sizeof(double) * n);
+    } else {
+      st = orc_stage(m, 0, dt, ch, U, U, A, NULL, 0);
+      if (st) status = st;
+      st = orc_stage(m, 1, dt, ch, U, A, Bf, NULL, 0);
+      if (st) status = st;
+      st = orc_stage(m, 2, dt, ch, U, Bf, A, NULL, 0);
+      if (st) status = st;
+      memcpy(U, A, sizeof(double) * n);
+    }
+    for (int q = 0; q < m->ninst; q++) {
+      if (dt[q] > 0.0 && dt[q] >= t_end[q] - t[q]) t[q] = t_end[q];
+      else t[q] += dt[q];
+    }
+    if (status) {
+      s++;
+      break;
+    }
+  }
+  if (nsteps_done) *nsteps_done = s;
+  free(A);
+  free(Bf);
+  free(dt);
+  free(ch);
+  return status;
+}
