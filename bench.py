@@ -1,0 +1,378 @@
+"""Benchmark: MHD cell-updates/s of the batched FP32-bulk block-AMR update and
+its fraction of the HBM roofline, beside the plain per-block FP64 path.
+
+One step = one full SSPRK3 time step (three stages: ghost fill, reconstruction,
+glm + HLLD flux, update, psi damping; CFL dt + conservation sums on the device)
+over every block of the workload.  Default workload: 3D block-AMR blast,
+18,304 blocks of 16^3 over 4 levels (ratio 2), FP32 bulk with FP64 pressure
+recovery, HLLD + vanleer, glm.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Prints one JSON line (rank 0).  Under torchrun each rank advances its own
+replica (the update shards by block but the halo exchange between GPUs is not
+built, so N > 1 runs independent replicas: weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+NOMINAL_HBM_GBS = 7900.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="c4", choices=["c4", "c5", "c3", "c2"])
+    p.add_argument("--kernel", default="auto", choices=["auto", "plain", "fused"])
+    p.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison leg")
+    p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU-baseline leg")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def make_workload(name, precision="fp32"):
+    from paper_2303_03026_gb300 import workloads as wl
+    if name == "c4":
+        W = wl.c4_blast_amr(base=6, precision=precision)
+        desc = {"workload": "3D block-AMR blast, %d blocks of 16^3 over 4 levels (ratio 2), "
+                            "shell 0.2<=r<=0.3, HLLD+vanleer+glm, SSPRK3" % W.nblocks,
+                "blocks": W.nblocks, "blocks_per_level": W.info["blocks_per_level"]}
+    elif name == "c5":
+        W = wl.c5_instances(precision=precision)
+        desc = {"workload": "256 uneven 2D instances 64^2..512^2 in 16^2 blocks, "
+                            "HLLD+vanleer+glm, SSPRK3, per-instance dt", "blocks": W.nblocks}
+    elif name == "c3":
+        W = wl.c3_turbulence(precision=precision)
+        desc = {"workload": "3D 256^3 Mach-1 beta-0.01 turbulence in 16^3 blocks, "
+                            "HLLD+vanleer+glm, SSPRK3", "blocks": W.nblocks}
+    else:
+        W = wl.c2_orszag_tang(1024, precision=precision)
+        desc = {"workload": "2D Orszag-Tang 1024^2 in 16^2 blocks, HLLD+koren+glm, SSPRK3",
+                "blocks": W.nblocks}
+    return W, desc
+
+
+def peaks():
+    try:
+        with open(PEAKS_PATH) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class Clocks:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines()]
+            os.unlink(self.path)
+        except Exception:
+            return out
+        mhz, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                mhz.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        if mhz:
+            out = {"sm_mhz": statistics.median(mhz), "sm_max_mhz": max(mx),
+                   "reasons": sorted(reasons), "samples": len(mhz)}
+        return out
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline(W, seconds_target=12.0, threads=None):
+    """The FP64 oracle as it stands, timed on the host cores on a bounded sample
+    of the workload's blocks: one full SSPRK3 step of ``nsample`` blocks."""
+    import oracle
+    threads = threads or os.cpu_count() or 1
+    m = oracle.mesh_for(W, threads)
+    U = W.U.astype(np.float64)
+    dt, ch = m.cfl(U)
+    rng = np.random.Generator(np.random.PCG64(11))
+    nsample = min(W.nblocks, 16)
+    while True:
+        blocks = np.sort(rng.choice(W.nblocks, nsample, replace=False)).astype(np.int32)
+        A = np.zeros_like(U)
+        t0 = time.perf_counter()
+        m.stage(0, dt, ch, U, U, blocks=blocks, out=A)
+        m.stage(1, dt, ch, U, A, blocks=blocks, out=A)
+        m.stage(2, dt, ch, U, A, blocks=blocks, out=A)
+        el = time.perf_counter() - t0
+        if el > seconds_target / 4 or nsample >= W.nblocks:
+            break
+        nsample = min(W.nblocks, int(nsample * max(2.0, (seconds_target / 4) / max(el, 1e-3))))
+    cells = nsample * W.ncell
+    return {"value": cells / el, "unit": "cell-updates/s", "cores": threads, "kind": "oracle",
+            "sample": "%d random blocks (%d cells) of the workload, one full SSPRK3 step "
+                      "(3 stages incl. ghost fill) in FP64, %.2f s" % (nsample, cells, el)}
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    W, desc = make_workload(args.workload, "fp64")
+    import oracle
+    threads = os.cpu_count() or 1
+    m = oracle.mesh_for(W, threads)
+    U = W.U
+    dt, ch = m.cfl(U)
+    rng = np.random.Generator(np.random.PCG64(13))
+    nsample = min(W.nblocks, max(threads * 4, 32))
+    blocks = np.sort(rng.choice(W.nblocks, nsample, replace=False)).astype(np.int32)
+    A = np.zeros_like(U)
+
+    def one():
+        m.stage(0, dt, ch, U, U, blocks=blocks, out=A)
+        m.stage(1, dt, ch, U, A, blocks=blocks, out=A)
+        m.stage(2, dt, ch, U, A, blocks=blocks, out=A)
+
+    for _ in range(args.warmup):
+        one()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one()
+    el = time.perf_counter() - t0
+    cells = nsample * W.ncell
+    value = cells * args.steps / el
+    line = {"impl": "reference", "metric": "MHD cell-updates/s", "value": value,
+            "unit": "cell-updates/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": dict(desc, sample_blocks=nsample),
+            "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": threads,
+                             "kind": "oracle",
+                             "sample": "%d random blocks (%d cells) per step, one full SSPRK3 "
+                                       "step each" % (nsample, cells)},
+            "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2303_03026_gb300 import amrvac
+
+    W, desc = make_workload(args.workload, "fp32")
+    cells = W.interior_cells()
+    S = amrvac.State.from_workload(W, device=dev, kernel=args.kernel)
+    U32 = torch.from_numpy(W.U.astype(np.float32)).to(dev)
+    S.set_conserved(U32)
+    stream = S.stream
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    # warm-up (also captures the step graph)
+    S.step(max(args.warmup, 3))
+    d = S.diag()
+    if d["status"] != 0:
+        raise RuntimeError("device error during warm-up: %s" % (d["error"],))
+
+    # timed region: K full steps, device-resident inputs (larger than L2)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n0 = S.launches
+    barrier()
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        S.step(args.steps)
+        ev1.record(stream)
+        barrier()
+    launches = S.launches - n0
+    ms = ev0.elapsed_time(ev1)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = cells * ws * args.steps / (ms / 1e3)
+    d = S.diag()
+    if d["status"] != 0:
+        raise RuntimeError("device error in the timed region: %s" % (d["error"],))
+
+    # per-stage kernel timing on the launching stream for the roofline
+    stage_ms = []
+    nst = 3
+    for rep in range(3):
+        S.cfl_dt()
+        row = []
+        for k in range(nst):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            S.stage(k)
+            e1.record(stream)
+            row.append((e0, e1))
+        stream.synchronize()
+        stage_ms.append([a.elapsed_time(b) for a, b in row])
+    stage_ms = np.median(np.array(stage_ms), axis=0)
+    passes = [2, 3, 3]
+    alg_bytes = [p * 9 * 4 * cells for p in passes]
+    hbm, src = peaks()
+    achieved = sum(alg_bytes) / (sum(stage_ms) / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None, "peak_source": src,
+                "kernel": "stage (fused)" if S._c.kernel != 1 and args.kernel != "plain" else
+                "stage (plain: prim+flux+update)",
+                "stage_ms": [float(x) for x in stage_ms],
+                "alg_bytes_per_cell_step": 288,
+                "frac_of_nominal_7900": achieved / NOMINAL_HBM_GBS}
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        n_e2e = max(2, min(args.steps, 5))
+        h_in = torch.from_numpy(W.U.astype(np.float32)).pin_memory()
+        h_out = torch.empty_like(h_in).pin_memory()
+        S.set_conserved(h_in)
+        S.step(1)
+        S.get_conserved(0, out=h_out)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            S.set_conserved(h_in)
+            S.step(1)
+            S.get_conserved(0, out=h_out)
+        barrier()
+        el = time.perf_counter() - t0
+        nbytes = h_in.numel() * 4
+        e2e = {"value": cells * ws * n_e2e / el, "unit": "cell-updates/s",
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+               "steps": n_e2e}
+
+    # plain FP64 per-block path on the same workload, and the FP32 error
+    fp64 = None
+    if not args.no_fp64:
+        W64 = W
+        S64 = amrvac.State.from_workload(W64, device=dev, kernel="plain")
+        U64 = torch.from_numpy(W.U.astype(np.float32).astype(np.float64)).to(dev)
+        S64.set_conserved(U64)
+        S64.step(2)
+        torch.cuda.synchronize(dev)
+        k64 = max(2, min(args.steps, 5))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(S64.stream)
+        S64.step(k64)
+        e1.record(S64.stream)
+        torch.cuda.synchronize(dev)
+        ms64 = e0.elapsed_time(e1) / k64
+        # accuracy at equal steps from the same state
+        S.set_conserved(U32)
+        S64.set_conserved(U64)
+        nacc = 5
+        S.step(nacc)
+        S64.step(nacc)
+        a = S.get_conserved(0, numpy=False).double()
+        b = S64.get_conserved(0, numpy=False)
+        l1 = ((a - b).abs().sum(dim=(1, 2)) / b.abs().sum(dim=(1, 2)).clamp_min(1e-300)).cpu()
+        fp64 = {"value": cells * ws / (ms64 / 1e3), "ms_per_step": ms64,
+                "speedup_fp32_fused_vs_fp64_plain": ms64 / ms_step,
+                "rel_l1_fp32_vs_fp64_after_%d_steps" % nacc:
+                    {n: float(x) for n, x in zip(("rho", "m_x", "m_y", "m_z", "e", "B_x", "B_y",
+                                                  "B_z", "psi"), l1.tolist())}}
+        S64.close()
+        del U64
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline(W)
+
+    if rank == 0:
+        line = {"metric": "MHD cell-updates/s (FP32-bulk batched block-AMR)", "value": value,
+                "unit": "cell-updates/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": dict(desc, cells=cells, l2="inputs larger than L2 (2.7 GB per buffer)",
+                               precision="fp32 bulk, fp64 pressure recovery, fp64 dt and sums",
+                               kernel=args.kernel, parallelism="replicas" if ws > 1 else "1 GPU"),
+                "clocks": clk.summary(), "gpu_launches": launches, "roofline": roofline,
+                "e2e": e2e, "fp64_plain": fp64, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    S.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

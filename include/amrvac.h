@@ -1,0 +1,221 @@
+/*
+ * amrvac.h - C ABI of the GB300 (sm_103a) ideal-MHD block-update library.
+ *
+ * The library advances the ideal-MHD equations with glm divergence cleaning on
+ * the blocks of a block-structured adaptive mesh, with the explicit
+ * finite-volume scheme of MPI-AMRVAC 3.0 (Keppens et al. 2023):
+ *   - conserved cell averages updated by interface fluxes in every substep of
+ *     an SSPRK(2,2) or SSPRK(3,3) scheme (Sect. 3, time-integration table);
+ *   - limited reconstruction of primitive variables to two face states per
+ *     interface with the `minmod`, `vanleer` or `koren` limiter, two ghost cells
+ *     per block face (Sect. 3 and the limiter table of Sect. 3.1.1);
+ *   - HLL (Harten 1983) or HLLD (Miyoshi & Kusano 2005) interface fluxes
+ *     (flux-scheme table of Sect. 3; Sect. 3.2.1);
+ *   - `glm` monopole control (Dedner 2002; table of Sect. 3.2.2);
+ *   - the CFL-limited explicit time step (Sect. 3);
+ *   - ghost cells filled from same-level neighbours, from finer neighbours by
+ *     restriction and from coarser neighbours by limited prolongation, i.e. the
+ *     internal boundary exchange of the AMR hierarchy (Sect. 8 describes its
+ *     MPI form; here it is a read from the device block pool).
+ * One explicit substep is the paper's advect1(alpha dt, t_a, u^a, t_b, u^b) of
+ * Sect. 4.2: u^b <- u^b + alpha dt F_ex(u^a) together with its boundary update.
+ *
+ * Conventions for every call:
+ *   - Every function returns an amrvac_status and never aborts the process.
+ *   - Device memory is owned by the caller: the library borrows the workspace
+ *     passed to amrvac_state_create for the state's lifetime and never frees
+ *     it; it allocates no device memory itself.  Host arrays are copied on call.
+ *   - All device work is enqueued on the stream given at creation, in call
+ *     order, and is asynchronous unless a host output pointer is given.  A
+ *     state is not thread-safe.
+ *   - Conserved variables, 9 per cell, in this order: rho, m_x, m_y, m_z, e,
+ *     B_x, B_y, B_z, psi; B in units where the magnetic pressure is B^2/2, so
+ *     p = (gamma - 1)(e - m^2/(2 rho) - B^2/2).  Three vector components are
+ *     always stored, in 1D and 2D too.
+ *   - Array layout [var][block][cell], cells x-fastest within a block,
+ *     interior cells only (ghost cells are never stored).
+ *   - Errors found on the device (small density or pressure, inconsistent
+ *     mesh lookups) are latched in a device status word and reported by the
+ *     next amrvac_get_diag or by any call that synchronises.
+ */
+#ifndef AMRVAC_H
+#define AMRVAC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define AMRVAC_NVAR 9
+#define AMRVAC_MAX_LEVELS 16
+
+typedef enum {
+  AMRVAC_OK = 0,
+  AMRVAC_E_INVALID = 1,      /* bad argument, config or block list            */
+  AMRVAC_E_NOMEM = 2,        /* workspace too small                           */
+  AMRVAC_E_CUDA = 3,         /* a CUDA runtime call failed                    */
+  AMRVAC_E_SMALL_VALUES = 4, /* density or pressure at or below its floor (Sect. 7.4:
+                                check_small_values stops and reports)         */
+  AMRVAC_E_TIMEOUT = 5,      /* reserved: a bounded device wait gave up       */
+  AMRVAC_E_STATE = 6         /* call out of order, or a mesh lookup failed    */
+} amrvac_status;
+
+typedef enum { AMRVAC_FLUX_HLL = 0, AMRVAC_FLUX_HLLD = 1 } amrvac_flux;
+typedef enum { AMRVAC_LIM_MINMOD = 0, AMRVAC_LIM_VANLEER = 1, AMRVAC_LIM_KOREN = 2 } amrvac_limiter;
+typedef enum { AMRVAC_SSPRK2 = 0, AMRVAC_SSPRK3 = 1 } amrvac_time;
+/* FP64: state and arithmetic in double.  FP32_BULK: state and stencil/Riemann
+ * arithmetic in float; thermal pressure recovered from the total energy in
+ * double; conservation sums and the time step in double. */
+typedef enum { AMRVAC_FP64 = 0, AMRVAC_FP32_BULK = 1 } amrvac_precision;
+typedef enum { AMRVAC_BC_PERIODIC = 0, AMRVAC_BC_OUTFLOW = 1 } amrvac_bc;
+/* PLAIN: one kernel per step of the method per stage, staging primitives and
+ * face fluxes in workspace scratch (the per-block baseline).  FUSED: one
+ * persistent kernel per stage doing ghost fill, reconstruction, flux, update
+ * and the time-step reduction with shared-memory staging.  AUTO picks FUSED
+ * for 16x16 (2D) and 16x16x16 (3D) blocks, PLAIN otherwise. */
+typedef enum { AMRVAC_KERNEL_AUTO = 0, AMRVAC_KERNEL_PLAIN = 1, AMRVAC_KERNEL_FUSED = 2 } amrvac_kernel;
+
+typedef struct {
+  int32_t ndim;           /* 1, 2 or 3                                          */
+  int32_t block_nx[3];    /* interior cells per block and dimension (>= 4 in
+                             active dims; entries of unused dims are ignored)  */
+  int32_t flux;           /* amrvac_flux                                        */
+  int32_t limiter;        /* amrvac_limiter                                     */
+  int32_t time;           /* amrvac_time                                        */
+  int32_t precision;      /* amrvac_precision                                   */
+  int32_t glm;            /* 1: glm cleaning (psi evolves); 0: psi stays 0      */
+  double glm_alpha;       /* psi damping: psi *= exp(-glm_alpha c_h dt / dx_min)
+                             after every Euler sub-step                         */
+  double courant;         /* CFL number C (Sect. 3)                             */
+  int32_t bc[3][2];       /* amrvac_bc per dimension and side                  */
+  double small_density;   /* check_small_values floors (Sect. 7.4)             */
+  double small_pressure;
+  int32_t check_small_values;
+  int32_t kernel;         /* amrvac_kernel                                      */
+} amrvac_config;
+
+/* One instance = one independent domain with its own gamma and clock. */
+typedef struct {
+  double xmin[3], xmax[3];
+  int32_t base_blocks[3]; /* level-0 blocks per dimension                       */
+  double gamma;
+  double t0, t_end;       /* the time step is clipped so that t never passes t_end */
+} amrvac_instance_desc;
+
+typedef struct {
+  int32_t code;           /* amrvac_status of the first device error, 0 if none */
+  int32_t block;          /* block index, cell index and variable where it was found */
+  int32_t cell;
+  int32_t var;
+} amrvac_error_info;
+
+typedef struct amrvac_state amrvac_state;
+
+/*
+ * Workspace size in bytes for a mesh; the caller allocates that much device
+ * memory (any allocator) and passes it to amrvac_state_create.
+ * block_meta: host int32 [nblocks][5] = (instance, level, i, j, k); level 0 is
+ * the base level, (i, j, k) the block index at that level (unused dims 0).
+ * The leaves must tile every instance's domain without overlap and be graded
+ * 2:1 across faces, edges and corners; otherwise AMRVAC_E_INVALID.
+ */
+amrvac_status amrvac_workspace_bytes(const amrvac_config* cfg, int32_t ninst,
+                                     const amrvac_instance_desc* inst, int32_t nblocks,
+                                     const int32_t* block_meta, size_t* bytes);
+
+/*
+ * Builds the mesh tables (neighbour table, per-level block maps) on the host,
+ * uploads them into the workspace and returns a state.  d_workspace must be
+ * 256-byte aligned and hold amrvac_workspace_bytes bytes.  cuda_stream is a
+ * cudaStream_t; graph capture in amrvac_step needs a stream other than the
+ * legacy default stream (0), otherwise steps are launched without a graph.
+ */
+amrvac_status amrvac_state_create(const amrvac_config* cfg, int32_t ninst,
+                                  const amrvac_instance_desc* inst, int32_t nblocks,
+                                  const int32_t* block_meta, void* d_workspace,
+                                  size_t workspace_bytes, void* cuda_stream,
+                                  amrvac_state** out);
+amrvac_status amrvac_state_destroy(amrvac_state* s);
+
+/*
+ * Copies conserved variables into (set) or out of (get) state buffer 0, 1 or 2.
+ * Buffer 0 holds U^n; 1 and 2 are the SSPRK stage registers.  src/dst are
+ * [var][block][cell] arrays in src_precision / dst_precision (AMRVAC_FP64 =
+ * double, AMRVAC_FP32_BULK = float), on the device (is_device = 1) or the host.
+ * Host copies of the state's own precision are asynchronous (page-locked
+ * memory is then required to stay valid until the stream reaches the copy);
+ * others synchronise.
+ */
+amrvac_status amrvac_set_conserved(amrvac_state* s, int32_t buffer, const void* src,
+                                   int32_t src_is_device, int32_t src_precision);
+amrvac_status amrvac_get_conserved(amrvac_state* s, int32_t buffer, void* dst,
+                                   int32_t dst_is_device, int32_t dst_precision);
+
+/* Per-instance clock: t (host array [ninst]) and t_end.  Marks dt invalid. */
+amrvac_status amrvac_set_time(amrvac_state* s, const double* h_t, const double* h_t_end);
+
+/*
+ * Ghost fill of buffer into d_padded_out (device, state precision):
+ * [var][block][padded cell] with (n_d + 4) cells per active dimension; the
+ * interior and the 2-deep face slabs are written, edge and corner cells are
+ * set to 0 (the unsplit scheme reads face ghosts only).  Same-level copy,
+ * periodic wrap, zero-gradient outflow, restriction (mean of the 2^d children)
+ * and prolongation (coarse value plus minmod-limited slopes times 1/4 of a
+ * coarse cell, on conserved variables).
+ */
+amrvac_status amrvac_fill_ghosts(amrvac_state* s, int32_t buffer, void* d_padded_out);
+
+/*
+ * CFL time step of buffer (Sect. 3): per instance dt = C / max over cells of
+ * sum_d (|v_d| + c_f,d)/dx_d, clipped to t_end - t, and the glm speed
+ * c_h = max over cells and d of (|v_d| + c_f,d).  Stored on the device for the
+ * next stages; also copied to h_dt_out[ninst] when it is not NULL (synchronises).
+ */
+amrvac_status amrvac_cfl_dt(amrvac_state* s, int32_t buffer, double* h_dt_out);
+
+/* Overrides the device dt and c_h of every instance (host arrays [ninst]). */
+amrvac_status amrvac_set_dt(amrvac_state* s, const double* h_dt, const double* h_ch);
+
+/*
+ * One SSPRK stage k (0-based) with the device-resident dt and c_h, i.e. one
+ * advect1 substep plus the convex combination of the Shu-Osher form:
+ *   out = a_k U^n + b_k (U_in + dt L(U_in)),  psi damped after the Euler part,
+ * SSPRK2: (a,b) = (0,1), (1/2,1/2); SSPRK3: (0,1), (3/4,1/4), (1/3,2/3).
+ * Buffers: stage 0 reads buffer 0 and writes 1; SSPRK2 stage 1 reads 0 and 1
+ * and writes 0; SSPRK3 stage 1 reads 0 and 1 and writes 2, stage 2 reads 0 and
+ * 2 and writes 0.  Instances whose dt is 0 are copied through unchanged.
+ */
+amrvac_status amrvac_stage(amrvac_state* s, int32_t stage);
+
+/*
+ * nsteps full time steps: all stages, then t += dt, the next dt and c_h from
+ * U^{n+1} and the conservation sums, all on the device (no host sync).  The
+ * first call computes dt if none is valid.  With a non-default stream the
+ * step is captured once as a CUDA graph and replayed.
+ */
+amrvac_status amrvac_step(amrvac_state* s, int32_t nsteps);
+
+/*
+ * Synchronises and reads per-instance t, dt, c_h ([ninst] each), the
+ * conservation sums h_sums[ninst][9] (integral of each conserved variable,
+ * FP64, fixed summation order; valid after a step or amrvac_cfl_dt) and the
+ * latched device error.  Any pointer may be NULL.  Returns the latched error
+ * code (AMRVAC_OK if none).
+ */
+amrvac_status amrvac_get_diag(amrvac_state* s, double* h_t, double* h_dt, double* h_ch,
+                              double* h_sums, amrvac_error_info* err);
+
+/* Clears the latched device error. */
+amrvac_status amrvac_clear_error(amrvac_state* s);
+
+/* Number of kernels this library launched on the state since creation. */
+int64_t amrvac_launch_count(const amrvac_state* s);
+
+const char* amrvac_error_string(amrvac_status st);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AMRVAC_H */

@@ -1,0 +1,281 @@
+"""Python binding of the amrvac C ABI (include/amrvac.h).
+
+Argument marshalling only: every step of the update runs in the CUDA library
+``_lib/libamrvac_gb300.so``.  PyTorch supplies the device workspace and the
+stream.  There is no CPU fallback: if the library is missing, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import workloads as wl
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libamrvac_gb300.so")
+
+STATUS = {0: "ok", 1: "invalid", 2: "nomem", 3: "cuda", 4: "small_values", 5: "timeout",
+          6: "state"}
+KERNEL = {"auto": 0, "plain": 1, "fused": 2}
+FP64, FP32 = 0, 1
+
+# every symbol include/amrvac.h declares
+SYMBOLS = ("amrvac_workspace_bytes", "amrvac_state_create", "amrvac_state_destroy",
+           "amrvac_set_conserved", "amrvac_get_conserved", "amrvac_set_time",
+           "amrvac_fill_ghosts", "amrvac_cfl_dt", "amrvac_set_dt", "amrvac_stage",
+           "amrvac_step", "amrvac_get_diag", "amrvac_clear_error", "amrvac_launch_count",
+           "amrvac_error_string")
+
+
+class AmrvacError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = int(status)
+        super().__init__("%s: amrvac status %d (%s)" % (what, self.status,
+                                                       STATUS.get(self.status, "?")))
+
+
+class Config(C.Structure):
+    _fields_ = [("ndim", C.c_int32), ("block_nx", C.c_int32 * 3), ("flux", C.c_int32),
+                ("limiter", C.c_int32), ("time", C.c_int32), ("precision", C.c_int32),
+                ("glm", C.c_int32), ("glm_alpha", C.c_double), ("courant", C.c_double),
+                ("bc", (C.c_int32 * 2) * 3), ("small_density", C.c_double),
+                ("small_pressure", C.c_double), ("check_small_values", C.c_int32),
+                ("kernel", C.c_int32)]
+
+
+class InstanceDesc(C.Structure):
+    _fields_ = [("xmin", C.c_double * 3), ("xmax", C.c_double * 3),
+                ("base_blocks", C.c_int32 * 3), ("gamma", C.c_double), ("t0", C.c_double),
+                ("t_end", C.c_double)]
+
+
+class ErrorInfo(C.Structure):
+    _fields_ = [("code", C.c_int32), ("block", C.c_int32), ("cell", C.c_int32),
+                ("var", C.c_int32)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError("libamrvac_gb300.so not built: run paper_2303_03026_gb300.build.build()")
+    L = C.CDLL(path)
+    vp, i32, dbl = C.c_void_p, C.c_int32, C.c_double
+    L.amrvac_workspace_bytes.argtypes = [C.POINTER(Config), i32, C.POINTER(InstanceDesc), i32,
+                                         vp, C.POINTER(C.c_size_t)]
+    L.amrvac_state_create.argtypes = [C.POINTER(Config), i32, C.POINTER(InstanceDesc), i32, vp,
+                                      vp, C.c_size_t, vp, C.POINTER(vp)]
+    L.amrvac_state_destroy.argtypes = [vp]
+    L.amrvac_set_conserved.argtypes = [vp, i32, vp, i32, i32]
+    L.amrvac_get_conserved.argtypes = [vp, i32, vp, i32, i32]
+    L.amrvac_set_time.argtypes = [vp, vp, vp]
+    L.amrvac_fill_ghosts.argtypes = [vp, i32, vp]
+    L.amrvac_cfl_dt.argtypes = [vp, i32, vp]
+    L.amrvac_set_dt.argtypes = [vp, vp, vp]
+    L.amrvac_stage.argtypes = [vp, i32]
+    L.amrvac_step.argtypes = [vp, i32]
+    L.amrvac_get_diag.argtypes = [vp, vp, vp, vp, vp, C.POINTER(ErrorInfo)]
+    L.amrvac_clear_error.argtypes = [vp]
+    L.amrvac_launch_count.argtypes = [vp]
+    L.amrvac_launch_count.restype = C.c_int64
+    L.amrvac_error_string.argtypes = [i32]
+    L.amrvac_error_string.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def make_config(cfg: wl.Config, kernel: str = "auto") -> Config:
+    c = Config()
+    c.ndim = cfg.ndim
+    for d in range(3):
+        c.block_nx[d] = int(cfg.block_nx[d]) if d < cfg.ndim else 1
+        c.bc[d][0] = wl.BC[cfg.bc[d][0]]
+        c.bc[d][1] = wl.BC[cfg.bc[d][1]]
+    c.flux = wl.FLUX[cfg.flux]
+    c.limiter = wl.LIMITER[cfg.limiter]
+    c.time = wl.TIME[cfg.time]
+    c.precision = wl.PRECISION[cfg.precision]
+    c.glm = int(bool(cfg.glm))
+    c.glm_alpha = float(cfg.glm_alpha)
+    c.courant = float(cfg.courant)
+    c.small_density = float(cfg.small_density)
+    c.small_pressure = float(cfg.small_pressure)
+    c.check_small_values = int(bool(cfg.check_small_values))
+    c.kernel = KERNEL[kernel]
+    return c
+
+
+def make_instances(instances) -> C.Array:
+    arr = (InstanceDesc * len(instances))()
+    for q, inst in enumerate(instances):
+        for d in range(3):
+            arr[q].xmin[d] = float(inst.xmin[d])
+            arr[q].xmax[d] = float(inst.xmax[d])
+            arr[q].base_blocks[d] = int(inst.base_blocks[d])
+        arr[q].gamma = float(inst.gamma)
+        arr[q].t0 = float(inst.t0)
+        arr[q].t_end = float(inst.t_end)
+    return arr
+
+
+def _check(st, what):
+    if st != 0:
+        raise AmrvacError(st, what)
+
+
+class State:
+    """One mesh + state on a GPU.  ``cfg``/``instances``/``block_meta`` follow
+    workloads.py; the device workspace is a torch uint8 tensor."""
+
+    def __init__(self, cfg, instances, block_meta, device="cuda:0", kernel="auto", stream=None):
+        import torch
+        self.torch = torch
+        L = load()
+        self.cfg = cfg
+        self.instances = list(instances)
+        self.ninst = len(self.instances)
+        self._c = make_config(cfg, kernel)
+        self._inst = make_instances(self.instances)
+        self.meta = np.ascontiguousarray(block_meta, np.int32)
+        self.nblocks = int(self.meta.shape[0])
+        self.ncell = int(np.prod([cfg.block_nx[d] if d < cfg.ndim else 1 for d in range(3)]))
+        self.precision = wl.PRECISION[cfg.precision]
+        self.dtype = torch.float64 if self.precision == FP64 else torch.float32
+        nbytes = C.c_size_t(0)
+        _check(L.amrvac_workspace_bytes(C.byref(self._c), self.ninst, self._inst, self.nblocks,
+                                        self.meta.ctypes.data, C.byref(nbytes)),
+               "amrvac_workspace_bytes")
+        self.device = torch.device(device)
+        self.workspace = torch.empty(int(nbytes.value) + 256, dtype=torch.uint8,
+                                     device=self.device)
+        base = self.workspace.data_ptr()
+        self._ws_ptr = (base + 255) // 256 * 256
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        h = C.c_void_p()
+        _check(L.amrvac_state_create(C.byref(self._c), self.ninst, self._inst, self.nblocks,
+                                     self.meta.ctypes.data, C.c_void_p(self._ws_ptr),
+                                     int(nbytes.value), C.c_void_p(self.stream.cuda_stream),
+                                     C.byref(h)), "amrvac_state_create")
+        self._h = h
+
+    @classmethod
+    def from_workload(cls, W, **kw):
+        return cls(W.cfg, W.instances, W.block_meta, **kw)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().amrvac_state_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def shape(self):
+        return (9, self.nblocks, self.ncell)
+
+    # ------------------------------------------------------------- data
+    def set_conserved(self, U, buffer=0):
+        """U: numpy array (host) or torch tensor (host or device), [9, nblocks, ncell]."""
+        torch = self.torch
+        if isinstance(U, np.ndarray):
+            U = np.ascontiguousarray(U)
+            assert U.shape == self.shape, U.shape
+            prec = FP64 if U.dtype == np.float64 else FP32
+            assert U.dtype in (np.float64, np.float32)
+            _check(load().amrvac_set_conserved(self._h, buffer, U.ctypes.data, 0, prec),
+                   "amrvac_set_conserved")
+            self.stream.synchronize()
+            return
+        assert tuple(U.shape) == self.shape and U.is_contiguous()
+        prec = FP64 if U.dtype == torch.float64 else FP32
+        _check(load().amrvac_set_conserved(self._h, buffer, U.data_ptr(), int(U.is_cuda), prec),
+               "amrvac_set_conserved")
+        if not U.is_cuda:
+            self.stream.synchronize()
+
+    def get_conserved(self, buffer=0, out=None, numpy=True, precision=None):
+        """Returns buffer as a numpy array (default) or a device tensor, or fills
+        ``out`` (torch tensor on host or device)."""
+        torch = self.torch
+        if out is None:
+            if numpy:
+                dt = np.float64 if (precision if precision is not None else self.precision) == FP64 \
+                    else np.float32
+                arr = np.empty(self.shape, dt)
+                prec = FP64 if dt == np.float64 else FP32
+                _check(load().amrvac_get_conserved(self._h, buffer, arr.ctypes.data, 0, prec),
+                       "amrvac_get_conserved")
+                self.stream.synchronize()
+                return arr
+            out = torch.empty(self.shape, dtype=self.dtype, device=self.device)
+        prec = FP64 if out.dtype == torch.float64 else FP32
+        _check(load().amrvac_get_conserved(self._h, buffer, out.data_ptr(), int(out.is_cuda), prec),
+               "amrvac_get_conserved")
+        if not out.is_cuda:
+            self.stream.synchronize()
+        return out
+
+    def fill_ghosts(self, buffer=0):
+        P = 1
+        for d in range(self.cfg.ndim):
+            P *= self.cfg.block_nx[d] + 4
+        out = self.torch.zeros((9, self.nblocks, P), dtype=self.dtype, device=self.device)
+        self.torch.cuda.current_stream(self.device).synchronize()
+        _check(load().amrvac_fill_ghosts(self._h, buffer, out.data_ptr()), "amrvac_fill_ghosts")
+        self.stream.synchronize()
+        return out.cpu().numpy()
+
+    # ------------------------------------------------------------- time
+    def set_time(self, t=None, t_end=None):
+        tp = None if t is None else np.ascontiguousarray(np.broadcast_to(t, (self.ninst,)), np.float64)
+        te = None if t_end is None else np.ascontiguousarray(
+            np.broadcast_to(t_end, (self.ninst,)), np.float64)
+        _check(load().amrvac_set_time(self._h, None if tp is None else tp.ctypes.data,
+                                      None if te is None else te.ctypes.data), "amrvac_set_time")
+
+    def cfl_dt(self, buffer=0):
+        dt = np.zeros(self.ninst)
+        _check(load().amrvac_cfl_dt(self._h, buffer, dt.ctypes.data), "amrvac_cfl_dt")
+        return dt
+
+    def set_dt(self, dt, ch):
+        dt = np.ascontiguousarray(np.broadcast_to(dt, (self.ninst,)), np.float64)
+        ch = np.ascontiguousarray(np.broadcast_to(ch, (self.ninst,)), np.float64)
+        _check(load().amrvac_set_dt(self._h, dt.ctypes.data, ch.ctypes.data), "amrvac_set_dt")
+
+    def stage(self, k):
+        _check(load().amrvac_stage(self._h, k), "amrvac_stage")
+
+    def step(self, n=1):
+        _check(load().amrvac_step(self._h, n), "amrvac_step")
+
+    def diag(self, raise_on_error=False):
+        t = np.zeros(self.ninst)
+        dt = np.zeros(self.ninst)
+        ch = np.zeros(self.ninst)
+        sums = np.zeros((self.ninst, 9))
+        err = ErrorInfo()
+        st = load().amrvac_get_diag(self._h, t.ctypes.data, dt.ctypes.data, ch.ctypes.data,
+                                    sums.ctypes.data, C.byref(err))
+        if st not in (0, 4, 6) or (raise_on_error and st != 0):
+            raise AmrvacError(st, "amrvac_get_diag")
+        return {"t": t, "dt": dt, "ch": ch, "sums": sums, "status": st,
+                "error": (err.code, err.block, err.cell, err.var)}
+
+    def clear_error(self):
+        _check(load().amrvac_clear_error(self._h), "amrvac_clear_error")
+
+    @property
+    def launches(self) -> int:
+        return int(load().amrvac_launch_count(self._h))

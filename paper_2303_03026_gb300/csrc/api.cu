@@ -1,0 +1,630 @@
+// C ABI of the amrvac GB300 library: mesh tables, workspace layout, state
+// management and the stage / step drivers (see include/amrvac.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "state.hpp"
+
+using namespace amrvac;
+
+namespace {
+
+constexpr size_t ALIGN = 256;
+
+size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
+
+struct Tables {
+  std::vector<int> blk, nbr, lmap, lmap_off, lnb, istart, iblocks;
+  std::vector<double> gamma, dx;
+  std::string err;
+};
+
+struct Layout {
+  size_t U[3], W, F[3], part, blk, nbr, lmap, lmap_off, lnb, gamma, dx, istart, iblocks, rt,
+      sums, err, work, total;
+};
+
+bool config_ok(const amrvac_config* c, std::string& err) {
+  if (!c) return err = "null config", false;
+  if (c->ndim < 1 || c->ndim > 3) return err = "ndim must be 1..3", false;
+  for (int d = 0; d < c->ndim; d++)
+    if (c->block_nx[d] < 4 || c->block_nx[d] > 4096) return err = "block_nx must be 4..4096", false;
+  if (c->flux != AMRVAC_FLUX_HLL && c->flux != AMRVAC_FLUX_HLLD) return err = "bad flux", false;
+  if (c->limiter < 0 || c->limiter > 2) return err = "bad limiter", false;
+  if (c->time != AMRVAC_SSPRK2 && c->time != AMRVAC_SSPRK3) return err = "bad time", false;
+  if (c->precision != AMRVAC_FP64 && c->precision != AMRVAC_FP32_BULK)
+    return err = "bad precision", false;
+  if (!(c->courant > 0.0) || !(c->glm_alpha >= 0.0)) return err = "bad courant/glm_alpha", false;
+  for (int d = 0; d < 3; d++)
+    for (int s = 0; s < 2; s++)
+      if (c->bc[d][s] != AMRVAC_BC_PERIODIC && c->bc[d][s] != AMRVAC_BC_OUTFLOW)
+        return err = "bad bc", false;
+  for (int d = 0; d < c->ndim; d++)
+    if ((c->bc[d][0] == AMRVAC_BC_PERIODIC) != (c->bc[d][1] == AMRVAC_BC_PERIODIC))
+      return err = "periodic bc must be set on both sides", false;
+  if (c->kernel < 0 || c->kernel > 2) return err = "bad kernel", false;
+  return true;
+}
+
+int nx_of(const amrvac_config* c, int d) { return d < c->ndim ? c->block_nx[d] : 1; }
+
+// Build and validate the block tables.  Per instance and level a dense map of
+// block positions: leaf id, MAP_REFINED or MAP_COARSER.
+bool build_tables(const amrvac_config* c, int ninst, const amrvac_instance_desc* inst,
+                  int nblocks, const int32_t* meta, Tables& T) {
+  if (ninst < 1 || nblocks < 1 || !inst || !meta) return T.err = "empty mesh", false;
+  std::vector<int> maxlev(ninst, -1);
+  for (int q = 0; q < ninst; q++) {
+    if (!(inst[q].gamma > 1.0)) return T.err = "gamma must exceed 1", false;
+    for (int d = 0; d < c->ndim; d++) {
+      if (inst[q].base_blocks[d] < 1) return T.err = "base_blocks must be >= 1", false;
+      if (!(inst[q].xmax[d] > inst[q].xmin[d])) return T.err = "empty domain", false;
+    }
+  }
+  for (int b = 0; b < nblocks; b++) {
+    const int32_t* r = meta + 5 * b;
+    if (r[0] < 0 || r[0] >= ninst) return T.err = "block instance out of range", false;
+    if (r[1] < 0 || r[1] >= MAXLEV) return T.err = "block level out of range", false;
+    for (int d = 0; d < c->ndim; d++) {
+      long n = (long)inst[r[0]].base_blocks[d] << r[1];
+      if (r[2 + d] < 0 || r[2 + d] >= n) return T.err = "block index out of range", false;
+    }
+    maxlev[r[0]] = std::max(maxlev[r[0]], (int)r[1]);
+  }
+  T.lmap_off.assign((size_t)ninst * MAXLEV, 0);
+  T.lnb.assign((size_t)ninst * MAXLEV * 3, 1);
+  T.dx.assign((size_t)ninst * MAXLEV * 3, 1.0);
+  T.gamma.resize(ninst);
+  size_t total = 0;
+  for (int q = 0; q < ninst; q++) {
+    if (maxlev[q] < 0) return T.err = "instance without blocks", false;
+    T.gamma[q] = inst[q].gamma;
+    for (int L = 0; L < MAXLEV; L++) {
+      size_t cnt = 1;
+      for (int d = 0; d < 3; d++) {
+        long n = d < c->ndim ? ((long)inst[q].base_blocks[d] << L) : 1;
+        if (L <= maxlev[q] && n > (1 << 20)) return T.err = "mesh too fine", false;
+        T.lnb[(q * MAXLEV + L) * 3 + d] = (int)std::min<long>(n, 1 << 30);
+        if (d < c->ndim)
+          T.dx[(q * MAXLEV + L) * 3 + d] =
+              (inst[q].xmax[d] - inst[q].xmin[d]) / ((double)n * c->block_nx[d]);
+        cnt *= (size_t)n;
+      }
+      T.lmap_off[q * MAXLEV + L] = (int)total;
+      if (L <= maxlev[q]) total += cnt;
+      if (total > (size_t)1 << 30) return T.err = "block maps too large", false;
+    }
+  }
+  T.lmap.assign(total, MAP_COARSER);
+  auto pos = [&](int q, int L, long i, long j, long k) -> int& {
+    const int* nb = &T.lnb[(q * MAXLEV + L) * 3];
+    return T.lmap[T.lmap_off[q * MAXLEV + L] + (size_t)((k * nb[1] + j) * nb[0] + i)];
+  };
+  for (int b = 0; b < nblocks; b++) {
+    const int32_t* r = meta + 5 * b;
+    long i = r[2], j = c->ndim > 1 ? r[3] : 0, k = c->ndim > 2 ? r[4] : 0;
+    int& m = pos(r[0], r[1], i, j, k);
+    if (m != MAP_COARSER) return T.err = "duplicate block", false;
+    m = b;
+  }
+  for (int b = 0; b < nblocks; b++) {
+    const int32_t* r = meta + 5 * b;
+    long p[3] = {r[2], c->ndim > 1 ? r[3] : 0, c->ndim > 2 ? r[4] : 0};
+    for (int L = r[1] - 1; L >= 0; L--) {
+      for (int d = 0; d < c->ndim; d++) p[d] >>= 1;
+      int& m = pos(r[0], L, p[0], p[1], p[2]);
+      if (m >= 0) return T.err = "overlapping blocks", false;
+      m = MAP_REFINED;
+    }
+  }
+  // coverage
+  for (int q = 0; q < ninst; q++)
+    for (int L = 0; L <= maxlev[q]; L++) {
+      const int* nb = &T.lnb[(q * MAXLEV + L) * 3];
+      for (long k = 0; k < nb[2]; k++)
+        for (long j = 0; j < nb[1]; j++)
+          for (long i = 0; i < nb[0]; i++) {
+            int m = pos(q, L, i, j, k);
+            if (L == 0 && m == MAP_COARSER) return T.err = "hole in the base level", false;
+            if (m != MAP_REFINED) continue;
+            if (L + 1 > maxlev[q]) return T.err = "refined position without children", false;
+            for (int oz = 0; oz < (c->ndim > 2 ? 2 : 1); oz++)
+              for (int oy = 0; oy < (c->ndim > 1 ? 2 : 1); oy++)
+                for (int ox = 0; ox < 2; ox++)
+                  if (pos(q, L + 1, 2 * i + ox, c->ndim > 1 ? 2 * j + oy : 0,
+                          c->ndim > 2 ? 2 * k + oz : 0) == MAP_COARSER)
+                    return T.err = "hole below a refined block", false;
+          }
+    }
+  // full 2:1 balance and the face neighbour table
+  T.blk.resize((size_t)nblocks * 5);
+  T.nbr.resize((size_t)nblocks * 6);
+  for (int b = 0; b < nblocks; b++) {
+    const int32_t* r = meta + 5 * b;
+    const int q = r[0], L = r[1];
+    long me[3] = {r[2], c->ndim > 1 ? r[3] : 0, c->ndim > 2 ? r[4] : 0};
+    for (int e = 0; e < 5; e++) T.blk[b * 5 + e] = e < 2 ? r[e] : (int)me[e - 2];
+    int lo[3], hi[3];
+    for (int d = 0; d < 3; d++) lo[d] = d < c->ndim ? -1 : 0, hi[d] = -lo[d];
+    for (int dz = lo[2]; dz <= hi[2]; dz++)
+      for (int dy = lo[1]; dy <= hi[1]; dy++)
+        for (int dxx = lo[0]; dxx <= hi[0]; dxx++) {
+          if (!dxx && !dy && !dz) continue;
+          long p[3] = {me[0] + dxx, me[1] + dy, me[2] + dz};
+          bool outside = false;
+          for (int d = 0; d < c->ndim; d++) {
+            long n = T.lnb[(q * MAXLEV + L) * 3 + d];
+            if (p[d] < 0 || p[d] >= n) {
+              if (c->bc[d][p[d] < 0 ? 0 : 1] == AMRVAC_BC_PERIODIC) p[d] = ((p[d] % n) + n) % n;
+              else outside = true;
+            }
+          }
+          if (outside) continue;
+          int LL = L;
+          int m = pos(q, LL, p[0], p[1], p[2]);
+          while (m == MAP_COARSER && LL > 0) {
+            LL--;
+            for (int d = 0; d < c->ndim; d++) p[d] >>= 1;
+            m = pos(q, LL, p[0], p[1], p[2]);
+          }
+          if (m == MAP_COARSER) return T.err = "uncovered neighbour", false;
+          if (LL < L - 1) return T.err = "mesh is not 2:1 balanced", false;
+        }
+    for (int d = 0; d < 3; d++)
+      for (int side = 0; side < 2; side++) {
+        int& out = T.nbr[b * 6 + d * 2 + side];
+        if (d >= c->ndim) {
+          out = NBR_OUTFLOW;
+          continue;
+        }
+        long p[3] = {me[0], me[1], me[2]};
+        p[d] += side ? 1 : -1;
+        long n = T.lnb[(q * MAXLEV + L) * 3 + d];
+        if (p[d] < 0 || p[d] >= n) {
+          if (c->bc[d][side] == AMRVAC_BC_PERIODIC) p[d] = ((p[d] % n) + n) % n;
+          else {
+            out = NBR_OUTFLOW;
+            continue;
+          }
+        }
+        int m = pos(q, L, p[0], p[1], p[2]);
+        out = m >= 0 ? m : NBR_GENERAL;
+      }
+  }
+  T.istart.assign(ninst + 1, 0);
+  for (int b = 0; b < nblocks; b++) T.istart[meta[5 * b] + 1]++;
+  for (int q = 0; q < ninst; q++) T.istart[q + 1] += T.istart[q];
+  T.iblocks.resize(nblocks);
+  std::vector<int> fill(T.istart.begin(), T.istart.end() - 1);
+  for (int b = 0; b < nblocks; b++) T.iblocks[fill[meta[5 * b]]++] = b;
+  return true;
+}
+
+bool use_fused_for(const amrvac_config* c) {
+  if (c->kernel == AMRVAC_KERNEL_PLAIN) return false;
+  if (c->kernel == AMRVAC_KERNEL_FUSED) return true;
+  return fused_supported(c);
+}
+
+Layout make_layout(const amrvac_config* c, int ninst, int nblocks, const Tables& T, bool fused) {
+  Layout L{};
+  size_t rs = c->precision == AMRVAC_FP64 ? 8 : 4;
+  size_t ncell = (size_t)nx_of(c, 0) * nx_of(c, 1) * nx_of(c, 2);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = off;
+    off = align_up(off + bytes);
+    return at;
+  };
+  for (int i = 0; i < 3; i++) L.U[i] = take(rs * NV * ncell * nblocks);
+  if (!fused) {
+    size_t np = 1;
+    for (int d = 0; d < 3; d++) np *= (size_t)(nx_of(c, d) + (d < c->ndim ? 2 * NG : 0));
+    L.W = take(rs * NV * np * nblocks);
+    for (int d = 0; d < 3; d++) {
+      size_t nf = 0;
+      if (d < c->ndim) nf = ncell / nx_of(c, d) * (nx_of(c, d) + 1);
+      L.F[d] = take(rs * NV * nf * nblocks);
+    }
+  }
+  L.part = take(sizeof(double) * NPART * nblocks);
+  L.blk = take(sizeof(int) * T.blk.size());
+  L.nbr = take(sizeof(int) * T.nbr.size());
+  L.lmap = take(sizeof(int) * T.lmap.size());
+  L.lmap_off = take(sizeof(int) * T.lmap_off.size());
+  L.lnb = take(sizeof(int) * T.lnb.size());
+  L.gamma = take(sizeof(double) * T.gamma.size());
+  L.dx = take(sizeof(double) * T.dx.size());
+  L.istart = take(sizeof(int) * T.istart.size());
+  L.iblocks = take(sizeof(int) * T.iblocks.size());
+  L.rt = take(sizeof(InstRT) * ninst);
+  L.sums = take(sizeof(double) * NV * ninst);
+  L.err = take(sizeof(int) * 4);
+  L.work = take(sizeof(int) * (size_t)nblocks);
+  L.total = off;
+  return L;
+}
+
+amrvac_status cuda_status(cudaError_t e) { return e == cudaSuccess ? AMRVAC_OK : AMRVAC_E_CUDA; }
+
+template <class T> T* at(amrvac_state* s, size_t off) { return (T*)(s->ws + off); }
+
+amrvac_status check_launch(amrvac_state* s, int n) {
+  if (n < 0) return AMRVAC_E_CUDA;
+  s->launches += n;
+  return AMRVAC_OK;
+}
+
+amrvac_status enqueue_stage(amrvac_state* s, int k, int epilogue, int* count) {
+  int n = s->use_fused ? launch_fused_stage(s, k, epilogue) : launch_plain_stage(s, k, epilogue);
+  if (n < 0) return AMRVAC_E_CUDA;
+  *count += n;
+  return AMRVAC_OK;
+}
+
+amrvac_status enqueue_step(amrvac_state* s, int* count) {
+  const int ns = num_stages(s->cfg.time);
+  for (int k = 0; k < ns; k++) {
+    amrvac_status st = enqueue_stage(s, k, k == ns - 1, count);
+    if (st) return st;
+  }
+  int n = launch_finalize(s, 1);
+  if (n < 0) return AMRVAC_E_CUDA;
+  *count += n;
+  return AMRVAC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* amrvac_error_string(amrvac_status st) {
+  switch (st) {
+    case AMRVAC_OK: return "ok";
+    case AMRVAC_E_INVALID: return "invalid argument, config or block list";
+    case AMRVAC_E_NOMEM: return "workspace too small";
+    case AMRVAC_E_CUDA: return "CUDA runtime error";
+    case AMRVAC_E_SMALL_VALUES: return "density or pressure at or below its floor";
+    case AMRVAC_E_TIMEOUT: return "bounded device wait gave up";
+    case AMRVAC_E_STATE: return "call out of order or inconsistent mesh lookup";
+  }
+  return "unknown status";
+}
+
+amrvac_status amrvac_workspace_bytes(const amrvac_config* cfg, int32_t ninst,
+                                     const amrvac_instance_desc* inst, int32_t nblocks,
+                                     const int32_t* block_meta, size_t* bytes) {
+  std::string err;
+  if (!bytes || !config_ok(cfg, err)) return AMRVAC_E_INVALID;
+  Tables T;
+  if (!build_tables(cfg, ninst, inst, nblocks, block_meta, T)) return AMRVAC_E_INVALID;
+  *bytes = make_layout(cfg, ninst, nblocks, T, use_fused_for(cfg)).total;
+  return AMRVAC_OK;
+}
+
+amrvac_status amrvac_state_create(const amrvac_config* cfg, int32_t ninst,
+                                  const amrvac_instance_desc* inst, int32_t nblocks,
+                                  const int32_t* block_meta, void* d_workspace,
+                                  size_t workspace_bytes, void* cuda_stream,
+                                  amrvac_state** out) {
+  std::string err;
+  if (!out || !config_ok(cfg, err)) return AMRVAC_E_INVALID;
+  *out = nullptr;
+  if (cfg->kernel == AMRVAC_KERNEL_FUSED && !fused_supported(cfg)) return AMRVAC_E_INVALID;
+  Tables T;
+  if (!build_tables(cfg, ninst, inst, nblocks, block_meta, T)) return AMRVAC_E_INVALID;
+  bool fused = use_fused_for(cfg);
+  Layout L = make_layout(cfg, ninst, nblocks, T, fused);
+  if (!d_workspace || ((uintptr_t)d_workspace % ALIGN) != 0) return AMRVAC_E_INVALID;
+  if (workspace_bytes < L.total) return AMRVAC_E_NOMEM;
+
+  amrvac_state* s = new amrvac_state();
+  s->cfg = *cfg;
+  for (int d = cfg->ndim; d < 3; d++) s->cfg.block_nx[d] = 1;
+  s->ninst = ninst;
+  s->nblocks = nblocks;
+  s->ndim = cfg->ndim;
+  s->ncell = nx_of(cfg, 0) * nx_of(cfg, 1) * nx_of(cfg, 2);
+  s->use_fused = fused;
+  s->real_size = cfg->precision == AMRVAC_FP64 ? 8 : 4;
+  s->stream = (cudaStream_t)cuda_stream;
+  s->ws = (char*)d_workspace;
+  s->ws_bytes = workspace_bytes;
+  s->meta.assign(block_meta, block_meta + 5 * (size_t)nblocks);
+  s->inst.assign(inst, inst + ninst);
+  for (int i = 0; i < 3; i++) s->U[i] = s->ws + L.U[i];
+  s->npad = 1;
+  for (int d = 0; d < 3; d++) {
+    s->P[d] = nx_of(cfg, d) + (d < cfg->ndim ? 2 * NG : 0);
+    s->npad *= (size_t)s->P[d];
+    s->nface[d] = d < cfg->ndim ? (size_t)s->ncell / nx_of(cfg, d) * (nx_of(cfg, d) + 1) : 0;
+  }
+  if (!fused) {
+    s->W = s->ws + L.W;
+    for (int d = 0; d < 3; d++) s->F[d] = s->ws + L.F[d];
+  }
+  DevMesh& M = s->mesh;
+  M.ndim = cfg->ndim;
+  for (int d = 0; d < 3; d++) {
+    M.nx[d] = nx_of(cfg, d);
+    M.bc[d][0] = cfg->bc[d][0];
+    M.bc[d][1] = cfg->bc[d][1];
+  }
+  M.ncell = s->ncell;
+  M.nblocks = nblocks;
+  M.ninst = ninst;
+  M.blk = at<int>(s, L.blk);
+  M.nbr = at<int>(s, L.nbr);
+  M.lmap = at<int>(s, L.lmap);
+  M.lmap_off = at<int>(s, L.lmap_off);
+  M.lnb = at<int>(s, L.lnb);
+  M.gamma = at<double>(s, L.gamma);
+  M.dx = at<double>(s, L.dx);
+  M.inst_start = at<int>(s, L.istart);
+  M.inst_blocks = at<int>(s, L.iblocks);
+  M.rt = at<InstRT>(s, L.rt);
+  M.part = at<double>(s, L.part);
+  M.sums = at<double>(s, L.sums);
+  M.err = at<int>(s, L.err);
+  s->d_work = at<int>(s, L.work);
+
+  std::vector<InstRT> rt(ninst);
+  for (int q = 0; q < ninst; q++) rt[q] = InstRT{inst[q].t0, inst[q].t_end, 0.0, 0.0};
+  cudaError_t e = cudaSuccess;
+  auto up = [&](void* dst, const void* src, size_t bytes) {
+    if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s->stream);
+  };
+  up((void*)M.blk, T.blk.data(), sizeof(int) * T.blk.size());
+  up((void*)M.nbr, T.nbr.data(), sizeof(int) * T.nbr.size());
+  up((void*)M.lmap, T.lmap.data(), sizeof(int) * T.lmap.size());
+  up((void*)M.lmap_off, T.lmap_off.data(), sizeof(int) * T.lmap_off.size());
+  up((void*)M.lnb, T.lnb.data(), sizeof(int) * T.lnb.size());
+  up((void*)M.gamma, T.gamma.data(), sizeof(double) * T.gamma.size());
+  up((void*)M.dx, T.dx.data(), sizeof(double) * T.dx.size());
+  up((void*)M.inst_start, T.istart.data(), sizeof(int) * T.istart.size());
+  up((void*)M.inst_blocks, T.iblocks.data(), sizeof(int) * T.iblocks.size());
+  up((void*)M.rt, rt.data(), sizeof(InstRT) * ninst);
+  // the work list of the fused kernel: blocks in storage order
+  std::vector<int> work(nblocks);
+  for (int b = 0; b < nblocks; b++) work[b] = b;
+  s->nwork = nblocks;
+  up((void*)s->d_work, work.data(), sizeof(int) * work.size());
+  if (e == cudaSuccess) e = cudaMemsetAsync(M.part, 0, sizeof(double) * NPART * nblocks, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(M.sums, 0, sizeof(double) * NV * ninst, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(M.err, 0, sizeof(int) * 4, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);  // host vectors die here
+  if (e != cudaSuccess) {
+    delete s;
+    return AMRVAC_E_CUDA;
+  }
+  *out = s;
+  return AMRVAC_OK;
+}
+
+amrvac_status amrvac_state_destroy(amrvac_state* s) {
+  if (!s) return AMRVAC_E_INVALID;
+  cudaError_t e = cudaStreamSynchronize(s->stream);
+  if (s->graph) cudaGraphExecDestroy(s->graph);
+  delete s;
+  return cuda_status(e);
+}
+
+static bool buffer_ok(int b) { return b >= 0 && b < 3; }
+
+amrvac_status amrvac_set_conserved(amrvac_state* s, int32_t buffer, const void* src,
+                                   int32_t src_is_device, int32_t src_precision) {
+  if (!s || !src || !buffer_ok(buffer)) return AMRVAC_E_INVALID;
+  if (src_precision != AMRVAC_FP64 && src_precision != AMRVAC_FP32_BULK) return AMRVAC_E_INVALID;
+  const size_t n = (size_t)NV * s->nblocks * s->ncell;
+  if (buffer == 0) s->dt_valid = false;
+  cudaError_t e;
+  if (src_precision == s->cfg.precision) {
+    e = cudaMemcpyAsync(s->U[buffer], src, n * s->real_size,
+                        src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                        s->stream);
+    return cuda_status(e);
+  }
+  if (src_is_device)
+    return check_launch(s, launch_convert(s, src, src_precision, s->U[buffer], s->cfg.precision, n));
+  // host source of the other precision: convert on the host
+  if (s->cfg.precision == AMRVAC_FP64) {
+    std::vector<double> tmp(n);
+    const float* f = (const float*)src;
+    for (size_t i = 0; i < n; i++) tmp[i] = f[i];
+    e = cudaMemcpyAsync(s->U[buffer], tmp.data(), n * 8, cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  } else {
+    std::vector<float> tmp(n);
+    const double* d = (const double*)src;
+    for (size_t i = 0; i < n; i++) tmp[i] = (float)d[i];
+    e = cudaMemcpyAsync(s->U[buffer], tmp.data(), n * 4, cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  }
+  return cuda_status(e);
+}
+
+amrvac_status amrvac_get_conserved(amrvac_state* s, int32_t buffer, void* dst,
+                                   int32_t dst_is_device, int32_t dst_precision) {
+  if (!s || !dst || !buffer_ok(buffer)) return AMRVAC_E_INVALID;
+  if (dst_precision != AMRVAC_FP64 && dst_precision != AMRVAC_FP32_BULK) return AMRVAC_E_INVALID;
+  const size_t n = (size_t)NV * s->nblocks * s->ncell;
+  cudaError_t e;
+  if (dst_precision == s->cfg.precision) {
+    e = cudaMemcpyAsync(dst, s->U[buffer], n * s->real_size,
+                        dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                        s->stream);
+    return cuda_status(e);
+  }
+  if (dst_is_device)
+    return check_launch(s, launch_convert(s, s->U[buffer], s->cfg.precision, dst, dst_precision, n));
+  if (s->cfg.precision == AMRVAC_FP64) {
+    std::vector<double> tmp(n);
+    e = cudaMemcpyAsync(tmp.data(), s->U[buffer], n * 8, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    float* f = (float*)dst;
+    for (size_t i = 0; i < n; i++) f[i] = (float)tmp[i];
+  } else {
+    std::vector<float> tmp(n);
+    e = cudaMemcpyAsync(tmp.data(), s->U[buffer], n * 4, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    double* d = (double*)dst;
+    for (size_t i = 0; i < n; i++) d[i] = tmp[i];
+  }
+  return cuda_status(e);
+}
+
+static amrvac_status read_rt(amrvac_state* s, std::vector<InstRT>& rt) {
+  rt.resize(s->ninst);
+  cudaError_t e = cudaMemcpyAsync(rt.data(), s->mesh.rt, sizeof(InstRT) * s->ninst,
+                                  cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  return cuda_status(e);
+}
+
+static amrvac_status write_rt(amrvac_state* s, const std::vector<InstRT>& rt) {
+  cudaError_t e = cudaMemcpyAsync(s->mesh.rt, rt.data(), sizeof(InstRT) * s->ninst,
+                                  cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  return cuda_status(e);
+}
+
+amrvac_status amrvac_set_time(amrvac_state* s, const double* h_t, const double* h_t_end) {
+  if (!s) return AMRVAC_E_INVALID;
+  std::vector<InstRT> rt;
+  amrvac_status st = read_rt(s, rt);
+  if (st) return st;
+  for (int q = 0; q < s->ninst; q++) {
+    if (h_t) rt[q].t = h_t[q];
+    if (h_t_end) rt[q].t_end = h_t_end[q];
+  }
+  s->dt_valid = false;
+  return write_rt(s, rt);
+}
+
+amrvac_status amrvac_set_dt(amrvac_state* s, const double* h_dt, const double* h_ch) {
+  if (!s || !h_dt || !h_ch) return AMRVAC_E_INVALID;
+  std::vector<InstRT> rt;
+  amrvac_status st = read_rt(s, rt);
+  if (st) return st;
+  for (int q = 0; q < s->ninst; q++) {
+    if (!(h_dt[q] >= 0.0) || !(h_ch[q] > 0.0)) return AMRVAC_E_INVALID;
+    rt[q].dt = h_dt[q];
+    rt[q].ch = h_ch[q];
+  }
+  st = write_rt(s, rt);
+  if (!st) s->dt_valid = true;
+  return st;
+}
+
+amrvac_status amrvac_fill_ghosts(amrvac_state* s, int32_t buffer, void* d_padded_out) {
+  if (!s || !buffer_ok(buffer) || !d_padded_out) return AMRVAC_E_INVALID;
+  return check_launch(s, launch_fill_ghosts(s, buffer, d_padded_out));
+}
+
+amrvac_status amrvac_cfl_dt(amrvac_state* s, int32_t buffer, double* h_dt_out) {
+  if (!s || !buffer_ok(buffer)) return AMRVAC_E_INVALID;
+  amrvac_status st = check_launch(s, launch_cfl_partials(s, buffer));
+  if (st) return st;
+  st = check_launch(s, launch_finalize(s, 0));
+  if (st) return st;
+  s->dt_valid = true;
+  if (h_dt_out) {
+    std::vector<InstRT> rt;
+    st = read_rt(s, rt);
+    if (st) return st;
+    for (int q = 0; q < s->ninst; q++) h_dt_out[q] = rt[q].dt;
+  }
+  return AMRVAC_OK;
+}
+
+amrvac_status amrvac_stage(amrvac_state* s, int32_t stage) {
+  if (!s || stage < 0 || stage >= num_stages(s->cfg.time)) return AMRVAC_E_INVALID;
+  if (!s->dt_valid) return AMRVAC_E_STATE;
+  int count = 0;
+  amrvac_status st = enqueue_stage(s, stage, stage == num_stages(s->cfg.time) - 1, &count);
+  s->launches += count;
+  return st;
+}
+
+amrvac_status amrvac_step(amrvac_state* s, int32_t nsteps) {
+  if (!s || nsteps < 0) return AMRVAC_E_INVALID;
+  if (!s->dt_valid) {
+    amrvac_status st = amrvac_cfl_dt(s, 0, nullptr);
+    if (st) return st;
+  }
+  if (nsteps == 0) return AMRVAC_OK;
+  if (s->stream == nullptr) {
+    for (int n = 0; n < nsteps; n++) {
+      int count = 0;
+      amrvac_status st = enqueue_step(s, &count);
+      s->launches += count;
+      if (st) return st;
+    }
+    return AMRVAC_OK;
+  }
+  if (!s->graph) {
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return AMRVAC_E_CUDA;
+    int count = 0;
+    amrvac_status st = enqueue_step(s, &count);
+    e = cudaStreamEndCapture(s->stream, &g);
+    if (st || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return st ? st : AMRVAC_E_CUDA;
+    }
+    e = cudaGraphInstantiate(&s->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      s->graph = nullptr;
+      return AMRVAC_E_CUDA;
+    }
+    s->graph_kernels = count;
+  }
+  for (int n = 0; n < nsteps; n++) {
+    cudaError_t e = cudaGraphLaunch(s->graph, s->stream);
+    if (e != cudaSuccess) return AMRVAC_E_CUDA;
+    s->launches += s->graph_kernels;
+  }
+  return AMRVAC_OK;
+}
+
+amrvac_status amrvac_get_diag(amrvac_state* s, double* h_t, double* h_dt, double* h_ch,
+                              double* h_sums, amrvac_error_info* err) {
+  if (!s) return AMRVAC_E_INVALID;
+  std::vector<InstRT> rt;
+  amrvac_status st = read_rt(s, rt);
+  if (st) return st;
+  int e4[4];
+  cudaError_t e = cudaMemcpy(e4, s->mesh.err, sizeof(e4), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && h_sums)
+    e = cudaMemcpy(h_sums, s->mesh.sums, sizeof(double) * NV * s->ninst, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return AMRVAC_E_CUDA;
+  for (int q = 0; q < s->ninst; q++) {
+    if (h_t) h_t[q] = rt[q].t;
+    if (h_dt) h_dt[q] = rt[q].dt;
+    if (h_ch) h_ch[q] = rt[q].ch;
+  }
+  if (err) {
+    err->code = e4[0];
+    err->block = e4[1];
+    err->cell = e4[2];
+    err->var = e4[3];
+  }
+  return (amrvac_status)e4[0];
+}
+
+amrvac_status amrvac_clear_error(amrvac_state* s) {
+  if (!s) return AMRVAC_E_INVALID;
+  return cuda_status(cudaMemsetAsync(s->mesh.err, 0, sizeof(int) * 4, s->stream));
+}
+
+int64_t amrvac_launch_count(const amrvac_state* s) { return s ? s->launches : -1; }
+
+}  // extern "C"

@@ -1,0 +1,70 @@
+// Shared device-side definitions of the amrvac GB300 library (not a public
+// header).  Tables live in the caller's workspace; kernels receive a DevMesh by
+// value.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/amrvac.h"
+
+namespace amrvac {
+
+constexpr int NV = 9;       // rho, m_x, m_y, m_z, e, B_x, B_y, B_z, psi
+constexpr int NG = 2;       // ghost cells per face (vanleer/koren/minmod: limiter table)
+constexpr int MAXLEV = AMRVAC_MAX_LEVELS;
+constexpr int NPART = 12;   // per-block partials: smax, chmax, sums[9], pad
+
+// face neighbour codes in DevMesh::nbr
+constexpr int NBR_OUTFLOW = -1;  // physical zero-gradient boundary
+constexpr int NBR_GENERAL = -2;  // level change: use the per-level block maps
+// per-level block map codes
+constexpr int MAP_REFINED = -1;  // covered by finer leaves
+constexpr int MAP_COARSER = -2;  // covered by a coarser leaf
+
+struct InstRT {      // per-instance clock and step parameters (device resident)
+  double t, t_end, dt, ch;
+};
+
+struct DevMesh {
+  int ndim;
+  int nx[3];
+  int ncell;
+  int nblocks;
+  int ninst;
+  int bc[3][2];
+  const int* blk;         // [nblocks][5]: inst, level, i, j, k
+  const int* nbr;         // [nblocks][6]: face (d, side) -> neighbour code
+  const int* lmap;        // concatenated dense per-(instance, level) block maps
+  const int* lmap_off;    // [ninst][MAXLEV] offset into lmap
+  const int* lnb;         // [ninst][MAXLEV][3] blocks per dimension at a level
+  const double* gamma;    // [ninst]
+  const double* dx;       // [ninst][MAXLEV][3] cell size
+  const int* inst_start;  // [ninst + 1] CSR of blocks per instance
+  const int* inst_blocks; // [nblocks]
+  InstRT* rt;             // [ninst]
+  double* part;           // [nblocks][NPART]
+  double* sums;           // [ninst][NV]
+  int* err;               // [4] code, block, cell, var
+};
+
+struct StageParams {
+  int k;                 // stage index
+  double a, b;           // out = a U0 + b (U + dt L)
+  double courant;
+  double glm_alpha;
+  double small_density, small_pressure;
+  int check_small;
+  int flux, limiter, glm;
+  int epilogue;          // 1: per-block dt / sums partials of the output
+};
+
+__device__ __forceinline__ void latch_error(int* err, int code, int b, int c, int v) {
+  if (atomicCAS(err, 0, code) == 0) {
+    err[1] = b;
+    err[2] = c;
+    err[3] = v;
+  }
+}
+
+}  // namespace amrvac

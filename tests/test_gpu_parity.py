@@ -1,0 +1,341 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle on the
+same seeded inputs.
+
+Tolerances (from the FP64 / FP32 arithmetic):
+  * FP64 path, one stage from identical inputs: relative L-inf <= 1e-12 per
+    variable (relative to the variable's max |value|); identically zero
+    variables must stay below 1e-12 of the state's scale in absolute terms.
+  * FP64 path, several full steps: 1e-10 (round-off of different summation
+    and FMA orders grows through the limiters' nonlinearity).
+  * FP32-bulk path, one stage: relative L1 <= 1e-5 on smooth flows and <= 1e-3
+    on shocked flows, against the FP64 oracle fed the same (float-rounded) state.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2303_03026_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+KERNELS = ["plain", "auto"]
+
+
+@pytest.fixture(scope="module")
+def amr():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2303_03026_gb300 import amrvac
+    return amrvac
+
+
+def _linf_by_var(got, ref):
+    out = []
+    scale_all = np.abs(ref).max()
+    for v in range(9):
+        m = np.abs(ref[v]).max()
+        d = np.abs(got[v] - ref[v]).max()
+        out.append(d / m if m > 0 else d / scale_all)
+    return np.array(out)
+
+
+def _l1_by_var(got, ref):
+    out = []
+    scale_all = np.abs(ref).mean()
+    for v in range(9):
+        s = np.abs(ref[v]).sum()
+        d = np.abs(got[v] - ref[v]).sum()
+        out.append(d / s if s > 1e-12 * scale_all * ref[v].size else d / (scale_all * ref[v].size))
+    return np.array(out)
+
+
+def _stage_parity(amr, orc, W, kernel, stages=None, tol=1e-12, blocks=None, threads=8):
+    S = amr.State.from_workload(W, kernel=kernel)
+    m = orc.mesh_for(W, threads)
+    U = W.U.astype(np.float32).astype(np.float64) if W.cfg.precision == "fp32" else W.U
+    dt, ch = m.cfl(U)
+    S.set_conserved(U.astype(np.float32) if W.cfg.precision == "fp32" else U)
+    S.set_dt(dt, ch)
+    ns = 2 if W.cfg.time == "ssprk2" else 3
+    # stage inputs: U^n and a perturbed copy as the stage register
+    rng = np.random.Generator(np.random.PCG64(99))
+    Uk = U * (1.0 + 1e-3 * rng.standard_normal(U.shape) * (U != 0))
+    Uk[4] = np.maximum(Uk[4], U[4])  # keep the pressure positive
+    if W.cfg.precision == "fp32":
+        Uk = Uk.astype(np.float32).astype(np.float64)
+    worst = []
+    for k in (stages if stages is not None else range(ns)):
+        u0, uin, uout = 0, (0 if k == 0 else (1 if (ns == 2 or k == 1) else 2)), \
+            (1 if k == 0 else (0 if (ns == 2 or k == 2) else 2))
+        if k > 0:
+            S.set_conserved(Uk.astype(np.float32) if W.cfg.precision == "fp32" else Uk, uin)
+        S.stage(k)
+        got = S.get_conserved(uout, precision=0)
+        src = U if k == 0 else Uk
+        ref, st = m.stage(k, dt, ch, U, src, blocks=blocks)
+        assert st == 0
+        d = S.diag()
+        assert d["status"] == 0, d
+        if blocks is not None:
+            got = got[:, blocks]
+            ref = ref[:, blocks]
+        if W.cfg.precision == "fp32":
+            e = _l1_by_var(got, ref)
+        else:
+            e = _linf_by_var(got, ref)
+        worst.append(e.max())
+        assert e.max() <= tol, (W.name, kernel, k, e)
+    S.close()
+    return max(worst)
+
+
+# ----------------------------------------------------------------------------
+# FP64 per-stage parity
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", range(16))
+def test_c1_riemann_stage_parity(amr, orc, seed):
+    W = wl.c1_riemann(seed=seed)
+    _stage_parity(amr, orc, W, "plain")
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("limiter,flux", [("koren", "hlld"), ("vanleer", "hll"),
+                                          ("minmod", "hlld")])
+def test_c2_orszag_tang_stage_parity(amr, orc, kernel, limiter, flux):
+    W = wl.c2_orszag_tang(128, limiter=limiter, flux=flux)
+    _stage_parity(amr, orc, W, kernel)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_cp_alfven_stage_parity(amr, orc, kernel):
+    W = wl.cp_alfven(64, limiter="koren")
+    W.U[8] = 1e-3 * np.sin(np.arange(W.U.shape[2]))[None, :]
+    _stage_parity(amr, orc, W, kernel)
+
+
+def test_small_amr_2d_stage_parity(amr, orc):
+    for periodic in (True, False):
+        W = wl.small_amr_2d(periodic=periodic)
+        _stage_parity(amr, orc, W, "plain")
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_small_amr_3d_stage_parity(amr, orc, kernel):
+    W = wl.c4_blast_amr(base=4, levels=3, bnx=16 if kernel == "auto" else 4,
+                        shell=(0.2, 0.26), precision="fp64")
+    _stage_parity(amr, orc, W, kernel)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_c3_small_stage_parity(amr, orc, kernel):
+    W = wl.c3_turbulence(n=32, bnx=16, precision="fp64")
+    _stage_parity(amr, orc, W, kernel)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_c5_small_stage_parity(amr, orc, kernel):
+    W = wl.c5_instances(count=6, nmin=32, nmax=96, precision="fp64")
+    _stage_parity(amr, orc, W, kernel)
+
+
+def test_ragged_blocks_1d_3d(amr, orc):
+    # block sizes that are not powers of two, several blocks, outflow
+    W = wl.riemann_1d((1.0, 0, 0, 0, 1.0, 1.0, 0), (0.125, 0, 0, 0, 0.1, -1.0, 0), n=120,
+                      nblocks=3, flux="hlld", time="ssprk3")
+    _stage_parity(amr, orc, W, "plain")
+    cfg = wl.Config(ndim=3, block_nx=(6, 5, 7), flux="hlld", limiter="koren", glm=True)
+    inst = wl.Instance(base_blocks=(2, 3, 1))
+    meta = wl.uniform_meta((2, 3, 1))
+    rng = np.random.Generator(np.random.PCG64(5))
+    n = meta.shape[0]
+    c = 6 * 5 * 7
+    prim = [1 + 0.2 * rng.random((n, c)), 0.3 * rng.standard_normal((n, c)),
+            0.3 * rng.standard_normal((n, c)), 0.3 * rng.standard_normal((n, c)),
+            1 + 0.2 * rng.random((n, c)), 0.5 + 0.1 * rng.standard_normal((n, c)),
+            0.1 * rng.standard_normal((n, c)), 0.1 * rng.standard_normal((n, c)),
+            0.01 * rng.standard_normal((n, c))]
+    U = wl.conserved_from_primitive(5 / 3, *prim)
+    _stage_parity(amr, orc, wl.Workload("ragged3d", cfg, [inst], meta, U), "plain")
+
+
+# ----------------------------------------------------------------------------
+# ghost fill, CFL, steps, sums, errors
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("which", ["amr2d", "amr3d", "uniform1d"])
+def test_fill_ghosts_parity(amr, orc, which):
+    if which == "amr2d":
+        W = wl.small_amr_2d()
+    elif which == "amr3d":
+        W = wl.c4_blast_amr(base=4, levels=3, bnx=4, shell=(0.2, 0.26), precision="fp64")
+    else:
+        W = wl.c1_riemann()
+    S = amr.State.from_workload(W, kernel="plain")
+    S.set_conserved(W.U)
+    got = S.fill_ghosts(0)
+    ref = orc.mesh_for(W).fill_ghosts(W.U)
+    e = _linf_by_var(got, ref)
+    assert e.max() <= 1e-15, e
+    S.close()
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_cfl_parity(amr, orc, kernel):
+    for W in (wl.c2_orszag_tang(64), wl.small_amr_2d(), wl.c5_instances(count=5, nmin=32,
+                                                                          nmax=64,
+                                                                          precision="fp64")):
+        S = amr.State.from_workload(W, kernel="plain" if W.cfg.block_nx[0] != 16 else kernel)
+        S.set_conserved(W.U)
+        dt = S.cfl_dt()
+        d = S.diag()
+        rdt, rch = orc.mesh_for(W).cfl(W.U)
+        np.testing.assert_allclose(dt, rdt, rtol=1e-13)
+        np.testing.assert_allclose(d["ch"], rch, rtol=1e-13)
+        np.testing.assert_allclose(d["sums"], orc.mesh_for(W).sums(W.U), rtol=1e-12,
+                                   atol=1e-13 * np.abs(W.U).max())
+        S.close()
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_full_steps_and_sums(amr, orc, kernel):
+    W = wl.c2_orszag_tang(128)
+    S = amr.State.from_workload(W, kernel=kernel)
+    S.set_conserved(W.U)
+    S.step(10)
+    d = S.diag(raise_on_error=True)
+    got = S.get_conserved(0)
+    m = orc.mesh_for(W, 8)
+    Uo, t, n, st = m.run(W.U, 1e30, maxsteps=10)
+    assert n == 10 and st == 0
+    e = _linf_by_var(got, Uo)
+    assert e.max() < 1e-10, e
+    assert abs(d["t"][0] - t[0]) < 1e-12 * t[0]
+    so = m.sums(Uo)
+    np.testing.assert_allclose(d["sums"], so, rtol=1e-12, atol=1e-14)
+    # conservation on the GPU itself (periodic)
+    s0 = m.sums(W.U)
+    assert np.abs(d["sums"][0, :8] - s0[0, :8]).max() < 1e-13 * np.abs(W.U[:8]).max()
+    assert S.launches > 0
+    S.close()
+
+
+def test_t_end_clip_and_c1_run(amr, orc):
+    W = wl.c1_riemann(seed=3)
+    S = amr.State.from_workload(W, kernel="plain")
+    S.set_conserved(W.U)
+    m = orc.mesh_for(W)
+    Uo, t, n, st = m.run(W.U, 0.1)
+    S.step(n + 3)  # extra steps must be no-ops once t_end is reached
+    d = S.diag(raise_on_error=True)
+    assert d["t"][0] == 0.1 and d["dt"][0] == 0.0
+    e = _linf_by_var(S.get_conserved(0), Uo)
+    assert e.max() < 1e-10, e
+    S.close()
+
+
+def test_small_values_latched(amr, orc):
+    W = wl.cp_alfven(32)
+    U = W.U.copy()
+    U[4, 3, 17] = 0.3
+    S = amr.State.from_workload(W, kernel="plain")
+    S.set_conserved(U)
+    S.set_dt(1e-3, 1.0)
+    S.stage(0)
+    d = S.diag()
+    assert d["status"] == 4 and d["error"][0] == 4
+    S.clear_error()
+    S.set_conserved(W.U)
+    S.stage(0)
+    assert S.diag()["status"] == 0
+    S.close()
+
+
+def test_instances_advance_independently(amr, orc):
+    W = wl.c5_instances(count=4, nmin=32, nmax=64, precision="fp64")
+    for q, inst in enumerate(W.instances):
+        inst.t_end = 0.01 * (q + 1)
+    S = amr.State.from_workload(W, kernel="plain")
+    S.set_conserved(W.U)
+    m = orc.mesh_for(W, 4)
+    Uo, t, n, st = m.run(W.U, np.array([i.t_end for i in W.instances]))
+    S.step(n)
+    d = S.diag(raise_on_error=True)
+    np.testing.assert_array_equal(d["t"], t)
+    e = _linf_by_var(S.get_conserved(0), Uo)
+    assert e.max() < 1e-10
+    S.close()
+
+
+# ----------------------------------------------------------------------------
+# FP32-bulk against the FP64 oracle
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_fp32_smooth_stage(amr, orc, kernel):
+    W = wl.cp_alfven(64, precision="fp32")
+    _stage_parity(amr, orc, W, kernel, tol=1e-5)
+    W = wl.c5_instances(count=6, nmin=32, nmax=96, precision="fp32")
+    _stage_parity(amr, orc, W, kernel, tol=1e-5)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_fp32_shocked_stage(amr, orc, kernel):
+    W = wl.c4_blast_amr(base=4, levels=3, bnx=16 if kernel == "auto" else 4,
+                        shell=(0.2, 0.26), precision="fp32")
+    _stage_parity(amr, orc, W, kernel, tol=1e-3)
+    W = wl.c3_turbulence(n=32, bnx=16, precision="fp32")
+    _stage_parity(amr, orc, W, kernel, tol=1e-5)
+
+
+def test_fp32_low_beta_pressure_recovery(amr, orc):
+    # beta = 0.01: e is dominated by B^2/2; the pressure after a stage must stay
+    # within the float storage error of the FP64 oracle
+    W = wl.c3_turbulence(n=32, bnx=16, precision="fp32", beta=0.01)
+    S = amr.State.from_workload(W, kernel="plain")
+    U = W.U.astype(np.float32).astype(np.float64)
+    S.set_conserved(U.astype(np.float32))
+    m = orc.mesh_for(W, 8)
+    dt, ch = m.cfl(U)
+    S.set_dt(dt, ch)
+    S.stage(0)
+    got = S.get_conserved(1, precision=0)
+    ref, _ = m.stage(0, dt, ch, U, U)
+    g = 5 / 3
+    p = lambda X: (g - 1) * (X[4] - 0.5 * (X[1] ** 2 + X[2] ** 2 + X[3] ** 2) / X[0]
+                             - 0.5 * (X[5] ** 2 + X[6] ** 2 + X[7] ** 2))
+    rel = np.abs(p(got) - p(ref)).mean() / np.abs(p(ref)).mean()
+    assert rel < 2e-4, rel
+    S.close()
+
+
+# ----------------------------------------------------------------------------
+# full-size workloads: sampled blocks against the oracle
+# ----------------------------------------------------------------------------
+
+def _sampled_full(amr, orc, W, kernel, nsample, tol):
+    rng = np.random.Generator(np.random.PCG64(7))
+    blocks = np.sort(rng.choice(W.nblocks, size=min(nsample, W.nblocks), replace=False))
+    return _stage_parity(amr, orc, W, kernel, stages=[0, 1], tol=tol, blocks=blocks)
+
+
+def test_full_c2_sampled(amr, orc):
+    _sampled_full(amr, orc, wl.c2_orszag_tang(1024), "auto", 48, 1e-12)
+
+
+def test_full_c3_sampled(amr, orc):
+    _sampled_full(amr, orc, wl.c3_turbulence(), "auto", 12, 1e-5)
+
+
+def test_full_c4_sampled(amr, orc):
+    W = wl.c4_blast_amr(base=6)
+    # sample from every level, including blocks next to level changes
+    _sampled_full(amr, orc, W, "auto", 16, 1e-3)
+
+
+def test_full_c5_sampled(amr, orc):
+    _sampled_full(amr, orc, wl.c5_instances(), "auto", 64, 1e-5)
