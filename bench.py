@@ -42,30 +42,36 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="c4", choices=["c4", "c5", "c3", "c2"])
     p.add_argument("--kernel", default="auto", choices=["auto", "plain", "fused"])
+    p.add_argument("--size", type=int, default=0,
+                   help="workload size (c4: level-0 blocks per dim; c3/c2: cells per dim; "
+                        "c5: instance count); 0 = the full configuration")
+    p.add_argument("--pressure", default="ff", choices=["ff", "fp64"],
+                   help="FP32-bulk pressure recovery: float-float or double")
     p.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison leg")
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU-baseline leg")
     p.add_argument("--no-e2e", action="store_true")
     return p.parse_args()
 
 
-def make_workload(name, precision="fp32"):
+def make_workload(name, precision="fp32", size=0):
     from paper_2303_03026_gb300 import workloads as wl
     if name == "c4":
-        W = wl.c4_blast_amr(base=6, precision=precision)
+        W = wl.c4_blast_amr(base=size or 6, precision=precision)
         desc = {"workload": "3D block-AMR blast, %d blocks of 16^3 over 4 levels (ratio 2), "
                             "shell 0.2<=r<=0.3, HLLD+vanleer+glm, SSPRK3" % W.nblocks,
                 "blocks": W.nblocks, "blocks_per_level": W.info["blocks_per_level"]}
     elif name == "c5":
-        W = wl.c5_instances(precision=precision)
+        W = wl.c5_instances(count=size or 256, precision=precision)
         desc = {"workload": "256 uneven 2D instances 64^2..512^2 in 16^2 blocks, "
                             "HLLD+vanleer+glm, SSPRK3, per-instance dt", "blocks": W.nblocks}
     elif name == "c3":
-        W = wl.c3_turbulence(precision=precision)
-        desc = {"workload": "3D 256^3 Mach-1 beta-0.01 turbulence in 16^3 blocks, "
-                            "HLLD+vanleer+glm, SSPRK3", "blocks": W.nblocks}
+        W = wl.c3_turbulence(n=size or 256, precision=precision)
+        desc = {"workload": "3D %d^3 Mach-1 beta-0.01 turbulence in 16^3 blocks, "
+                            "HLLD+vanleer+glm, SSPRK3" % (size or 256), "blocks": W.nblocks}
     else:
-        W = wl.c2_orszag_tang(1024, precision=precision)
-        desc = {"workload": "2D Orszag-Tang 1024^2 in 16^2 blocks, HLLD+koren+glm, SSPRK3",
+        W = wl.c2_orszag_tang(size or 1024, precision=precision)
+        desc = {"workload": "2D Orszag-Tang %d^2 in 16^2 blocks, HLLD+koren+glm, SSPRK3"
+                            % (size or 1024),
                 "blocks": W.nblocks}
     return W, desc
 
@@ -157,10 +163,11 @@ def cpu_baseline(W, seconds_target=12.0, threads=None):
     while True:
         blocks = np.sort(rng.choice(W.nblocks, nsample, replace=False)).astype(np.int32)
         A = np.zeros_like(U)
+        B = np.zeros_like(U)
         t0 = time.perf_counter()
         m.stage(0, dt, ch, U, U, blocks=blocks, out=A)
-        m.stage(1, dt, ch, U, A, blocks=blocks, out=A)
-        m.stage(2, dt, ch, U, A, blocks=blocks, out=A)
+        m.stage(1, dt, ch, U, A, blocks=blocks, out=B)
+        m.stage(2, dt, ch, U, B, blocks=blocks, out=A)
         el = time.perf_counter() - t0
         if el > seconds_target / 4 or nsample >= W.nblocks:
             break
@@ -175,7 +182,7 @@ def run_reference(args):
     ws, rank, local = dist_env()
     if rank != 0:
         return
-    W, desc = make_workload(args.workload, "fp64")
+    W, desc = make_workload(args.workload, "fp64", args.size)
     import oracle
     threads = os.cpu_count() or 1
     m = oracle.mesh_for(W, threads)
@@ -185,11 +192,12 @@ def run_reference(args):
     nsample = min(W.nblocks, max(threads * 4, 32))
     blocks = np.sort(rng.choice(W.nblocks, nsample, replace=False)).astype(np.int32)
     A = np.zeros_like(U)
+    B = np.zeros_like(U)
 
     def one():
         m.stage(0, dt, ch, U, U, blocks=blocks, out=A)
-        m.stage(1, dt, ch, U, A, blocks=blocks, out=A)
-        m.stage(2, dt, ch, U, A, blocks=blocks, out=A)
+        m.stage(1, dt, ch, U, A, blocks=blocks, out=B)
+        m.stage(2, dt, ch, U, B, blocks=blocks, out=A)
 
     for _ in range(args.warmup):
         one()
@@ -228,9 +236,9 @@ def main():
     __graft_entry__.build()
     from paper_2303_03026_gb300 import amrvac
 
-    W, desc = make_workload(args.workload, "fp32")
+    W, desc = make_workload(args.workload, "fp32", args.size)
     cells = W.interior_cells()
-    S = amrvac.State.from_workload(W, device=dev, kernel=args.kernel)
+    S = amrvac.State.from_workload(W, device=dev, kernel=args.kernel, pressure=args.pressure)
     U32 = torch.from_numpy(W.U.astype(np.float32)).to(dev)
     S.set_conserved(U32)
     stream = S.stream
@@ -363,7 +371,9 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
                 "config": dict(desc, cells=cells, l2="inputs larger than L2 (2.7 GB per buffer)",
-                               precision="fp32 bulk, fp64 pressure recovery, fp64 dt and sums",
+                               precision="fp32 bulk; pressure recovery and per-thread sums in %s; "
+                                         "fp64 dt and block/instance sums" %
+                                         ("float-float" if args.pressure == "ff" else "fp64"),
                                kernel=args.kernel, parallelism="replicas" if ws > 1 else "1 GPU"),
                 "clocks": clk.summary(), "gpu_launches": launches, "roofline": roofline,
                 "e2e": e2e, "fp64_plain": fp64, "cpu_baseline": cpu}

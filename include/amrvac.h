@@ -70,6 +70,13 @@ typedef enum { AMRVAC_SSPRK2 = 0, AMRVAC_SSPRK3 = 1 } amrvac_time;
  * double; conservation sums and the time step in double. */
 typedef enum { AMRVAC_FP64 = 0, AMRVAC_FP32_BULK = 1 } amrvac_precision;
 typedef enum { AMRVAC_BC_PERIODIC = 0, AMRVAC_BC_OUTFLOW = 1 } amrvac_bc;
+/* Thermal-pressure recovery in FP32_BULK: the subtraction e - m^2/(2 rho) -
+ * B^2/2 (and the per-thread conservation sums) in double (FP64), or in
+ * float-float (FF, a pair of floats with a ~48-bit significand: the B_i^2 are
+ * exact via FMA, e - m^2/(2 rho) exact via TwoSum), which avoids the scarce
+ * FP64 units of GB300 at equal accuracy for float-stored inputs.  Ignored for
+ * AMRVAC_FP64 states. */
+typedef enum { AMRVAC_PRESSURE_FP64 = 0, AMRVAC_PRESSURE_FF = 1 } amrvac_pressure;
 /* PLAIN: one kernel per step of the method per stage, staging primitives and
  * face fluxes in workspace scratch (the per-block baseline).  FUSED: one
  * persistent kernel per stage doing ghost fill, reconstruction, flux, update
@@ -94,6 +101,7 @@ typedef struct {
   double small_pressure;
   int32_t check_small_values;
   int32_t kernel;         /* amrvac_kernel                                      */
+  int32_t pressure;       /* amrvac_pressure (FP32_BULK only)                   */
 } amrvac_config;
 
 /* One instance = one independent domain with its own gamma and clock. */

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libamrvac_gb300.so")
 STATUS = {0: "ok", 1: "invalid", 2: "nomem", 3: "cuda", 4: "small_values", 5: "timeout",
           6: "state"}
 KERNEL = {"auto": 0, "plain": 1, "fused": 2}
+PRESSURE = {"fp64": 0, "ff": 1}
 FP64, FP32 = 0, 1
 
 # every symbol include/amrvac.h declares
@@ -42,7 +43,7 @@ class Config(C.Structure):
                 ("glm", C.c_int32), ("glm_alpha", C.c_double), ("courant", C.c_double),
                 ("bc", (C.c_int32 * 2) * 3), ("small_density", C.c_double),
                 ("small_pressure", C.c_double), ("check_small_values", C.c_int32),
-                ("kernel", C.c_int32)]
+                ("kernel", C.c_int32), ("pressure", C.c_int32)]
 
 
 class InstanceDesc(C.Structure):
@@ -91,7 +92,7 @@ def load(path: str = LIB_PATH):
     return L
 
 
-def make_config(cfg: wl.Config, kernel: str = "auto") -> Config:
+def make_config(cfg: wl.Config, kernel: str = "auto", pressure: str = "fp64") -> Config:
     c = Config()
     c.ndim = cfg.ndim
     for d in range(3):
@@ -109,6 +110,7 @@ def make_config(cfg: wl.Config, kernel: str = "auto") -> Config:
     c.small_pressure = float(cfg.small_pressure)
     c.check_small_values = int(bool(cfg.check_small_values))
     c.kernel = KERNEL[kernel]
+    c.pressure = PRESSURE[pressure]
     return c
 
 
@@ -134,14 +136,15 @@ class State:
     """One mesh + state on a GPU.  ``cfg``/``instances``/``block_meta`` follow
     workloads.py; the device workspace is a torch uint8 tensor."""
 
-    def __init__(self, cfg, instances, block_meta, device="cuda:0", kernel="auto", stream=None):
+    def __init__(self, cfg, instances, block_meta, device="cuda:0", kernel="auto", stream=None,
+                 pressure="fp64"):
         import torch
         self.torch = torch
         L = load()
         self.cfg = cfg
         self.instances = list(instances)
         self.ninst = len(self.instances)
-        self._c = make_config(cfg, kernel)
+        self._c = make_config(cfg, kernel, pressure)
         self._inst = make_instances(self.instances)
         self.meta = np.ascontiguousarray(block_meta, np.int32)
         self.nblocks = int(self.meta.shape[0])
@@ -199,9 +202,14 @@ class State:
             return
         assert tuple(U.shape) == self.shape and U.is_contiguous()
         prec = FP64 if U.dtype == torch.float64 else FP32
+        if U.is_cuda:
+            # the tensor was produced on torch's current stream
+            self.stream.wait_stream(torch.cuda.current_stream(self.device))
         _check(load().amrvac_set_conserved(self._h, buffer, U.data_ptr(), int(U.is_cuda), prec),
                "amrvac_set_conserved")
-        if not U.is_cuda:
+        if U.is_cuda:
+            U.record_stream(self.stream)
+        else:
             self.stream.synchronize()
 
     def get_conserved(self, buffer=0, out=None, numpy=True, precision=None):
@@ -220,9 +228,14 @@ class State:
                 return arr
             out = torch.empty(self.shape, dtype=self.dtype, device=self.device)
         prec = FP64 if out.dtype == torch.float64 else FP32
+        if out.is_cuda:
+            self.stream.wait_stream(torch.cuda.current_stream(self.device))
         _check(load().amrvac_get_conserved(self._h, buffer, out.data_ptr(), int(out.is_cuda), prec),
                "amrvac_get_conserved")
-        if not out.is_cuda:
+        if out.is_cuda:
+            # later torch work on the result is ordered after the copy
+            torch.cuda.current_stream(self.device).wait_stream(self.stream)
+        else:
             self.stream.synchronize()
         return out
 

@@ -18,6 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libamrvac_gb300.so")
 SOURCES = ["api.cu", "plain.cu", "fused.cu"]
+# the fused kernel source is compiled once per (precision, dimension, limiter)
+FUSED_GROUPS = [(t, d, l) for t in ("float", "double") for d in (2, 3) for l in (0, 1, 2)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
               "--expt-relaxed-constexpr"]
@@ -51,17 +53,27 @@ def build(force: bool = False, verbose: bool = False) -> str:
     nvcc = _nvcc()
     objs = []
 
-    def compile_one(src):
-        obj = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
-        cmd = [nvcc] + ARCH + NVCC_FLAGS + ["-I", os.path.join(ROOT, "include"), "-c",
-                                            os.path.join(CSRC, src), "-o", obj]
+    units = [(src, src.replace(".cu", ".o"), []) for src in SOURCES]
+    for t, d, l in FUSED_GROUPS:
+        # FP32 bulk: approximate single-precision division and square root
+        # (MUFU based, <= 2 ulp) and flush-to-zero; double arithmetic unaffected
+        fast = ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"] if t == "float" else []
+        units.append(("fused_inst.cu", "fused_%s_%dd_l%d.o" % (t, d, l),
+                      ["-DAMRVAC_FT=" + t, "-DAMRVAC_FD=%d" % d, "-DAMRVAC_FL=%d" % l] + fast))
+
+    def compile_one(unit):
+        src, objname, defs = unit
+        obj = os.path.join(OUT_DIR, objname)
+        cmd = [nvcc] + ARCH + NVCC_FLAGS + defs + ["-I", os.path.join(ROOT, "include"), "-c",
+                                                   os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s" % (src, r.stderr[-6000:]))
         return obj, r.stderr
 
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        for obj, log in ex.map(compile_one, SOURCES):
+    workers = max(2, min(len(units), os.cpu_count() or 2))
+    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+        for obj, log in ex.map(compile_one, units):
             objs.append(obj)
             if verbose:
                 sys.stderr.write(log)

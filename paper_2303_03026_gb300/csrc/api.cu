@@ -27,8 +27,18 @@ struct Tables {
 
 struct Layout {
   size_t U[3], W, F[3], part, blk, nbr, lmap, lmap_off, lnb, gamma, dx, istart, iblocks, rt,
-      sums, err, work, total;
+      sums, err, work, slab, total;
+  int slab_ctas;
 };
+
+// resident CTAs the fused kernel may use on the current device (upper bound)
+int fused_ctas() {
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
+    nsm = 160;
+  return nsm * 4;
+}
 
 bool config_ok(const amrvac_config* c, std::string& err) {
   if (!c) return err = "null config", false;
@@ -49,6 +59,8 @@ bool config_ok(const amrvac_config* c, std::string& err) {
     if ((c->bc[d][0] == AMRVAC_BC_PERIODIC) != (c->bc[d][1] == AMRVAC_BC_PERIODIC))
       return err = "periodic bc must be set on both sides", false;
   if (c->kernel < 0 || c->kernel > 2) return err = "bad kernel", false;
+  if (c->pressure != AMRVAC_PRESSURE_FP64 && c->pressure != AMRVAC_PRESSURE_FF)
+    return err = "bad pressure", false;
   return true;
 }
 
@@ -247,6 +259,13 @@ Layout make_layout(const amrvac_config* c, int ninst, int nblocks, const Tables&
   L.sums = take(sizeof(double) * NV * ninst);
   L.err = take(sizeof(int) * 4);
   L.work = take(sizeof(int) * (size_t)nblocks);
+  L.slab_ctas = 0;
+  L.slab = 0;
+  if (fused) {
+    L.slab_ctas = fused_ctas();
+    size_t per = (size_t)2 * c->ndim * NV * 2 * 16 * (c->ndim == 3 ? 16 : 1);
+    L.slab = take(rs * per * L.slab_ctas);
+  }
   L.total = off;
   return L;
 }
@@ -373,6 +392,10 @@ amrvac_status amrvac_state_create(const amrvac_config* cfg, int32_t ninst,
   M.sums = at<double>(s, L.sums);
   M.err = at<int>(s, L.err);
   s->d_work = at<int>(s, L.work);
+  if (fused) {
+    s->slab = s->ws + L.slab;
+    s->slab_ctas = L.slab_ctas;
+  }
 
   std::vector<InstRT> rt(ninst);
   for (int q = 0; q < ninst; q++) rt[q] = InstRT{inst[q].t0, inst[q].t_end, 0.0, 0.0};

@@ -57,6 +57,7 @@ struct StageParams {
   int check_small;
   int flux, limiter, glm;
   int epilogue;          // 1: per-block dt / sums partials of the output
+  int pressure_ff;       // FP32 bulk: float-float pressure recovery and sums
 };
 
 __device__ __forceinline__ void latch_error(int* err, int code, int b, int c, int v) {

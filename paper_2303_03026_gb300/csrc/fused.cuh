@@ -1,0 +1,454 @@
+// Fused persistent stage kernel for 16x16 (2D) and 16x16x16 (3D) blocks.
+//
+// One CTA of 256 threads owns one block at a time and loops over the work
+// list (grid = resident CTAs).  Thread (x, y) owns a column of the block.
+//   3D: march over z with a ring of 5 primitive planes in shared memory, each
+//       with its 2-cell x/y halo (planes z-2 .. z+2).  Per plane:
+//         load plane z+2 (own column; 128 threads also load the x/y halo):
+//           ghost fill (same-level read, outflow clamp, or AMR lookup) and
+//           conserved -> primitive (double-precision pressure for FP32 bulk)
+//         sync; x- and y-face fluxes of plane z into shared memory (the 32
+//           extra faces of the +x / +y block boundary by one rotating warp);
+//           the z-face z+1/2 flux from the thread's own column (registers)
+//         sync; update of cell (x, y, z): flux divergence with the z-face
+//           flux carried from the previous plane, psi damping, SSPRK
+//           combination; optional per-block dt / conservation partials.
+//   2D: the same with one plane and no z faces.
+// Every face flux of the block is computed once (block-boundary faces are
+// computed by both neighbours).  Arithmetic follows physics.cuh.
+#pragma once
+
+#include "ghost.cuh"
+#include "physics.cuh"
+#include "reduce.cuh"
+#include "state.hpp"
+
+namespace amrvac {
+
+constexpr int FB = 16;          // block edge handled by the fused kernel
+constexpr int FPW = FB + 2 * NG;  // padded plane width (row stride 20 floats)
+constexpr int FXW = 20;           // row stride of the face-flux arrays
+
+// Thread (x, y) of a warp: lanes 0-15 take row r, lanes 16-31 row r + 4, so the
+// two half-warps of a row-stride-20 array fall on disjoint banks (4*20 = 16 mod 32).
+__device__ __forceinline__ int fused_row(int warp, int lane) {
+  return (warp & 3) + (warp >> 2) * 8 + (lane >> 4) * 4;
+}
+
+template <class T, int DIM> struct FusedSmem {
+  static constexpr int NSLOT = DIM == 3 ? 5 : 1;
+  T plane[NSLOT][NV][FPW][FPW];
+  T fx[NV][FB][FXW];       // x faces: column i = face i - 1/2, i = 0..16
+  T fy[NV][FB + 1][FXW];   // y faces: row j = face j - 1/2
+  double red[8][NPART];
+  double damp;
+};
+
+template <class T> __device__ __forceinline__ T over_dx(T a, T dx, T idx);
+template <> __device__ __forceinline__ double over_dx(double a, double dx, double) { return a / dx; }
+template <> __device__ __forceinline__ float over_dx(float a, float, float idx) { return a * idx; }
+
+// face flux from a 4-cell stencil accessor S(v, t), t = 0..3 for cells
+// f-2, f-1, f, f+1 around the face f-1/2
+template <class T, int D, int LIM, int FLUX, class Acc>
+__device__ __forceinline__ void stencil_flux(Acc S, int glm, T g, T ch, T* f) {
+  T wl[NV], wr[NV];
+#pragma unroll
+  for (int v = 0; v < NV; v++) {
+    T a = S(v, 0), b = S(v, 1), c = S(v, 2), e = S(v, 3);
+    wl[v] = recon_plus<T>(LIM, a, b, c);
+    wr[v] = recon_minus<T>(LIM, b, c, e);
+  }
+  if (!(wl[0] > T(0)) || !(wl[4] > T(0)) || !(wr[0] > T(0)) || !(wr[4] > T(0))) {
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+      wl[v] = S(v, 1);
+      wr[v] = S(v, 2);
+    }
+  }
+  face_flux_d<T, D>(FLUX, glm, g, ch, wl, wr, f);
+}
+
+template <class T, int DIM, int LIM, int FLUX>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
+    k_fused(DevMesh M, const T* U0, const T* __restrict__ Uk, T* out,
+            const int* __restrict__ work, int nwork, T* __restrict__ slab_all, StageParams sp) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  FusedSmem<T, DIM>& S = *reinterpret_cast<FusedSmem<T, DIM>*>(smraw);
+  constexpr int NZ = DIM == 3 ? FB : 1;
+  constexpr int NSLOT = FusedSmem<T, DIM>::NSLOT;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int x = lane & 15, y = fused_row(warp, lane);
+  const size_t vs = (size_t)M.nblocks * M.ncell;
+  const int ncell = M.ncell;
+  const bool ff = sp.pressure_ff != 0;
+  constexpr int NT2 = DIM == 3 ? FB : 1;          // second tangential extent of a face
+  constexpr int SLAB_FACE = NV * 2 * FB * NT2;    // one face: [v][layer][t2][t1]
+  T* __restrict__ slab = slab_all + (size_t)blockIdx.x * (2 * DIM) * SLAB_FACE;
+
+  // halo cell of this thread (threads 0..127): x-halo then y-halo
+  int hx = 0, hy = 0;
+  if (tid < 64) {
+    int side = tid >> 5, r = tid & 31;
+    hy = r >> 1;
+    hx = side ? FB + (r & 1) : -2 + (r & 1);
+  } else if (tid < 128) {
+    int u = tid - 64, side = u >> 5, r = u & 31;
+    hx = r & 15;
+    hy = side ? FB + (r >> 4) : -2 + (r >> 4);
+  }
+
+  for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+    const int b = work[wi];
+    const int q = M.blk[b * 5], L = M.blk[b * 5 + 1];
+    const InstRT rt = M.rt[q];
+    const double gammad = M.gamma[q];
+    const T g = (T)gammad;
+    const float gm1f = (float)(gammad - 1.0);
+    const T rho_floor = (T)sp.small_density, p_floor = (T)sp.small_pressure;
+    const double* dxl = M.dx + (q * MAXLEV + L) * 3;
+    const double dxd[3] = {dxl[0], dxl[1], dxl[2]};
+
+    if (rt.dt == 0.0) {
+      Partial p;
+      partial_zero(p);
+      // finished instance: copied through unchanged
+      for (int c = tid; c < ncell; c += 256) {
+        T u[NV];
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+          size_t at = (size_t)v * vs + (size_t)b * ncell + c;
+          u[v] = Uk[at];
+          out[at] = u[v];
+        }
+        if (sp.epilogue) accumulate_cell(M, u, gammad, dxd, p);
+      }
+      if (sp.epilogue) block_reduce_red(S.red, p, M.part + (size_t)b * NPART);
+      continue;
+    }
+
+    const T ch = (T)rt.ch, dt = (T)rt.dt, ca = (T)sp.a, cb = (T)sp.b;
+    const T dx0 = (T)dxd[0], dx1 = (T)dxd[1], dx2 = (T)dxd[2];
+    const T idx0 = T(1) / dx0, idx1 = T(1) / dx1, idx2 = T(1) / dx2;
+    double dxmin = fmin(dxd[0], dxd[1]);
+    if (DIM == 3) dxmin = fmin(dxmin, dxd[2]);
+    T damp;
+    if constexpr (sizeof(T) == 4) {
+      // float bulk: the damping factor in float (exp of a float argument)
+      damp = sp.glm ? expf((float)(-sp.glm_alpha * rt.ch * rt.dt / dxmin)) : 1.0f;
+    } else {
+      if (tid == 0) S.damp = sp.glm ? exp(-sp.glm_alpha * rt.ch * rt.dt / dxmin) : 1.0;
+    }
+
+    // ---- ghost values of level-change faces: built once per block into this
+    // CTA's slab scratch (all threads), then read like a neighbour block
+    int nb[6];
+#pragma unroll
+    for (int f = 0; f < 6; f++) nb[f] = f < 2 * DIM ? M.nbr[b * 6 + f] : NBR_OUTFLOW;
+    bool any_general = false;
+#pragma unroll
+    for (int f = 0; f < 2 * DIM; f++) any_general |= nb[f] == NBR_GENERAL;
+    __syncthreads();  // the previous block is done with the shared scratch
+    if (any_general) {
+      const int bidx[3] = {M.blk[b * 5 + 2], M.blk[b * 5 + 3], M.blk[b * 5 + 4]};
+      T* cs = &S.fx[0][0][0];  // coarse value + slopes, [cell][1 + DIM][NV]
+      for (int f = 0; f < 2 * DIM; f++) {
+        if (nb[f] != NBR_GENERAL) continue;
+        const int d = f >> 1, side = f & 1;
+        // global level-L index of ghost (layer, t1, t2) of this face
+        auto ghost_p = [&](int layer, int t1, int t2, int* p) {
+          int loc[3];
+          const int n = side ? FB + layer : layer - 2;
+          if (d == 0) { loc[0] = n; loc[1] = t1; loc[2] = t2; }
+          else if (d == 1) { loc[0] = t1; loc[1] = n; loc[2] = t2; }
+          else { loc[0] = t1; loc[1] = t2; loc[2] = n; }
+#pragma unroll
+          for (int e = 0; e < 3; e++) p[e] = e < DIM ? bidx[e] * FB + loc[e] : 0;
+          wrap_level(M, q, L, p);
+        };
+        int pn[3];
+        ghost_p(0, 0, 0, pn);
+        int cell;
+        const int code = map_at(M, q, L, pn, &cell);
+        T* sf = slab + f * SLAB_FACE;
+        if (code == MAP_REFINED) {
+          // restriction: mean of the finer children
+          for (int e = tid; e < 2 * FB * NT2; e += 256) {
+            const int t1 = e % FB, t2 = (e / FB) % NT2, layer = e / (FB * NT2);
+            int p[3];
+            ghost_p(layer, t1, t2, p);
+            T u[NV];
+            level_value_down(M, Uk, vs, q, L, p, u);
+#pragma unroll
+            for (int v = 0; v < NV; v++) sf[((v * 2 + layer) * NT2 + t2) * FB + t1] = u[v];
+          }
+        } else {
+          // prolongation: value and minmod slopes once per coarse cell ...
+          constexpr int NC2 = DIM == 3 ? FB / 2 : 1;
+          for (int e = tid; e < (FB / 2) * NC2 * DIM; e += 256) {
+            const int dd = e % DIM, cc = e / DIM;
+            const int ct1 = cc % (FB / 2), ct2 = cc / (FB / 2);
+            int p[3];
+            ghost_p(0, 2 * ct1, 2 * ct2, p);
+            int qc[3];
+#pragma unroll
+            for (int k2 = 0; k2 < 3; k2++) qc[k2] = k2 < DIM ? (p[k2] >> 1) : 0;
+            T uc[NV], um[NV], up[NV];
+            level_value_down(M, Uk, vs, q, L - 1, qc, uc);
+            int qm[3] = {qc[0], qc[1], qc[2]}, qp[3] = {qc[0], qc[1], qc[2]};
+            qm[dd] -= 1;
+            qp[dd] += 1;
+            level_value_down(M, Uk, vs, q, L - 1, qm, um);
+            level_value_down(M, Uk, vs, q, L - 1, qp, up);
+#pragma unroll
+            for (int v = 0; v < NV; v++) {
+              cs[(cc * (1 + DIM) + 1 + dd) * NV + v] = minmod_g(uc[v] - um[v], up[v] - uc[v]);
+              if (dd == 0) cs[(cc * (1 + DIM)) * NV + v] = uc[v];
+            }
+          }
+          __syncthreads();
+          // ... then every fine ghost: coarse value + sum_d (+-1/4) slope_d
+          for (int e = tid; e < 2 * FB * NT2; e += 256) {
+            const int t1 = e % FB, t2 = (e / FB) % NT2, layer = e / (FB * NT2);
+            int p[3];
+            ghost_p(layer, t1, t2, p);
+            const int cc = (t2 >> 1) * (FB / 2) + (t1 >> 1);
+            const T* c0 = cs + (cc * (1 + DIM)) * NV;
+#pragma unroll
+            for (int v = 0; v < NV; v++) {
+              T val = c0[v];
+#pragma unroll
+              for (int dd = 0; dd < DIM; dd++) {
+                const T wgt = (p[dd] & 1) ? T(0.25) : T(-0.25);
+                val = val + wgt * c0[(1 + dd) * NV + v];
+              }
+              sf[((v * 2 + layer) * NT2 + t2) * FB + t1] = val;
+            }
+          }
+          __syncthreads();  // cs is reused by the next face
+        }
+      }
+      __syncthreads();
+    }
+
+    // conserved value of block-local cell (i, j, k); at most one index outside
+    auto fetch = [&](int i, int j, int k, T* u) {
+      int f = -1, n = 0, t1 = 0, t2 = 0;
+      if (i < 0 || i >= FB) { f = i < 0 ? 0 : 1; n = i; t1 = j; t2 = k; }
+      else if (j < 0 || j >= FB) { f = j < 0 ? 2 : 3; n = j; t1 = i; t2 = k; }
+      else if (DIM == 3 && (k < 0 || k >= FB)) { f = k < 0 ? 4 : 5; n = k; t1 = i; t2 = j; }
+      if (f < 0) {
+        read_cell(M, Uk, vs, b, (k * FB + j) * FB + i, u);
+        return;
+      }
+      const int code = nb[f];
+      if (code == NBR_GENERAL) {
+        const int layer = n < 0 ? n + 2 : n - FB;
+        const T* sf = slab + f * SLAB_FACE + (layer * NT2 + t2) * FB + t1;
+#pragma unroll
+        for (int v = 0; v < NV; v++) u[v] = sf[v * 2 * NT2 * FB];
+        return;
+      }
+      // same-level neighbour (wrapped index) or outflow clamp (own block)
+      const int nn = code >= 0 ? (n < 0 ? n + FB : n - FB) : (n < 0 ? 0 : FB - 1);
+      const int src = code >= 0 ? code : b;
+      int ii = i, jj = j, kk = k;
+      if (f < 2) ii = nn;
+      else if (f < 4) jj = nn;
+      else kk = nn;
+      read_cell(M, Uk, vs, src, (kk * FB + jj) * FB + ii, u);
+    };
+
+    auto load_plane = [&](int pz) {
+      const int slot = ((pz % NSLOT) + NSLOT) % NSLOT;
+      T u[NV], w[NV];
+      fetch(x, y, DIM == 3 ? pz : 0, u);
+      cons2prim(gammad, u, w, ff, gm1f);
+      if (sp.check_small && (!(w[0] > rho_floor) || !(w[4] > p_floor)))
+        latch_error(M.err, AMRVAC_E_SMALL_VALUES, b, tid, 0);
+#pragma unroll
+      for (int v = 0; v < NV; v++) S.plane[slot][v][y + NG][x + NG] = w[v];
+      if (tid < 128 && pz >= 0 && pz < NZ) {
+        fetch(hx, hy, DIM == 3 ? pz : 0, u);
+        cons2prim(gammad, u, w, ff, gm1f);
+        if (sp.check_small && (!(w[0] > rho_floor) || !(w[4] > p_floor)))
+          latch_error(M.err, AMRVAC_E_SMALL_VALUES, b, tid, 1);
+#pragma unroll
+        for (int v = 0; v < NV; v++) S.plane[slot][v][hy + NG][hx + NG] = w[v];
+      }
+    };
+
+    auto zflux = [&](int zc, T* f) {
+      // z face between planes zc-1 and zc of the thread's own column
+      int s0 = (zc - 2 + 2 * NSLOT) % NSLOT, s1 = (zc - 1 + 2 * NSLOT) % NSLOT;
+      int s2 = (zc + 2 * NSLOT) % NSLOT, s3 = (zc + 1 + 2 * NSLOT) % NSLOT;
+      auto acc = [&](int v, int t) -> T {
+        int s = t == 0 ? s0 : (t == 1 ? s1 : (t == 2 ? s2 : s3));
+        return S.plane[s][v][y + NG][x + NG];
+      };
+      stencil_flux<T, 2, LIM, FLUX>(acc, sp.glm, g, ch, f);
+    };
+
+    T fzp[NV];
+    if (DIM == 3) {
+      load_plane(-2);
+      load_plane(-1);
+      load_plane(0);
+      load_plane(1);
+      zflux(0, fzp);  // own column only: no barrier needed
+    } else {
+      load_plane(0);
+    }
+
+    if constexpr (sizeof(T) == 8) {
+      __syncthreads();
+      damp = S.damp;
+    }
+
+#pragma unroll 1
+    for (int z = 0; z < NZ; z++) {
+      if (DIM == 3) load_plane(z + 2);
+      __syncthreads();
+      const int sl = z % NSLOT;
+      {
+        T f[NV];
+        auto ax = [&](int v, int t) -> T { return S.plane[sl][v][y + NG][x + t]; };
+        stencil_flux<T, 0, LIM, FLUX>(ax, sp.glm, g, ch, f);
+#pragma unroll
+        for (int v = 0; v < NV; v++) S.fx[v][y][x] = f[v];
+        auto ay = [&](int v, int t) -> T { return S.plane[sl][v][y + t][x + NG]; };
+        stencil_flux<T, 1, LIM, FLUX>(ay, sp.glm, g, ch, f);
+#pragma unroll
+        for (int v = 0; v < NV; v++) S.fy[v][y][x] = f[v];
+        // faces on the +x block boundary (one rotating warp, lanes 0..15) and on
+        // the +y boundary (another warp): 32 extra faces per plane
+        if (warp == (z & 7) && lane < FB) {
+          auto ae = [&](int v, int t) -> T { return S.plane[sl][v][lane + NG][FB + t]; };
+          stencil_flux<T, 0, LIM, FLUX>(ae, sp.glm, g, ch, f);
+#pragma unroll
+          for (int v = 0; v < NV; v++) S.fx[v][lane][FB] = f[v];
+        }
+        if (warp == ((z + 4) & 7) && lane < FB) {
+          auto ae = [&](int v, int t) -> T { return S.plane[sl][v][FB + t][lane + NG]; };
+          stencil_flux<T, 1, LIM, FLUX>(ae, sp.glm, g, ch, f);
+#pragma unroll
+          for (int v = 0; v < NV; v++) S.fy[v][FB][lane] = f[v];
+        }
+      }
+      T fz[NV];
+      if (DIM == 3) zflux(z + 1, fz);
+      __syncthreads();
+
+      const int c = (z * FB + y) * FB + x;
+      T un[NV];
+#pragma unroll
+      for (int v = 0; v < NV; v++) {
+        T acc = over_dx<T>(S.fx[v][y][x + 1] - S.fx[v][y][x], dx0, idx0);
+        acc += over_dx<T>(S.fy[v][y + 1][x] - S.fy[v][y][x], dx1, idx1);
+        if (DIM == 3) acc += over_dx<T>(fz[v] - fzp[v], dx2, idx2);
+        const size_t at = (size_t)v * vs + (size_t)b * ncell + c;
+        T ut = Uk[at] - dt * acc;
+        if (v == 8) ut = ut * damp;
+        un[v] = sp.k == 0 ? ut : ca * U0[at] + cb * ut;
+        out[at] = un[v];
+      }
+      if (DIM == 3) {
+#pragma unroll
+        for (int v = 0; v < NV; v++) fzp[v] = fz[v];
+      }
+    }
+    if (sp.epilogue) {
+      // per-block CFL / conservation partials of the new state: each thread
+      // re-reads the column it has just written
+      Partial p;
+      partial_zero(p);
+      if constexpr (sizeof(T) == 4) {
+        if (ff) {
+          // float speeds, float-float conservation sums per thread
+          float sm = 0.f, cm = 0.f;
+          float hi[NV], lo[NV];
+#pragma unroll
+          for (int v = 0; v < NV; v++) hi[v] = lo[v] = 0.f;
+          const float idd[3] = {(float)(1.0 / dxd[0]), (float)(1.0 / dxd[1]),
+                                (float)(1.0 / dxd[2])};
+#pragma unroll 1
+          for (int z = 0; z < NZ; z++) {
+            const int c = (z * FB + y) * FB + x;
+            float u[NV], w[NV];
+#pragma unroll
+            for (int v = 0; v < NV; v++) u[v] = out[(size_t)v * vs + (size_t)b * ncell + c];
+            cons2prim(gammad, u, w, true, gm1f);
+            float s = 0.f;
+#pragma unroll
+            for (int d = 0; d < DIM; d++) {
+              float spd = fabsf(w[1 + d]) + fast_speed((float)g, w, d);
+              s += spd * idd[d];
+              cm = fmaxf(cm, spd);
+            }
+            sm = fmaxf(sm, s);
+#pragma unroll
+            for (int v = 0; v < NV; v++) {
+              ff2 t = two_sum(hi[v], u[v]);
+              hi[v] = t.hi;
+              lo[v] = __fadd_rn(lo[v], t.lo);
+            }
+          }
+          p.smax = sm;
+          p.chm = cm;
+#pragma unroll
+          for (int v = 0; v < NV; v++) p.sum[v] = (double)hi[v] + (double)lo[v];
+          block_reduce_red(S.red, p, M.part + (size_t)b * NPART);
+          continue;
+        }
+      }
+#pragma unroll 1
+      for (int z = 0; z < NZ; z++) {
+        const int c = (z * FB + y) * FB + x;
+        T u[NV];
+#pragma unroll
+        for (int v = 0; v < NV; v++) u[v] = out[(size_t)v * vs + (size_t)b * ncell + c];
+        accumulate_cell(M, u, gammad, dxd, p);  // FP64 sums
+      }
+      block_reduce_red(S.red, p, M.part + (size_t)b * NPART);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- launcher
+
+template <class T, int DIM, int LIM, int FLUX>
+static int launch_one(amrvac_state* s, const T* U0, const T* Uk, T* out, StageParams sp) {
+  auto kern = k_fused<T, DIM, LIM, FLUX>;
+  const int smem = (int)sizeof(FusedSmem<T, DIM>);
+  static int configured_grid = 0;  // per instantiation: resident CTAs on this device
+  if (configured_grid == 0) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+        cudaSuccess)
+      return -1;
+    int dev = 0, nsm = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+    configured_grid = nsm * (per_sm > 0 ? per_sm : 1);
+  }
+  int grid = s->nwork < configured_grid ? s->nwork : configured_grid;
+  if (grid > s->slab_ctas) grid = s->slab_ctas;
+  kern<<<grid, 256, smem, s->stream>>>(s->mesh, U0, Uk, out, s->d_work, s->nwork, (T*)s->slab,
+                                       sp);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+template <class T, int DIM, int LIM>
+int launch_fused_l(amrvac_state* s, int k, int epilogue) {
+  int u0, uin, uout;
+  stage_buffers(s->cfg.time, k, &u0, &uin, &uout);
+  StageParams sp = make_stage_params(s, k, epilogue);
+  const T* U0 = (const T*)s->U[u0];
+  const T* Uk = (const T*)s->U[uin];
+  T* out = (T*)s->U[uout];
+  if (s->cfg.flux == AMRVAC_FLUX_HLLD)
+    return launch_one<T, DIM, LIM, AMRVAC_FLUX_HLLD>(s, U0, Uk, out, sp);
+  return launch_one<T, DIM, LIM, AMRVAC_FLUX_HLL>(s, U0, Uk, out, sp);
+}
+
+}  // namespace amrvac

@@ -27,8 +27,9 @@ template <> struct Num<float> {
   static constexpr float hlld_eps = 1e-5f;
 };
 
+// sign with sgn(0) = 0, by selects (no integer-to-float conversion)
 template <class T> __device__ __forceinline__ T sgnT(T x) {
-  return (T)((x > T(0)) - (x < T(0)));
+  return x > T(0) ? T(1) : (x < T(0) ? T(-1) : T(0));
 }
 
 // ---------------------------------------------------------------- primitives
@@ -42,21 +43,67 @@ __device__ __forceinline__ double pressure_of(double gamma, const double* u, dou
 
 __device__ __forceinline__ float pressure_of(double gamma, const float* u, float vx, float vy,
                                              float vz) {
+  // (gamma-1)(e - ke) - (gamma-1)/2 B^2 with e, B_i exact in double
   float ke = 0.5f * (u[1] * vx + u[2] * vy + u[3] * vz);
   double bx = u[5], by = u[6], bz = u[7];
-  double me = 0.5 * (bx * bx + by * by + bz * bz);
-  return (float)((gamma - 1.0) * ((double)u[4] - (double)ke - me));
+  double b2 = fma(bz, bz, fma(by, by, bx * bx));
+  double gm1 = gamma - 1.0;
+  return (float)fma(-0.5 * gm1, b2, gm1 * ((double)u[4] - (double)ke));
 }
 
+// ---- float-float (double-single) helpers: a value is hi + lo with |lo| <= ulp(hi)/2
+struct ff2 {
+  float hi, lo;
+};
+
+// a + b = s + e exactly (Knuth TwoSum)
+__device__ __forceinline__ ff2 two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+
+// Same pressure as pressure_of(double, float*, ...) with the subtraction in
+// float-float: B_i^2 = hi + lo exactly by FMA, e - ke exactly by TwoSum, the
+// remaining sums compensated; one final rounding to float.
+__device__ __forceinline__ float pressure_ff(float gm1, const float* u, float vx, float vy,
+                                             float vz) {
+  float ke = 0.5f * (u[1] * vx + u[2] * vy + u[3] * vz);
+  float bx = u[5], by = u[6], bz = u[7];
+  float h = __fmul_rn(bx, bx);
+  float l = __fmaf_rn(bx, bx, -h);
+  float t = __fmul_rn(by, by);
+  l = __fadd_rn(l, __fmaf_rn(by, by, -t));
+  ff2 s = two_sum(h, t);
+  l = __fadd_rn(l, s.lo);
+  t = __fmul_rn(bz, bz);
+  l = __fadd_rn(l, __fmaf_rn(bz, bz, -t));
+  s = two_sum(s.hi, t);
+  l = __fadd_rn(l, s.lo);                       // B^2 = s.hi + l
+  ff2 a = two_sum(u[4], -ke);                   // e - ke exactly
+  ff2 d = two_sum(a.hi, -0.5f * s.hi);          // 0.5 * s.hi is exact
+  float rest = __fadd_rn(__fadd_rn(d.lo, a.lo), -0.5f * l);
+  return gm1 * __fadd_rn(d.hi, rest);
+}
+
+// gm1f: (float)(gamma - 1), used by the float-float pressure
 template <class T>
-__device__ __forceinline__ void cons2prim(double gamma, const T* u, T* w) {
+__device__ __forceinline__ void cons2prim(double gamma, const T* u, T* w, bool ff = false,
+                                          float gm1f = 0.f) {
   T rho = u[0];
-  T vx = u[1] / rho, vy = u[2] / rho, vz = u[3] / rho;
+  T ir = T(1) / rho;
+  T vx = u[1] * ir, vy = u[2] * ir, vz = u[3] * ir;
   w[0] = rho;
   w[1] = vx;
   w[2] = vy;
   w[3] = vz;
-  w[4] = pressure_of(gamma, u, vx, vy, vz);
+  if constexpr (sizeof(T) == 4) {
+    if (ff) w[4] = pressure_ff(gm1f, (const float*)u, vx, vy, vz);
+    else w[4] = pressure_of(gamma, u, vx, vy, vz);
+  } else {
+    w[4] = pressure_of(gamma, u, vx, vy, vz);
+  }
   w[5] = u[5];
   w[6] = u[6];
   w[7] = u[7];
@@ -67,11 +114,12 @@ __device__ __forceinline__ void cons2prim(double gamma, const T* u, T* w) {
 template <class T>
 __device__ __forceinline__ T fast_speed(T gamma, const T* w, int d) {
   int t1 = d == 2 ? 0 : d + 1, t2 = d == 0 ? 2 : d - 1;
-  T rho = w[0];
-  T a2 = gamma * w[4] / rho;
+  T ir = T(1) / w[0];
+  T a2 = gamma * w[4] * ir;
   T bn = w[5 + d], b1 = w[5 + t1], b2 = w[5 + t2];
-  T bt2 = (b1 * b1 + b2 * b2) / rho;
-  T bb = (bn * bn + b1 * b1 + b2 * b2) / rho;
+  T bt = b1 * b1 + b2 * b2;
+  T bt2 = bt * ir;
+  T bb = (bn * bn + bt) * ir;
   T dd = a2 - bb;
   return sqrt(T(0.5) * (a2 + bb + sqrt(dd * dd + T(4) * a2 * bt2)));
 }
@@ -107,12 +155,13 @@ template <class T> __device__ __forceinline__ T recon_minus(int lim, T a, T b, T
 // ---------------------------------------------------------------- Riemann
 // local frame: q = (rho, u, v, w, p, -, By, Bz), normal field bx shared.
 
+// ig1 = 1/(gamma - 1)
 template <class T>
-__device__ __forceinline__ void local_cons_flux(T g, const T* q, T bx, T* U, T* F, T& pt) {
+__device__ __forceinline__ void local_cons_flux(T ig1, const T* q, T bx, T* U, T* F, T& pt) {
   T rho = q[0], u = q[1], v = q[2], w = q[3], p = q[4], by = q[6], bz = q[7];
   T b2 = bx * bx + by * by + bz * bz;
   pt = p + T(0.5) * b2;
-  T e = p / (g - T(1)) + T(0.5) * rho * (u * u + v * v + w * w) + T(0.5) * b2;
+  T e = p * ig1 + T(0.5) * rho * (u * u + v * v + w * w) + T(0.5) * b2;
   T vb = u * bx + v * by + w * bz;
   U[0] = rho;
   U[1] = rho * u;
@@ -133,27 +182,29 @@ __device__ __forceinline__ void local_cons_flux(T g, const T* q, T bx, T* U, T* 
 }
 
 template <class T> __device__ __forceinline__ T local_fast(T g, const T* q, T bx) {
-  T rho = q[0];
-  T a2 = g * q[4] / rho;
-  T bt2 = (q[6] * q[6] + q[7] * q[7]) / rho;
-  T bb = (bx * bx + q[6] * q[6] + q[7] * q[7]) / rho;
+  T ir = T(1) / q[0];
+  T bt = q[6] * q[6] + q[7] * q[7];
+  T a2 = g * q[4] * ir;
+  T bt2 = bt * ir;
+  T bb = (bx * bx + bt) * ir;
   T dd = a2 - bb;
   return sqrt(T(0.5) * (a2 + bb + sqrt(dd * dd + T(4) * a2 * bt2)));
 }
 
 template <class T>
-__device__ __forceinline__ void hll_local(T g, const T* ql, const T* qr, T bx, T* f) {
+__device__ __forceinline__ void hll_local(T g, T ig1, const T* ql, const T* qr, T bx, T* f) {
   T UL[8], UR[8], FL[8], FR[8], ptl, ptr;
-  local_cons_flux(g, ql, bx, UL, FL, ptl);
-  local_cons_flux(g, qr, bx, UR, FR, ptr);
+  local_cons_flux(ig1, ql, bx, UL, FL, ptl);
+  local_cons_flux(ig1, qr, bx, UR, FR, ptr);
   T cfl = local_fast(g, ql, bx), cfr = local_fast(g, qr, bx);
   T sl = fmin(ql[1] - cfl, qr[1] - cfr);
   T sr = fmax(ql[1] + cfl, qr[1] + cfr);
+  T inv = T(1) / (sr - sl);
 #pragma unroll
   for (int c = 0; c < 8; c++) {
     if (sl >= T(0)) f[c] = FL[c];
     else if (sr <= T(0)) f[c] = FR[c];
-    else f[c] = (sr * FL[c] - sl * FR[c] + sl * sr * (UR[c] - UL[c])) / (sr - sl);
+    else f[c] = (sr * FL[c] - sl * FR[c] + sl * sr * (UR[c] - UL[c])) * inv;
   }
 }
 
@@ -162,12 +213,13 @@ template <class T> struct StarState {
 };
 
 template <class T>
-__device__ __forceinline__ StarState<T> hlld_star(const T* q, const T* U, T pt, T s, T sm, T pts,
+__device__ __forceinline__ StarState<T> hlld_star(const T* q, T e, T pt, T s, T sm, T pts,
                                                   T bx) {
   StarState<T> r;
   T rho = q[0], u = q[1], v = q[2], w = q[3], by = q[6], bz = q[7];
   T su = s - u;
-  r.rs = rho * su / (s - sm);
+  T isd = T(1) / (s - sm);
+  r.rs = rho * su * isd;
   T big = rho * su * (s - sm);
   T den = big - bx * bx;
   T scale = fmax(fabs(big), bx * bx);
@@ -177,8 +229,9 @@ __device__ __forceinline__ StarState<T> hlld_star(const T* q, const T* U, T pt, 
     r.bys = by;
     r.bzs = bz;
   } else {
-    T tv = bx * (sm - u) / den;
-    T tb = (rho * su * su - bx * bx) / den;
+    T iden = T(1) / den;
+    T tv = bx * (sm - u) * iden;
+    T tb = (rho * su * su - bx * bx) * iden;
     r.vs = v - by * tv;
     r.ws = w - bz * tv;
     r.bys = by * tb;
@@ -186,76 +239,104 @@ __device__ __forceinline__ StarState<T> hlld_star(const T* q, const T* U, T pt, 
   }
   T vb = u * bx + v * by + w * bz;
   T vbs = sm * bx + r.vs * r.bys + r.ws * r.bzs;
-  r.es = (su * U[4] - pt * u + pts * sm + bx * (vb - vbs)) / (s - sm);
+  r.es = (su * e - pt * u + pts * sm + bx * (vb - vbs)) * isd;
   return r;
 }
 
+// physical flux and conserved state of a local state with total pressure pt
+// and total energy e already formed
 template <class T>
-__device__ __forceinline__ void hlld_local(T g, const T* ql, const T* qr, T bx, T* f) {
-  T UL[8], UR[8], FL[8], FR[8], ptl, ptr;
-  local_cons_flux(g, ql, bx, UL, FL, ptl);
-  local_cons_flux(g, qr, bx, UR, FR, ptr);
+__device__ __forceinline__ void phys_flux_state(const T* q, T bx, T pt, T e, T* U, T* F) {
+  T rho = q[0], u = q[1], v = q[2], w = q[3], by = q[6], bz = q[7];
+  T mu = rho * u;
+  U[0] = rho;
+  U[1] = mu;
+  U[2] = rho * v;
+  U[3] = rho * w;
+  U[4] = e;
+  U[5] = bx;
+  U[6] = by;
+  U[7] = bz;
+  F[0] = mu;
+  F[1] = mu * u + pt - bx * bx;
+  F[2] = mu * v - bx * by;
+  F[3] = mu * w - bx * bz;
+  F[4] = (e + pt) * u - bx * (u * bx + v * by + w * bz);
+  F[5] = T(0);
+  F[6] = by * u - bx * v;
+  F[7] = bz * u - bx * w;
+}
+
+// HLLD (Miyoshi & Kusano 2005).  Both single-star states are formed (the
+// double-star states average them); the upwind side of the interface is then
+// chosen by selects, and the flux is F_s + c1 (U*_s - U_s) + c2 (U**_s - U*_s)
+// with (c1, c2) = (0, 0), (S_s, 0) or (S_s, S*_s) for the outer, single-star
+// and double-star regions: one physical flux instead of two and no divergent
+// region branches.
+template <class T>
+__device__ __forceinline__ void hlld_local(T g, T ig1, const T* ql, const T* qr, T bx, T* f) {
+  T ptl, ptr, el, er;
+  {
+    T b2 = bx * bx + ql[6] * ql[6] + ql[7] * ql[7];
+    ptl = ql[4] + T(0.5) * b2;
+    el = ql[4] * ig1 + T(0.5) * ql[0] * (ql[1] * ql[1] + ql[2] * ql[2] + ql[3] * ql[3]) +
+         T(0.5) * b2;
+    b2 = bx * bx + qr[6] * qr[6] + qr[7] * qr[7];
+    ptr = qr[4] + T(0.5) * b2;
+    er = qr[4] * ig1 + T(0.5) * qr[0] * (qr[1] * qr[1] + qr[2] * qr[2] + qr[3] * qr[3]) +
+         T(0.5) * b2;
+  }
   T cfl = local_fast(g, ql, bx), cfr = local_fast(g, qr, bx);
   T ul = ql[1], ur = qr[1];
   T cmax = fmax(cfl, cfr);
   T sl = fmin(ul, ur) - cmax;
   T sr = fmax(ul, ur) + cmax;
-  if (sl > T(0)) {
-#pragma unroll
-    for (int c = 0; c < 8; c++) f[c] = FL[c];
-    return;
-  }
-  if (sr < T(0)) {
-#pragma unroll
-    for (int c = 0; c < 8; c++) f[c] = FR[c];
-    return;
-  }
   T rl = ql[0], rr = qr[0];
   T sul = sl - ul, sur = sr - ur;
-  T den = sur * rr - sul * rl;
-  T sm = (sur * rr * ur - sul * rl * ul - ptr + ptl) / den;
-  T pts = (sur * rr * ptl - sul * rl * ptr + rl * rr * sur * sul * (ur - ul)) / den;
-  StarState<T> L = hlld_star(ql, UL, ptl, sl, sm, pts, bx);
-  StarState<T> R = hlld_star(qr, UR, ptr, sr, sm, pts, bx);
+  T iden = T(1) / (sur * rr - sul * rl);
+  T sm = (sur * rr * ur - sul * rl * ul - ptr + ptl) * iden;
+  T pts = (sur * rr * ptl - sul * rl * ptr + rl * rr * sur * sul * (ur - ul)) * iden;
+  StarState<T> L = hlld_star(ql, el, ptl, sl, sm, pts, bx);
+  StarState<T> R = hlld_star(qr, er, ptr, sr, sm, pts, bx);
   T sqrl = sqrt(L.rs), sqrr = sqrt(R.rs);
   T ssl = sm - fabs(bx) / sqrl, ssr = sm + fabs(bx) / sqrr;
   T sb = sgnT(bx);
-  T ssum = sqrl + sqrr;
-  T vss = (sqrl * L.vs + sqrr * R.vs + (R.bys - L.bys) * sb) / ssum;
-  T wss = (sqrl * L.ws + sqrr * R.ws + (R.bzs - L.bzs) * sb) / ssum;
-  T byss = (sqrl * R.bys + sqrr * L.bys + sqrl * sqrr * (R.vs - L.vs) * sb) / ssum;
-  T bzss = (sqrl * R.bzs + sqrr * L.bzs + sqrl * sqrr * (R.ws - L.ws) * sb) / ssum;
+  T issum = T(1) / (sqrl + sqrr);
+  T vss = (sqrl * L.vs + sqrr * R.vs + (R.bys - L.bys) * sb) * issum;
+  T wss = (sqrl * L.ws + sqrr * R.ws + (R.bzs - L.bzs) * sb) * issum;
+  T byss = (sqrl * R.bys + sqrr * L.bys + sqrl * sqrr * (R.vs - L.vs) * sb) * issum;
+  T bzss = (sqrl * R.bzs + sqrr * L.bzs + sqrl * sqrr * (R.ws - L.ws) * sb) * issum;
   T vbss = sm * bx + vss * byss + wss * bzss;
   T essl = L.es - sqrl * (sm * bx + L.vs * L.bys + L.ws * L.bzs - vbss) * sb;
   T essr = R.es + sqrr * (sm * bx + R.vs * R.bys + R.ws * R.bzs - vbss) * sb;
-  // select the region of the fan that contains the interface (x/t = 0)
-  if (ssl >= T(0)) {
-    T US[8] = {L.rs, L.rs * sm, L.rs * L.vs, L.rs * L.ws, L.es, bx, L.bys, L.bzs};
+  // region of the fan that contains x/t = 0 (same tie rules as the oracle)
+  const bool left = sm >= T(0);
+  const bool outer = left ? (sl > T(0)) : (sr < T(0));
+  const bool single = left ? (ssl >= T(0)) : !(ssr >= T(0));
+  T q[8];
 #pragma unroll
-    for (int c = 0; c < 8; c++) f[c] = FL[c] + sl * (US[c] - UL[c]);
-  } else if (sm >= T(0)) {
-    T US[8] = {L.rs, L.rs * sm, L.rs * L.vs, L.rs * L.ws, L.es, bx, L.bys, L.bzs};
-    T USS[8] = {L.rs, L.rs * sm, L.rs * vss, L.rs * wss, essl, bx, byss, bzss};
+  for (int c = 0; c < 8; c++) q[c] = left ? ql[c] : qr[c];
+  T U[8], F[8];
+  phys_flux_state(q, bx, left ? ptl : ptr, left ? el : er, U, F);
+  const T rs = left ? L.rs : R.rs, vs = left ? L.vs : R.vs, ws = left ? L.ws : R.ws;
+  const T bys = left ? L.bys : R.bys, bzs = left ? L.bzs : R.bzs, es = left ? L.es : R.es;
+  const T c1 = left ? sl : sr, c2 = left ? ssl : ssr;
+  const T US[8] = {rs, rs * sm, rs * vs, rs * ws, es, bx, bys, bzs};
+  const T USS[8] = {rs, rs * sm, rs * vss, rs * wss, left ? essl : essr, bx, byss, bzss};
 #pragma unroll
-    for (int c = 0; c < 8; c++) f[c] = (FL[c] + sl * (US[c] - UL[c])) + ssl * (USS[c] - US[c]);
-  } else if (ssr >= T(0)) {
-    T US[8] = {R.rs, R.rs * sm, R.rs * R.vs, R.rs * R.ws, R.es, bx, R.bys, R.bzs};
-    T USS[8] = {R.rs, R.rs * sm, R.rs * vss, R.rs * wss, essr, bx, byss, bzss};
-#pragma unroll
-    for (int c = 0; c < 8; c++) f[c] = (FR[c] + sr * (US[c] - UR[c])) + ssr * (USS[c] - US[c]);
-  } else {
-    T US[8] = {R.rs, R.rs * sm, R.rs * R.vs, R.rs * R.ws, R.es, bx, R.bys, R.bzs};
-#pragma unroll
-    for (int c = 0; c < 8; c++) f[c] = FR[c] + sr * (US[c] - UR[c]);
+  for (int c = 0; c < 8; c++) {
+    T fs = F[c] + c1 * (US[c] - U[c]);
+    T v = single ? fs : fs + c2 * (USS[c] - US[c]);
+    f[c] = outer ? F[c] : v;
   }
 }
 
-// Face flux along d from primitive face states wl, wr (global frame).
-template <class T>
-__device__ __forceinline__ void face_flux(int flux, int glm, T g, T ch, int d, const T* wl,
-                                          const T* wr, T* f) {
-  int t1 = d == 2 ? 0 : d + 1, t2 = d == 0 ? 2 : d - 1;
-  T bnl = wl[5 + d], bnr = wr[5 + d];
+// Face flux along D from primitive face states wl, wr (global frame).
+template <class T, int D>
+__device__ __forceinline__ void face_flux_d(int flux, int glm, T g, T ch, const T* wl,
+                                            const T* wr, T* f) {
+  constexpr int t1 = D == 2 ? 0 : D + 1, t2 = D == 0 ? 2 : D - 1;
+  T bnl = wl[5 + D], bnr = wr[5 + D];
   T bns, psis;
   if (glm) {
     bns = T(0.5) * (bnl + bnr) - (wr[8] - wl[8]) / (T(2) * ch);
@@ -264,20 +345,29 @@ __device__ __forceinline__ void face_flux(int flux, int glm, T g, T ch, int d, c
     bns = T(0.5) * (bnl + bnr);
     psis = T(0);
   }
-  T ql[8] = {wl[0], wl[1 + d], wl[1 + t1], wl[1 + t2], wl[4], bns, wl[5 + t1], wl[5 + t2]};
-  T qr[8] = {wr[0], wr[1 + d], wr[1 + t1], wr[1 + t2], wr[4], bns, wr[5 + t1], wr[5 + t2]};
+  T ql[8] = {wl[0], wl[1 + D], wl[1 + t1], wl[1 + t2], wl[4], bns, wl[5 + t1], wl[5 + t2]};
+  T qr[8] = {wr[0], wr[1 + D], wr[1 + t1], wr[1 + t2], wr[4], bns, wr[5 + t1], wr[5 + t2]};
   T fl[8];
-  if (flux == AMRVAC_FLUX_HLL) hll_local(g, ql, qr, bns, fl);
-  else hlld_local(g, ql, qr, bns, fl);
+  const T ig1 = T(1) / (g - T(1));
+  if (flux == AMRVAC_FLUX_HLL) hll_local(g, ig1, ql, qr, bns, fl);
+  else hlld_local(g, ig1, ql, qr, bns, fl);
   f[0] = fl[0];
-  f[1 + d] = fl[1];
+  f[1 + D] = fl[1];
   f[1 + t1] = fl[2];
   f[1 + t2] = fl[3];
   f[4] = fl[4];
-  f[5 + d] = glm ? psis : T(0);
+  f[5 + D] = glm ? psis : T(0);
   f[5 + t1] = fl[6];
   f[5 + t2] = fl[7];
   f[8] = glm ? ch * ch * bns : T(0);
+}
+
+template <class T>
+__device__ __forceinline__ void face_flux(int flux, int glm, T g, T ch, int d, const T* wl,
+                                          const T* wr, T* f) {
+  if (d == 0) face_flux_d<T, 0>(flux, glm, g, ch, wl, wr, f);
+  else if (d == 1) face_flux_d<T, 1>(flux, glm, g, ch, wl, wr, f);
+  else face_flux_d<T, 2>(flux, glm, g, ch, wl, wr, f);
 }
 
 }  // namespace amrvac

@@ -9,6 +9,7 @@
 
 #include "ghost.cuh"
 #include "physics.cuh"
+#include "reduce.cuh"
 #include "state.hpp"
 
 namespace amrvac {
@@ -99,70 +100,10 @@ __global__ void __launch_bounds__(256) k_flux(DevMesh M, const T* __restrict__ W
   }
 }
 
-// ------------------------------------------------------------------ reductions
-
-struct Partial {
-  double smax, chm, sum[NV];
-};
-
-__device__ __forceinline__ void partial_zero(Partial& p) {
-  p.smax = 0.0;
-  p.chm = 0.0;
-#pragma unroll
-  for (int v = 0; v < NV; v++) p.sum[v] = 0.0;
-}
-
-// deterministic block reduction (fixed shuffle tree + fixed warp order) of a
-// Partial; thread 0 writes it to part[b]
-__device__ void block_reduce_store(Partial& p, double* part_b) {
-  __shared__ double sh[32][NPART];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    p.smax = fmax(p.smax, __shfl_xor_sync(0xffffffffu, p.smax, o));
-    p.chm = fmax(p.chm, __shfl_xor_sync(0xffffffffu, p.chm, o));
-#pragma unroll
-    for (int v = 0; v < NV; v++) p.sum[v] += __shfl_xor_sync(0xffffffffu, p.sum[v], o);
-  }
-  if (lane == 0) {
-    sh[warp][0] = p.smax;
-    sh[warp][1] = p.chm;
-#pragma unroll
-    for (int v = 0; v < NV; v++) sh[warp][2 + v] = p.sum[v];
-  }
-  __syncthreads();
-  if (threadIdx.x < NPART) {
-    const int nw = blockDim.x >> 5;
-    double acc = sh[0][threadIdx.x];
-    for (int w = 1; w < nw; w++) {
-      double x = sh[w][threadIdx.x];
-      acc = threadIdx.x < 2 ? fmax(acc, x) : acc + x;
-    }
-    part_b[threadIdx.x] = threadIdx.x < 2 + NV ? acc : 0.0;
-  }
-  __syncthreads();
-}
-
-template <class T>
-__device__ __forceinline__ void accumulate_cell(const DevMesh& M, const T* u, double gamma,
-                                                const double* dx, Partial& p) {
-  T w[NV];
-  cons2prim(gamma, u, w);
-  double s = 0.0;
-  for (int d = 0; d < M.ndim; d++) {
-    T spd = fabs(w[1 + d]) + fast_speed((T)gamma, w, d);
-    s += (double)spd / dx[d];
-    p.chm = fmax(p.chm, (double)spd);
-  }
-  p.smax = fmax(p.smax, s);
-#pragma unroll
-  for (int v = 0; v < NV; v++) p.sum[v] += (double)u[v];
-}
-
 // ------------------------------------------------------------------ k_update
 
 template <class T>
-__global__ void __launch_bounds__(256) k_update(DevMesh M, const T* __restrict__ U0,
+__global__ void __launch_bounds__(256) k_update(DevMesh M, const T* U0,
                                                 const T* Uk, T* out, const T* __restrict__ F0,
                                                 const T* __restrict__ F1,
                                                 const T* __restrict__ F2, StageParams sp) {
@@ -350,6 +291,7 @@ StageParams make_stage_params(const amrvac_state* s, int k, int epilogue) {
   sp.limiter = s->cfg.limiter;
   sp.glm = s->cfg.glm;
   sp.epilogue = epilogue;
+  sp.pressure_ff = s->cfg.precision == AMRVAC_FP32_BULK && s->cfg.pressure == AMRVAC_PRESSURE_FF;
   return sp;
 }
 

@@ -29,6 +29,10 @@ struct amrvac_state {
   // fused-path work list: blocks grouped for the persistent kernel
   int* d_work = nullptr;
   int nwork = 0;
+  // fused path: per-CTA ghost slabs of level-change faces (2*ndim faces x 2
+  // layers x 16 x 16 cells x 9 vars per CTA)
+  void* slab = nullptr;
+  int slab_ctas = 0;
   // host copies
   std::vector<int32_t> meta;
   std::vector<amrvac_instance_desc> inst;

@@ -347,7 +347,7 @@ def solenoidal_velocity(n: int, seed: int, kmin: int = 1, kmax: int = 16) -> np.
     k2 = np.where(kk > 0, kk * kk, 1.0)
     dot = (kvec * vh).sum(0)
     vh = vh - kvec * dot / k2
-    v = np.stack([np.fft.irfftn(vh[c], s=(n, n, n)) for c in range(3)])
+    v = np.stack([np.fft.irfftn(vh[c], s=(n, n, n), axes=(0, 1, 2)) for c in range(3)])
     rms = math.sqrt(float((v * v).sum(0).mean()))
     return v / rms
 

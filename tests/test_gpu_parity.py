@@ -9,6 +9,10 @@ Tolerances (from the FP64 / FP32 arithmetic):
     and FMA orders grows through the limiters' nonlinearity).
   * FP32-bulk path, one stage: relative L1 <= 1e-5 on smooth flows and <= 1e-3
     on shocked flows, against the FP64 oracle fed the same (float-rounded) state.
+  * psi is measured in absolute terms against its natural scale c_h |B| (psi
+    carries the units of c_h B): psi is generated from the discrete div B, a
+    near-cancellation of face differences, and is ~0 on divergence-free data,
+    so a norm relative to psi itself is meaningless there.
 """
 import math
 
@@ -33,28 +37,37 @@ def amr():
     return amrvac
 
 
-def _linf_by_var(got, ref):
+def _bmag(ref):
+    return np.sqrt(ref[5] ** 2 + ref[6] ** 2 + ref[7] ** 2)
+
+
+def _linf_by_var(got, ref, ch=None):
     out = []
     scale_all = np.abs(ref).max()
     for v in range(9):
         m = np.abs(ref[v]).max()
+        if v == 8 and ch is not None:
+            m = max(m, float(np.max(ch)) * _bmag(ref).max())
         d = np.abs(got[v] - ref[v]).max()
         out.append(d / m if m > 0 else d / scale_all)
     return np.array(out)
 
 
-def _l1_by_var(got, ref):
+def _l1_by_var(got, ref, ch=None):
     out = []
     scale_all = np.abs(ref).mean()
     for v in range(9):
         s = np.abs(ref[v]).sum()
+        if v == 8 and ch is not None:
+            s = max(s, float(np.max(ch)) * _bmag(ref).sum())
         d = np.abs(got[v] - ref[v]).sum()
         out.append(d / s if s > 1e-12 * scale_all * ref[v].size else d / (scale_all * ref[v].size))
     return np.array(out)
 
 
-def _stage_parity(amr, orc, W, kernel, stages=None, tol=1e-12, blocks=None, threads=8):
-    S = amr.State.from_workload(W, kernel=kernel)
+def _stage_parity(amr, orc, W, kernel, stages=None, tol=1e-12, blocks=None, threads=8,
+                  pressure="fp64"):
+    S = amr.State.from_workload(W, kernel=kernel, pressure=pressure)
     m = orc.mesh_for(W, threads)
     U = W.U.astype(np.float32).astype(np.float64) if W.cfg.precision == "fp32" else W.U
     dt, ch = m.cfl(U)
@@ -84,9 +97,9 @@ def _stage_parity(amr, orc, W, kernel, stages=None, tol=1e-12, blocks=None, thre
             got = got[:, blocks]
             ref = ref[:, blocks]
         if W.cfg.precision == "fp32":
-            e = _l1_by_var(got, ref)
+            e = _l1_by_var(got, ref, ch)
         else:
-            e = _linf_by_var(got, ref)
+            e = _linf_by_var(got, ref, ch)
         worst.append(e.max())
         assert e.max() <= tol, (W.name, kernel, k, e)
     S.close()
@@ -250,6 +263,7 @@ def test_small_values_latched(amr, orc):
     assert d["status"] == 4 and d["error"][0] == 4
     S.clear_error()
     S.set_conserved(W.U)
+    S.set_dt(1e-3, 1.0)  # a new U^n invalidates the time step
     S.stage(0)
     assert S.diag()["status"] == 0
     S.close()
@@ -275,28 +289,36 @@ def test_instances_advance_independently(amr, orc):
 # FP32-bulk against the FP64 oracle
 # ----------------------------------------------------------------------------
 
+PRESSURES = ["fp64", "ff"]
+
+
+@pytest.mark.parametrize("pressure", PRESSURES)
 @pytest.mark.parametrize("kernel", KERNELS)
-def test_fp32_smooth_stage(amr, orc, kernel):
+def test_fp32_smooth_stage(amr, orc, kernel, pressure):
     W = wl.cp_alfven(64, precision="fp32")
-    _stage_parity(amr, orc, W, kernel, tol=1e-5)
+    _stage_parity(amr, orc, W, kernel, tol=1e-5, pressure=pressure)
     W = wl.c5_instances(count=6, nmin=32, nmax=96, precision="fp32")
-    _stage_parity(amr, orc, W, kernel, tol=1e-5)
+    _stage_parity(amr, orc, W, kernel, tol=1e-5, pressure=pressure)
 
 
+@pytest.mark.parametrize("pressure", PRESSURES)
 @pytest.mark.parametrize("kernel", KERNELS)
-def test_fp32_shocked_stage(amr, orc, kernel):
+def test_fp32_shocked_stage(amr, orc, kernel, pressure):
     W = wl.c4_blast_amr(base=4, levels=3, bnx=16 if kernel == "auto" else 4,
                         shell=(0.2, 0.26), precision="fp32")
-    _stage_parity(amr, orc, W, kernel, tol=1e-3)
+    _stage_parity(amr, orc, W, kernel, tol=1e-3, pressure=pressure)
     W = wl.c3_turbulence(n=32, bnx=16, precision="fp32")
-    _stage_parity(amr, orc, W, kernel, tol=1e-5)
+    _stage_parity(amr, orc, W, kernel, tol=1e-5, pressure=pressure)
 
 
-def test_fp32_low_beta_pressure_recovery(amr, orc):
-    # beta = 0.01: e is dominated by B^2/2; the pressure after a stage must stay
-    # within the float storage error of the FP64 oracle
-    W = wl.c3_turbulence(n=32, bnx=16, precision="fp32", beta=0.01)
-    S = amr.State.from_workload(W, kernel="plain")
+@pytest.mark.parametrize("pressure", PRESSURES)
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("beta", [0.01, 1e-4])
+def test_fp32_low_beta_pressure_recovery(amr, orc, kernel, pressure, beta):
+    # low beta: e is dominated by B^2/2; the pressure after a stage must stay
+    # within the float storage error of the FP64 oracle (which grows as 1/beta)
+    W = wl.c3_turbulence(n=32, bnx=16, precision="fp32", beta=beta)
+    S = amr.State.from_workload(W, kernel=kernel, pressure=pressure)
     U = W.U.astype(np.float32).astype(np.float64)
     S.set_conserved(U.astype(np.float32))
     m = orc.mesh_for(W, 8)
@@ -309,7 +331,7 @@ def test_fp32_low_beta_pressure_recovery(amr, orc):
     p = lambda X: (g - 1) * (X[4] - 0.5 * (X[1] ** 2 + X[2] ** 2 + X[3] ** 2) / X[0]
                              - 0.5 * (X[5] ** 2 + X[6] ** 2 + X[7] ** 2))
     rel = np.abs(p(got) - p(ref)).mean() / np.abs(p(ref)).mean()
-    assert rel < 2e-4, rel
+    assert rel < 2e-6 / beta, rel
     S.close()
 
 
