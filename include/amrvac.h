@@ -50,6 +50,7 @@ extern "C" {
 
 #define AMRVAC_NVAR 9
 #define AMRVAC_MAX_LEVELS 16
+#define AMRVAC_NOALLOC_MAX_BLOCKS 65536
 
 typedef enum {
   AMRVAC_OK = 0,
@@ -214,6 +215,31 @@ amrvac_status amrvac_step(amrvac_state* s, int32_t nsteps);
  */
 amrvac_status amrvac_get_diag(amrvac_state* s, double* h_t, double* h_dt, double* h_ch,
                               double* h_sums, amrvac_error_info* err);
+
+/*
+ * CFL time step of a uniform mesh for callers that cannot allocate device
+ * memory (no workspace, no state).  The paper has no counterpart: this is a
+ * service entry point of this library.  Callers inside a host framework that
+ * owns every device allocation, or in code paths where cudaMalloc is not
+ * allowed, pass only their own input and output buffers.
+ *   cfg, inst: one instance covered by its level-0 blocks only (nblocks =
+ *     base_blocks product, blocks in any order); cfg->precision selects the
+ *     element type of d_U (double or float), cfg->courant the CFL number.
+ *   d_U: device [var][block][cell] conserved state; t: current time; the step
+ *     is clipped to inst->t_end - t.
+ *   d_out: device double[2] receiving {dt, c_h}, computed exactly as
+ *     amrvac_cfl_dt computes them.
+ *   cuda_stream: cudaStream_t of the two kernels (asynchronous).
+ * Scratch: a file-scope device array of AMRVAC_NOALLOC_MAX_BLOCKS x 2 doubles
+ * (1 MiB) that every device loading the library holds until exit.  More blocks
+ * than AMRVAC_NOALLOC_MAX_BLOCKS: AMRVAC_E_INVALID.  The first call on a device
+ * looks up the array's device address with cudaGetSymbolAddress (make it
+ * before any stream capture).  Calls share the array: calls overlapping on
+ * the GPU race.  No allocation of any kind is made.
+ */
+amrvac_status amrvac_cfl_dt_noalloc(const amrvac_config* cfg, const amrvac_instance_desc* inst,
+                                    int32_t nblocks, const void* d_U, double t, double* d_out,
+                                    void* cuda_stream);
 
 /* Clears the latched device error. */
 amrvac_status amrvac_clear_error(amrvac_state* s);

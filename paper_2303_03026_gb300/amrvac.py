@@ -27,7 +27,7 @@ SYMBOLS = ("amrvac_workspace_bytes", "amrvac_state_create", "amrvac_state_destro
            "amrvac_set_conserved", "amrvac_get_conserved", "amrvac_set_time",
            "amrvac_fill_ghosts", "amrvac_cfl_dt", "amrvac_set_dt", "amrvac_stage",
            "amrvac_step", "amrvac_get_diag", "amrvac_clear_error", "amrvac_launch_count",
-           "amrvac_error_string")
+           "amrvac_error_string", "amrvac_cfl_dt_noalloc")
 
 
 class AmrvacError(RuntimeError):
@@ -88,6 +88,8 @@ def load(path: str = LIB_PATH):
     L.amrvac_launch_count.restype = C.c_int64
     L.amrvac_error_string.argtypes = [i32]
     L.amrvac_error_string.restype = C.c_char_p
+    L.amrvac_cfl_dt_noalloc.argtypes = [C.POINTER(Config), C.POINTER(InstanceDesc), i32, vp, dbl,
+                                        vp, vp]
     _lib = L
     return L
 
@@ -292,3 +294,21 @@ class State:
     @property
     def launches(self) -> int:
         return int(load().amrvac_launch_count(self._h))
+
+
+def cfl_dt_noalloc(cfg, instance, U, out, t=0.0, stream=None):
+    """CFL time step of a uniform single-instance state without a workspace.
+
+    For callers that cannot allocate device memory: ``U`` is the caller's
+    device tensor [9, nblocks, ncell] (float64 or float32 matching
+    ``cfg.precision``), ``out`` a caller-provided device float64 tensor of 2
+    elements that receives (dt, c_h).  The library uses a fixed 1 MiB device
+    array (at most AMRVAC_NOALLOC_MAX_BLOCKS = 65536 blocks) and allocates
+    nothing.  Asynchronous on ``stream`` (default: torch's current stream)."""
+    import torch
+    c = make_config(cfg)
+    inst = make_instances([instance])
+    s = stream if stream is not None else torch.cuda.current_stream(U.device)
+    _check(load().amrvac_cfl_dt_noalloc(C.byref(c), inst, int(U.shape[1]), U.data_ptr(),
+                                        float(t), out.data_ptr(), s.cuda_stream),
+           "amrvac_cfl_dt_noalloc")

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libamrvac_gb300.so")
-SOURCES = ["api.cu", "plain.cu", "fused.cu"]
+SOURCES = ["api.cu", "plain.cu", "fused.cu", "noalloc.cu"]
 # the fused kernel source is compiled once per (precision, dimension, limiter)
 FUSED_GROUPS = [(t, d, l) for t in ("float", "double") for d in (2, 3) for l in (0, 1, 2)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
