@@ -1,10 +1,11 @@
 // Fused persistent stage kernel for 16x16 (2D) and 16x16x16 (3D) blocks.
 //
-// One CTA of 256 threads owns one block at a time and loops over the work
-// list (grid = resident CTAs).  Thread (x, y) owns a column of the block.
+// One CTA of 272 threads owns one block at a time and loops over the work
+// list (grid = resident CTAs).  Thread (x, y) < 256 owns a column of the block;
+// 16 helper threads take the +x/+y block-boundary faces and the halo cells.
 //   3D: march over z with a ring of 5 primitive planes in shared memory, each
 //       with its 2-cell x/y halo (planes z-2 .. z+2).  Per plane:
-//         load plane z+2 (own column; 128 threads also load the x/y halo):
+//         load plane z+2 (own column; the helper threads load the x/y halo):
 //           ghost fill (same-level read, outflow clamp, or AMR lookup) and
 //           conserved -> primitive (double-precision pressure for FP32 bulk)
 //         sync; x- and y-face fluxes of plane z into shared memory (the 32
@@ -26,6 +27,11 @@
 namespace amrvac {
 
 constexpr int FB = 16;          // block edge handled by the fused kernel
+// threads per CTA: 256 column owners (x- and y-face of their cell, z-face of
+// their column, their cell's update) and 16 helpers (the 32 faces on the +x/+y
+// block boundary and the 128 x/y halo cells of each plane), so that every warp
+// carries about three flux evaluations per plane
+constexpr int FT = FB * FB + FB;
 constexpr int FPW = FB + 2 * NG;  // padded plane width (row stride 20 floats)
 constexpr int FXW = 20;           // row stride of the face-flux arrays
 
@@ -43,6 +49,52 @@ template <class T, int DIM> struct FusedSmem {
   double red[8][NPART];
   double damp;
 };
+
+// asynchronous global -> shared copy of one element (Ampere+ cp.async; the
+// issuing thread waits with cp_async_wait_all before reading the data)
+template <class T>
+__device__ __forceinline__ void cp_async_elem(T* smem_dst, const T* gmem_src) {
+  const unsigned dst = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(dst), "l"(gmem_src),
+               "n"(sizeof(T)));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+// deterministic CTA reduction of the owners' partials (warps 0..7; the partial
+// helper warp only joins the barriers); thread 0..NPART-1 store part_b
+__device__ __forceinline__ void cta_reduce_store(double (*red)[NPART], Partial& p, bool owner,
+                                                 double* part_b) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (owner) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      p.smax = fmax(p.smax, __shfl_xor_sync(0xffffffffu, p.smax, o));
+      p.chm = fmax(p.chm, __shfl_xor_sync(0xffffffffu, p.chm, o));
+#pragma unroll
+      for (int v = 0; v < NV; v++) p.sum[v] += __shfl_xor_sync(0xffffffffu, p.sum[v], o);
+    }
+    if (lane == 0) {
+      red[warp][0] = p.smax;
+      red[warp][1] = p.chm;
+#pragma unroll
+      for (int v = 0; v < NV; v++) red[warp][2 + v] = p.sum[v];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < NPART) {
+    double acc = red[0][threadIdx.x];
+    for (int w = 1; w < 8; w++) {
+      double x = red[w][threadIdx.x];
+      acc = threadIdx.x < 2 ? fmax(acc, x) : acc + x;
+    }
+    part_b[threadIdx.x] = threadIdx.x < 2 + NV ? acc : 0.0;
+  }
+  __syncthreads();
+}
 
 template <class T> __device__ __forceinline__ T over_dx(T a, T dx, T idx);
 template <> __device__ __forceinline__ double over_dx(double a, double dx, double) { return a / dx; }
@@ -70,7 +122,7 @@ __device__ __forceinline__ void stencil_flux(Acc S, int glm, T g, T ch, T* f) {
 }
 
 template <class T, int DIM, int LIM, int FLUX>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
     k_fused(DevMesh M, const T* U0, const T* __restrict__ Uk, T* out,
             const int* __restrict__ work, int nwork, T* __restrict__ slab_all, StageParams sp) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -86,17 +138,20 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
   constexpr int SLAB_FACE = NV * 2 * FB * NT2;    // one face: [v][layer][t2][t1]
   T* __restrict__ slab = slab_all + (size_t)blockIdx.x * (2 * DIM) * SLAB_FACE;
 
-  // halo cell of this thread (threads 0..127): x-halo then y-halo
-  int hx = 0, hy = 0;
-  if (tid < 64) {
-    int side = tid >> 5, r = tid & 31;
-    hy = r >> 1;
-    hx = side ? FB + (r & 1) : -2 + (r & 1);
-  } else if (tid < 128) {
-    int u = tid - 64, side = u >> 5, r = u & 31;
-    hx = r & 15;
-    hy = side ? FB + (r >> 4) : -2 + (r >> 4);
-  }
+  const bool owner = tid < FB * FB;
+  const int hr = tid - FB * FB;  // helper index 0..15
+  // halo cell h (0..127) of a plane: x-halo (h < 64) then y-halo
+  auto halo_xy = [](int h, int& hx, int& hy) {
+    if (h < 64) {
+      int side = h >> 5, r = h & 31;
+      hy = r >> 1;
+      hx = side ? FB + (r & 1) : -2 + (r & 1);
+    } else {
+      int u = h - 64, side = u >> 5, r = u & 31;
+      hx = r & 15;
+      hy = side ? FB + (r >> 4) : -2 + (r >> 4);
+    }
+  };
 
   for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
     const int b = work[wi];
@@ -113,7 +168,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
       Partial p;
       partial_zero(p);
       // finished instance: copied through unchanged
-      for (int c = tid; c < ncell; c += 256) {
+      for (int c = tid; owner && c < ncell; c += FB * FB) {
         T u[NV];
 #pragma unroll
         for (int v = 0; v < NV; v++) {
@@ -123,7 +178,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
         }
         if (sp.epilogue) accumulate_cell(M, u, gammad, dxd, p);
       }
-      if (sp.epilogue) block_reduce_red(S.red, p, M.part + (size_t)b * NPART);
+      if (sp.epilogue) cta_reduce_store(S.red, p, owner, M.part + (size_t)b * NPART);
       continue;
     }
 
@@ -173,7 +228,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
         T* sf = slab + f * SLAB_FACE;
         if (code == MAP_REFINED) {
           // restriction: mean of the finer children
-          for (int e = tid; e < 2 * FB * NT2; e += 256) {
+          for (int e = tid; e < 2 * FB * NT2; e += FT) {
             const int t1 = e % FB, t2 = (e / FB) % NT2, layer = e / (FB * NT2);
             int p[3];
             ghost_p(layer, t1, t2, p);
@@ -185,7 +240,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
         } else {
           // prolongation: value and minmod slopes once per coarse cell ...
           constexpr int NC2 = DIM == 3 ? FB / 2 : 1;
-          for (int e = tid; e < (FB / 2) * NC2 * DIM; e += 256) {
+          for (int e = tid; e < (FB / 2) * NC2 * DIM; e += FT) {
             const int dd = e % DIM, cc = e / DIM;
             const int ct1 = cc % (FB / 2), ct2 = cc / (FB / 2);
             int p[3];
@@ -208,7 +263,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
           }
           __syncthreads();
           // ... then every fine ghost: coarse value + sum_d (+-1/4) slope_d
-          for (int e = tid; e < 2 * FB * NT2; e += 256) {
+          for (int e = tid; e < 2 * FB * NT2; e += FT) {
             const int t1 = e % FB, t2 = (e / FB) % NT2, layer = e / (FB * NT2);
             int p[3];
             ghost_p(layer, t1, t2, p);
@@ -231,50 +286,103 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
       __syncthreads();
     }
 
-    // conserved value of block-local cell (i, j, k); at most one index outside
-    auto fetch = [&](int i, int j, int k, T* u) {
+    // location of the conserved values of block-local cell (i, j, k), at most
+    // one index outside: own block, same-level neighbour (wrapped index),
+    // outflow clamp (own block) or this CTA's ghost slab; vstride between vars
+    auto locate = [&](int i, int j, int k, const T*& ptr, size_t& vstride) {
       int f = -1, n = 0, t1 = 0, t2 = 0;
       if (i < 0 || i >= FB) { f = i < 0 ? 0 : 1; n = i; t1 = j; t2 = k; }
       else if (j < 0 || j >= FB) { f = j < 0 ? 2 : 3; n = j; t1 = i; t2 = k; }
       else if (DIM == 3 && (k < 0 || k >= FB)) { f = k < 0 ? 4 : 5; n = k; t1 = i; t2 = j; }
+      vstride = vs;
       if (f < 0) {
-        read_cell(M, Uk, vs, b, (k * FB + j) * FB + i, u);
+        ptr = Uk + (size_t)b * ncell + (k * FB + j) * FB + i;
         return;
       }
       const int code = nb[f];
       if (code == NBR_GENERAL) {
         const int layer = n < 0 ? n + 2 : n - FB;
-        const T* sf = slab + f * SLAB_FACE + (layer * NT2 + t2) * FB + t1;
-#pragma unroll
-        for (int v = 0; v < NV; v++) u[v] = sf[v * 2 * NT2 * FB];
+        ptr = slab + f * SLAB_FACE + (layer * NT2 + t2) * FB + t1;
+        vstride = 2 * NT2 * FB;
         return;
       }
-      // same-level neighbour (wrapped index) or outflow clamp (own block)
       const int nn = code >= 0 ? (n < 0 ? n + FB : n - FB) : (n < 0 ? 0 : FB - 1);
       const int src = code >= 0 ? code : b;
       int ii = i, jj = j, kk = k;
       if (f < 2) ii = nn;
       else if (f < 4) jj = nn;
       else kk = nn;
-      read_cell(M, Uk, vs, src, (kk * FB + jj) * FB + ii, u);
+      ptr = Uk + (size_t)src * ncell + (kk * FB + jj) * FB + ii;
     };
 
-    auto load_plane = [&](int pz) {
-      const int slot = ((pz % NSLOT) + NSLOT) % NSLOT;
+    auto to_prim = [&](T* cell, int which) {
+      // cell: the 9 values of one cell in a plane slot (stride FPW*FPW), in place
       T u[NV], w[NV];
-      fetch(x, y, DIM == 3 ? pz : 0, u);
+#pragma unroll
+      for (int v = 0; v < NV; v++) u[v] = cell[v * FPW * FPW];
       cons2prim(gammad, u, w, ff, gm1f);
       if (sp.check_small && (!(w[0] > rho_floor) || !(w[4] > p_floor)))
-        latch_error(M.err, AMRVAC_E_SMALL_VALUES, b, tid, 0);
+        latch_error(M.err, AMRVAC_E_SMALL_VALUES, b, tid, which);
 #pragma unroll
-      for (int v = 0; v < NV; v++) S.plane[slot][v][y + NG][x + NG] = w[v];
-      if (tid < 128 && pz >= 0 && pz < NZ) {
-        fetch(hx, hy, DIM == 3 ? pz : 0, u);
-        cons2prim(gammad, u, w, ff, gm1f);
-        if (sp.check_small && (!(w[0] > rho_floor) || !(w[4] > p_floor)))
-          latch_error(M.err, AMRVAC_E_SMALL_VALUES, b, tid, 1);
+      for (int v = 0; v < NV; v++) cell[v * FPW * FPW] = w[v];
+    };
+
+    // 2D: synchronous load + conversion of the single plane
+    auto load_plane = [&](int pz) {
+      const int slot = ((pz % NSLOT) + NSLOT) % NSLOT;
+      const T* ptr;
+      size_t st;
+      if (owner) {
+        locate(x, y, 0, ptr, st);
 #pragma unroll
-        for (int v = 0; v < NV; v++) S.plane[slot][v][hy + NG][hx + NG] = w[v];
+        for (int v = 0; v < NV; v++) S.plane[slot][v][y + NG][x + NG] = ptr[v * st];
+        to_prim(&S.plane[slot][0][y + NG][x + NG], 0);
+      } else {
+        for (int m = 0; m < 8; m++) {
+          int hx, hy;
+          halo_xy(hr + FB * m, hx, hy);
+          locate(hx, hy, 0, ptr, st);
+#pragma unroll
+          for (int v = 0; v < NV; v++) S.plane[slot][v][hy + NG][hx + NG] = ptr[v * st];
+          to_prim(&S.plane[slot][0][hy + NG][hx + NG], 1);
+        }
+      }
+    };
+
+    // 3D: asynchronous copy of plane pz's conserved values into its ring slot
+    // (own column; threads 0..127 also their halo cell of interior planes) ...
+    auto issue_plane = [&](int pz) {
+      const int slot = ((pz % NSLOT) + NSLOT) % NSLOT;
+      const T* ptr;
+      size_t st;
+      if (owner) {
+        locate(x, y, pz, ptr, st);
+#pragma unroll
+        for (int v = 0; v < NV; v++)
+          cp_async_elem(&S.plane[slot][v][y + NG][x + NG], ptr + v * st);
+      } else if (pz >= 0 && pz < NZ) {
+        for (int m = 0; m < 8; m++) {
+          int hx, hy;
+          halo_xy(hr + FB * m, hx, hy);
+          locate(hx, hy, pz, ptr, st);
+#pragma unroll
+          for (int v = 0; v < NV; v++)
+            cp_async_elem(&S.plane[slot][v][hy + NG][hx + NG], ptr + v * st);
+        }
+      }
+      cp_async_commit();
+    };
+    // ... and, once this thread's copies have landed, their in-place conversion
+    auto convert_plane = [&](int pz) {
+      const int slot = ((pz % NSLOT) + NSLOT) % NSLOT;
+      if (owner) {
+        to_prim(&S.plane[slot][0][y + NG][x + NG], 0);
+      } else if (pz >= 0 && pz < NZ) {
+        for (int m = 0; m < 8; m++) {
+          int hx, hy;
+          halo_xy(hr + FB * m, hx, hy);
+          to_prim(&S.plane[slot][0][hy + NG][hx + NG], 1);
+        }
       }
     };
 
@@ -291,11 +399,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
 
     T fzp[NV];
     if (DIM == 3) {
-      load_plane(-2);
-      load_plane(-1);
-      load_plane(0);
-      load_plane(1);
-      zflux(0, fzp);  // own column only: no barrier needed
+      for (int pz = -2; pz <= 1; pz++) issue_plane(pz);
+      cp_async_wait_all();
+      for (int pz = -2; pz <= 1; pz++) convert_plane(pz);
+      issue_plane(2);
+      if (owner) zflux(0, fzp);  // own column only: no barrier needed
     } else {
       load_plane(0);
     }
@@ -307,37 +415,38 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
 
 #pragma unroll 1
     for (int z = 0; z < NZ; z++) {
-      if (DIM == 3) load_plane(z + 2);
+      if (DIM == 3) {
+        // this thread's copies of plane z+2 (issued one iteration ago) have
+        // landed; prefetch plane z+3 into the slot of plane z-2, which no thread
+        // reads any more.  Plane z+2 is converted after the x/y faces below.
+        cp_async_wait_all();
+        if (z + 3 <= NZ + 1) issue_plane(z + 3);
+      }
       __syncthreads();
       const int sl = z % NSLOT;
       {
+        // owners: the x and y faces on the low side of their cell; helpers: the
+        // x face at the +x block boundary of row hr and the y face at the +y
+        // boundary of column hr
+        const int fxr = owner ? y : hr, fxc = owner ? x : FB;
+        const int fyr = owner ? y : FB, fyc = owner ? x : hr;
         T f[NV];
-        auto ax = [&](int v, int t) -> T { return S.plane[sl][v][y + NG][x + t]; };
+        auto ax = [&](int v, int t) -> T { return S.plane[sl][v][fxr + NG][fxc + t]; };
         stencil_flux<T, 0, LIM, FLUX>(ax, sp.glm, g, ch, f);
 #pragma unroll
-        for (int v = 0; v < NV; v++) S.fx[v][y][x] = f[v];
-        auto ay = [&](int v, int t) -> T { return S.plane[sl][v][y + t][x + NG]; };
+        for (int v = 0; v < NV; v++) S.fx[v][fxr][fxc] = f[v];
+        auto ay = [&](int v, int t) -> T { return S.plane[sl][v][fyr + t][fyc + NG]; };
         stencil_flux<T, 1, LIM, FLUX>(ay, sp.glm, g, ch, f);
 #pragma unroll
-        for (int v = 0; v < NV; v++) S.fy[v][y][x] = f[v];
-        // faces on the +x block boundary (one rotating warp, lanes 0..15) and on
-        // the +y boundary (another warp): 32 extra faces per plane
-        if (warp == (z & 7) && lane < FB) {
-          auto ae = [&](int v, int t) -> T { return S.plane[sl][v][lane + NG][FB + t]; };
-          stencil_flux<T, 0, LIM, FLUX>(ae, sp.glm, g, ch, f);
-#pragma unroll
-          for (int v = 0; v < NV; v++) S.fx[v][lane][FB] = f[v];
-        }
-        if (warp == ((z + 4) & 7) && lane < FB) {
-          auto ae = [&](int v, int t) -> T { return S.plane[sl][v][FB + t][lane + NG]; };
-          stencil_flux<T, 1, LIM, FLUX>(ae, sp.glm, g, ch, f);
-#pragma unroll
-          for (int v = 0; v < NV; v++) S.fy[v][FB][lane] = f[v];
-        }
+        for (int v = 0; v < NV; v++) S.fy[v][fyr][fyc] = f[v];
       }
+      // plane z+2 -> primitives (owners: own column, needed by the z face below;
+      // helpers: the halo, needed two planes later), balancing the two phases
+      if (DIM == 3) convert_plane(z + 2);
       T fz[NV];
-      if (DIM == 3) zflux(z + 1, fz);
+      if (DIM == 3 && owner) zflux(z + 1, fz);
       __syncthreads();
+      if (!owner) continue;  // helpers: no cell of their own
 
       const int c = (z * FB + y) * FB + x;
       T un[NV];
@@ -372,7 +481,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
           const float idd[3] = {(float)(1.0 / dxd[0]), (float)(1.0 / dxd[1]),
                                 (float)(1.0 / dxd[2])};
 #pragma unroll 1
-          for (int z = 0; z < NZ; z++) {
+          for (int z = 0; owner && z < NZ; z++) {
             const int c = (z * FB + y) * FB + x;
             float u[NV], w[NV];
 #pragma unroll
@@ -397,19 +506,19 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
           p.chm = cm;
 #pragma unroll
           for (int v = 0; v < NV; v++) p.sum[v] = (double)hi[v] + (double)lo[v];
-          block_reduce_red(S.red, p, M.part + (size_t)b * NPART);
+          cta_reduce_store(S.red, p, owner, M.part + (size_t)b * NPART);
           continue;
         }
       }
 #pragma unroll 1
-      for (int z = 0; z < NZ; z++) {
+      for (int z = 0; owner && z < NZ; z++) {
         const int c = (z * FB + y) * FB + x;
         T u[NV];
 #pragma unroll
         for (int v = 0; v < NV; v++) u[v] = out[(size_t)v * vs + (size_t)b * ncell + c];
         accumulate_cell(M, u, gammad, dxd, p);  // FP64 sums
       }
-      block_reduce_red(S.red, p, M.part + (size_t)b * NPART);
+      cta_reduce_store(S.red, p, owner, M.part + (size_t)b * NPART);
     }
   }
 }
@@ -428,12 +537,12 @@ static int launch_one(amrvac_state* s, const T* U0, const T* Uk, T* out, StagePa
     int dev = 0, nsm = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, FT, smem);
     configured_grid = nsm * (per_sm > 0 ? per_sm : 1);
   }
   int grid = s->nwork < configured_grid ? s->nwork : configured_grid;
   if (grid > s->slab_ctas) grid = s->slab_ctas;
-  kern<<<grid, 256, smem, s->stream>>>(s->mesh, U0, Uk, out, s->d_work, s->nwork, (T*)s->slab,
+  kern<<<grid, FT, smem, s->stream>>>(s->mesh, U0, Uk, out, s->d_work, s->nwork, (T*)s->slab,
                                        sp);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
