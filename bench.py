@@ -45,6 +45,12 @@ def parse():
     p.add_argument("--size", type=int, default=0,
                    help="workload size (c4: level-0 blocks per dim; c3/c2: cells per dim; "
                         "c5: instance count); 0 = the full configuration")
+    p.add_argument("--flux", default=None, choices=["hll", "hlld"],
+                   help="override the workload's flux scheme")
+    p.add_argument("--limiter", default=None, choices=["minmod", "vanleer", "koren"],
+                   help="override the workload's limiter")
+    p.add_argument("--no-variants", action="store_true",
+                   help="skip the HLL and FP64-pressure variant timings")
     p.add_argument("--pressure", default="ff", choices=["ff", "fp64"],
                    help="FP32-bulk pressure recovery: float-float or double")
     p.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison leg")
@@ -152,26 +158,27 @@ def dist_env():
 
 def cpu_baseline(W, seconds_target=12.0, threads=None):
     """The FP64 oracle as it stands, timed on the host cores on a bounded sample
-    of the workload's blocks: one full SSPRK3 step of ``nsample`` blocks."""
+    of the workload's blocks: one full SSPRK3 step of ``nsample`` blocks, the
+    sample sized from a small probe so that it takes about seconds_target."""
     import oracle
     threads = threads or os.cpu_count() or 1
     m = oracle.mesh_for(W, threads)
     U = W.U.astype(np.float64)
     dt, ch = m.cfl(U)
     rng = np.random.Generator(np.random.PCG64(11))
-    nsample = min(W.nblocks, 16)
-    while True:
+    A = np.zeros_like(U)
+    B = np.zeros_like(U)
+    nsample = min(W.nblocks, max(16, threads))
+    for final in (False, True):
         blocks = np.sort(rng.choice(W.nblocks, nsample, replace=False)).astype(np.int32)
-        A = np.zeros_like(U)
-        B = np.zeros_like(U)
         t0 = time.perf_counter()
         m.stage(0, dt, ch, U, U, blocks=blocks, out=A)
         m.stage(1, dt, ch, U, A, blocks=blocks, out=B)
         m.stage(2, dt, ch, U, B, blocks=blocks, out=A)
         el = time.perf_counter() - t0
-        if el > seconds_target / 4 or nsample >= W.nblocks:
+        if final or nsample >= W.nblocks:
             break
-        nsample = min(W.nblocks, int(nsample * max(2.0, (seconds_target / 4) / max(el, 1e-3))))
+        nsample = min(W.nblocks, max(nsample, int(nsample * seconds_target / max(el, 1e-3))))
     cells = nsample * W.ncell
     return {"value": cells / el, "unit": "cell-updates/s", "cores": threads, "kind": "oracle",
             "sample": "%d random blocks (%d cells) of the workload, one full SSPRK3 step "
@@ -221,6 +228,44 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def traffic_from_profile(workload, size, kernel_digest):
+    """DRAM bytes per cell-update of the fused stage kernel from the committed
+    ncu summary, when it was taken on the current build (else None)."""
+    path = os.path.join(ROOT, "profiles", "k_fused_dram_traffic.txt")
+    try:
+        rows = [r.split() for r in open(path) if r.strip() and not r.startswith("#")]
+    except OSError:
+        return None
+    for r in rows:
+        kv = dict(x.split("=", 1) for x in r if "=" in x)
+        if kv.get("workload") == workload and kv.get("build") == kernel_digest:
+            return float(kv["dram_bytes_per_cell_step"])
+    return None
+
+
+def max_over_ranks(value, device):
+    """Maximum of a float over all ranks (the slowest rank's time); identity
+    without an initialised process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def time_steps(torch, S, k):
+    """ms per full step over k graph-launched steps (events on the state's stream)."""
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    S.stream.synchronize()
+    e0.record(S.stream)
+    S.step(k)
+    e1.record(S.stream)
+    S.stream.synchronize()
+    return e0.elapsed_time(e1) / k
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -235,9 +280,17 @@ def main():
     import __graft_entry__
     __graft_entry__.build()
     from paper_2303_03026_gb300 import amrvac
+    from paper_2303_03026_gb300 import build as libbuild
 
     W, desc = make_workload(args.workload, "fp32", args.size)
+    if args.flux:
+        W.cfg.flux = args.flux
+    if args.limiter:
+        W.cfg.limiter = args.limiter
+    desc["scheme"] = "%s + %s + %s, SSPRK3" % (W.cfg.flux.upper(), W.cfg.limiter,
+                                               "glm" if W.cfg.glm else "no glm")
     cells = W.interior_cells()
+    state_bytes = 9 * 4 * cells
     S = amrvac.State.from_workload(W, device=dev, kernel=args.kernel, pressure=args.pressure)
     U32 = torch.from_numpy(W.U.astype(np.float32)).to(dev)
     S.set_conserved(U32)
@@ -256,7 +309,7 @@ def main():
     if d["status"] != 0:
         raise RuntimeError("device error during warm-up: %s" % (d["error"],))
 
-    # timed region: K full steps, device-resident inputs (larger than L2)
+    # timed region: K full steps, device-resident inputs
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     n0 = S.launches
     barrier()
@@ -266,12 +319,7 @@ def main():
         ev1.record(stream)
         barrier()
     launches = S.launches - n0
-    ms = ev0.elapsed_time(ev1)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dev)
     ms_step = ms / args.steps
     value = cells * ws * args.steps / (ms / 1e3)
     d = S.diag()
@@ -280,11 +328,10 @@ def main():
 
     # per-stage kernel timing on the launching stream for the roofline
     stage_ms = []
-    nst = 3
     for rep in range(3):
         S.cfl_dt()
         row = []
-        for k in range(nst):
+        for k in range(3):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             S.stage(k)
@@ -297,13 +344,70 @@ def main():
     alg_bytes = [p * 9 * 4 * cells for p in passes]
     hbm, src = peaks()
     achieved = sum(alg_bytes) / (sum(stage_ms) / 1e3) / 1e9
+    fused = args.kernel != "plain" and (W.cfg.block_nx[0] == 16)
+    digest = libbuild._digest()[:16]
+    tr = traffic_from_profile(args.workload + (str(args.size) if args.size else ""), args.size,
+                              digest) if fused else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None, "peak_source": src,
-                "kernel": "stage (fused)" if S._c.kernel != 1 and args.kernel != "plain" else
-                "stage (plain: prim+flux+update)",
+                "frac": achieved / hbm,
+                "traffic": tr * cells / 3.0 if tr is not None else None,
+                "traffic_unit": "DRAM bytes per stage launch (ncu, mean of the 3 stages)",
+                "peak_source": src,
+                "kernel": "k_fused (one persistent launch per SSPRK stage)" if fused else
+                "plain per-block kernels (prim + flux x ndim + update) per stage",
                 "stage_ms": [float(x) for x in stage_ms],
                 "alg_bytes_per_cell_step": 288,
+                "alg_bytes_per_launch": [int(b) for b in alg_bytes],
                 "frac_of_nominal_7900": achieved / NOMINAL_HBM_GBS}
+
+    # variants on the same workload: HLL flux, FP64 pressure recovery
+    variants = {}
+    if not args.no_variants and fused:
+        for name, kw in (("hll_vanleer", {"flux": "hll"}), ("fp64_pressure", {"pressure": "fp64"})):
+            Wv, _ = W, None
+            old_flux = W.cfg.flux
+            if "flux" in kw:
+                W.cfg.flux = kw["flux"]
+            Sv = amrvac.State.from_workload(W, device=dev, kernel=args.kernel,
+                                            pressure=kw.get("pressure", args.pressure))
+            W.cfg.flux = old_flux
+            Sv.set_conserved(U32)
+            Sv.step(2)
+            msv = time_steps(torch, Sv, max(3, min(args.steps, 10)))
+            variants[name] = {"value": cells * ws / (msv / 1e3), "ms_per_step": msv,
+                              "frac": 288 * cells / (msv / 1e3) / 1e9 / hbm}
+            Sv.close()
+
+    # C5 batching: the same instances advanced one at a time
+    one_at_a_time = None
+    if args.workload == "c5" and not args.no_variants:
+        import paper_2303_03026_gb300.workloads as wlm
+        states = []
+        off = 0
+        for q, inst in enumerate(W.instances):
+            nb = int((W.block_meta[:, 0] == q).sum())
+            meta = W.block_meta[off:off + nb].copy()
+            meta[:, 0] = 0
+            Sq = amrvac.State(W.cfg, [inst], meta, device=dev, kernel=args.kernel,
+                              pressure=args.pressure, stream=stream)
+            Sq.set_conserved(U32[:, off:off + nb].contiguous())
+            Sq.step(1)
+            states.append(Sq)
+            off += nb
+        stream.synchronize()
+        kq = max(2, min(args.steps, 5))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(kq):
+            for Sq in states:
+                Sq.step(1)
+        e1.record(stream)
+        stream.synchronize()
+        msq = e0.elapsed_time(e1) / kq
+        one_at_a_time = {"value": cells / (msq / 1e3), "ms_per_step": msq,
+                         "batched_speedup": msq / ms_step, "instances": len(states)}
+        for Sq in states:
+            Sq.close()
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -330,19 +434,13 @@ def main():
     # plain FP64 per-block path on the same workload, and the FP32 error
     fp64 = None
     if not args.no_fp64:
-        W64 = W
+        import dataclasses
+        W64 = dataclasses.replace(W, cfg=dataclasses.replace(W.cfg, precision="fp64"))
         S64 = amrvac.State.from_workload(W64, device=dev, kernel="plain")
         U64 = torch.from_numpy(W.U.astype(np.float32).astype(np.float64)).to(dev)
         S64.set_conserved(U64)
         S64.step(2)
-        torch.cuda.synchronize(dev)
-        k64 = max(2, min(args.steps, 5))
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(S64.stream)
-        S64.step(k64)
-        e1.record(S64.stream)
-        torch.cuda.synchronize(dev)
-        ms64 = e0.elapsed_time(e1) / k64
+        ms64 = time_steps(torch, S64, max(2, min(args.steps, 5)))
         # accuracy at equal steps from the same state
         S.set_conserved(U32)
         S64.set_conserved(U64)
@@ -365,18 +463,24 @@ def main():
         cpu = cpu_baseline(W)
 
     if rank == 0:
+        l2 = ("inputs larger than L2 (%.2f GB per state register)" % (state_bytes / 1e9)
+              if state_bytes > 129e6 else
+              "inputs smaller than L2 (%.0f MB per register): not a roofline measurement"
+              % (state_bytes / 1e6))
         line = {"metric": "MHD cell-updates/s (FP32-bulk batched block-AMR)", "value": value,
                 "unit": "cell-updates/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
-                "config": dict(desc, cells=cells, l2="inputs larger than L2 (2.7 GB per buffer)",
+                "config": dict(desc, cells=cells, l2=l2,
                                precision="fp32 bulk; pressure recovery and per-thread sums in %s; "
                                          "fp64 dt and block/instance sums" %
                                          ("float-float" if args.pressure == "ff" else "fp64"),
-                               kernel=args.kernel, parallelism="replicas" if ws > 1 else "1 GPU"),
+                               kernel=args.kernel, build=digest,
+                               parallelism="replicas" if ws > 1 else "1 GPU"),
                 "clocks": clk.summary(), "gpu_launches": launches, "roofline": roofline,
-                "e2e": e2e, "fp64_plain": fp64, "cpu_baseline": cpu}
+                "e2e": e2e, "variants": variants or None, "one_at_a_time": one_at_a_time,
+                "fp64_plain": fp64, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     S.close()
     if ws > 1:

@@ -241,6 +241,47 @@ amrvac_status amrvac_cfl_dt_noalloc(const amrvac_config* cfg, const amrvac_insta
                                     int32_t nblocks, const void* d_U, double t, double* d_out,
                                     void* cuda_stream);
 
+/*
+ * Checkpoint / restart (Sect. 7.5: snapshots hold the conserved variables and
+ * are used to restart).  save synchronises and writes a raw binary file:
+ * header {magic "AMRVACGB", version 1, ndim, block_nx[3], nblocks, ninst,
+ * precision}, the block list int32 [nblocks][5], per instance {t, t_end, dt,
+ * c_h, dt_valid} and buffer 0 (U^n) in the state's precision.  load reads such
+ * a file into a state created with the same config and block list
+ * (AMRVAC_E_INVALID otherwise) and restores U^n and the clocks, so that the
+ * continued run repeats the uninterrupted one bit for bit.
+ */
+amrvac_status amrvac_state_save(amrvac_state* s, const char* path);
+amrvac_status amrvac_state_load(amrvac_state* s, const char* path);
+
+/*
+ * Launch shape of the fused stage kernel (its tile is the 16^d block):
+ * resident CTAs per SM (0 = as many as fit), work-list order (0 = Morton curve
+ * per instance, 1 = storage order) and block scheduling (0 = static, 1 =
+ * dynamic via a device counter).  None of them changes the arithmetic: results
+ * are bit-identical across tunings.  Setting a tuning drops the captured step
+ * graph.  Not part of the paper (a GB300 launch-shape choice).
+ */
+typedef struct {
+  int32_t ctas_per_sm;
+  int32_t order;
+  int32_t dynamic;
+  double ms_per_step;      /* measured by amrvac_autotune, else 0 */
+} amrvac_tuning;
+
+amrvac_status amrvac_set_tuning(amrvac_state* s, const amrvac_tuning* t);
+amrvac_status amrvac_get_tuning(amrvac_state* s, amrvac_tuning* t);
+
+/*
+ * Times every launch shape over trial_steps full steps on the state itself
+ * (U^n and the clocks are restored after each trial and at the end), keeps the
+ * fastest and returns it in *best.  With cache_path, a tuning stored there for
+ * the same (ndim, block size, precision, flux, limiter, pressure, block-count
+ * bucket) is applied without timing, and a new result is appended.
+ */
+amrvac_status amrvac_autotune(amrvac_state* s, int32_t trial_steps, const char* cache_path,
+                              amrvac_tuning* best);
+
 /* Clears the latched device error. */
 amrvac_status amrvac_clear_error(amrvac_state* s);
 

@@ -27,7 +27,8 @@ SYMBOLS = ("amrvac_workspace_bytes", "amrvac_state_create", "amrvac_state_destro
            "amrvac_set_conserved", "amrvac_get_conserved", "amrvac_set_time",
            "amrvac_fill_ghosts", "amrvac_cfl_dt", "amrvac_set_dt", "amrvac_stage",
            "amrvac_step", "amrvac_get_diag", "amrvac_clear_error", "amrvac_launch_count",
-           "amrvac_error_string", "amrvac_cfl_dt_noalloc")
+           "amrvac_error_string", "amrvac_cfl_dt_noalloc", "amrvac_state_save",
+           "amrvac_state_load", "amrvac_set_tuning", "amrvac_get_tuning", "amrvac_autotune")
 
 
 class AmrvacError(RuntimeError):
@@ -50,6 +51,15 @@ class InstanceDesc(C.Structure):
     _fields_ = [("xmin", C.c_double * 3), ("xmax", C.c_double * 3),
                 ("base_blocks", C.c_int32 * 3), ("gamma", C.c_double), ("t0", C.c_double),
                 ("t_end", C.c_double)]
+
+
+class Tuning(C.Structure):
+    _fields_ = [("ctas_per_sm", C.c_int32), ("order", C.c_int32), ("dynamic", C.c_int32),
+                ("ms_per_step", C.c_double)]
+
+    def as_dict(self):
+        return {"ctas_per_sm": self.ctas_per_sm, "order": ("morton", "storage")[self.order],
+                "dynamic": bool(self.dynamic), "ms_per_step": self.ms_per_step}
 
 
 class ErrorInfo(C.Structure):
@@ -88,6 +98,11 @@ def load(path: str = LIB_PATH):
     L.amrvac_launch_count.restype = C.c_int64
     L.amrvac_error_string.argtypes = [i32]
     L.amrvac_error_string.restype = C.c_char_p
+    L.amrvac_set_tuning.argtypes = [vp, C.POINTER(Tuning)]
+    L.amrvac_get_tuning.argtypes = [vp, C.POINTER(Tuning)]
+    L.amrvac_autotune.argtypes = [vp, i32, C.c_char_p, C.POINTER(Tuning)]
+    L.amrvac_state_save.argtypes = [vp, C.c_char_p]
+    L.amrvac_state_load.argtypes = [vp, C.c_char_p]
     L.amrvac_cfl_dt_noalloc.argtypes = [C.POINTER(Config), C.POINTER(InstanceDesc), i32, vp, dbl,
                                         vp, vp]
     _lib = L
@@ -287,6 +302,28 @@ class State:
             raise AmrvacError(st, "amrvac_get_diag")
         return {"t": t, "dt": dt, "ch": ch, "sums": sums, "status": st,
                 "error": (err.code, err.block, err.cell, err.var)}
+
+    def set_tuning(self, ctas_per_sm=0, order="morton", dynamic=False):
+        t = Tuning(int(ctas_per_sm), {"morton": 0, "storage": 1}[order], int(bool(dynamic)), 0.0)
+        _check(load().amrvac_set_tuning(self._h, C.byref(t)), "amrvac_set_tuning")
+
+    def get_tuning(self):
+        t = Tuning()
+        _check(load().amrvac_get_tuning(self._h, C.byref(t)), "amrvac_get_tuning")
+        return t.as_dict()
+
+    def autotune(self, trial_steps=3, cache=None):
+        t = Tuning()
+        _check(load().amrvac_autotune(self._h, int(trial_steps),
+                                      None if cache is None else os.fsencode(cache), C.byref(t)),
+               "amrvac_autotune")
+        return t.as_dict()
+
+    def save(self, path):
+        _check(load().amrvac_state_save(self._h, os.fsencode(path)), "amrvac_state_save")
+
+    def restore(self, path):
+        _check(load().amrvac_state_load(self._h, os.fsencode(path)), "amrvac_state_load")
 
     def clear_error(self):
         _check(load().amrvac_clear_error(self._h), "amrvac_clear_error")

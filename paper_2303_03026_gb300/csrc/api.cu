@@ -27,7 +27,7 @@ struct Tables {
 
 struct Layout {
   size_t U[3], W, F[3], part, blk, nbr, lmap, lmap_off, lnb, gamma, dx, istart, iblocks, rt,
-      sums, err, work, slab, total;
+      sums, err, work, work2, counter, slab, total;
   int slab_ctas;
 };
 
@@ -259,6 +259,8 @@ Layout make_layout(const amrvac_config* c, int ninst, int nblocks, const Tables&
   L.sums = take(sizeof(double) * NV * ninst);
   L.err = take(sizeof(int) * 4);
   L.work = take(sizeof(int) * (size_t)nblocks);
+  L.work2 = take(sizeof(int) * (size_t)nblocks);
+  L.counter = take(sizeof(int) * 4);
   L.slab_ctas = 0;
   L.slab = 0;
   if (fused) {
@@ -392,6 +394,9 @@ amrvac_status amrvac_state_create(const amrvac_config* cfg, int32_t ninst,
   M.sums = at<double>(s, L.sums);
   M.err = at<int>(s, L.err);
   s->d_work = at<int>(s, L.work);
+  s->d_work_morton = s->d_work;
+  s->d_work_storage = at<int>(s, L.work2);
+  s->d_counter = at<int>(s, L.counter);
   if (fused) {
     s->slab = s->ws + L.slab;
     s->slab_ctas = L.slab_ctas;
@@ -413,14 +418,43 @@ amrvac_status amrvac_state_create(const amrvac_config* cfg, int32_t ninst,
   up((void*)M.inst_start, T.istart.data(), sizeof(int) * T.istart.size());
   up((void*)M.inst_blocks, T.iblocks.data(), sizeof(int) * T.iblocks.size());
   up((void*)M.rt, rt.data(), sizeof(InstRT) * ninst);
-  // the work list of the fused kernel: blocks in storage order
+  // the work list of the fused kernel: per instance, blocks along a Morton
+  // (Z-order) curve of their position at the instance's finest level, so that
+  // blocks processed at the same time share neighbours (and halos) in L2
   std::vector<int> work(nblocks);
-  for (int b = 0; b < nblocks; b++) work[b] = b;
+  {
+    std::vector<int> maxlev(ninst, 0);
+    for (int b = 0; b < nblocks; b++)
+      maxlev[block_meta[5 * b]] = std::max(maxlev[block_meta[5 * b]], (int)block_meta[5 * b + 1]);
+    auto spread = [](uint64_t v) {  // 21 bits -> every third bit
+      v &= 0x1fffff;
+      v = (v | v << 32) & 0x1f00000000ffffull;
+      v = (v | v << 16) & 0x1f0000ff0000ffull;
+      v = (v | v << 8) & 0x100f00f00f00f00full;
+      v = (v | v << 4) & 0x10c30c30c30c30c3ull;
+      v = (v | v << 2) & 0x1249249249249249ull;
+      return v;
+    };
+    std::vector<std::pair<std::pair<int, uint64_t>, int>> keys(nblocks);
+    for (int b = 0; b < nblocks; b++) {
+      const int32_t* r = block_meta + 5 * b;
+      const int sh = maxlev[r[0]] - r[1];
+      uint64_t code = spread((uint64_t)r[2] << sh) | spread((uint64_t)(cfg->ndim > 1 ? r[3] : 0) << sh) << 1 |
+                      spread((uint64_t)(cfg->ndim > 2 ? r[4] : 0) << sh) << 2;
+      keys[b] = {{r[0], code}, b};
+    }
+    std::sort(keys.begin(), keys.end());
+    for (int b = 0; b < nblocks; b++) work[b] = keys[b].second;
+  }
+  std::vector<int> work_storage(nblocks);
+  for (int b = 0; b < nblocks; b++) work_storage[b] = b;
+  up((void*)s->d_work_storage, work_storage.data(), sizeof(int) * work_storage.size());
   s->nwork = nblocks;
   up((void*)s->d_work, work.data(), sizeof(int) * work.size());
   if (e == cudaSuccess) e = cudaMemsetAsync(M.part, 0, sizeof(double) * NPART * nblocks, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(M.sums, 0, sizeof(double) * NV * ninst, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(M.err, 0, sizeof(int) * 4, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->d_counter, 0, sizeof(int) * 4, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);  // host vectors die here
   if (e != cudaSuccess) {
     delete s;
@@ -641,6 +675,199 @@ amrvac_status amrvac_get_diag(amrvac_state* s, double* h_t, double* h_dt, double
     err->var = e4[3];
   }
   return (amrvac_status)e4[0];
+}
+
+namespace {
+struct SaveHeader {
+  char magic[8];
+  int32_t version, ndim, nx[3], nblocks, ninst, precision;
+};
+}  // namespace
+
+amrvac_status amrvac_state_save(amrvac_state* s, const char* path) {
+  if (!s || !path) return AMRVAC_E_INVALID;
+  std::vector<InstRT> rt;
+  amrvac_status st = read_rt(s, rt);
+  if (st) return st;
+  const size_t n = (size_t)NV * s->nblocks * s->ncell;
+  std::vector<char> u(n * s->real_size);
+  cudaError_t e = cudaMemcpyAsync(u.data(), s->U[0], u.size(), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return AMRVAC_E_CUDA;
+  FILE* f = fopen(path, "wb");
+  if (!f) return AMRVAC_E_INVALID;
+  SaveHeader h;
+  memcpy(h.magic, "AMRVACGB", 8);
+  h.version = 1;
+  h.ndim = s->ndim;
+  for (int d = 0; d < 3; d++) h.nx[d] = s->cfg.block_nx[d];
+  h.nblocks = s->nblocks;
+  h.ninst = s->ninst;
+  h.precision = s->cfg.precision;
+  bool ok = fwrite(&h, sizeof(h), 1, f) == 1;
+  ok = ok && fwrite(s->meta.data(), sizeof(int32_t), s->meta.size(), f) == s->meta.size();
+  for (int q = 0; q < s->ninst && ok; q++) {
+    double rec[5] = {rt[q].t, rt[q].t_end, rt[q].dt, rt[q].ch, s->dt_valid ? 1.0 : 0.0};
+    ok = fwrite(rec, sizeof(rec), 1, f) == 1;
+  }
+  ok = ok && fwrite(u.data(), 1, u.size(), f) == u.size();
+  ok = (fclose(f) == 0) && ok;
+  return ok ? AMRVAC_OK : AMRVAC_E_INVALID;
+}
+
+amrvac_status amrvac_state_load(amrvac_state* s, const char* path) {
+  if (!s || !path) return AMRVAC_E_INVALID;
+  FILE* f = fopen(path, "rb");
+  if (!f) return AMRVAC_E_INVALID;
+  SaveHeader h;
+  bool ok = fread(&h, sizeof(h), 1, f) == 1 && memcmp(h.magic, "AMRVACGB", 8) == 0 &&
+            h.version == 1 && h.ndim == s->ndim && h.nblocks == s->nblocks &&
+            h.ninst == s->ninst && h.precision == s->cfg.precision;
+  for (int d = 0; d < 3 && ok; d++) ok = h.nx[d] == s->cfg.block_nx[d];
+  std::vector<int32_t> meta(s->meta.size());
+  ok = ok && fread(meta.data(), sizeof(int32_t), meta.size(), f) == meta.size() && meta == s->meta;
+  std::vector<InstRT> rt(s->ninst);
+  bool dt_valid = true;
+  for (int q = 0; q < s->ninst && ok; q++) {
+    double rec[5];
+    ok = fread(rec, sizeof(rec), 1, f) == 1;
+    rt[q] = InstRT{rec[0], rec[1], rec[2], rec[3]};
+    dt_valid = dt_valid && rec[4] != 0.0;
+  }
+  const size_t n = (size_t)NV * s->nblocks * s->ncell;
+  std::vector<char> u(n * s->real_size);
+  ok = ok && fread(u.data(), 1, u.size(), f) == u.size();
+  fclose(f);
+  if (!ok) return AMRVAC_E_INVALID;
+  cudaError_t e = cudaMemcpyAsync(s->U[0], u.data(), u.size(), cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return AMRVAC_E_CUDA;
+  amrvac_status st = write_rt(s, rt);
+  if (st) return st;
+  s->dt_valid = dt_valid;
+  return AMRVAC_OK;
+}
+
+amrvac_status amrvac_set_tuning(amrvac_state* s, const amrvac_tuning* t) {
+  if (!s || !t || t->ctas_per_sm < 0 || t->ctas_per_sm > 32 || (t->order != 0 && t->order != 1) ||
+      (t->dynamic != 0 && t->dynamic != 1))
+    return AMRVAC_E_INVALID;
+  cudaError_t e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return AMRVAC_E_CUDA;
+  s->tune = *t;
+  s->d_work = t->order == 0 ? s->d_work_morton : s->d_work_storage;
+  if (s->graph) {
+    cudaGraphExecDestroy(s->graph);
+    s->graph = nullptr;
+  }
+  return AMRVAC_OK;
+}
+
+amrvac_status amrvac_get_tuning(amrvac_state* s, amrvac_tuning* t) {
+  if (!s || !t) return AMRVAC_E_INVALID;
+  *t = s->tune;
+  return AMRVAC_OK;
+}
+
+namespace {
+
+std::string tuning_key(const amrvac_state* s) {
+  int bucket = 0;
+  while ((1 << (bucket + 1)) <= s->nblocks) bucket++;
+  char buf[160];
+  snprintf(buf, sizeof(buf), "d%d_n%dx%dx%d_p%d_f%d_l%d_pr%d_b%d", s->ndim, s->cfg.block_nx[0],
+           s->cfg.block_nx[1], s->cfg.block_nx[2], s->cfg.precision, s->cfg.flux, s->cfg.limiter,
+           s->cfg.pressure, bucket);
+  return buf;
+}
+
+}  // namespace
+
+amrvac_status amrvac_autotune(amrvac_state* s, int32_t trial_steps, const char* cache_path,
+                              amrvac_tuning* best) {
+  if (!s || trial_steps < 1) return AMRVAC_E_INVALID;
+  const std::string key = tuning_key(s);
+  if (cache_path) {
+    if (FILE* f = fopen(cache_path, "r")) {
+      char k[160];
+      amrvac_tuning t{};
+      amrvac_tuning found{};
+      bool have = false;
+      while (fscanf(f, "%159s %d %d %d %lf", k, &t.ctas_per_sm, &t.order, &t.dynamic,
+                    &t.ms_per_step) == 5)
+        if (key == k) found = t, have = true;  // the last entry for a key wins
+      fclose(f);
+      if (have) {
+        amrvac_status st = amrvac_set_tuning(s, &found);
+        if (!st && best) *best = found;
+        return st;
+      }
+    }
+  }
+  if (!s->use_fused) {  // the plain path has no launch shape to tune
+    amrvac_tuning t{0, 0, 0, 0.0};
+    if (best) *best = t;
+    return amrvac_set_tuning(s, &t);
+  }
+  // back up U^n and the clocks: every trial starts from the same state
+  std::vector<InstRT> rt0;
+  amrvac_status st = read_rt(s, rt0);
+  if (st) return st;
+  const size_t bytes = (size_t)NV * s->nblocks * s->ncell * s->real_size;
+  std::vector<char> u0(bytes);
+  cudaError_t e = cudaMemcpyAsync(u0.data(), s->U[0], bytes, cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return AMRVAC_E_CUDA;
+  const bool valid0 = s->dt_valid;
+  auto restore = [&]() -> amrvac_status {
+    cudaError_t r = cudaMemcpyAsync(s->U[0], u0.data(), bytes, cudaMemcpyHostToDevice, s->stream);
+    if (r == cudaSuccess) r = cudaStreamSynchronize(s->stream);
+    if (r != cudaSuccess) return AMRVAC_E_CUDA;
+    amrvac_status w = write_rt(s, rt0);
+    s->dt_valid = valid0;
+    return w;
+  };
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return AMRVAC_E_CUDA;
+  amrvac_tuning cand[8];
+  int nc = 0;
+  for (int ctas : {0, 1})
+    for (int order : {0, 1})
+      for (int dyn : {0, 1}) cand[nc++] = amrvac_tuning{ctas, order, dyn, 0.0};
+  amrvac_tuning win{0, 0, 0, 1e300};
+  for (int c = 0; c < nc && !st; c++) {
+    st = amrvac_set_tuning(s, &cand[c]);
+    if (!st) st = restore();
+    if (!st) st = amrvac_step(s, 1);  // warm-up and graph capture
+    if (st) break;
+    if (cudaEventRecord(e0, s->stream) != cudaSuccess) st = AMRVAC_E_CUDA;
+    if (!st) st = amrvac_step(s, trial_steps);
+    if (!st && cudaEventRecord(e1, s->stream) != cudaSuccess) st = AMRVAC_E_CUDA;
+    if (!st && cudaEventSynchronize(e1) != cudaSuccess) st = AMRVAC_E_CUDA;
+    float ms = 0.f;
+    if (!st && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) st = AMRVAC_E_CUDA;
+    cand[c].ms_per_step = ms / trial_steps;
+    if (!st && cand[c].ms_per_step < win.ms_per_step) win = cand[c];
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st) {
+    restore();
+    return st;
+  }
+  st = amrvac_set_tuning(s, &win);
+  if (!st) st = restore();
+  if (st) return st;
+  if (best) *best = win;
+  if (cache_path) {
+    if (FILE* f = fopen(cache_path, "a")) {
+      fprintf(f, "%s %d %d %d %.6f\n", key.c_str(), win.ctas_per_sm, win.order, win.dynamic,
+              win.ms_per_step);
+      fclose(f);
+    }
+  }
+  return AMRVAC_OK;
 }
 
 amrvac_status amrvac_clear_error(amrvac_state* s) {

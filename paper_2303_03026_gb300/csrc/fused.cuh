@@ -48,6 +48,7 @@ template <class T, int DIM> struct FusedSmem {
   T fy[NV][FB + 1][FXW];   // y faces: row j = face j - 1/2
   double red[8][NPART];
   double damp;
+  int next;
 };
 
 // asynchronous global -> shared copy of one element (Ampere+ cp.async; the
@@ -124,7 +125,8 @@ __device__ __forceinline__ void stencil_flux(Acc S, int glm, T g, T ch, T* f) {
 template <class T, int DIM, int LIM, int FLUX>
 __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
     k_fused(DevMesh M, const T* U0, const T* __restrict__ Uk, T* out,
-            const int* __restrict__ work, int nwork, T* __restrict__ slab_all, StageParams sp) {
+            const int* __restrict__ work, int nwork, T* __restrict__ slab_all,
+            int* __restrict__ counter, StageParams sp) {
   extern __shared__ __align__(16) unsigned char smraw[];
   FusedSmem<T, DIM>& S = *reinterpret_cast<FusedSmem<T, DIM>*>(smraw);
   constexpr int NZ = DIM == 3 ? FB : 1;
@@ -153,7 +155,16 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
     }
   };
 
-  for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+  // work distribution: static (CTA i takes items i, i + grid, ...) or dynamic
+  // (each CTA draws its next item from a counter the host zeroes per launch)
+  auto next_work = [&](int wi) -> int {
+    if (!counter) return wi + gridDim.x;
+    __syncthreads();
+    if (tid == 0) S.next = atomicAdd(counter, 1);
+    __syncthreads();
+    return S.next;
+  };
+  for (int wi = counter ? next_work(0) : blockIdx.x; wi < nwork; wi = next_work(wi)) {
     const int b = work[wi];
     const int q = M.blk[b * 5], L = M.blk[b * 5 + 1];
     const InstRT rt = M.rt[q];
@@ -529,22 +540,28 @@ template <class T, int DIM, int LIM, int FLUX>
 static int launch_one(amrvac_state* s, const T* U0, const T* Uk, T* out, StageParams sp) {
   auto kern = k_fused<T, DIM, LIM, FLUX>;
   const int smem = (int)sizeof(FusedSmem<T, DIM>);
-  static int configured_grid = 0;  // per instantiation: resident CTAs on this device
-  if (configured_grid == 0) {
+  static int nsm = 0, per_sm = 0;  // per instantiation, this device
+  if (nsm == 0) {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
         cudaSuccess)
       return -1;
-    int dev = 0, nsm = 0, per_sm = 0;
+    int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, FT, smem);
-    configured_grid = nsm * (per_sm > 0 ? per_sm : 1);
+    if (per_sm < 1) per_sm = 1;
   }
-  int grid = s->nwork < configured_grid ? s->nwork : configured_grid;
+  int ctas = s->tune.ctas_per_sm > 0 && s->tune.ctas_per_sm < per_sm ? s->tune.ctas_per_sm : per_sm;
+  int grid = nsm * ctas;
+  if (grid > s->nwork) grid = s->nwork;
   if (grid > s->slab_ctas) grid = s->slab_ctas;
+  int n = 1;
+  if (s->tune.dynamic) {
+    if (cudaMemsetAsync(s->d_counter, 0, sizeof(int), s->stream) != cudaSuccess) return -1;
+  }
   kern<<<grid, FT, smem, s->stream>>>(s->mesh, U0, Uk, out, s->d_work, s->nwork, (T*)s->slab,
-                                       sp);
-  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+                                       s->tune.dynamic ? s->d_counter : nullptr, sp);
+  return cudaPeekAtLastError() == cudaSuccess ? n : -1;
 }
 
 template <class T, int DIM, int LIM>

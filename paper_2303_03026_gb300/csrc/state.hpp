@@ -33,6 +33,11 @@ struct amrvac_state {
   // layers x 16 x 16 cells x 9 vars per CTA)
   void* slab = nullptr;
   int slab_ctas = 0;
+  // launch shape of the fused kernel (see amrvac_tuning)
+  amrvac_tuning tune{0, 0, 0, 0.0};
+  int* d_work_morton = nullptr;
+  int* d_work_storage = nullptr;
+  int* d_counter = nullptr;
   // host copies
   std::vector<int32_t> meta;
   std::vector<amrvac_instance_desc> inst;

@@ -361,3 +361,90 @@ def test_full_c4_sampled(amr, orc):
 
 def test_full_c5_sampled(amr, orc):
     _sampled_full(amr, orc, wl.c5_instances(), "auto", 64, 1e-5)
+
+
+# ----------------------------------------------------------------------------
+# checkpoint / restart
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("which", ["c2_fp64", "c3_fp32"])
+def test_restart_repeats_uninterrupted_run_bitwise(amr, tmp_path, which):
+    if which == "c2_fp64":
+        W = wl.c2_orszag_tang(128)
+        U = W.U
+    else:
+        W = wl.c3_turbulence(n=32, bnx=16, precision="fp32")
+        U = W.U.astype(np.float32)
+    A = amr.State.from_workload(W)
+    A.set_conserved(U)
+    A.step(10)
+    ref = A.get_conserved(0)
+    tref = A.diag()["t"]
+    A.close()
+    B = amr.State.from_workload(W)
+    B.set_conserved(U)
+    B.step(5)
+    path = str(tmp_path / "ckpt.bin")
+    B.save(path)
+    B.close()
+    C = amr.State.from_workload(W)
+    C.restore(path)
+    C.step(5)
+    got = C.get_conserved(0)
+    np.testing.assert_array_equal(got, ref)
+    np.testing.assert_array_equal(C.diag()["t"], tref)
+    # a checkpoint does not load into a different mesh
+    D = amr.State.from_workload(wl.c2_orszag_tang(64) if which == "c2_fp64" else
+                                wl.c3_turbulence(n=48, bnx=16, precision="fp32"))
+    with pytest.raises(amr.AmrvacError):
+        D.restore(path)
+    C.close()
+    D.close()
+
+
+# ----------------------------------------------------------------------------
+# launch-shape tuning and the autotuner
+# ----------------------------------------------------------------------------
+
+def test_every_launch_shape_is_bit_identical(amr):
+    W = wl.c4_blast_amr(base=4, levels=3, bnx=16, shell=(0.2, 0.26), precision="fp32")
+    U = W.U.astype(np.float32)
+    ref = None
+    for ctas in (0, 1):
+        for order in ("morton", "storage"):
+            for dyn in (False, True):
+                S = amr.State.from_workload(W, pressure="ff")
+                S.set_tuning(ctas, order, dyn)
+                S.set_conserved(U)
+                S.step(3)
+                got = S.get_conserved(0)
+                d = S.diag(raise_on_error=True)
+                if ref is None:
+                    ref, dref = got, d
+                np.testing.assert_array_equal(got, ref)
+                np.testing.assert_array_equal(d["dt"], dref["dt"])
+                np.testing.assert_array_equal(d["sums"], dref["sums"])
+                S.close()
+
+
+def test_autotune_restores_state_and_caches(amr, tmp_path):
+    W = wl.c4_blast_amr(base=4, levels=3, bnx=16, shell=(0.2, 0.26), precision="fp32")
+    U = W.U.astype(np.float32)
+    cache = str(tmp_path / "tune.txt")
+    A = amr.State.from_workload(W, pressure="ff")
+    A.set_conserved(U)
+    best = A.autotune(trial_steps=2, cache=cache)
+    assert best["ms_per_step"] > 0
+    assert A.get_tuning()["order"] == best["order"]
+    A.step(2)
+    got = A.get_conserved(0)
+    B = amr.State.from_workload(W, pressure="ff")
+    B.set_conserved(U)
+    B.step(2)
+    np.testing.assert_array_equal(got, B.get_conserved(0))
+    # the second state of the same shape reads the cache instead of timing
+    again = B.autotune(trial_steps=2, cache=cache)
+    assert again == best
+    assert len(open(cache).read().strip().splitlines()) == 1
+    A.close()
+    B.close()
