@@ -56,6 +56,8 @@ def parse():
     p.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison leg")
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU-baseline leg")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-tune", action="store_true",
+                   help="skip the launch-shape autotuning before the timed region")
     return p.parse_args()
 
 
@@ -303,6 +305,11 @@ def main():
             dist.barrier()
         torch.cuda.synchronize(dev)
 
+    # launch-shape autotuning (untimed set-up; restores the state it times on)
+    tuning = None
+    if not args.no_tune and args.kernel != "plain":
+        tuning = S.autotune(trial_steps=3)
+
     # warm-up (also captures the step graph)
     S.step(max(args.warmup, 3))
     d = S.diag()
@@ -372,6 +379,8 @@ def main():
                                             pressure=kw.get("pressure", args.pressure))
             W.cfg.flux = old_flux
             Sv.set_conserved(U32)
+            if tuning is not None:
+                Sv.set_tuning(tuning["ctas_per_sm"], tuning["order"], tuning["dynamic"])
             Sv.step(2)
             msv = time_steps(torch, Sv, max(3, min(args.steps, 10)))
             variants[name] = {"value": cells * ws / (msv / 1e3), "ms_per_step": msv,
@@ -476,7 +485,7 @@ def main():
                                precision="fp32 bulk; pressure recovery and per-thread sums in %s; "
                                          "fp64 dt and block/instance sums" %
                                          ("float-float" if args.pressure == "ff" else "fp64"),
-                               kernel=args.kernel, build=digest,
+                               kernel=args.kernel, build=digest, tuning=tuning,
                                parallelism="replicas" if ws > 1 else "1 GPU"),
                 "clocks": clk.summary(), "gpu_launches": launches, "roofline": roofline,
                 "e2e": e2e, "variants": variants or None, "one_at_a_time": one_at_a_time,

@@ -21,6 +21,7 @@
 
 #include "ghost.cuh"
 #include "physics.cuh"
+#include "physics_f2.cuh"
 #include "reduce.cuh"
 #include "state.hpp"
 
@@ -105,6 +106,11 @@ template <> __device__ __forceinline__ float over_dx(float a, float, float idx) 
 // f-2, f-1, f, f+1 around the face f-1/2
 template <class T, int D, int LIM, int FLUX, class Acc>
 __device__ __forceinline__ void stencil_flux(Acc S, int glm, T g, T ch, T* f) {
+  if constexpr (sizeof(T) == 4) {
+    // FP32 bulk: left/right states packed in float2 lanes (physics_f2.cuh)
+    stencil_flux_f2<D, LIM, FLUX>(S, glm, g, ch, f);
+    return;
+  }
   T wl[NV], wr[NV];
 #pragma unroll
   for (int v = 0; v < NV; v++) {

@@ -311,6 +311,43 @@ def test_fp32_shocked_stage(amr, orc, kernel, pressure):
     _stage_parity(amr, orc, W, kernel, tol=1e-5, pressure=pressure)
 
 
+def _riemann_2d(n=64, angle=0.0, flux="hlld", limiter="vanleer"):
+    """2D MHD shock tube (Brio-Wu-like states, plus transverse velocity and
+    B_z) along a direction in the plane, in 16^2 blocks: all HLLD fan regions."""
+    cfg = wl.Config(ndim=2, block_nx=(16, 16, 1), flux=flux, limiter=limiter, time="ssprk3",
+                    precision="fp32", glm=True, bc=(("outflow", "outflow"),) * 3)
+    nb = n // 16
+    inst = wl.Instance(base_blocks=(nb, nb, 1), gamma=5 / 3)
+    meta = wl.uniform_meta((nb, nb, 1))
+    c, s_ = math.cos(angle), math.sin(angle)
+
+    def prim(inst, x, y, z):
+        xi = (x - 0.5) * c + (y - 0.5) * s_
+        L = xi < 0.0
+        rho = np.where(L, 1.0, 0.125)
+        p = np.where(L, 1.0, 0.1)
+        un = np.where(L, 0.3, -0.2)
+        ut = np.where(L, 0.1, -0.4)
+        bn = 0.75 + 0 * x
+        bt = np.where(L, 1.0, -1.0)
+        bz = np.where(L, 0.2, 0.5)
+        vx, vy = un * c - ut * s_, un * s_ + ut * c
+        bx, by = bn * c - bt * s_, bn * s_ + bt * c
+        return wl.conserved_from_primitive(5 / 3, rho, vx, vy, 0.05 + 0 * x, p, bx, by, bz)
+
+    U = wl._fill_from_function(cfg, [inst], meta, prim)
+    return wl.Workload("riemann2d", cfg, [inst], meta, U)
+
+
+@pytest.mark.parametrize("flux", ["hlld", "hll"])
+@pytest.mark.parametrize("angle", [0.0, 0.5 * math.pi, 0.3])
+def test_fp32_fused_riemann_2d_strict(amr, orc, flux, angle):
+    # per stage from identical inputs the FP32 error is at the float rounding
+    # level even across shocks: checked at 1e-5 (stricter than the 1e-3 bound)
+    W = _riemann_2d(angle=angle, flux=flux)
+    _stage_parity(amr, orc, W, "fused", tol=1e-5, pressure="ff")
+
+
 @pytest.mark.parametrize("pressure", PRESSURES)
 @pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("beta", [0.01, 1e-4])
@@ -444,7 +481,9 @@ def test_autotune_restores_state_and_caches(amr, tmp_path):
     np.testing.assert_array_equal(got, B.get_conserved(0))
     # the second state of the same shape reads the cache instead of timing
     again = B.autotune(trial_steps=2, cache=cache)
-    assert again == best
+    assert {k: again[k] for k in ("ctas_per_sm", "order", "dynamic")} == \
+        {k: best[k] for k in ("ctas_per_sm", "order", "dynamic")}
+    assert abs(again["ms_per_step"] - best["ms_per_step"]) < 1e-5  # cached with 6 decimals
     assert len(open(cache).read().strip().splitlines()) == 1
     A.close()
     B.close()
