@@ -199,8 +199,8 @@ amrvac_status amrvac_set_dt(amrvac_state* s, const double* h_dt, const double* h
 amrvac_status amrvac_stage(amrvac_state* s, int32_t stage);
 
 /*
- * nsteps full time steps: all stages, then t += dt, the next dt and c_h from
- * U^{n+1} and the conservation sums, all on the device (no host sync).  The
+ * nsteps full time steps: all stages, then t += dt and the next dt and c_h
+ * from U^{n+1}, all on the device (no host sync).  The
  * first call computes dt if none is valid.  With a non-default stream the
  * step is captured once as a CUDA graph and replayed.
  */
@@ -208,10 +208,10 @@ amrvac_status amrvac_step(amrvac_state* s, int32_t nsteps);
 
 /*
  * Synchronises and reads per-instance t, dt, c_h ([ninst] each), the
- * conservation sums h_sums[ninst][9] (integral of each conserved variable,
- * FP64, fixed summation order; valid after a step or amrvac_cfl_dt) and the
- * latched device error.  Any pointer may be NULL.  Returns the latched error
- * code (AMRVAC_OK if none).
+ * conservation sums h_sums[ninst][9] (integral of each conserved variable of
+ * buffer 0 = U^n, reduced on the device in FP64 in a fixed order when h_sums is
+ * not NULL) and the latched device error.  Any pointer may be NULL.  Returns
+ * the latched error code (AMRVAC_OK if none).
  */
 amrvac_status amrvac_get_diag(amrvac_state* s, double* h_t, double* h_dt, double* h_ch,
                               double* h_sums, amrvac_error_info* err);

@@ -655,6 +655,10 @@ amrvac_status amrvac_step(amrvac_state* s, int32_t nsteps) {
 amrvac_status amrvac_get_diag(amrvac_state* s, double* h_t, double* h_dt, double* h_ch,
                               double* h_sums, amrvac_error_info* err) {
   if (!s) return AMRVAC_E_INVALID;
+  if (h_sums) {
+    amrvac_status st = check_launch(s, launch_sums(s, 0));
+    if (st) return st;
+  }
   std::vector<InstRT> rt;
   amrvac_status st = read_rt(s, rt);
   if (st) return st;

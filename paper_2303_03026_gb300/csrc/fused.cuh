@@ -13,7 +13,8 @@
 //           the z-face z+1/2 flux from the thread's own column (registers)
 //         sync; update of cell (x, y, z): flux divergence with the z-face
 //           flux carried from the previous plane, psi damping, SSPRK
-//           combination; optional per-block dt / conservation partials.
+//           combination; in the last stage the CFL terms of the new state
+//           (reduced per block for the time step).
 //   2D: the same with one plane and no z faces.
 // Every face flux of the block is computed once (block-boundary faces are
 // computed by both neighbours).  Arithmetic follows physics.cuh.
@@ -43,10 +44,12 @@ __device__ __forceinline__ int fused_row(int warp, int lane) {
 }
 
 template <class T, int DIM> struct FusedSmem {
-  static constexpr int NSLOT = DIM == 3 ? 5 : 1;
+  static constexpr int NSLOT = DIM == 3 ? 4 : 1;
   T plane[NSLOT][NV][FPW][FPW];
-  T fx[NV][FB][FXW];       // x faces: column i = face i - 1/2, i = 0..16
-  T fy[NV][FB + 1][FXW];   // y faces: row j = face j - 1/2
+  // face fluxes of the current plane, double-buffered by plane parity so that
+  // one barrier per plane separates writers and readers
+  T fx[2][NV][FB][FXW];       // x faces: column i = face i - 1/2, i = 0..16
+  T fy[2][NV][FB + 1][FXW];   // y faces: row j = face j - 1/2
   double red[8][NPART];
   double damp;
   int next;
@@ -96,6 +99,47 @@ __device__ __forceinline__ void cta_reduce_store(double (*red)[NPART], Partial& 
     part_b[threadIdx.x] = threadIdx.x < 2 + NV ? acc : 0.0;
   }
   __syncthreads();
+}
+
+// CTA maximum of the owners' two CFL terms into part_b[0], part_b[1]
+__device__ __forceinline__ void cta_reduce_max2(double (*red)[NPART], double smax, double cmax,
+                                                bool owner, double* part_b) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (owner) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+      cmax = fmax(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+    }
+    if (lane == 0) {
+      red[warp][0] = smax;
+      red[warp][1] = cmax;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    double acc = red[0][threadIdx.x];
+    for (int w = 1; w < 8; w++) acc = fmax(acc, red[w][threadIdx.x]);
+    part_b[threadIdx.x] = acc;
+  }
+}
+
+// CFL terms of a conserved cell: running max of sum_d (|v_d| + c_f,d)/dx_d and
+// of |v_d| + c_f,d
+template <class T, int DIM>
+__device__ __forceinline__ void cfl_terms(const T* u, double gammad, T g, bool ff, float gm1f,
+                                          const T* idx, T& smx, T& cmx) {
+  T w[NV];
+  cons2prim(gammad, u, w, ff, gm1f);
+  T s = T(0);
+#pragma unroll
+  for (int d = 0; d < DIM; d++) {
+    T spd = fabs(w[1 + d]) + fast_speed(g, w, d);
+    s += spd * idx[d];
+    cmx = fmax(cmx, spd);
+  }
+  smx = fmax(smx, s);
 }
 
 template <class T> __device__ __forceinline__ T over_dx(T a, T dx, T idx);
@@ -181,9 +225,10 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
     const double* dxl = M.dx + (q * MAXLEV + L) * 3;
     const double dxd[3] = {dxl[0], dxl[1], dxl[2]};
 
+    const T idd[3] = {T(1) / (T)dxd[0], T(1) / (T)dxd[1], T(1) / (T)dxd[2]};
+    T smx = T(0), cmx = T(0);  // CFL terms of the new state (last stage)
+
     if (rt.dt == 0.0) {
-      Partial p;
-      partial_zero(p);
       // finished instance: copied through unchanged
       for (int c = tid; owner && c < ncell; c += FB * FB) {
         T u[NV];
@@ -193,9 +238,9 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
           u[v] = Uk[at];
           out[at] = u[v];
         }
-        if (sp.epilogue) accumulate_cell(M, u, gammad, dxd, p);
+        if (sp.epilogue) cfl_terms<T, DIM>(u, gammad, g, ff, gm1f, idd, smx, cmx);
       }
-      if (sp.epilogue) cta_reduce_store(S.red, p, owner, M.part + (size_t)b * NPART);
+      if (sp.epilogue) cta_reduce_max2(S.red, smx, cmx, owner, M.part + (size_t)b * NPART);
       continue;
     }
 
@@ -223,7 +268,7 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
     __syncthreads();  // the previous block is done with the shared scratch
     if (any_general) {
       const int bidx[3] = {M.blk[b * 5 + 2], M.blk[b * 5 + 3], M.blk[b * 5 + 4]};
-      T* cs = &S.fx[0][0][0];  // coarse value + slopes, [cell][1 + DIM][NV]
+      T* cs = &S.fx[0][0][0][0];  // coarse value + slopes, [cell][1 + DIM][NV]
       for (int f = 0; f < 2 * DIM; f++) {
         if (nb[f] != NBR_GENERAL) continue;
         const int d = f >> 1, side = f & 1;
@@ -419,28 +464,28 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
       for (int pz = -2; pz <= 1; pz++) issue_plane(pz);
       cp_async_wait_all();
       for (int pz = -2; pz <= 1; pz++) convert_plane(pz);
-      issue_plane(2);
-      if (owner) zflux(0, fzp);  // own column only: no barrier needed
+      if (owner) zflux(0, fzp);  // own column only
     } else {
       load_plane(0);
     }
+    __syncthreads();  // planes 0 and 1 (with halos) visible to all threads
 
     if constexpr (sizeof(T) == 8) {
       __syncthreads();
       damp = S.damp;
     }
 
+    // One barrier per plane.  Iteration z: issue the copies of plane z+2 into
+    // the slot of plane z-2 (its last readers were the faces of plane z-2 and
+    // this thread's own z face of iteration z-1); x/y faces of plane z into the
+    // flux buffer of parity z; wait for and convert plane z+2; z face z+1/2;
+    // barrier; update of plane z.  The buffer of parity z is rewritten at
+    // iteration z+2, after the barrier of iteration z+1, which every thread
+    // passes only after its update of plane z.
 #pragma unroll 1
     for (int z = 0; z < NZ; z++) {
-      if (DIM == 3) {
-        // this thread's copies of plane z+2 (issued one iteration ago) have
-        // landed; prefetch plane z+3 into the slot of plane z-2, which no thread
-        // reads any more.  Plane z+2 is converted after the x/y faces below.
-        cp_async_wait_all();
-        if (z + 3 <= NZ + 1) issue_plane(z + 3);
-      }
-      __syncthreads();
-      const int sl = z % NSLOT;
+      if (DIM == 3) issue_plane(z + 2);
+      const int sl = z % NSLOT, fb = z & 1;
       {
         // owners: the x and y faces on the low side of their cell; helpers: the
         // x face at the +x block boundary of row hr and the y face at the +y
@@ -451,15 +496,18 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
         auto ax = [&](int v, int t) -> T { return S.plane[sl][v][fxr + NG][fxc + t]; };
         stencil_flux<T, 0, LIM, FLUX>(ax, sp.glm, g, ch, f);
 #pragma unroll
-        for (int v = 0; v < NV; v++) S.fx[v][fxr][fxc] = f[v];
+        for (int v = 0; v < NV; v++) S.fx[fb][v][fxr][fxc] = f[v];
         auto ay = [&](int v, int t) -> T { return S.plane[sl][v][fyr + t][fyc + NG]; };
         stencil_flux<T, 1, LIM, FLUX>(ay, sp.glm, g, ch, f);
 #pragma unroll
-        for (int v = 0; v < NV; v++) S.fy[v][fyr][fyc] = f[v];
+        for (int v = 0; v < NV; v++) S.fy[fb][v][fyr][fyc] = f[v];
       }
       // plane z+2 -> primitives (owners: own column, needed by the z face below;
-      // helpers: the halo, needed two planes later), balancing the two phases
-      if (DIM == 3) convert_plane(z + 2);
+      // helpers: the halo, needed two planes later)
+      if (DIM == 3) {
+        cp_async_wait_all();
+        convert_plane(z + 2);
+      }
       T fz[NV];
       if (DIM == 3 && owner) zflux(z + 1, fz);
       __syncthreads();
@@ -469,8 +517,8 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
       T un[NV];
 #pragma unroll
       for (int v = 0; v < NV; v++) {
-        T acc = over_dx<T>(S.fx[v][y][x + 1] - S.fx[v][y][x], dx0, idx0);
-        acc += over_dx<T>(S.fy[v][y + 1][x] - S.fy[v][y][x], dx1, idx1);
+        T acc = over_dx<T>(S.fx[fb][v][y][x + 1] - S.fx[fb][v][y][x], dx0, idx0);
+        acc += over_dx<T>(S.fy[fb][v][y + 1][x] - S.fy[fb][v][y][x], dx1, idx1);
         if (DIM == 3) acc += over_dx<T>(fz[v] - fzp[v], dx2, idx2);
         const size_t at = (size_t)v * vs + (size_t)b * ncell + c;
         T ut = Uk[at] - dt * acc;
@@ -478,65 +526,13 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
         un[v] = sp.k == 0 ? ut : ca * U0[at] + cb * ut;
         out[at] = un[v];
       }
+      if (sp.epilogue) cfl_terms<T, DIM>(un, gammad, g, ff, gm1f, idd, smx, cmx);
       if (DIM == 3) {
 #pragma unroll
         for (int v = 0; v < NV; v++) fzp[v] = fz[v];
       }
     }
-    if (sp.epilogue) {
-      // per-block CFL / conservation partials of the new state: each thread
-      // re-reads the column it has just written
-      Partial p;
-      partial_zero(p);
-      if constexpr (sizeof(T) == 4) {
-        if (ff) {
-          // float speeds, float-float conservation sums per thread
-          float sm = 0.f, cm = 0.f;
-          float hi[NV], lo[NV];
-#pragma unroll
-          for (int v = 0; v < NV; v++) hi[v] = lo[v] = 0.f;
-          const float idd[3] = {(float)(1.0 / dxd[0]), (float)(1.0 / dxd[1]),
-                                (float)(1.0 / dxd[2])};
-#pragma unroll 1
-          for (int z = 0; owner && z < NZ; z++) {
-            const int c = (z * FB + y) * FB + x;
-            float u[NV], w[NV];
-#pragma unroll
-            for (int v = 0; v < NV; v++) u[v] = out[(size_t)v * vs + (size_t)b * ncell + c];
-            cons2prim(gammad, u, w, true, gm1f);
-            float s = 0.f;
-#pragma unroll
-            for (int d = 0; d < DIM; d++) {
-              float spd = fabsf(w[1 + d]) + fast_speed((float)g, w, d);
-              s += spd * idd[d];
-              cm = fmaxf(cm, spd);
-            }
-            sm = fmaxf(sm, s);
-#pragma unroll
-            for (int v = 0; v < NV; v++) {
-              ff2 t = two_sum(hi[v], u[v]);
-              hi[v] = t.hi;
-              lo[v] = __fadd_rn(lo[v], t.lo);
-            }
-          }
-          p.smax = sm;
-          p.chm = cm;
-#pragma unroll
-          for (int v = 0; v < NV; v++) p.sum[v] = (double)hi[v] + (double)lo[v];
-          cta_reduce_store(S.red, p, owner, M.part + (size_t)b * NPART);
-          continue;
-        }
-      }
-#pragma unroll 1
-      for (int z = 0; owner && z < NZ; z++) {
-        const int c = (z * FB + y) * FB + x;
-        T u[NV];
-#pragma unroll
-        for (int v = 0; v < NV; v++) u[v] = out[(size_t)v * vs + (size_t)b * ncell + c];
-        accumulate_cell(M, u, gammad, dxd, p);  // FP64 sums
-      }
-      cta_reduce_store(S.red, p, owner, M.part + (size_t)b * NPART);
-    }
+    if (sp.epilogue) cta_reduce_max2(S.red, smx, cmx, owner, M.part + (size_t)b * NPART);
   }
 }
 

@@ -238,7 +238,69 @@ __global__ void __launch_bounds__(256) k_finalize(DevMesh M, double courant, int
     r.dt = d;
     r.ch = sh[0][1];
     M.rt[q] = r;
-    for (int v = 0; v < NV; v++) M.sums[q * NV + v] = sh[0][2 + v];
+  }
+}
+
+// ------------------------------------------------------------------ sums
+
+// per-block integrals of each conserved variable of U (FP64, fixed order)
+template <class T>
+__global__ void __launch_bounds__(256) k_sums(DevMesh M, const T* __restrict__ U) {
+  const size_t vs = (size_t)M.nblocks * M.ncell;
+  __shared__ double sh[8][NV];
+  for (int b = blockIdx.x; b < M.nblocks; b += gridDim.x) {
+    double s[NV];
+#pragma unroll
+    for (int v = 0; v < NV; v++) s[v] = 0.0;
+    for (int c = threadIdx.x; c < M.ncell; c += blockDim.x) {
+#pragma unroll
+      for (int v = 0; v < NV; v++) s[v] += (double)U[(size_t)v * vs + (size_t)b * M.ncell + c];
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int v = 0; v < NV; v++) s[v] += __shfl_xor_sync(0xffffffffu, s[v], o);
+    if (lane == 0)
+      for (int v = 0; v < NV; v++) sh[warp][v] = s[v];
+    __syncthreads();
+    if (threadIdx.x < NV) {
+      double acc = sh[0][threadIdx.x];
+      for (int w = 1; w < (int)(blockDim.x >> 5); w++) acc += sh[w][threadIdx.x];
+      M.part[(size_t)b * NPART + 2 + threadIdx.x] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+// per-instance sums of the block integrals times the cell volume (fixed order)
+__global__ void __launch_bounds__(256) k_sums_finalize(DevMesh M) {
+  const int q = blockIdx.x;
+  if (q >= M.ninst) return;
+  __shared__ double sh[8][NV];
+  double sum[NV];
+#pragma unroll
+  for (int v = 0; v < NV; v++) sum[v] = 0.0;
+  for (int n = M.inst_start[q] + threadIdx.x; n < M.inst_start[q + 1]; n += blockDim.x) {
+    const int b = M.inst_blocks[n];
+    const double* dxl = M.dx + (q * MAXLEV + M.blk[b * 5 + 1]) * 3;
+    double dv = dxl[0];
+    for (int d = 1; d < M.ndim; d++) dv *= dxl[d];
+#pragma unroll
+    for (int v = 0; v < NV; v++) sum[v] += M.part[(size_t)b * NPART + 2 + v] * dv;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int v = 0; v < NV; v++) sum[v] += __shfl_xor_sync(0xffffffffu, sum[v], o);
+  if (lane == 0)
+    for (int v = 0; v < NV; v++) sh[warp][v] = sum[v];
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double acc = sh[0][threadIdx.x];
+    for (int w = 1; w < (int)(blockDim.x >> 5); w++) acc += sh[w][threadIdx.x];
+    M.sums[q * NV + threadIdx.x] = acc;
   }
 }
 
@@ -331,6 +393,16 @@ int launch_cfl_partials(amrvac_state* s, int buffer) {
 int launch_finalize(amrvac_state* s, int advance) {
   k_finalize<<<s->ninst, 256, 0, s->stream>>>(s->mesh, s->cfg.courant, advance);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_sums(amrvac_state* s, int buffer) {
+  int grid = s->nblocks < 152 * 16 ? s->nblocks : 152 * 16;
+  if (s->cfg.precision == AMRVAC_FP64)
+    k_sums<double><<<grid, 256, 0, s->stream>>>(s->mesh, (const double*)s->U[buffer]);
+  else
+    k_sums<float><<<grid, 256, 0, s->stream>>>(s->mesh, (const float*)s->U[buffer]);
+  k_sums_finalize<<<s->ninst, 256, 0, s->stream>>>(s->mesh);
+  return cudaPeekAtLastError() == cudaSuccess ? 2 : -1;
 }
 
 int launch_fill_ghosts(amrvac_state* s, int buffer, void* out) {
