@@ -50,6 +50,10 @@ template <class T, int DIM> struct FusedSmem {
   // one barrier per plane separates writers and readers
   T fx[2][NV][FB][FXW];       // x faces: column i = face i - 1/2, i = 0..16
   T fy[2][NV][FB + 1][FXW];   // y faces: row j = face j - 1/2
+  // float path: U0 of the owners' cells of the current plane, copied in while
+  // the plane's faces are computed (the fp64 path reads U0 directly: a
+  // double slot would not fit beside its planes)
+  T u0[sizeof(T) == 4 ? NV : 1][FB * FB];
   double red[8][NPART];
   double damp;
   int next;
@@ -62,6 +66,15 @@ __device__ __forceinline__ void cp_async_elem(T* smem_dst, const T* gmem_src) {
   const unsigned dst = (unsigned)__cvta_generic_to_shared(smem_dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(dst), "l"(gmem_src),
                "n"(sizeof(T)));
+}
+// the same, ordered after this thread's earlier shared-memory reads of the
+// destination (the copy overwrites values the thread read one plane before)
+template <class T>
+__device__ __forceinline__ void cp_async_elem_after_reads(T* smem_dst, const T* gmem_src) {
+  const unsigned dst = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(dst), "l"(gmem_src),
+               "n"(sizeof(T))
+               : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait_all() {
@@ -475,16 +488,27 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
       damp = S.damp;
     }
 
-    // One barrier per plane.  Iteration z: issue the copies of plane z+2 into
-    // the slot of plane z-2 (its last readers were the faces of plane z-2 and
-    // this thread's own z face of iteration z-1); x/y faces of plane z into the
+    // One barrier per plane.  Iteration z: issue the copies of U0 of plane z
+    // (stages k > 0) and of plane z+2 into the slot of plane z-2 (its last
+    // readers were the faces of plane z-2 and this thread's own z face of
+    // iteration z-1); x/y faces of plane z into the
     // flux buffer of parity z; wait for and convert plane z+2; z face z+1/2;
     // barrier; update of plane z.  The buffer of parity z is rewritten at
     // iteration z+2, after the barrier of iteration z+1, which every thread
     // passes only after its update of plane z.
+    constexpr bool PRE0 = sizeof(T) == 4;
+    const bool pre0 = PRE0 && sp.k != 0 && owner;
 #pragma unroll 1
     for (int z = 0; z < NZ; z++) {
-      if (DIM == 3) issue_plane(z + 2);
+      if (pre0) {
+        // U0 of this thread's cell of plane z (a DRAM read), landing while the
+        // faces below are computed; read back by the same thread only
+        const T* src = U0 + (size_t)b * ncell + (z * FB + y) * FB + x;
+#pragma unroll
+        for (int v = 0; v < NV; v++) cp_async_elem_after_reads(&S.u0[v][tid], src + v * vs);
+      }
+      if (DIM == 3) issue_plane(z + 2);  // commits this thread's copies as one group
+      else if (pre0) cp_async_commit();
       const int sl = z % NSLOT, fb = z & 1;
       {
         // owners: the x and y faces on the low side of their cell; helpers: the
@@ -508,6 +532,7 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
         cp_async_wait_all();
         convert_plane(z + 2);
       }
+      if (DIM != 3 && pre0) cp_async_wait_all();
       T fz[NV];
       if (DIM == 3 && owner) zflux(z + 1, fz);
       __syncthreads();
@@ -523,7 +548,7 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
         const size_t at = (size_t)v * vs + (size_t)b * ncell + c;
         T ut = Uk[at] - dt * acc;
         if (v == 8) ut = ut * damp;
-        un[v] = sp.k == 0 ? ut : ca * U0[at] + cb * ut;
+        un[v] = sp.k == 0 ? ut : ca * (PRE0 ? S.u0[v][tid] : U0[at]) + cb * ut;
         out[at] = un[v];
       }
       if (sp.epilogue) cfl_terms<T, DIM>(un, gammad, g, ff, gm1f, idd, smx, cmx);
