@@ -20,25 +20,15 @@ constexpr size_t ALIGN = 256;
 size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Tables {
-  std::vector<int> blk, nbr, lmap, lmap_off, lnb, istart, iblocks;
+  std::vector<int> blk, nbr, gface, glist, lmap, lmap_off, lnb, istart, iblocks;
   std::vector<double> gamma, dx;
   std::string err;
 };
 
 struct Layout {
-  size_t U[3], W, F[3], part, blk, nbr, lmap, lmap_off, lnb, gamma, dx, istart, iblocks, rt,
-      sums, err, work, work2, counter, slab, total;
-  int slab_ctas;
+  size_t U[3], W, F[3], part, blk, nbr, gface, glist, lmap, lmap_off, lnb, gamma, dx, istart,
+      iblocks, rt, sums, err, work, work2, counter, gslab, total;
 };
-
-// resident CTAs the fused kernel may use on the current device (upper bound)
-int fused_ctas() {
-  int dev = 0, nsm = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
-    nsm = 160;
-  return nsm * 4;
-}
 
 bool config_ok(const amrvac_config* c, std::string& err) {
   if (!c) return err = "null config", false;
@@ -209,6 +199,15 @@ bool build_tables(const amrvac_config* c, int ninst, const amrvac_instance_desc*
         out = m >= 0 ? m : NBR_GENERAL;
       }
   }
+  // level-change faces: one ghost slab each
+  T.gface.assign((size_t)nblocks * 6, -1);
+  T.glist.clear();
+  for (int b = 0; b < nblocks; b++)
+    for (int f = 0; f < 6; f++)
+      if (T.nbr[b * 6 + f] == NBR_GENERAL) {
+        T.gface[b * 6 + f] = (int)T.glist.size();
+        T.glist.push_back(b * 6 + f);
+      }
   T.istart.assign(ninst + 1, 0);
   for (int b = 0; b < nblocks; b++) T.istart[meta[5 * b] + 1]++;
   for (int q = 0; q < ninst; q++) T.istart[q + 1] += T.istart[q];
@@ -248,6 +247,8 @@ Layout make_layout(const amrvac_config* c, int ninst, int nblocks, const Tables&
   L.part = take(sizeof(double) * NPART * nblocks);
   L.blk = take(sizeof(int) * T.blk.size());
   L.nbr = take(sizeof(int) * T.nbr.size());
+  L.gface = take(sizeof(int) * T.gface.size());
+  L.glist = take(sizeof(int) * (T.glist.size() + 1));
   L.lmap = take(sizeof(int) * T.lmap.size());
   L.lmap_off = take(sizeof(int) * T.lmap_off.size());
   L.lnb = take(sizeof(int) * T.lnb.size());
@@ -261,12 +262,10 @@ Layout make_layout(const amrvac_config* c, int ninst, int nblocks, const Tables&
   L.work = take(sizeof(int) * (size_t)nblocks);
   L.work2 = take(sizeof(int) * (size_t)nblocks);
   L.counter = take(sizeof(int) * 4);
-  L.slab_ctas = 0;
-  L.slab = 0;
+  L.gslab = 0;
   if (fused) {
-    L.slab_ctas = fused_ctas();
-    size_t per = (size_t)2 * c->ndim * NV * 2 * 16 * (c->ndim == 3 ? 16 : 1);
-    L.slab = take(rs * per * L.slab_ctas);
+    size_t per = (size_t)NV * 2 * 16 * (c->ndim == 3 ? 16 : 1);  // one face
+    L.gslab = take(rs * per * T.glist.size());
   }
   L.total = off;
   return L;
@@ -382,6 +381,7 @@ amrvac_status amrvac_state_create(const amrvac_config* cfg, int32_t ninst,
   M.ninst = ninst;
   M.blk = at<int>(s, L.blk);
   M.nbr = at<int>(s, L.nbr);
+  M.gface = at<int>(s, L.gface);
   M.lmap = at<int>(s, L.lmap);
   M.lmap_off = at<int>(s, L.lmap_off);
   M.lnb = at<int>(s, L.lnb);
@@ -398,8 +398,9 @@ amrvac_status amrvac_state_create(const amrvac_config* cfg, int32_t ninst,
   s->d_work_storage = at<int>(s, L.work2);
   s->d_counter = at<int>(s, L.counter);
   if (fused) {
-    s->slab = s->ws + L.slab;
-    s->slab_ctas = L.slab_ctas;
+    s->gslab = s->ws + L.gslab;
+    s->d_glist = at<int>(s, L.glist);
+    s->ngen = (int)T.glist.size();
   }
 
   std::vector<InstRT> rt(ninst);
@@ -410,6 +411,8 @@ amrvac_status amrvac_state_create(const amrvac_config* cfg, int32_t ninst,
   };
   up((void*)M.blk, T.blk.data(), sizeof(int) * T.blk.size());
   up((void*)M.nbr, T.nbr.data(), sizeof(int) * T.nbr.size());
+  up((void*)M.gface, T.gface.data(), sizeof(int) * T.gface.size());
+  if (fused) up((void*)s->d_glist, T.glist.data(), sizeof(int) * T.glist.size());
   up((void*)M.lmap, T.lmap.data(), sizeof(int) * T.lmap.size());
   up((void*)M.lmap_off, T.lmap_off.data(), sizeof(int) * T.lmap_off.size());
   up((void*)M.lnb, T.lnb.data(), sizeof(int) * T.lnb.size());

@@ -35,6 +35,7 @@ struct DevMesh {
   int bc[3][2];
   const int* blk;         // [nblocks][5]: inst, level, i, j, k
   const int* nbr;         // [nblocks][6]: face (d, side) -> neighbour code
+  const int* gface;       // [nblocks][6]: ghost-slab index of a level-change face, else -1
   const int* lmap;        // concatenated dense per-(instance, level) block maps
   const int* lmap_off;    // [ninst][MAXLEV] offset into lmap
   const int* lnb;         // [ninst][MAXLEV][3] blocks per dimension at a level

@@ -3,16 +3,19 @@
 // One CTA of 272 threads owns one block at a time and loops over the work
 // list (grid = resident CTAs).  Thread (x, y) < 256 owns a column of the block;
 // 16 helper threads take the +x/+y block-boundary faces and the halo cells.
-//   3D: march over z with a ring of 5 primitive planes in shared memory, each
-//       with its 2-cell x/y halo (planes z-2 .. z+2).  Per plane:
-//         load plane z+2 (own column; the helper threads load the x/y halo):
-//           ghost fill (same-level read, outflow clamp, or AMR lookup) and
-//           conserved -> primitive (double-precision pressure for FP32 bulk)
-//         sync; x- and y-face fluxes of plane z into shared memory (the 32
-//           extra faces of the +x / +y block boundary by one rotating warp);
-//           the z-face z+1/2 flux from the thread's own column (registers)
-//         sync; update of cell (x, y, z): flux divergence with the z-face
-//           flux carried from the previous plane, psi damping, SSPRK
+//   3D: march over z with a ring of 4 primitive planes in shared memory, each
+//       with its 2-cell x/y halo.  Iteration z:
+//         cp.async copies of plane z+2 (own column; helpers: the x/y halo):
+//           same-level neighbour, outflow clamp or the ghost slab of a
+//           level-change face (built before the launch by k_ghost_slabs);
+//           for stages k > 0 also U0 of the owner's cell of plane z;
+//         x- and y-face fluxes of plane z into shared memory (double-buffered
+//           by plane parity);
+//         wait for the copies, conserved -> primitive of plane z+2 in place
+//           (float-float or fp64 pressure for FP32 bulk);
+//         the z-face z+1/2 flux of the thread's own column (registers);
+//         one barrier; update of cell (x, y, z): flux divergence with the
+//           z-face flux carried from the previous plane, psi damping, SSPRK
 //           combination; in the last stage the CFL terms of the new state
 //           (reduced per block for the time step).
 //   2D: the same with one plane and no z faces.
@@ -185,10 +188,106 @@ __device__ __forceinline__ void stencil_flux(Acc S, int glm, T g, T ch, T* f) {
   face_flux_d<T, D>(FLUX, glm, g, ch, wl, wr, f);
 }
 
+// Ghost values of every level-change face of the mesh, from the stage input
+// Uk: restriction (mean of the finer children) where the neighbour is finer,
+// prolongation (coarse value plus minmod-limited slopes times +-1/4, slopes
+// computed once per coarse cell) where it is coarser.  One CTA per face at a
+// time; slab gi belongs to face glist[gi] = block * 6 + face and holds
+// [v][layer][t2][t1], layer = ghost index along the normal from the low end
+// (cells -2, -1 on a low face, 16, 17 on a high face).
+template <class T, int DIM>
+__global__ void __launch_bounds__(256)
+    k_ghost_slabs(DevMesh M, const T* __restrict__ Uk, T* __restrict__ gslab,
+                  const int* __restrict__ glist, int ngen) {
+  constexpr int NT2 = DIM == 3 ? FB : 1;
+  constexpr int SLAB_FACE = NV * 2 * FB * NT2;
+  constexpr int NC2 = DIM == 3 ? FB / 2 : 1;
+  __shared__ T cs[(FB / 2) * NC2 * (1 + DIM) * NV];  // [coarse cell][value, slopes][v]
+  const int tid = threadIdx.x;
+  const size_t vs = (size_t)M.nblocks * M.ncell;
+  for (int gi = blockIdx.x; gi < ngen; gi += gridDim.x) {
+    const int b = glist[gi] / 6, f = glist[gi] % 6;
+    const int q = M.blk[b * 5], L = M.blk[b * 5 + 1];
+    const int bidx[3] = {M.blk[b * 5 + 2], M.blk[b * 5 + 3], M.blk[b * 5 + 4]};
+    const int d = f >> 1, side = f & 1;
+    // global level-L index of ghost (layer, t1, t2) of this face
+    auto ghost_p = [&](int layer, int t1, int t2, int* p) {
+      int loc[3];
+      const int n = side ? FB + layer : layer - 2;
+      if (d == 0) { loc[0] = n; loc[1] = t1; loc[2] = t2; }
+      else if (d == 1) { loc[0] = t1; loc[1] = n; loc[2] = t2; }
+      else { loc[0] = t1; loc[1] = t2; loc[2] = n; }
+#pragma unroll
+      for (int e = 0; e < 3; e++) p[e] = e < DIM ? bidx[e] * FB + loc[e] : 0;
+      wrap_level(M, q, L, p);
+    };
+    int pn[3];
+    ghost_p(0, 0, 0, pn);
+    int cell;
+    const int code = map_at(M, q, L, pn, &cell);
+    T* sf = gslab + (size_t)gi * SLAB_FACE;
+    if (code == MAP_REFINED) {
+      // restriction: mean of the finer children
+      for (int e = tid; e < 2 * FB * NT2; e += blockDim.x) {
+        const int t1 = e % FB, t2 = (e / FB) % NT2, layer = e / (FB * NT2);
+        int p[3];
+        ghost_p(layer, t1, t2, p);
+        T u[NV];
+        level_value_down(M, Uk, vs, q, L, p, u);
+#pragma unroll
+        for (int v = 0; v < NV; v++) sf[((v * 2 + layer) * NT2 + t2) * FB + t1] = u[v];
+      }
+    } else {
+      // prolongation: value and minmod slopes once per coarse cell ...
+      for (int e = tid; e < (FB / 2) * NC2 * DIM; e += blockDim.x) {
+        const int dd = e % DIM, cc = e / DIM;
+        const int ct1 = cc % (FB / 2), ct2 = cc / (FB / 2);
+        int p[3];
+        ghost_p(0, 2 * ct1, 2 * ct2, p);
+        int qc[3];
+#pragma unroll
+        for (int k2 = 0; k2 < 3; k2++) qc[k2] = k2 < DIM ? (p[k2] >> 1) : 0;
+        T uc[NV], um[NV], up[NV];
+        level_value_down(M, Uk, vs, q, L - 1, qc, uc);
+        int qm[3] = {qc[0], qc[1], qc[2]}, qp[3] = {qc[0], qc[1], qc[2]};
+        qm[dd] -= 1;
+        qp[dd] += 1;
+        level_value_down(M, Uk, vs, q, L - 1, qm, um);
+        level_value_down(M, Uk, vs, q, L - 1, qp, up);
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+          cs[(cc * (1 + DIM) + 1 + dd) * NV + v] = minmod_g(uc[v] - um[v], up[v] - uc[v]);
+          if (dd == 0) cs[(cc * (1 + DIM)) * NV + v] = uc[v];
+        }
+      }
+      __syncthreads();
+      // ... then every fine ghost: coarse value + sum_d (+-1/4) slope_d
+      for (int e = tid; e < 2 * FB * NT2; e += blockDim.x) {
+        const int t1 = e % FB, t2 = (e / FB) % NT2, layer = e / (FB * NT2);
+        int p[3];
+        ghost_p(layer, t1, t2, p);
+        const int cc = (t2 >> 1) * (FB / 2) + (t1 >> 1);
+        const T* c0 = cs + (cc * (1 + DIM)) * NV;
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+          T val = c0[v];
+#pragma unroll
+          for (int dd = 0; dd < DIM; dd++) {
+            const T wgt = (p[dd] & 1) ? T(0.25) : T(-0.25);
+            val = val + wgt * c0[(1 + dd) * NV + v];
+          }
+          sf[((v * 2 + layer) * NT2 + t2) * FB + t1] = val;
+        }
+      }
+    }
+    __syncthreads();  // cs is reused by the next face
+  }
+}
+
 template <class T, int DIM, int LIM, int FLUX>
 __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
     k_fused(DevMesh M, const T* U0, const T* __restrict__ Uk, T* out,
-            const int* __restrict__ work, int nwork, T* __restrict__ slab_all,
+            const int* __restrict__ work, int nwork, const T* __restrict__ gslab,
             int* __restrict__ counter, StageParams sp) {
   extern __shared__ __align__(16) unsigned char smraw[];
   FusedSmem<T, DIM>& S = *reinterpret_cast<FusedSmem<T, DIM>*>(smraw);
@@ -201,7 +300,6 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
   const bool ff = sp.pressure_ff != 0;
   constexpr int NT2 = DIM == 3 ? FB : 1;          // second tangential extent of a face
   constexpr int SLAB_FACE = NV * 2 * FB * NT2;    // one face: [v][layer][t2][t1]
-  T* __restrict__ slab = slab_all + (size_t)blockIdx.x * (2 * DIM) * SLAB_FACE;
 
   const bool owner = tid < FB * FB;
   const int hr = tid - FB * FB;  // helper index 0..15
@@ -270,100 +368,18 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
       if (tid == 0) S.damp = sp.glm ? exp(-sp.glm_alpha * rt.ch * rt.dt / dxmin) : 1.0;
     }
 
-    // ---- ghost values of level-change faces: built once per block into this
-    // CTA's slab scratch (all threads), then read like a neighbour block
+    // face neighbour codes; a level-change face reads its ghost slab, built
+    // from the stage input by k_ghost_slabs: code -3 - (slab index)
     int nb[6];
 #pragma unroll
-    for (int f = 0; f < 6; f++) nb[f] = f < 2 * DIM ? M.nbr[b * 6 + f] : NBR_OUTFLOW;
-    bool any_general = false;
-#pragma unroll
-    for (int f = 0; f < 2 * DIM; f++) any_general |= nb[f] == NBR_GENERAL;
-    __syncthreads();  // the previous block is done with the shared scratch
-    if (any_general) {
-      const int bidx[3] = {M.blk[b * 5 + 2], M.blk[b * 5 + 3], M.blk[b * 5 + 4]};
-      T* cs = &S.fx[0][0][0][0];  // coarse value + slopes, [cell][1 + DIM][NV]
-      for (int f = 0; f < 2 * DIM; f++) {
-        if (nb[f] != NBR_GENERAL) continue;
-        const int d = f >> 1, side = f & 1;
-        // global level-L index of ghost (layer, t1, t2) of this face
-        auto ghost_p = [&](int layer, int t1, int t2, int* p) {
-          int loc[3];
-          const int n = side ? FB + layer : layer - 2;
-          if (d == 0) { loc[0] = n; loc[1] = t1; loc[2] = t2; }
-          else if (d == 1) { loc[0] = t1; loc[1] = n; loc[2] = t2; }
-          else { loc[0] = t1; loc[1] = t2; loc[2] = n; }
-#pragma unroll
-          for (int e = 0; e < 3; e++) p[e] = e < DIM ? bidx[e] * FB + loc[e] : 0;
-          wrap_level(M, q, L, p);
-        };
-        int pn[3];
-        ghost_p(0, 0, 0, pn);
-        int cell;
-        const int code = map_at(M, q, L, pn, &cell);
-        T* sf = slab + f * SLAB_FACE;
-        if (code == MAP_REFINED) {
-          // restriction: mean of the finer children
-          for (int e = tid; e < 2 * FB * NT2; e += FT) {
-            const int t1 = e % FB, t2 = (e / FB) % NT2, layer = e / (FB * NT2);
-            int p[3];
-            ghost_p(layer, t1, t2, p);
-            T u[NV];
-            level_value_down(M, Uk, vs, q, L, p, u);
-#pragma unroll
-            for (int v = 0; v < NV; v++) sf[((v * 2 + layer) * NT2 + t2) * FB + t1] = u[v];
-          }
-        } else {
-          // prolongation: value and minmod slopes once per coarse cell ...
-          constexpr int NC2 = DIM == 3 ? FB / 2 : 1;
-          for (int e = tid; e < (FB / 2) * NC2 * DIM; e += FT) {
-            const int dd = e % DIM, cc = e / DIM;
-            const int ct1 = cc % (FB / 2), ct2 = cc / (FB / 2);
-            int p[3];
-            ghost_p(0, 2 * ct1, 2 * ct2, p);
-            int qc[3];
-#pragma unroll
-            for (int k2 = 0; k2 < 3; k2++) qc[k2] = k2 < DIM ? (p[k2] >> 1) : 0;
-            T uc[NV], um[NV], up[NV];
-            level_value_down(M, Uk, vs, q, L - 1, qc, uc);
-            int qm[3] = {qc[0], qc[1], qc[2]}, qp[3] = {qc[0], qc[1], qc[2]};
-            qm[dd] -= 1;
-            qp[dd] += 1;
-            level_value_down(M, Uk, vs, q, L - 1, qm, um);
-            level_value_down(M, Uk, vs, q, L - 1, qp, up);
-#pragma unroll
-            for (int v = 0; v < NV; v++) {
-              cs[(cc * (1 + DIM) + 1 + dd) * NV + v] = minmod_g(uc[v] - um[v], up[v] - uc[v]);
-              if (dd == 0) cs[(cc * (1 + DIM)) * NV + v] = uc[v];
-            }
-          }
-          __syncthreads();
-          // ... then every fine ghost: coarse value + sum_d (+-1/4) slope_d
-          for (int e = tid; e < 2 * FB * NT2; e += FT) {
-            const int t1 = e % FB, t2 = (e / FB) % NT2, layer = e / (FB * NT2);
-            int p[3];
-            ghost_p(layer, t1, t2, p);
-            const int cc = (t2 >> 1) * (FB / 2) + (t1 >> 1);
-            const T* c0 = cs + (cc * (1 + DIM)) * NV;
-#pragma unroll
-            for (int v = 0; v < NV; v++) {
-              T val = c0[v];
-#pragma unroll
-              for (int dd = 0; dd < DIM; dd++) {
-                const T wgt = (p[dd] & 1) ? T(0.25) : T(-0.25);
-                val = val + wgt * c0[(1 + dd) * NV + v];
-              }
-              sf[((v * 2 + layer) * NT2 + t2) * FB + t1] = val;
-            }
-          }
-          __syncthreads();  // cs is reused by the next face
-        }
-      }
-      __syncthreads();
+    for (int f = 0; f < 6; f++) {
+      nb[f] = f < 2 * DIM ? M.nbr[b * 6 + f] : NBR_OUTFLOW;
+      if (nb[f] == NBR_GENERAL) nb[f] = -3 - M.gface[b * 6 + f];
     }
 
     // location of the conserved values of block-local cell (i, j, k), at most
     // one index outside: own block, same-level neighbour (wrapped index),
-    // outflow clamp (own block) or this CTA's ghost slab; vstride between vars
+    // outflow clamp (own block) or the face's ghost slab; vstride between vars
     auto locate = [&](int i, int j, int k, const T*& ptr, size_t& vstride) {
       int f = -1, n = 0, t1 = 0, t2 = 0;
       if (i < 0 || i >= FB) { f = i < 0 ? 0 : 1; n = i; t1 = j; t2 = k; }
@@ -375,9 +391,9 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
         return;
       }
       const int code = nb[f];
-      if (code == NBR_GENERAL) {
+      if (code <= -3) {
         const int layer = n < 0 ? n + 2 : n - FB;
-        ptr = slab + f * SLAB_FACE + (layer * NT2 + t2) * FB + t1;
+        ptr = gslab + (size_t)(-3 - code) * SLAB_FACE + (layer * NT2 + t2) * FB + t1;
         vstride = 2 * NT2 * FB;
         return;
       }
@@ -581,12 +597,19 @@ static int launch_one(amrvac_state* s, const T* U0, const T* Uk, T* out, StagePa
   int ctas = s->tune.ctas_per_sm > 0 && s->tune.ctas_per_sm < per_sm ? s->tune.ctas_per_sm : per_sm;
   int grid = nsm * ctas;
   if (grid > s->nwork) grid = s->nwork;
-  if (grid > s->slab_ctas) grid = s->slab_ctas;
   int n = 1;
+  if (s->ngen > 0) {
+    // ghost slabs of the level-change faces of the stage input
+    const int g = s->ngen < nsm * 8 ? s->ngen : nsm * 8;
+    k_ghost_slabs<T, DIM><<<g, 256, 0, s->stream>>>(s->mesh, Uk, (T*)s->gslab, s->d_glist,
+                                                     s->ngen);
+    n++;
+  }
   if (s->tune.dynamic) {
     if (cudaMemsetAsync(s->d_counter, 0, sizeof(int), s->stream) != cudaSuccess) return -1;
   }
-  kern<<<grid, FT, smem, s->stream>>>(s->mesh, U0, Uk, out, s->d_work, s->nwork, (T*)s->slab,
+  kern<<<grid, FT, smem, s->stream>>>(s->mesh, U0, Uk, out, s->d_work, s->nwork,
+                                       (const T*)s->gslab,
                                        s->tune.dynamic ? s->d_counter : nullptr, sp);
   return cudaPeekAtLastError() == cudaSuccess ? n : -1;
 }

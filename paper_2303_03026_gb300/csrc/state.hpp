@@ -29,10 +29,11 @@ struct amrvac_state {
   // fused-path work list: blocks grouped for the persistent kernel
   int* d_work = nullptr;
   int nwork = 0;
-  // fused path: per-CTA ghost slabs of level-change faces (2*ndim faces x 2
-  // layers x 16 x 16 cells x 9 vars per CTA)
-  void* slab = nullptr;
-  int slab_ctas = 0;
+  // fused path: ghost slabs of the level-change faces (2 layers x 16 x 16
+  // cells x 9 vars each), rebuilt from the stage input before every stage
+  void* gslab = nullptr;
+  int* d_glist = nullptr;  // [ngen] b * 6 + face
+  int ngen = 0;
   // launch shape of the fused kernel (see amrvac_tuning)
   amrvac_tuning tune{0, 0, 0, 0.0};
   int* d_work_morton = nullptr;
