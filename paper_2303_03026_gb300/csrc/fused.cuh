@@ -1,4 +1,5 @@
-// Fused persistent stage kernel for 16x16 (2D) and 16x16x16 (3D) blocks.
+// Fused persistent stage kernels for 16x16x16 (3D, here) and 16x16 (2D,
+// fused2d.cuh) blocks.
 //
 // One CTA of 272 threads owns one block at a time and loops over the work
 // list (grid = resident CTAs).  Thread (x, y) < 256 owns a column of the block;
@@ -18,7 +19,7 @@
 //           z-face flux carried from the previous plane, psi damping, SSPRK
 //           combination; in the last stage the CFL terms of the new state
 //           (reduced per block for the time step).
-//   2D: the same with one plane and no z faces.
+//   2D: k_fused2d (fused2d.cuh), pipelined over blocks instead of planes.
 // Every face flux of the block is computed once (block-boundary faces are
 // computed by both neighbours).  Arithmetic follows physics.cuh.
 #pragma once
@@ -290,6 +291,7 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
             const int* __restrict__ work, int nwork, const T* __restrict__ gslab,
             int* __restrict__ counter, StageParams sp) {
   extern __shared__ __align__(16) unsigned char smraw[];
+  static_assert(DIM == 3, "16x16 blocks in 2D use k_fused2d");
   FusedSmem<T, DIM>& S = *reinterpret_cast<FusedSmem<T, DIM>*>(smraw);
   constexpr int NZ = DIM == 3 ? FB : 1;
   constexpr int NSLOT = FusedSmem<T, DIM>::NSLOT;
@@ -418,29 +420,7 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
       for (int v = 0; v < NV; v++) cell[v * FPW * FPW] = w[v];
     };
 
-    // 2D: synchronous load + conversion of the single plane
-    auto load_plane = [&](int pz) {
-      const int slot = ((pz % NSLOT) + NSLOT) % NSLOT;
-      const T* ptr;
-      size_t st;
-      if (owner) {
-        locate(x, y, 0, ptr, st);
-#pragma unroll
-        for (int v = 0; v < NV; v++) S.plane[slot][v][y + NG][x + NG] = ptr[v * st];
-        to_prim(&S.plane[slot][0][y + NG][x + NG], 0);
-      } else {
-        for (int m = 0; m < 8; m++) {
-          int hx, hy;
-          halo_xy(hr + FB * m, hx, hy);
-          locate(hx, hy, 0, ptr, st);
-#pragma unroll
-          for (int v = 0; v < NV; v++) S.plane[slot][v][hy + NG][hx + NG] = ptr[v * st];
-          to_prim(&S.plane[slot][0][hy + NG][hx + NG], 1);
-        }
-      }
-    };
-
-    // 3D: asynchronous copy of plane pz's conserved values into its ring slot
+    // asynchronous copy of plane pz's conserved values into its ring slot
     // (own column; threads 0..127 also their halo cell of interior planes) ...
     auto issue_plane = [&](int pz) {
       const int slot = ((pz % NSLOT) + NSLOT) % NSLOT;
@@ -489,14 +469,10 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
     };
 
     T fzp[NV];
-    if (DIM == 3) {
-      for (int pz = -2; pz <= 1; pz++) issue_plane(pz);
-      cp_async_wait_all();
-      for (int pz = -2; pz <= 1; pz++) convert_plane(pz);
-      if (owner) zflux(0, fzp);  // own column only
-    } else {
-      load_plane(0);
-    }
+    for (int pz = -2; pz <= 1; pz++) issue_plane(pz);
+    cp_async_wait_all();
+    for (int pz = -2; pz <= 1; pz++) convert_plane(pz);
+    if (owner) zflux(0, fzp);  // own column only
     __syncthreads();  // planes 0 and 1 (with halos) visible to all threads
 
     if constexpr (sizeof(T) == 8) {
@@ -523,8 +499,7 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
 #pragma unroll
         for (int v = 0; v < NV; v++) cp_async_elem_after_reads(&S.u0[v][tid], src + v * vs);
       }
-      if (DIM == 3) issue_plane(z + 2);  // commits this thread's copies as one group
-      else if (pre0) cp_async_commit();
+      issue_plane(z + 2);  // commits this thread's copies as one group
       const int sl = z % NSLOT, fb = z & 1;
       {
         // owners: the x and y faces on the low side of their cell; helpers: the
@@ -548,7 +523,6 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
         cp_async_wait_all();
         convert_plane(z + 2);
       }
-      if (DIM != 3 && pre0) cp_async_wait_all();
       T fz[NV];
       if (DIM == 3 && owner) zflux(z + 1, fz);
       __syncthreads();
@@ -577,12 +551,18 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
   }
 }
 
+}  // namespace amrvac
+
+#include "fused2d.cuh"
+
+namespace amrvac {
+
 // ---------------------------------------------------------------- launcher
 
 template <class T, int DIM, int LIM, int FLUX>
 static int launch_one(amrvac_state* s, const T* U0, const T* Uk, T* out, StageParams sp) {
-  auto kern = k_fused<T, DIM, LIM, FLUX>;
-  const int smem = (int)sizeof(FusedSmem<T, DIM>);
+  auto kern = DIM == 3 ? k_fused<T, 3, LIM, FLUX> : k_fused2d<T, LIM, FLUX>;
+  const int smem = DIM == 3 ? (int)sizeof(FusedSmem<T, 3>) : (int)sizeof(Fused2dSmem<T>);
   static int nsm = 0, per_sm = 0;  // per instantiation, this device
   if (nsm == 0) {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
