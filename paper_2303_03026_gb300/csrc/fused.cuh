@@ -3,17 +3,19 @@
 //
 // One CTA of 272 threads owns one block at a time and loops over the work
 // list (grid = resident CTAs).  Thread (x, y) < 256 owns a column of the block;
-// 16 helper threads take the +x/+y block-boundary faces and the halo cells.
+// 16 helper threads take the +x/+y block-boundary faces and convert the halo.
 //   3D: march over z with a ring of 4 primitive planes in shared memory, each
 //       with its 2-cell x/y halo.  Iteration z:
-//         cp.async copies of plane z+2 (own column; helpers: the x/y halo):
+//         cp.async copies of plane z+2 (own column; threads 0..127: one x/y
+//           halo cell each):
 //           same-level neighbour, outflow clamp or the ghost slab of a
 //           level-change face (built before the launch by k_ghost_slabs);
 //           for stages k > 0 also U0 of the owner's cell of plane z;
 //         x- and y-face fluxes of plane z into shared memory (double-buffered
 //           by plane parity);
-//         wait for the copies, conserved -> primitive of plane z+2 in place
-//           (float-float or fp64 pressure for FP32 bulk);
+//         wait for the copies, conserved -> primitive in place of the own
+//           cells of plane z+2 and (helpers, eight cells each) of the halo
+//           of plane z+1 (float-float or fp64 pressure for FP32 bulk);
 //         the z-face z+1/2 flux of the thread's own column (registers);
 //         one barrier; update of cell (x, y, z): flux divergence with the
 //           z-face flux carried from the previous plane, psi damping, SSPRK
@@ -431,10 +433,9 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
 #pragma unroll
         for (int v = 0; v < NV; v++)
           cp_async_elem(&S.plane[slot][v][y + NG][x + NG], ptr + v * st);
-      } else if (pz >= 0 && pz < NZ) {
-        for (int m = 0; m < 8; m++) {
+        if (tid < 128 && pz >= 0 && pz < NZ) {
           int hx, hy;
-          halo_xy(hr + FB * m, hx, hy);
+          halo_xy(tid, hx, hy);
           locate(hx, hy, pz, ptr, st);
 #pragma unroll
           for (int v = 0; v < NV; v++)
@@ -443,17 +444,20 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
       }
       cp_async_commit();
     };
-    // ... and, once this thread's copies have landed, their in-place conversion
+    // ... once this thread's copies have landed, the owner's in-place
+    // conversion of its own cell ...
     auto convert_plane = [&](int pz) {
       const int slot = ((pz % NSLOT) + NSLOT) % NSLOT;
-      if (owner) {
-        to_prim(&S.plane[slot][0][y + NG][x + NG], 0);
-      } else if (pz >= 0 && pz < NZ) {
-        for (int m = 0; m < 8; m++) {
-          int hx, hy;
-          halo_xy(hr + FB * m, hx, hy);
-          to_prim(&S.plane[slot][0][hy + NG][hx + NG], 1);
-        }
+      if (owner) to_prim(&S.plane[slot][0][y + NG][x + NG], 0);
+    };
+    // ... and, one barrier after its copies landed, the helpers' conversion of
+    // the halo of plane pz (eight cells each)
+    auto convert_halo = [&](int pz) {
+      const int slot = ((pz % NSLOT) + NSLOT) % NSLOT;
+      for (int m = 0; m < 8; m++) {
+        int hx, hy;
+        halo_xy(hr + FB * m, hx, hy);
+        to_prim(&S.plane[slot][0][hy + NG][hx + NG], 1);
       }
     };
 
@@ -473,7 +477,9 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
     cp_async_wait_all();
     for (int pz = -2; pz <= 1; pz++) convert_plane(pz);
     if (owner) zflux(0, fzp);  // own column only
-    __syncthreads();  // planes 0 and 1 (with halos) visible to all threads
+    __syncthreads();  // the halo copies of planes 0 and 1 are visible
+    if (!owner) convert_halo(0);
+    __syncthreads();  // plane 0 with its halo in primitives
 
     if constexpr (sizeof(T) == 8) {
       __syncthreads();
@@ -483,9 +489,9 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
     // One barrier per plane.  Iteration z: issue the copies of U0 of plane z
     // (stages k > 0) and of plane z+2 into the slot of plane z-2 (its last
     // readers were the faces of plane z-2 and this thread's own z face of
-    // iteration z-1); x/y faces of plane z into the
-    // flux buffer of parity z; wait for and convert plane z+2; z face z+1/2;
-    // barrier; update of plane z.  The buffer of parity z is rewritten at
+    // iteration z-1); x/y faces of plane z into the flux buffer of parity z;
+    // wait for and convert the own cells of plane z+2, convert the halo of
+    // plane z+1; z face z+1/2; barrier; update of plane z.  The buffer of parity z is rewritten at
     // iteration z+2, after the barrier of iteration z+1, which every thread
     // passes only after its update of plane z.
     constexpr bool PRE0 = sizeof(T) == 4;
@@ -517,12 +523,12 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
 #pragma unroll
         for (int v = 0; v < NV; v++) S.fy[fb][v][fyr][fyc] = f[v];
       }
-      // plane z+2 -> primitives (owners: own column, needed by the z face below;
-      // helpers: the halo, needed two planes later)
-      if (DIM == 3) {
-        cp_async_wait_all();
-        convert_plane(z + 2);
-      }
+      // owners: own cell of plane z+2 -> primitives (needed by the z face
+      // below); helpers: the halo of plane z+1, whose copies the owners
+      // waited for before the previous barrier (needed next iteration)
+      cp_async_wait_all();
+      convert_plane(z + 2);
+      if (!owner && z + 1 < NZ) convert_halo(z + 1);
       T fz[NV];
       if (DIM == 3 && owner) zflux(z + 1, fz);
       __syncthreads();
