@@ -3,7 +3,7 @@
 //
 // One CTA of 272 threads owns one block at a time and loops over the work
 // list (grid = resident CTAs).  Thread (x, y) < 256 owns a column of the block;
-// 16 helper threads take the +x/+y block-boundary faces and convert the halo.
+// 16 helper threads take the 32 faces on the +x/+y block boundary.
 //   3D: march over z with a ring of 4 primitive planes in shared memory, each
 //       with its 2-cell x/y halo.  Iteration z:
 //         cp.async copies of plane z+2 (own column; threads 0..127: one x/y
@@ -14,8 +14,8 @@
 //         x- and y-face fluxes of plane z into shared memory (double-buffered
 //           by plane parity);
 //         wait for the copies, conserved -> primitive in place of the own
-//           cells of plane z+2 and (helpers, eight cells each) of the halo
-//           of plane z+1 (float-float or fp64 pressure for FP32 bulk);
+//           cells of plane z+2 and (owners 128..255, one cell each) of the
+//           halo of plane z+1 (float-float or fp64 pressure for FP32 bulk);
 //         the z-face z+1/2 flux of the thread's own column (registers);
 //         one barrier; update of cell (x, y, z): flux divergence with the
 //           z-face flux carried from the previous plane, psi damping, SSPRK
@@ -36,9 +36,10 @@ namespace amrvac {
 
 constexpr int FB = 16;          // block edge handled by the fused kernel
 // threads per CTA: 256 column owners (x- and y-face of their cell, z-face of
-// their column, their cell's update) and 16 helpers (the 32 faces on the +x/+y
-// block boundary and the 128 x/y halo cells of each plane), so that every warp
-// carries about three flux evaluations per plane
+// their column, their cell's update; owners 0..127 also copy in and owners
+// 128..255 convert one of the 128 x/y halo cells of each plane) and 16
+// helpers (the 32 faces on the +x/+y block boundary).  The 2D kernel uses the
+// same roles with threads 0..127 copying and converting the halo.
 constexpr int FT = FB * FB + FB;
 constexpr int FPW = FB + 2 * NG;  // padded plane width (row stride 20 floats)
 constexpr int FXW = 20;           // row stride of the face-flux arrays
@@ -450,13 +451,13 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
       const int slot = ((pz % NSLOT) + NSLOT) % NSLOT;
       if (owner) to_prim(&S.plane[slot][0][y + NG][x + NG], 0);
     };
-    // ... and, one barrier after its copies landed, the helpers' conversion of
-    // the halo of plane pz (eight cells each)
+    // ... and, one barrier after their copies landed, the conversion of the
+    // halo cells of plane pz by owners 128..255 (one cell each)
     auto convert_halo = [&](int pz) {
       const int slot = ((pz % NSLOT) + NSLOT) % NSLOT;
-      for (int m = 0; m < 8; m++) {
+      if (tid >= 128 && tid < 256) {
         int hx, hy;
-        halo_xy(hr + FB * m, hx, hy);
+        halo_xy(tid - 128, hx, hy);
         to_prim(&S.plane[slot][0][hy + NG][hx + NG], 1);
       }
     };
@@ -478,7 +479,7 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
     for (int pz = -2; pz <= 1; pz++) convert_plane(pz);
     if (owner) zflux(0, fzp);  // own column only
     __syncthreads();  // the halo copies of planes 0 and 1 are visible
-    if (!owner) convert_halo(0);
+    convert_halo(0);
     __syncthreads();  // plane 0 with its halo in primitives
 
     if constexpr (sizeof(T) == 8) {
@@ -491,7 +492,7 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
     // readers were the faces of plane z-2 and this thread's own z face of
     // iteration z-1); x/y faces of plane z into the flux buffer of parity z;
     // wait for and convert the own cells of plane z+2, convert the halo of
-    // plane z+1; z face z+1/2; barrier; update of plane z.  The buffer of parity z is rewritten at
+    // plane z+1 (owners 128..255); z face z+1/2; barrier; update of plane z.  The buffer of parity z is rewritten at
     // iteration z+2, after the barrier of iteration z+1, which every thread
     // passes only after its update of plane z.
     constexpr bool PRE0 = sizeof(T) == 4;
@@ -524,11 +525,12 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
         for (int v = 0; v < NV; v++) S.fy[fb][v][fyr][fyc] = f[v];
       }
       // owners: own cell of plane z+2 -> primitives (needed by the z face
-      // below); helpers: the halo of plane z+1, whose copies the owners
-      // waited for before the previous barrier (needed next iteration)
+      // below); owners 128..255 also a halo cell of plane z+1, whose copies
+      // owners 0..127 waited for before the previous barrier (needed next
+      // iteration)
       cp_async_wait_all();
       convert_plane(z + 2);
-      if (!owner && z + 1 < NZ) convert_halo(z + 1);
+      if (z + 1 < NZ) convert_halo(z + 1);
       T fz[NV];
       if (DIM == 3 && owner) zflux(z + 1, fz);
       __syncthreads();
