@@ -237,19 +237,20 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def traffic_from_profile(workload, size, kernel_digest):
-    """DRAM bytes per cell-update of the fused stage kernel from the committed
-    ncu summary, when it was taken on the current build (else None)."""
-    path = os.path.join(ROOT, "profiles", "k_fused_dram_traffic.txt")
+def counters_from_profile(workload, kernel_digest):
+    """Per cell-update counters of the fused stage kernel (DRAM bytes, warp
+    instructions) from the committed ncu summary, when it was taken on the
+    current build (else {})."""
+    path = os.path.join(ROOT, "profiles", "k_fused_c4_counters.txt")
     try:
         rows = [r.split() for r in open(path) if r.strip() and not r.startswith("#")]
     except OSError:
-        return None
+        return {}
     for r in rows:
         kv = dict(x.split("=", 1) for x in r if "=" in x)
         if kv.get("workload") == workload and kv.get("build") == kernel_digest:
-            return float(kv["dram_bytes_per_cell_step"])
-    return None
+            return kv
+    return {}
 
 
 def max_over_ranks(value, device):
@@ -333,6 +334,7 @@ def main():
         ev1.record(stream)
         barrier()
     launches = S.launches - n0
+    clocks = clk.summary()
     ms = max_over_ranks(ev0.elapsed_time(ev1), dev)
     ms_step = ms / args.steps
     value = cells * ws * args.steps / (ms / 1e3)
@@ -360,15 +362,32 @@ def main():
     achieved = sum(alg_bytes) / (sum(stage_ms) / 1e3) / 1e9
     fused = args.kernel != "plain" and (W.cfg.block_nx[0] == 16)
     digest = libbuild._digest()[:16]
-    tr = traffic_from_profile(args.workload + (str(args.size) if args.size else ""), args.size,
-                              digest) if fused else None
+    kv = counters_from_profile(args.workload + (str(args.size) if args.size else ""),
+                               digest) if fused and W.cfg.flux == "hlld" else {}
+    tr = float(kv["dram_bytes_per_cell_step"]) if "dram_bytes_per_cell_step" in kv else None
+    # issue ceiling beside the HBM bound: one warp instruction per cycle per
+    # SM sub-partition (4 per SM) at the SM clock sampled during the timed steps
+    issue = None
+    if "warp_inst_per_cell_step" in kv:
+        nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 0
+        ipc = float(kv["warp_inst_per_cell_step"])
+        if mhz:
+            peak_i = nsm * 4 * mhz * 1e6
+            ach_i = ipc * cells / (sum(stage_ms) / 1e3)
+            issue = {"achieved": ach_i, "peak": peak_i, "unit": "warp-instr/s",
+                     "frac": ach_i / peak_i, "warp_inst_per_cell_step": ipc,
+                     "peak_basis": "%d SMs x 4 issue slots x %.0f MHz (sampled)" % (nsm, mhz)}
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm,
                 "traffic": tr * cells / 3.0 if tr is not None else None,
                 "traffic_unit": "DRAM bytes per stage launch (ncu, mean of the 3 stages)",
                 "peak_source": src,
-                "kernel": "k_fused (one persistent launch per SSPRK stage)" if fused else
-                "plain per-block kernels (prim + flux x ndim + update) per stage",
+                "kernel": ("k_fused%s (one persistent launch per SSPRK stage, after the "
+                           "k_ghost_slabs pre-pass where the mesh has level-change faces; "
+                           "stage_ms covers both)" % ("" if W.cfg.ndim == 3 else "2d"))
+                if fused else "plain per-block kernels (prim + flux x ndim + update) per stage",
+                "issue_ceiling": issue,
                 "stage_ms": [float(x) for x in stage_ms],
                 "alg_bytes_per_cell_step": 288,
                 "alg_bytes_per_launch": [int(b) for b in alg_bytes],
@@ -494,7 +513,7 @@ def main():
                                          ("float-float" if args.pressure == "ff" else "fp64"),
                                kernel=args.kernel, build=digest, tuning=tuning,
                                parallelism="replicas" if ws > 1 else "1 GPU"),
-                "clocks": clk.summary(), "gpu_launches": launches, "roofline": roofline,
+                "clocks": clocks, "gpu_launches": launches, "roofline": roofline,
                 "e2e": e2e, "variants": variants or None, "one_at_a_time": one_at_a_time,
                 "fp64_plain": fp64, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)

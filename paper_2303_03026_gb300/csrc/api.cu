@@ -27,7 +27,7 @@ struct Tables {
 
 struct Layout {
   size_t U[3], W, F[3], part, blk, nbr, gface, glist, lmap, lmap_off, lnb, gamma, dx, istart,
-      iblocks, rt, sums, err, work, work2, counter, gslab, total;
+      iblocks, rt, sums, err, work, work2, counter, gslab, lcf, lcd, total;
 };
 
 bool config_ok(const amrvac_config* c, std::string& err) {
@@ -263,6 +263,8 @@ Layout make_layout(const amrvac_config* c, int ninst, int nblocks, const Tables&
   L.work2 = take(sizeof(int) * (size_t)nblocks);
   L.counter = take(sizeof(int) * 4);
   L.gslab = 0;
+  L.lcf = take(sizeof(float) * LC_N * MAXLEV * ninst);
+  L.lcd = take(sizeof(double) * LC_N * MAXLEV * ninst);
   if (fused) {
     size_t per = (size_t)NV * 2 * 16 * (c->ndim == 3 ? 16 : 1);  // one face
     L.gslab = take(rs * per * T.glist.size());
@@ -393,6 +395,8 @@ amrvac_status amrvac_state_create(const amrvac_config* cfg, int32_t ninst,
   M.part = at<double>(s, L.part);
   M.sums = at<double>(s, L.sums);
   M.err = at<int>(s, L.err);
+  M.lcf = at<float>(s, L.lcf);
+  M.lcd = at<double>(s, L.lcd);
   s->d_work = at<int>(s, L.work);
   s->d_work_morton = s->d_work;
   s->d_work_storage = at<int>(s, L.work2);

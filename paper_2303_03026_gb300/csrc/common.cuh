@@ -14,6 +14,11 @@ constexpr int NV = 9;       // rho, m_x, m_y, m_z, e, B_x, B_y, B_z, psi
 constexpr int NG = 2;       // ghost cells per face (vanleer/koren/minmod: limiter table)
 constexpr int MAXLEV = AMRVAC_MAX_LEVELS;
 constexpr int NPART = 12;   // per-block partials: smax, chmax, sums[9], pad
+// per-(instance, level) stage constants of the fused kernels, refreshed from
+// InstRT before every fused stage: dt, ch, psi damping factor, dx[3],
+// 1/dx[3], finished flag (dt == 0), gamma, gamma - 1
+constexpr int LC_N = 12;
+enum { LC_DT = 0, LC_CH = 1, LC_DAMP = 2, LC_DX = 3, LC_IDX = 6, LC_SKIP = 9, LC_G = 10, LC_GM1 = 11 };
 
 // face neighbour codes in DevMesh::nbr
 constexpr int NBR_OUTFLOW = -1;  // physical zero-gradient boundary
@@ -47,7 +52,17 @@ struct DevMesh {
   double* part;           // [nblocks][NPART]
   double* sums;           // [ninst][NV]
   int* err;               // [4] code, block, cell, var
+  float* lcf;             // [ninst][MAXLEV][LC_N] stage constants, float (FP32 bulk)
+  double* lcd;            // [ninst][MAXLEV][LC_N] stage constants, double (FP64)
 };
+
+template <class T> __device__ __forceinline__ const T* level_consts(const DevMesh& M);
+template <> __device__ __forceinline__ const float* level_consts<float>(const DevMesh& M) {
+  return M.lcf;
+}
+template <> __device__ __forceinline__ const double* level_consts<double>(const DevMesh& M) {
+  return M.lcd;
+}
 
 struct StageParams {
   int k;                 // stage index
@@ -59,7 +74,14 @@ struct StageParams {
   int flux, limiter, glm;
   int epilogue;          // 1: per-block dt / sums partials of the output
   int pressure_ff;       // FP32 bulk: float-float pressure recovery and sums
+  float af, bf;          // a, b, small_density, small_pressure rounded to float
+  float small_density_f, small_pressure_f;
 };
+
+// a StageParams value in the kernel's arithmetic type (no conversion in-kernel)
+template <class T> __device__ __forceinline__ T sp_val(double d, float f);
+template <> __device__ __forceinline__ float sp_val<float>(double, float f) { return f; }
+template <> __device__ __forceinline__ double sp_val<double>(double d, float) { return d; }
 
 __device__ __forceinline__ void latch_error(int* err, int code, int b, int c, int v) {
   if (atomicCAS(err, 0, code) == 0) {

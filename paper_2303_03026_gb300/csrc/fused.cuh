@@ -62,7 +62,6 @@ template <class T, int DIM> struct FusedSmem {
   // double slot would not fit beside its planes)
   T u0[sizeof(T) == 4 ? NV : 1][FB * FB];
   double red[8][NPART];
-  double damp;
   int next;
 };
 
@@ -333,18 +332,17 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
   for (int wi = counter ? next_work(0) : blockIdx.x; wi < nwork; wi = next_work(wi)) {
     const int b = work[wi];
     const int q = M.blk[b * 5], L = M.blk[b * 5 + 1];
-    const InstRT rt = M.rt[q];
     const double gammad = M.gamma[q];
-    const T g = (T)gammad;
-    const float gm1f = (float)(gammad - 1.0);
-    const T rho_floor = (T)sp.small_density, p_floor = (T)sp.small_pressure;
-    const double* dxl = M.dx + (q * MAXLEV + L) * 3;
-    const double dxd[3] = {dxl[0], dxl[1], dxl[2]};
-
-    const T idd[3] = {T(1) / (T)dxd[0], T(1) / (T)dxd[1], T(1) / (T)dxd[2]};
+    // stage constants of the block's level in the arithmetic type
+    const T* lc = level_consts<T>(M) + (q * MAXLEV + L) * LC_N;
+    const T g = lc[LC_G];
+    const float gm1f = (float)lc[LC_GM1];
+    const T rho_floor = sp_val<T>(sp.small_density, sp.small_density_f);
+    const T p_floor = sp_val<T>(sp.small_pressure, sp.small_pressure_f);
+    const T idd[3] = {lc[LC_IDX], lc[LC_IDX + 1], lc[LC_IDX + 2]};
     T smx = T(0), cmx = T(0);  // CFL terms of the new state (last stage)
 
-    if (rt.dt == 0.0) {
+    if (lc[LC_SKIP] != T(0)) {
       // finished instance: copied through unchanged
       for (int c = tid; owner && c < ncell; c += FB * FB) {
         T u[NV];
@@ -360,18 +358,11 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
       continue;
     }
 
-    const T ch = (T)rt.ch, dt = (T)rt.dt, ca = (T)sp.a, cb = (T)sp.b;
-    const T dx0 = (T)dxd[0], dx1 = (T)dxd[1], dx2 = (T)dxd[2];
-    const T idx0 = T(1) / dx0, idx1 = T(1) / dx1, idx2 = T(1) / dx2;
-    double dxmin = fmin(dxd[0], dxd[1]);
-    if (DIM == 3) dxmin = fmin(dxmin, dxd[2]);
-    T damp;
-    if constexpr (sizeof(T) == 4) {
-      // float bulk: the damping factor in float (exp of a float argument)
-      damp = sp.glm ? expf((float)(-sp.glm_alpha * rt.ch * rt.dt / dxmin)) : 1.0f;
-    } else {
-      if (tid == 0) S.damp = sp.glm ? exp(-sp.glm_alpha * rt.ch * rt.dt / dxmin) : 1.0;
-    }
+    const T ch = lc[LC_CH], dt = lc[LC_DT];
+    const T ca = sp_val<T>(sp.a, sp.af), cb = sp_val<T>(sp.b, sp.bf);
+    const T dx0 = lc[LC_DX], dx1 = lc[LC_DX + 1], dx2 = lc[LC_DX + 2];
+    const T idx0 = idd[0], idx1 = idd[1], idx2 = idd[2];
+    const T damp = lc[LC_DAMP];
 
     // face neighbour codes; a level-change face reads its ghost slab, built
     // from the stage input by k_ghost_slabs: code -3 - (slab index)
@@ -482,10 +473,6 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
     convert_halo(0);
     __syncthreads();  // plane 0 with its halo in primitives
 
-    if constexpr (sizeof(T) == 8) {
-      __syncthreads();
-      damp = S.damp;
-    }
 
     // One barrier per plane.  Iteration z: issue the copies of U0 of plane z
     // (stages k > 0) and of plane z+2 into the slot of plane z-2 (its last
@@ -607,12 +594,14 @@ int launch_fused_l(amrvac_state* s, int k, int epilogue) {
   int u0, uin, uout;
   stage_buffers(s->cfg.time, k, &u0, &uin, &uout);
   StageParams sp = make_stage_params(s, k, epilogue);
+  if (launch_level_consts(s) < 0) return -1;
   const T* U0 = (const T*)s->U[u0];
   const T* Uk = (const T*)s->U[uin];
   T* out = (T*)s->U[uout];
-  if (s->cfg.flux == AMRVAC_FLUX_HLLD)
-    return launch_one<T, DIM, LIM, AMRVAC_FLUX_HLLD>(s, U0, Uk, out, sp);
-  return launch_one<T, DIM, LIM, AMRVAC_FLUX_HLL>(s, U0, Uk, out, sp);
+  const int n = s->cfg.flux == AMRVAC_FLUX_HLLD
+                    ? launch_one<T, DIM, LIM, AMRVAC_FLUX_HLLD>(s, U0, Uk, out, sp)
+                    : launch_one<T, DIM, LIM, AMRVAC_FLUX_HLL>(s, U0, Uk, out, sp);
+  return n < 0 ? -1 : n + 1;
 }
 
 }  // namespace amrvac

@@ -152,19 +152,17 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
       cp_async_wait_all();
     }
     const int q = M.blk[b * 5], L = M.blk[b * 5 + 1];
-    const InstRT rt = M.rt[q];
     const double gammad = M.gamma[q];
-    const T g = (T)gammad;
-    const float gm1f = (float)(gammad - 1.0);
-    const double* dxl = M.dx + (q * MAXLEV + L) * 3;
-    const double dxd[3] = {dxl[0], dxl[1], 1.0};
-    const T idd[3] = {T(1) / (T)dxd[0], T(1) / (T)dxd[1], T(0)};
+    const T* lc = level_consts<T>(M) + (q * MAXLEV + L) * LC_N;
+    const T g = lc[LC_G];
+    const float gm1f = (float)lc[LC_GM1];
+    const T idd[3] = {lc[LC_IDX], lc[LC_IDX + 1], T(0)};
     T smx = T(0), cmx = T(0);
     int wnn;
     double* part_b = M.part + (size_t)b * NPART;
     if (sp.epilogue && tid == 0) part_b[0] = part_b[1] = 0.0;
 
-    if (rt.dt == 0.0) {
+    if (lc[LC_SKIP] != T(0)) {
       // finished instance: copied through unchanged
       if (owner) {
         T u[NV];
@@ -180,7 +178,8 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
       __syncthreads();
       wnn = counter ? S.next : wn + gridDim.x;
     } else {
-      const T rho_floor = (T)sp.small_density, p_floor = (T)sp.small_pressure;
+      const T rho_floor = sp_val<T>(sp.small_density, sp.small_density_f);
+      const T p_floor = sp_val<T>(sp.small_pressure, sp.small_pressure_f);
       auto to_prim = [&](int i, int j, int which) {
         T u[NV], w[NV];
 #pragma unroll
@@ -196,7 +195,8 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
       __syncthreads();
       if (counter && tid == 0) S.next = atomicAdd(counter, 1);
 
-      const T ch = (T)rt.ch, dt = (T)rt.dt, ca = (T)sp.a, cb = (T)sp.b;
+      const T ch = lc[LC_CH], dt = lc[LC_DT];
+      const T ca = sp_val<T>(sp.a, sp.af), cb = sp_val<T>(sp.b, sp.bf);
       {
         // owners: the x and y faces on the low side of their cell; helpers:
         // the x face at the +x block boundary of row hr and the y face at the
@@ -216,14 +216,9 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
       __syncthreads();
       wnn = counter ? S.next : wn + gridDim.x;
       if (owner) {
-        const T dx0 = (T)dxd[0], dx1 = (T)dxd[1];
-        const T idx0 = T(1) / dx0, idx1 = T(1) / dx1;
-        T damp;
-        if constexpr (sizeof(T) == 4)
-          damp = sp.glm ? expf((float)(-sp.glm_alpha * rt.ch * rt.dt / fmin(dxd[0], dxd[1])))
-                        : 1.0f;
-        else
-          damp = sp.glm ? exp(-sp.glm_alpha * rt.ch * rt.dt / fmin(dxd[0], dxd[1])) : 1.0;
+        const T dx0 = lc[LC_DX], dx1 = lc[LC_DX + 1];
+        const T idx0 = idd[0], idx1 = idd[1];
+        const T damp = lc[LC_DAMP];
         const int c = y * FB + x;
         T un[NV];
 #pragma unroll

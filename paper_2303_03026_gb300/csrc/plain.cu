@@ -354,7 +354,49 @@ StageParams make_stage_params(const amrvac_state* s, int k, int epilogue) {
   sp.glm = s->cfg.glm;
   sp.epilogue = epilogue;
   sp.pressure_ff = s->cfg.precision == AMRVAC_FP32_BULK && s->cfg.pressure == AMRVAC_PRESSURE_FF;
+  sp.af = (float)sp.a;
+  sp.bf = (float)sp.b;
+  sp.small_density_f = (float)sp.small_density;
+  sp.small_pressure_f = (float)sp.small_pressure;
   return sp;
+}
+
+// per-(instance, level) stage constants of the fused kernels from InstRT and
+// the level's cell size (one thread per level)
+__global__ void k_level_consts(DevMesh M, double glm_alpha, int glm) {
+  const int q = blockIdx.x, L = threadIdx.x;
+  if (q >= M.ninst || L >= MAXLEV) return;
+  const InstRT rt = M.rt[q];
+  const double* dx = M.dx + (q * MAXLEV + L) * 3;
+  double dxmin = fmin(dx[0], dx[1]);
+  if (M.ndim == 3) dxmin = fmin(dxmin, dx[2]);
+  const double g = M.gamma[q];
+  float* f = M.lcf + (q * MAXLEV + L) * LC_N;
+  double* d = M.lcd + (q * MAXLEV + L) * LC_N;
+  d[LC_DT] = rt.dt;
+  f[LC_DT] = (float)rt.dt;
+  d[LC_CH] = rt.ch;
+  f[LC_CH] = (float)rt.ch;
+  d[LC_DAMP] = glm ? exp(-glm_alpha * rt.ch * rt.dt / dxmin) : 1.0;
+  // float bulk: the damping factor is the exp of the float-rounded argument
+  f[LC_DAMP] = glm ? expf((float)(-glm_alpha * rt.ch * rt.dt / dxmin)) : 1.0f;
+  for (int e = 0; e < 3; e++) {
+    d[LC_DX + e] = dx[e];
+    f[LC_DX + e] = (float)dx[e];
+    d[LC_IDX + e] = 1.0 / dx[e];
+    f[LC_IDX + e] = 1.0f / (float)dx[e];
+  }
+  d[LC_SKIP] = rt.dt == 0.0 ? 1.0 : 0.0;
+  f[LC_SKIP] = rt.dt == 0.0 ? 1.0f : 0.0f;
+  d[LC_G] = g;
+  f[LC_G] = (float)g;
+  d[LC_GM1] = g - 1.0;
+  f[LC_GM1] = (float)(g - 1.0);
+}
+
+int launch_level_consts(amrvac_state* s) {
+  k_level_consts<<<s->ninst, MAXLEV, 0, s->stream>>>(s->mesh, s->cfg.glm_alpha, s->cfg.glm);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 template <class T> static int plain_stage_t(amrvac_state* s, int k, int epilogue) {

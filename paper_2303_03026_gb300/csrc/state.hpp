@@ -95,6 +95,7 @@ int launch_plain_stage(amrvac_state* s, int k, int epilogue);
 int launch_cfl_partials(amrvac_state* s, int buffer);
 int launch_finalize(amrvac_state* s, int advance);
 int launch_sums(amrvac_state* s, int buffer);
+int launch_level_consts(amrvac_state* s);
 int launch_fill_ghosts(amrvac_state* s, int buffer, void* out);
 int launch_convert(amrvac_state* s, const void* src, int src_prec, void* dst, int dst_prec,
                    size_t n);
