@@ -75,10 +75,38 @@ __device__ void level_value_down(const DevMesh& M, const T* U, size_t vs, int q,
     return;
   }
   const int n1 = M.ndim > 1 ? 2 : 1, n2 = M.ndim > 2 ? 2 : 1;
-  const int nchild = 2 * n1 * n2;
+  // 1 / (number of children), exact (a power of two)
+  const T inv = M.ndim == 3 ? T(0.125) : (M.ndim == 2 ? T(0.25) : T(0.5));
   T sum[NV];
 #pragma unroll
   for (int v = 0; v < NV; v++) sum[v] = T(0);
+  // fast path: with even block edges the children of p are one 2^d cube of
+  // cells in a single level-(L+1) block; when that block is a leaf, one lookup
+  // and independent loads, summed in the order of the general loop below
+  if ((M.nx[0] & 1) == 0 && (M.ndim < 2 || (M.nx[1] & 1) == 0) &&
+      (M.ndim < 3 || (M.nx[2] & 1) == 0)) {
+    int c0[3] = {2 * p[0], M.ndim > 1 ? 2 * p[1] : 0, M.ndim > 2 ? 2 * p[2] : 0};
+    int cc;
+    const int r2 = map_at(M, q, L + 1, c0, &cc);
+    if (r2 >= 0) {
+      const T* src = U + (size_t)r2 * M.ncell + cc;
+      const int sy = M.nx[0], sz = M.nx[0] * M.nx[1];
+#pragma unroll
+      for (int oz = 0; oz < 2; oz++)
+#pragma unroll
+        for (int oy = 0; oy < 2; oy++)
+#pragma unroll
+          for (int ox = 0; ox < 2; ox++) {
+            if (oz >= n2 || oy >= n1) continue;
+            const int off = ox + oy * sy + oz * sz;
+#pragma unroll
+            for (int v = 0; v < NV; v++) sum[v] += src[(size_t)v * vs + off];
+          }
+#pragma unroll
+      for (int v = 0; v < NV; v++) out[v] = sum[v] * inv;
+      return;
+    }
+  }
   for (int oz = 0; oz < n2; oz++)
     for (int oy = 0; oy < n1; oy++)
       for (int ox = 0; ox < 2; ox++) {
@@ -111,7 +139,7 @@ __device__ void level_value_down(const DevMesh& M, const T* U, size_t vs, int q,
                 for (int v = 0; v < NV; v++) s2[v] += t3[v];
               }
 #pragma unroll
-          for (int v = 0; v < NV; v++) tmp[v] = s2[v] * (T(1) / T(nchild));
+          for (int v = 0; v < NV; v++) tmp[v] = s2[v] * inv;
         } else {
           latch_error(M.err, AMRVAC_E_STATE, -1, L + 1, 2);
 #pragma unroll
@@ -121,7 +149,7 @@ __device__ void level_value_down(const DevMesh& M, const T* U, size_t vs, int q,
         for (int v = 0; v < NV; v++) sum[v] += tmp[v];
       }
 #pragma unroll
-  for (int v = 0; v < NV; v++) out[v] = sum[v] * (T(1) / T(nchild));
+  for (int v = 0; v < NV; v++) out[v] = sum[v] * inv;
 }
 
 template <class T> __device__ __forceinline__ T minmod_g(T a, T b) {
