@@ -508,8 +508,8 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
                 "config": dict(desc, cells=cells, l2=l2,
-                               precision="fp32 bulk; pressure recovery and per-thread sums in %s; "
-                                         "fp64 dt and block/instance sums" %
+                               precision="fp32 bulk; pressure recovery in %s; fp64 dt, c_h "
+                                         "and conservation sums" %
                                          ("float-float" if args.pressure == "ff" else "fp64"),
                                kernel=args.kernel, build=digest, tuning=tuning,
                                parallelism="replicas" if ws > 1 else "1 GPU"),
