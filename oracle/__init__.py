@@ -70,6 +70,8 @@ def lib():
             L.orc_set_threads.argtypes = [C.c_void_p, C.c_int]
             L.orc_fill_ghosts.argtypes = [C.c_void_p, dp, dp]
             L.orc_stage.argtypes = [C.c_void_p, C.c_int, dp, dp, dp, dp, dp, C.c_void_p, C.c_int]
+            L.orc_stage2.argtypes = [C.c_void_p, C.c_int, dp, dp, dp, dp, dp, dp, dp,
+                                     C.c_void_p, C.c_int]
             L.orc_cfl.argtypes = [C.c_void_p, dp, dp, dp, dp, dp]
             L.orc_sums.argtypes = [C.c_void_p, dp, dp]
             L.orc_run.argtypes = [C.c_void_p, dp, dp, dp, C.c_int, C.c_double,
@@ -83,13 +85,16 @@ def lib():
                                         dp, dp, dp]
             L.orc_stage_coeffs.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_double),
                                            C.POINTER(C.c_double)]
+            L.orc_stage_coeffs6.argtypes = [C.c_int, C.c_int, dp]
+            L.orc_num_stages.argtypes = [C.c_int]
+            L.orc_num_stages.restype = C.c_int
             _lib = L
     return _lib
 
 
-_FLUX = {"hll": 0, "hlld": 1}
+_FLUX = {"hll": 0, "hlld": 1, "tvdlf": 2}
 _LIM = {"minmod": 0, "vanleer": 1, "koren": 2}
-_TIME = {"ssprk2": 0, "ssprk3": 1}
+_TIME = {"ssprk2": 0, "ssprk3": 1, "ssprk43": 2, "ssprk54": 3}
 _BC = {"periodic": 0, "outflow": 1}
 
 
@@ -176,6 +181,17 @@ class Mesh:
                                  sub.ctypes.data_as(C.c_void_p), sub.shape[0])
         return out, st
 
+    def stage2(self, k, dt, ch, U0, Uk, U2):
+        """Stage k with its second output (SSPRK(5,4) stage 3): returns
+        (out, out2, status) on fresh arrays."""
+        dt = np.ascontiguousarray(np.broadcast_to(dt, (self.ninst,)), np.float64)
+        ch = np.ascontiguousarray(np.broadcast_to(ch, (self.ninst,)), np.float64)
+        U0, Uk, U2 = self._u(U0), self._u(Uk), self._u(U2)
+        out = np.zeros_like(Uk)
+        out2 = np.zeros_like(Uk)
+        st = lib().orc_stage2(self._h, k, dt, ch, U0, Uk, U2, out, out2, None, 0)
+        return out, out2, st
+
     def cfl(self, U, t=None, t_end=None):
         t = np.zeros(self.ninst) if t is None else np.ascontiguousarray(
             np.broadcast_to(t, (self.ninst,)), np.float64)
@@ -245,3 +261,15 @@ def stage_coeffs(time, k):
     b = C.c_double()
     lib().orc_stage_coeffs(_TIME[time], k, C.byref(a), C.byref(b))
     return a.value, b.value
+
+
+def stage_coeffs6(time, k):
+    """{a, b, c, a2, b2, c2} of stage k: out = a U0 + b (Uk + c dt L(Uk)),
+    out2 = a2 U2 + b2 (Uk + c2 dt L(Uk))."""
+    co = np.zeros(6)
+    lib().orc_stage_coeffs6(_TIME[time], k, co)
+    return co
+
+
+def num_stages(time):
+    return lib().orc_num_stages(_TIME[time])

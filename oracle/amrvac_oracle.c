@@ -21,7 +21,10 @@
  *    reconstructions; the fallback form is our reading).
  *  - HLL (Harten 1983) with Davis speed bounds; HLLD (Miyoshi & Kusano 2005)
  *    with outer speeds min/max(u) -/+ max(c_f) and a degeneracy threshold.
- *  - SSPRK(2,2) and SSPRK(3,3) in Shu-Osher form (Gottlieb 2005, Sect. 3).
+ *  - SSPRK(2,2), SSPRK(3,3) (Gottlieb 2005), SSPRK(4,3) and SSPRK(5,4)
+ *    (Spiteri & Ruuth 2002) in Shu-Osher form (Sect. 3, time-integration
+ *    table); psi is damped over each Euler part's time step.
+ *  - TVD Lax-Friedrichs flux with the fastest local signal speed.
  *  - CFL: dt = C / max over cells of sum_d (|v_d| + c_f,d)/dx_d, from U^n,
  *    global per instance, no subcycling; c_h = max (|v_d| + c_f,d).
  *  - AMR ghost values (the paper gives no operators): same level -> copy;
@@ -267,6 +270,19 @@ static void hll_local(double g, const double* ql, const double* qr, double bx, d
   }
 }
 
+/* TVD Lax-Friedrichs (the `tvdlf' flux of the flux-scheme table, Sect. 3.2.1):
+ * the local Lax-Friedrichs flux with the fastest signal speed of the two sides,
+ * c_max = max(|u_L| + c_fL, |u_R| + c_fR):
+ *   F = (F_L + F_R)/2 - c_max (U_R - U_L)/2 */
+static void tvdlf_local(double g, const double* ql, const double* qr, double bx, double* f) {
+  double UL[8], UR[8], FL[8], FR[8], ptl, ptr;
+  local_cons_flux(g, ql, bx, UL, FL, &ptl);
+  local_cons_flux(g, qr, bx, UR, FR, &ptr);
+  double cl = fabs(ql[1]) + local_fast(g, ql, bx), cr = fabs(qr[1]) + local_fast(g, qr, bx);
+  double cmax = dmax(cl, cr);
+  for (int c = 0; c < 8; c++) f[c] = 0.5 * (FL[c] + FR[c]) - 0.5 * cmax * (UR[c] - UL[c]);
+}
+
 /* one side of the HLLD single-star state, Miyoshi & Kusano 2005 */
 typedef struct {
   double rs, vs, ws, bys, bzs, es;
@@ -372,7 +388,8 @@ void orc_face_flux(int flux, int glm, double gamma, double ch, int dir, const do
   double qr[8] = {wr[0], wr[1 + dir], wr[1 + t1], wr[1 + t2], wr[4], bns, wr[5 + t1], wr[5 + t2]};
   double fl[8];
   if (flux == 0) hll_local(gamma, ql, qr, bns, fl);
-  else hlld_local(gamma, ql, qr, bns, fl);
+  else if (flux == 1) hlld_local(gamma, ql, qr, bns, fl);
+  else tvdlf_local(gamma, ql, qr, bns, fl);
   f[RHO] = fl[0];
   f[MX + dir] = fl[1];
   f[MX + t1] = fl[2];
@@ -384,20 +401,69 @@ void orc_face_flux(int flux, int glm, double gamma, double ch, int dir, const do
   f[PSI] = glm ? ch * ch * bns : 0.0;
 }
 
-void orc_stage_coeffs(int time, int k, double* a, double* b) {
-  if (k == 0) {
-    *a = 0.0;
-    *b = 1.0;
-  } else if (time == 0) {
-    *a = 0.5;
-    *b = 0.5;
-  } else if (k == 1) {
-    *a = 0.75;
-    *b = 0.25;
+/* Shu-Osher coefficients of stage k (Sect. 3, time-integration table):
+ *   out  = a  U0 + b  (Uk + c  dt L(Uk))
+ *   out2 = a2 U2 + b2 (Uk + c2 dt L(Uk))   (b2 != 0 only in stage 3 of SSPRK(5,4))
+ * SSPRK(2,2) (Heun) and SSPRK(3,3): Gottlieb 2005.  SSPRK(4,3) and SSPRK(5,4):
+ * the optimal schemes of Spiteri & Ruuth 2002 (cited by the table), written as
+ *   SSPRK(4,3): u1 = u0 + dt/2 L(u0); u2 = u1 + dt/2 L(u1);
+ *               u3 = 2/3 u0 + 1/3 (u2 + dt/2 L(u2)); u4 = u3 + dt/2 L(u3)
+ *   SSPRK(5,4): u1 = u0 + 0.391752226571890 dt L(u0)
+ *               u2 = 0.444370493651235 u0 + 0.555629506348765 u1
+ *                    + 0.368410593050371 dt L(u1)
+ *               u3 = 0.620101851488403 u0 + 0.379898148511597 u2
+ *                    + 0.251891774271694 dt L(u2)
+ *               u4 = 0.178079954393132 u0 + 0.821920045606868 u3
+ *                    + 0.544974750228521 dt L(u3)
+ *               u5 = 0.517231671970585 u2 + 0.096059710526147 u3
+ *                    + 0.063692468666290 dt L(u3) + 0.386708617503269 u4
+ *                    + 0.226007483236906 dt L(u4)
+ * For SSPRK(5,4) stage 3 also returns w = 0.517... u2 + 0.096... u3 + 0.0636...
+ * dt L(u3) (out2), and stage 4 is u5 = w + 0.386... u4 + 0.226... dt L(u4) with
+ * U0 = w.  co = {a, b, c, a2, b2, c2}. */
+void orc_stage_coeffs6(int time, int k, double* co) {
+  double a = 0.0, b = 1.0, c = 1.0, a2 = 0.0, b2 = 0.0, c2 = 0.0;
+  if (time == 0) {
+    if (k == 1) a = 0.5, b = 0.5;
+  } else if (time == 1) {
+    if (k == 1) a = 0.75, b = 0.25;
+    else if (k == 2) a = 1.0 / 3.0, b = 2.0 / 3.0;
+  } else if (time == 2) {
+    c = 0.5;
+    if (k == 2) a = 2.0 / 3.0, b = 1.0 / 3.0;
   } else {
-    *a = 1.0 / 3.0;
-    *b = 2.0 / 3.0;
+    switch (k) {
+      case 0: c = 0.391752226571890; break;
+      case 1:
+        a = 0.444370493651235, b = 0.555629506348765;
+        c = 0.368410593050371 / b;
+        break;
+      case 2:
+        a = 0.620101851488403, b = 0.379898148511597;
+        c = 0.251891774271694 / b;
+        break;
+      case 3:
+        a = 0.178079954393132, b = 0.821920045606868;
+        c = 0.544974750228521 / b;
+        a2 = 0.517231671970585, b2 = 0.096059710526147;
+        c2 = 0.063692468666290 / b2;
+        break;
+      default:
+        a = 1.0, b = 0.386708617503269;
+        c = 0.226007483236906 / b;
+        break;
+    }
   }
+  co[0] = a, co[1] = b, co[2] = c, co[3] = a2, co[4] = b2, co[5] = c2;
+}
+
+int orc_num_stages(int time) { return time == 0 ? 2 : time == 1 ? 3 : time == 2 ? 4 : 5; }
+
+void orc_stage_coeffs(int time, int k, double* a, double* b) {
+  double co[6];
+  orc_stage_coeffs6(time, k, co);
+  *a = co[0];
+  *b = co[1];
 }
 
 /* ------------------------------------------------------------------------ */
@@ -687,7 +753,8 @@ static int small_values(const orc_mesh* m, const double* w) {
 
 /* One stage on one block.  scratch: cons/prim padded (NV*np each) + fluxes. */
 static int block_stage(const orc_mesh* m, int b, int k, const double* dtv, const double* chv,
-                       const double* U0, const double* Uk, double* out, double* scratch) {
+                       const double* U0, const double* Uk, const double* U2, double* out,
+                       double* out2, double* scratch) {
   padinfo pi = pad_of(m);
   const blockinfo* B = &m->blk[b];
   const int* nx = m->cfg.nx;
@@ -696,11 +763,18 @@ static int block_stage(const orc_mesh* m, int b, int k, const double* dtv, const
   const size_t nvb = (size_t)m->nblocks * m->ncell;
   int status = ST_OK;
 
+  double co[6];
+  orc_stage_coeffs6(m->cfg.time, k, co);
+  const int second = out2 != NULL && co[4] != 0.0;
+
   if (dt == 0.0) {
+    /* finished instance: every stage output is the stage input */
     for (int v = 0; v < NV; v++)
       for (int c = 0; c < m->ncell; c++) {
         size_t at = (size_t)v * nvb + (size_t)b * m->ncell + c;
-        out[at] = Uk[at];
+        double u = Uk[at];
+        out[at] = u;
+        if (second) out2[at] = u;
       }
     return ST_OK;
   }
@@ -771,9 +845,10 @@ static int block_stage(const orc_mesh* m, int b, int k, const double* dtv, const
   cell_dx(m, B->inst, B->level, dx);
   double dxmin = dx[0];
   for (int d = 1; d < m->cfg.ndim; d++) dxmin = dmin(dxmin, dx[d]);
-  double damp = m->cfg.glm ? exp(-m->cfg.glm_alpha * ch * dt / dxmin) : 1.0;
-  double a, bb;
-  orc_stage_coeffs(m->cfg.time, k, &a, &bb);
+  /* psi damping over each Euler part's time step c dt */
+  double damp = m->cfg.glm ? exp(-m->cfg.glm_alpha * ch * (co[2] * dt) / dxmin) : 1.0;
+  double damp2 = m->cfg.glm ? exp(-m->cfg.glm_alpha * ch * (co[5] * dt) / dxmin) : 1.0;
+  const double a = co[0], bb = co[1];
   for (int kk = 0; kk < nx[2]; kk++)
     for (int j = 0; j < nx[1]; j++)
       for (int i = 0; i < nx[0]; i++) {
@@ -790,9 +865,17 @@ static int block_stage(const orc_mesh* m, int b, int k, const double* dtv, const
             acc += (F[d][v * nf[d] + fq] - F[d][v * nf[d] + fm]) / dx[d];
           }
           size_t at = (size_t)v * nvb + (size_t)b * m->ncell + cell;
-          double ut = Uk[at] - dt * acc;
+          double ut = Uk[at] - (co[2] * dt) * acc;
           if (v == PSI) ut = ut * damp;
-          out[at] = (k == 0) ? ut : a * U0[at] + bb * ut;
+          /* a plain Euler stage (a = 0, b = 1) does not read U0 */
+          double o = (a == 0.0 && bb == 1.0) ? ut : a * U0[at] + bb * ut;
+          if (second) {
+            double ut2 = Uk[at] - (co[5] * dt) * acc;
+            if (v == PSI) ut2 = ut2 * damp2;
+            double o2 = co[3] * U2[at] + co[4] * ut2;
+            out2[at] = o2; /* U2 and U0 were read above: out2/out may alias them */
+          }
+          out[at] = o;
         }
       }
   return status;
@@ -805,8 +888,8 @@ static int block_stage(const orc_mesh* m, int b, int k, const double* dtv, const
 typedef struct {
   const orc_mesh* m;
   int k;
-  const double *dt, *ch, *U0, *Uk;
-  double* out;
+  const double *dt, *ch, *U0, *Uk, *U2;
+  double *out, *out2;
   const int32_t* list;
   int n, t, nt;
   int status;
@@ -826,7 +909,8 @@ static void* stage_worker(void* arg) {
   J->status = ST_OK;
   for (int q = J->t; q < J->n; q += J->nt) {
     int b = J->list ? J->list[q] : q;
-    int s = block_stage(J->m, b, J->k, J->dt, J->ch, J->U0, J->Uk, J->out, scratch);
+    int s = block_stage(J->m, b, J->k, J->dt, J->ch, J->U0, J->Uk, J->U2, J->out, J->out2,
+                        scratch);
     if (s) J->status = s;
   }
   free(scratch);
@@ -835,13 +919,19 @@ static void* stage_worker(void* arg) {
 
 int orc_stage(const orc_mesh* m, int k, const double* dt, const double* ch, const double* U0,
               const double* Uk, double* out, const int32_t* sub, int nsub) {
+  return orc_stage2(m, k, dt, ch, U0, Uk, NULL, out, NULL, sub, nsub);
+}
+
+int orc_stage2(const orc_mesh* m, int k, const double* dt, const double* ch, const double* U0,
+               const double* Uk, const double* U2, double* out, double* out2,
+               const int32_t* sub, int nsub) {
   int n = sub ? nsub : m->nblocks;
   int nt = m->nthreads;
   if (nt > n) nt = n > 0 ? n : 1;
   stage_job* jobs = (stage_job*)calloc((size_t)nt, sizeof(stage_job));
   pthread_t* th = (pthread_t*)calloc((size_t)nt, sizeof(pthread_t));
   for (int t = 0; t < nt; t++) {
-    stage_job J = {m, k, dt, ch, U0, Uk, out, sub, n, t, nt, 0};
+    stage_job J = {m, k, dt, ch, U0, Uk, U2, out, out2, sub, n, t, nt, 0};
     jobs[t] = J;
     if (nt > 1) pthread_create(&th[t], NULL, stage_worker, &jobs[t]);
     else stage_worker(&jobs[t]);
@@ -929,22 +1019,33 @@ int orc_run(orc_mesh* m, double* U, double* t, const double* t_end, int maxsteps
     int any = 0;
     for (int q = 0; q < m->ninst; q++) any |= dt[q] > 0.0;
     if (!any) break;
-    int st;
+    int st[5] = {0, 0, 0, 0, 0};
     if (m->cfg.time == 0) {
-      st = orc_stage(m, 0, dt, ch, U, U, A, NULL, 0);
-      if (st) status = st;
-      st = orc_stage(m, 1, dt, ch, U, A, Bf, NULL, 0);
-      if (st) status = st;
+      st[0] = orc_stage(m, 0, dt, ch, U, U, A, NULL, 0);
+      st[1] = orc_stage(m, 1, dt, ch, U, A, Bf, NULL, 0);
       memcpy(U, Bf, sizeof(double) * n);
-    } else {
-      st = orc_stage(m, 0, dt, ch, U, U, A, NULL, 0);
-      if (st) status = st;
-      st = orc_stage(m, 1, dt, ch, U, A, Bf, NULL, 0);
-      if (st) status = st;
-      st = orc_stage(m, 2, dt, ch, U, Bf, A, NULL, 0);
-      if (st) status = st;
+    } else if (m->cfg.time == 1) {
+      st[0] = orc_stage(m, 0, dt, ch, U, U, A, NULL, 0);
+      st[1] = orc_stage(m, 1, dt, ch, U, A, Bf, NULL, 0);
+      st[2] = orc_stage(m, 2, dt, ch, U, Bf, A, NULL, 0);
       memcpy(U, A, sizeof(double) * n);
+    } else if (m->cfg.time == 2) {
+      /* u1 -> A, u2 -> Bf, u3 -> A, u4 -> U */
+      st[0] = orc_stage(m, 0, dt, ch, U, U, A, NULL, 0);
+      st[1] = orc_stage(m, 1, dt, ch, U, A, Bf, NULL, 0);
+      st[2] = orc_stage(m, 2, dt, ch, U, Bf, A, NULL, 0);
+      st[3] = orc_stage(m, 3, dt, ch, U, A, U, NULL, 0);
+    } else {
+      /* u1 -> A, u2 -> Bf, u3 -> A; stage 3: u4 -> Bf (over u2, its own
+       * cells) and w -> U (over u0); stage 4: u5 = w + ... -> U */
+      st[0] = orc_stage(m, 0, dt, ch, U, U, A, NULL, 0);
+      st[1] = orc_stage(m, 1, dt, ch, U, A, Bf, NULL, 0);
+      st[2] = orc_stage(m, 2, dt, ch, U, Bf, A, NULL, 0);
+      st[3] = orc_stage2(m, 3, dt, ch, U, A, Bf, Bf, U, NULL, 0);
+      st[4] = orc_stage(m, 4, dt, ch, U, Bf, U, NULL, 0);
     }
+    for (int e = 0; e < 5; e++)
+      if (st[e]) status = st[e];
     for (int q = 0; q < m->ninst; q++) {
       if (dt[q] > 0.0 && dt[q] >= t_end[q] - t[q]) t[q] = t_end[q];
       else t[q] += dt[q];

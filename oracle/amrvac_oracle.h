@@ -12,9 +12,9 @@
  * -ffp-contract=off.  Every quantity follows the method's definition with no
  * blocking or fusion.  Points where the paper names a method without printing
  * its formula are resolved by the published method it cites (Harten 1983 for
- * HLL, Miyoshi & Kusano 2005 for HLLD, Dedner 2002 for glm, Gottlieb 2005 for
- * SSPRK, van Leer 1974 and Koren 1993 for the limiters); the readings are listed
- * at each function.
+ * HLL, Miyoshi & Kusano 2005 for HLLD, Dedner 2002 for glm, Gottlieb 2005 and
+ * Spiteri & Ruuth 2002 for SSPRK, van Leer 1974 and Koren 1993 for the
+ * limiters); the readings are listed at each function.
  */
 #ifndef AMRVAC_ORACLE_H
 #define AMRVAC_ORACLE_H
@@ -30,9 +30,9 @@ extern "C" {
 typedef struct {
   int ndim;              /* 1, 2 or 3 */
   int nx[3];             /* cells per block per dimension (1 for unused dims) */
-  int flux;              /* 0 hll, 1 hlld */
+  int flux;              /* 0 hll, 1 hlld, 2 tvdlf */
   int limiter;           /* 0 minmod, 1 vanleer, 2 koren */
-  int time;              /* 0 ssprk2, 1 ssprk3 */
+  int time;              /* 0 ssprk(2,2), 1 ssprk(3,3), 2 ssprk(4,3), 3 ssprk(5,4) */
   int glm;               /* 1: Dedner glm cleaning; 0: none (psi stays 0) */
   double glm_alpha;      /* psi damping parameter alpha_p */
   double courant;
@@ -61,11 +61,18 @@ void orc_set_threads(orc_mesh* m, int nthreads);
 int orc_fill_ghosts(const orc_mesh* m, const double* U, double* padded);
 
 /* One SSPRK stage k on the listed blocks (all when sub == NULL):
- * out = a_k U0 + b_k (Uk + dt L(Uk)), psi damped after the Euler sub-step.
- * dt, ch are per instance.  Returns 0 or 4 (small values found). */
+ * out = a_k U0 + b_k (Uk + c_k dt L(Uk)), psi of the Euler part damped over
+ * c_k dt (coefficients: orc_stage_coeffs6).  dt, ch are per instance.  Returns
+ * 0 or 4 (small values found). */
 int orc_stage(const orc_mesh* m, int k, const double* dt, const double* ch,
               const double* U0, const double* Uk, double* out,
               const int32_t* sub, int nsub);
+/* The same with the second output of SSPRK(5,4) stage 3:
+ * out2 = a2 U2 + b2 (Uk + c2 dt L(Uk)) when out2 != NULL and b2 != 0.  out may
+ * be U2's array and out2 U0's (each cell is read before it is written). */
+int orc_stage2(const orc_mesh* m, int k, const double* dt, const double* ch,
+               const double* U0, const double* Uk, const double* U2, double* out,
+               double* out2, const int32_t* sub, int nsub);
 
 /* CFL: per instance dt = courant / max sum_d (|v_d|+c_f,d)/dx_d and
  * ch = max (|v_d|+c_f,d); dt clipped to t_end - t. */
@@ -92,6 +99,9 @@ void orc_face_flux(int flux, int glm, double gamma, double ch, int dir,
                    const double* wl, const double* wr, double* f);
 /* stage coefficients a_k, b_k used by orc_stage */
 void orc_stage_coeffs(int time, int k, double* a, double* b);
+/* all six: {a, b, c, a2, b2, c2} */
+void orc_stage_coeffs6(int time, int k, double* co);
+int orc_num_stages(int time);
 
 #ifdef __cplusplus
 }
