@@ -63,9 +63,18 @@ typedef enum {
   AMRVAC_E_STATE = 6         /* call out of order, or a mesh lookup failed    */
 } amrvac_status;
 
-typedef enum { AMRVAC_FLUX_HLL = 0, AMRVAC_FLUX_HLLD = 1 } amrvac_flux;
+/* flux-scheme table of Sect. 3.2.1: HLL (Harten 1983), HLLD (Miyoshi & Kusano
+ * 2005), TVD Lax-Friedrichs (local LF with the fastest signal speed) */
+typedef enum { AMRVAC_FLUX_HLL = 0, AMRVAC_FLUX_HLLD = 1, AMRVAC_FLUX_TVDLF = 2 } amrvac_flux;
 typedef enum { AMRVAC_LIM_MINMOD = 0, AMRVAC_LIM_VANLEER = 1, AMRVAC_LIM_KOREN = 2 } amrvac_limiter;
-typedef enum { AMRVAC_SSPRK2 = 0, AMRVAC_SSPRK3 = 1 } amrvac_time;
+/* time-integration table of Sect. 3: SSPRK(2,2), SSPRK(3,3) (Gottlieb 2005),
+ * SSPRK(4,3) and SSPRK(5,4) (Spiteri & Ruuth 2002) */
+typedef enum {
+  AMRVAC_SSPRK2 = 0,
+  AMRVAC_SSPRK3 = 1,
+  AMRVAC_SSPRK43 = 2,
+  AMRVAC_SSPRK54 = 3
+} amrvac_time;
 /* FP64: state and arithmetic in double.  FP32_BULK: state and stencil/Riemann
  * arithmetic in float; thermal pressure recovered from the total energy in
  * double; conservation sums and the time step in double. */
@@ -190,11 +199,23 @@ amrvac_status amrvac_set_dt(amrvac_state* s, const double* h_dt, const double* h
 /*
  * One SSPRK stage k (0-based) with the device-resident dt and c_h, i.e. one
  * advect1 substep plus the convex combination of the Shu-Osher form:
- *   out = a_k U^n + b_k (U_in + dt L(U_in)),  psi damped after the Euler part,
- * SSPRK2: (a,b) = (0,1), (1/2,1/2); SSPRK3: (0,1), (3/4,1/4), (1/3,2/3).
- * Buffers: stage 0 reads buffer 0 and writes 1; SSPRK2 stage 1 reads 0 and 1
- * and writes 0; SSPRK3 stage 1 reads 0 and 1 and writes 2, stage 2 reads 0 and
- * 2 and writes 0.  Instances whose dt is 0 are copied through unchanged.
+ *   out = a_k U0 + b_k (U_in + c_k dt L(U_in)),
+ * psi of the Euler part damped by exp(-alpha c_h c_k dt / dx_min).
+ *   SSPRK2  (a,b,c): (0,1,1), (1/2,1/2,1)
+ *   SSPRK3:  (0,1,1), (3/4,1/4,1), (1/3,2/3,1)
+ *   SSPRK43: (0,1,1/2), (0,1,1/2), (2/3,1/3,1/2), (0,1,1/2)
+ *   SSPRK54: the Spiteri-Ruuth scheme; stage 3 also writes
+ *            w = a2 u2 + b2 (u3 + c2 dt L(u3)) and stage 4 is
+ *            u5 = w + b4 (u4 + c4 dt L(u4)) (U0 = w).
+ * Buffers (U0, U_in [, U2] -> out [, out2]): stage 0: (0, 0) -> 1.
+ *   SSPRK2:  stage 1: (0, 1) -> 0
+ *   SSPRK3:  stage 1: (0, 1) -> 2; stage 2: (0, 2) -> 0
+ *   SSPRK43: stage 1: (0, 1) -> 2; stage 2: (0, 2) -> 1; stage 3: (-, 1) -> 0
+ *   SSPRK54: stage 1: (0, 1) -> 2; stage 2: (0, 2) -> 1;
+ *            stage 3: (0, 1, 2) -> 2, w -> 0; stage 4: (0, 2) -> 0
+ * (a buffer read and written in one stage is only read at the cells the same
+ * thread writes).  After the last stage buffer 0 holds U^{n+1}.  Instances
+ * whose dt is 0 are copied through unchanged.
  */
 amrvac_status amrvac_stage(amrvac_state* s, int32_t stage);
 

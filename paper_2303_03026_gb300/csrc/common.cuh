@@ -15,10 +15,14 @@ constexpr int NG = 2;       // ghost cells per face (vanleer/koren/minmod: limit
 constexpr int MAXLEV = AMRVAC_MAX_LEVELS;
 constexpr int NPART = 12;   // per-block partials: smax, chmax, sums[9], pad
 // per-(instance, level) stage constants of the fused kernels, refreshed from
-// InstRT before every fused stage: dt, ch, psi damping factor, dx[3],
-// 1/dx[3], finished flag (dt == 0), gamma, gamma - 1
-constexpr int LC_N = 12;
-enum { LC_DT = 0, LC_CH = 1, LC_DAMP = 2, LC_DX = 3, LC_IDX = 6, LC_SKIP = 9, LC_G = 10, LC_GM1 = 11 };
+// InstRT before every fused stage: c dt (the stage's Euler step), ch, psi
+// damping factor over c dt, dx[3], 1/dx[3], finished flag (dt == 0), gamma,
+// gamma - 1, and c2 dt with its damping factor (second output)
+constexpr int LC_N = 16;
+enum {
+  LC_DT = 0, LC_CH = 1, LC_DAMP = 2, LC_DX = 3, LC_IDX = 6, LC_SKIP = 9, LC_G = 10,
+  LC_GM1 = 11, LC_DT2 = 12, LC_DAMP2 = 13
+};
 
 // face neighbour codes in DevMesh::nbr
 constexpr int NBR_OUTFLOW = -1;  // physical zero-gradient boundary
@@ -66,7 +70,10 @@ template <> __device__ __forceinline__ const double* level_consts<double>(const 
 
 struct StageParams {
   int k;                 // stage index
-  double a, b;           // out = a U0 + b (U + dt L)
+  double a, b, c;        // out = a U0 + b (U + c dt L)
+  double a2, b2, c2;     // out2 = a2 U2 + b2 (U + c2 dt L) when has2
+  int plain;             // a == 0 and b == 1: out = U + c dt L (U0 not read)
+  int has2;
   double courant;
   double glm_alpha;
   double small_density, small_pressure;
@@ -74,7 +81,7 @@ struct StageParams {
   int flux, limiter, glm;
   int epilogue;          // 1: per-block dt / sums partials of the output
   int pressure_ff;       // FP32 bulk: float-float pressure recovery and sums
-  float af, bf;          // a, b, small_density, small_pressure rounded to float
+  float af, bf, a2f, b2f;  // a, b, a2, b2, small_density, small_pressure in float
   float small_density_f, small_pressure_f;
 };
 

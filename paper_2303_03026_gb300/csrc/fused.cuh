@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(256)
 
 template <class T, int DIM, int LIM, int FLUX>
 __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
-    k_fused(DevMesh M, const T* U0, const T* __restrict__ Uk, T* out,
+    k_fused(DevMesh M, const T* U0, const T* __restrict__ Uk, const T* U2, T* out, T* out2,
             const int* __restrict__ work, int nwork, const T* __restrict__ gslab,
             int* __restrict__ counter, StageParams sp) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -351,6 +351,7 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
           size_t at = (size_t)v * vs + (size_t)b * ncell + c;
           u[v] = Uk[at];
           out[at] = u[v];
+          if (sp.has2) out2[at] = u[v];
         }
         if (sp.epilogue) cfl_terms<T, DIM>(u, gammad, g, ff, gm1f, idd, smx, cmx);
       }
@@ -483,7 +484,7 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
     // iteration z+2, after the barrier of iteration z+1, which every thread
     // passes only after its update of plane z.
     constexpr bool PRE0 = sizeof(T) == 4;
-    const bool pre0 = PRE0 && sp.k != 0 && owner;
+    const bool pre0 = PRE0 && !sp.plain && owner;
 #pragma unroll 1
     for (int z = 0; z < NZ; z++) {
       if (pre0) {
@@ -531,9 +532,17 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
         acc += over_dx<T>(S.fy[fb][v][y + 1][x] - S.fy[fb][v][y][x], dx1, idx1);
         if (DIM == 3) acc += over_dx<T>(fz[v] - fzp[v], dx2, idx2);
         const size_t at = (size_t)v * vs + (size_t)b * ncell + c;
-        T ut = Uk[at] - dt * acc;
+        const T uk = Uk[at];
+        T ut = uk - dt * acc;
         if (v == 8) ut = ut * damp;
-        un[v] = sp.k == 0 ? ut : ca * (PRE0 ? S.u0[v][tid] : U0[at]) + cb * ut;
+        un[v] = sp.plain ? ut : ca * (PRE0 ? S.u0[v][tid] : U0[at]) + cb * ut;
+        if (sp.has2) {
+          // SSPRK(5,4) stage 3: w = a2 U2 + b2 (Uk + c2 dt L); U2 is out's
+          // register and out2 is U0's, both read above before their writes
+          T ut2 = uk - lc[LC_DT2] * acc;
+          if (v == 8) ut2 = ut2 * lc[LC_DAMP2];
+          out2[at] = sp_val<T>(sp.a2, sp.a2f) * U2[at] + sp_val<T>(sp.b2, sp.b2f) * ut2;
+        }
         out[at] = un[v];
       }
       if (sp.epilogue) cfl_terms<T, DIM>(un, gammad, g, ff, gm1f, idd, smx, cmx);
@@ -555,7 +564,8 @@ namespace amrvac {
 // ---------------------------------------------------------------- launcher
 
 template <class T, int DIM, int LIM, int FLUX>
-static int launch_one(amrvac_state* s, const T* U0, const T* Uk, T* out, StageParams sp) {
+static int launch_one(amrvac_state* s, const T* U0, const T* Uk, const T* U2, T* out, T* out2,
+                      StageParams sp) {
   auto kern = DIM == 3 ? k_fused<T, 3, LIM, FLUX> : k_fused2d<T, LIM, FLUX>;
   const int smem = DIM == 3 ? (int)sizeof(FusedSmem<T, 3>) : (int)sizeof(Fused2dSmem<T>);
   static int nsm = 0, per_sm = 0;  // per instantiation, this device
@@ -583,7 +593,7 @@ static int launch_one(amrvac_state* s, const T* U0, const T* Uk, T* out, StagePa
   if (s->tune.dynamic) {
     if (cudaMemsetAsync(s->d_counter, 0, sizeof(int), s->stream) != cudaSuccess) return -1;
   }
-  kern<<<grid, FT, smem, s->stream>>>(s->mesh, U0, Uk, out, s->d_work, s->nwork,
+  kern<<<grid, FT, smem, s->stream>>>(s->mesh, U0, Uk, U2, out, out2, s->d_work, s->nwork,
                                        (const T*)s->gslab,
                                        s->tune.dynamic ? s->d_counter : nullptr, sp);
   return cudaPeekAtLastError() == cudaSuccess ? n : -1;
@@ -591,16 +601,21 @@ static int launch_one(amrvac_state* s, const T* U0, const T* Uk, T* out, StagePa
 
 template <class T, int DIM, int LIM>
 int launch_fused_l(amrvac_state* s, int k, int epilogue) {
-  int u0, uin, uout;
-  stage_buffers(s->cfg.time, k, &u0, &uin, &uout);
+  const StageBuffers sb = stage_buffers(s->cfg.time, k);
   StageParams sp = make_stage_params(s, k, epilogue);
-  if (launch_level_consts(s) < 0) return -1;
-  const T* U0 = (const T*)s->U[u0];
-  const T* Uk = (const T*)s->U[uin];
-  T* out = (T*)s->U[uout];
-  const int n = s->cfg.flux == AMRVAC_FLUX_HLLD
-                    ? launch_one<T, DIM, LIM, AMRVAC_FLUX_HLLD>(s, U0, Uk, out, sp)
-                    : launch_one<T, DIM, LIM, AMRVAC_FLUX_HLL>(s, U0, Uk, out, sp);
+  if (launch_level_consts(s, k) < 0) return -1;
+  const T* U0 = (const T*)s->U[sb.u0];
+  const T* Uk = (const T*)s->U[sb.uin];
+  const T* U2 = sb.u2 >= 0 ? (const T*)s->U[sb.u2] : nullptr;
+  T* out = (T*)s->U[sb.out];
+  T* out2 = sb.out2 >= 0 ? (T*)s->U[sb.out2] : nullptr;
+  int n;
+  if (s->cfg.flux == AMRVAC_FLUX_HLLD)
+    n = launch_one<T, DIM, LIM, AMRVAC_FLUX_HLLD>(s, U0, Uk, U2, out, out2, sp);
+  else if (s->cfg.flux == AMRVAC_FLUX_HLL)
+    n = launch_one<T, DIM, LIM, AMRVAC_FLUX_HLL>(s, U0, Uk, U2, out, out2, sp);
+  else
+    n = launch_one<T, DIM, LIM, AMRVAC_FLUX_TVDLF>(s, U0, Uk, U2, out, out2, sp);
   return n < 0 ? -1 : n + 1;
 }
 

@@ -48,7 +48,7 @@ template <class T> struct Fused2dSmem {
 
 template <class T, int LIM, int FLUX>
 __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
-    k_fused2d(DevMesh M, const T* U0, const T* __restrict__ Uk, T* out,
+    k_fused2d(DevMesh M, const T* U0, const T* __restrict__ Uk, const T* U2, T* out, T* out2,
               const int* __restrict__ work, int nwork, const T* __restrict__ gslab,
               int* __restrict__ counter, StageParams sp) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
 #pragma unroll
       for (int v = 0; v < NV; v++)
         cp_async_elem_after_reads(&S.cons[s][v][y + NG][x + NG], ptr + v * st);
-      if (sp.k != 0) {
+      if (!sp.plain) {
         const T* src = U0 + (size_t)bb * ncell + y * FB + x;
 #pragma unroll
         for (int v = 0; v < NV; v++) cp_async_elem_after_reads(&S.u0[s][v][tid], src + v * vs);
@@ -170,6 +170,7 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
         for (int v = 0; v < NV; v++) {
           u[v] = S.cons[s][v][y + NG][x + NG];
           out[(size_t)v * vs + (size_t)b * ncell + y * FB + x] = u[v];
+          if (sp.has2) out2[(size_t)v * vs + (size_t)b * ncell + y * FB + x] = u[v];
         }
         if (sp.epilogue) cfl_terms<T, 2>(u, gammad, g, ff, gm1f, idd, smx, cmx);
       }
@@ -225,10 +226,19 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
         for (int v = 0; v < NV; v++) {
           T acc = over_dx<T>(S.fx[v][y][x + 1] - S.fx[v][y][x], dx0, idx0);
           acc += over_dx<T>(S.fy[v][y + 1][x] - S.fy[v][y][x], dx1, idx1);
-          T ut = S.cons[s][v][y + NG][x + NG] - dt * acc;
+          const T uk = S.cons[s][v][y + NG][x + NG];
+          T ut = uk - dt * acc;
           if (v == 8) ut = ut * damp;
-          un[v] = sp.k == 0 ? ut : ca * S.u0[s][v][tid] + cb * ut;
-          out[(size_t)v * vs + (size_t)b * ncell + c] = un[v];
+          un[v] = sp.plain ? ut : ca * S.u0[s][v][tid] + cb * ut;
+          const size_t at = (size_t)v * vs + (size_t)b * ncell + c;
+          if (sp.has2) {
+            // SSPRK(5,4) stage 3: w = a2 U2 + b2 (Uk + c2 dt L); U2 is out's
+            // register (read here before its write), out2 is U0's (in smem)
+            T ut2 = uk - lc[LC_DT2] * acc;
+            if (v == 8) ut2 = ut2 * lc[LC_DAMP2];
+            out2[at] = sp_val<T>(sp.a2, sp.a2f) * U2[at] + sp_val<T>(sp.b2, sp.b2f) * ut2;
+          }
+          out[at] = un[v];
         }
         if (sp.epilogue) cfl_terms<T, 2>(un, gammad, g, ff, gm1f, idd, smx, cmx);
       }

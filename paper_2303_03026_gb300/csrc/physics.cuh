@@ -208,6 +208,18 @@ __device__ __forceinline__ void hll_local(T g, T ig1, const T* ql, const T* qr, 
   }
 }
 
+// TVD Lax-Friedrichs: (F_L + F_R)/2 - c_max (U_R - U_L)/2 with the fastest
+// signal speed of the two sides, c_max = max(|u_L| + c_fL, |u_R| + c_fR)
+template <class T>
+__device__ __forceinline__ void tvdlf_local(T g, T ig1, const T* ql, const T* qr, T bx, T* f) {
+  T UL[8], UR[8], FL[8], FR[8], ptl, ptr;
+  local_cons_flux(ig1, ql, bx, UL, FL, ptl);
+  local_cons_flux(ig1, qr, bx, UR, FR, ptr);
+  T cmax = fmax(fabs(ql[1]) + local_fast(g, ql, bx), fabs(qr[1]) + local_fast(g, qr, bx));
+#pragma unroll
+  for (int c = 0; c < 8; c++) f[c] = T(0.5) * (FL[c] + FR[c]) - T(0.5) * cmax * (UR[c] - UL[c]);
+}
+
 template <class T> struct StarState {
   T rs, vs, ws, bys, bzs, es;
 };
@@ -350,7 +362,8 @@ __device__ __forceinline__ void face_flux_d(int flux, int glm, T g, T ch, const 
   T fl[8];
   const T ig1 = T(1) / (g - T(1));
   if (flux == AMRVAC_FLUX_HLL) hll_local(g, ig1, ql, qr, bns, fl);
-  else hlld_local(g, ig1, ql, qr, bns, fl);
+  else if (flux == AMRVAC_FLUX_HLLD) hlld_local(g, ig1, ql, qr, bns, fl);
+  else tvdlf_local(g, ig1, ql, qr, bns, fl);
   f[0] = fl[0];
   f[1 + D] = fl[1];
   f[1 + t1] = fl[2];

@@ -97,6 +97,27 @@ __device__ __forceinline__ void hll_pair(float g, float ig1, const Side2& q, flo
   }
 }
 
+// TVD Lax-Friedrichs with both sides' physical fluxes in packed lanes
+__device__ __forceinline__ void tvdlf_pair(float g, float ig1, const Side2& q, float bx,
+                                           float* f) {
+  const float bx2 = bx * bx;
+  float2 pt, e;
+  pt_e2(q, bx2, ig1, pt, e);
+  const float2 cf = fast2(g, q.rho, q.p, q.by, q.bz, bx2);
+  const float cmax = fmaxf(fabsf(q.u.x) + cf.x, fabsf(q.u.y) + cf.y);
+  float UL[8], FL[8], UR[8], FR[8];
+  side_flux(q.rho.x, q.u.x, q.v.x, q.w.x, q.by.x, q.bz.x, bx, pt.x, e.x, UL, FL);
+  side_flux(q.rho.y, q.u.y, q.v.y, q.w.y, q.by.y, q.bz.y, bx, pt.y, e.y, UR, FR);
+#pragma unroll
+  for (int c = 0; c < 8; c += 2) {
+    const float2 fl = make_float2(FL[c], FL[c + 1]), fr = make_float2(FR[c], FR[c + 1]);
+    const float2 ul = make_float2(UL[c], UL[c + 1]), ur = make_float2(UR[c], UR[c + 1]);
+    const float2 t = fma2(sp2(-0.5f * cmax), sub2(ur, ul), mul2(sp2(0.5f), add2(fl, fr)));
+    f[c] = t.x;
+    f[c + 1] = t.y;
+  }
+}
+
 __device__ __forceinline__ void hlld_pair(float g, float ig1, const Side2& q, float bx, float* f) {
   const float bx2 = bx * bx;
   float2 pt, e;
@@ -237,7 +258,8 @@ __device__ __forceinline__ void stencil_flux_f2(Acc st, int glm, float g, float 
   float fl[8];
   const float ig1 = 1.f / (g - 1.f);
   if (FLUX == AMRVAC_FLUX_HLL) hll_pair(g, ig1, q, bns, fl);
-  else hlld_pair(g, ig1, q, bns, fl);
+  else if (FLUX == AMRVAC_FLUX_HLLD) hlld_pair(g, ig1, q, bns, fl);
+  else tvdlf_pair(g, ig1, q, bns, fl);
   f[0] = fl[0];
   f[1 + D] = fl[1];
   f[1 + t1] = fl[2];

@@ -104,7 +104,8 @@ __global__ void __launch_bounds__(256) k_flux(DevMesh M, const T* __restrict__ W
 
 template <class T>
 __global__ void __launch_bounds__(256) k_update(DevMesh M, const T* U0,
-                                                const T* Uk, T* out, const T* __restrict__ F0,
+                                                const T* Uk, const T* U2, T* out, T* out2,
+                                                const T* __restrict__ F0,
                                                 const T* __restrict__ F1,
                                                 const T* __restrict__ F2, StageParams sp) {
   const size_t vs = (size_t)M.nblocks * M.ncell;
@@ -123,15 +124,21 @@ __global__ void __launch_bounds__(256) k_update(DevMesh M, const T* U0,
     const double gamma = M.gamma[q];
     double dxmin = dx[0];
     for (int d = 1; d < M.ndim; d++) dxmin = fmin(dxmin, dx[d]);
-    const T damp = sp.glm ? (T)exp(-sp.glm_alpha * rt.ch * rt.dt / dxmin) : T(1);
-    const T dt = (T)rt.dt, a = (T)sp.a, bb = (T)sp.b;
+    const double dt1 = sp.c * rt.dt, dt2 = sp.c2 * rt.dt;
+    const T damp = sp.glm ? (T)exp(-sp.glm_alpha * rt.ch * dt1 / dxmin) : T(1);
+    const T damp2 = sp.glm ? (T)exp(-sp.glm_alpha * rt.ch * dt2 / dxmin) : T(1);
+    const T dt = (T)dt1, dtb = (T)dt2, a = (T)sp.a, bb = (T)sp.b;
+    const T a2 = (T)sp.a2, b2 = (T)sp.b2;
     const T idx0 = (T)dx[0], idx1 = (T)dx[1], idx2 = (T)dx[2];
     for (int c = threadIdx.x; c < M.ncell; c += blockDim.x) {
       int i = c % nx0, j = (c / nx0) % nx1, k = c / (nx0 * nx1);
-      T un[NV];
+      T un[NV], u2n[NV];
       if (rt.dt == 0.0) {
 #pragma unroll
-        for (int v = 0; v < NV; v++) un[v] = Uk[(size_t)v * vs + (size_t)b * M.ncell + c];
+        for (int v = 0; v < NV; v++) {
+          un[v] = Uk[(size_t)v * vs + (size_t)b * M.ncell + c];
+          u2n[v] = un[v];
+        }
       } else {
         size_t f0 = ((size_t)k * nx1 + j) * (nx0 + 1) + i;
         size_t f1 = ((size_t)k * (nx1 + 1) + j) * nx0 + i;
@@ -151,11 +158,20 @@ __global__ void __launch_bounds__(256) k_update(DevMesh M, const T* U0,
           size_t at = (size_t)v * vs + (size_t)b * M.ncell + c;
           T ut = Uk[at] - dt * acc;
           if (v == 8) ut = ut * damp;
-          un[v] = sp.k == 0 ? ut : a * U0[at] + bb * ut;
+          un[v] = sp.plain ? ut : a * U0[at] + bb * ut;
+          if (sp.has2) {
+            T ut2 = Uk[at] - dtb * acc;
+            if (v == 8) ut2 = ut2 * damp2;
+            u2n[v] = a2 * U2[at] + b2 * ut2;
+          }
         }
       }
+      // written after every read: out may be U2's register and out2 U0's
 #pragma unroll
-      for (int v = 0; v < NV; v++) out[(size_t)v * vs + (size_t)b * M.ncell + c] = un[v];
+      for (int v = 0; v < NV; v++) {
+        out[(size_t)v * vs + (size_t)b * M.ncell + c] = un[v];
+        if (sp.has2) out2[(size_t)v * vs + (size_t)b * M.ncell + c] = u2n[v];
+      }
       if (sp.epilogue) accumulate_cell(M, un, gamma, dx, p);
     }
     if (sp.epilogue) block_reduce_store(p, M.part + (size_t)b * NPART);
@@ -343,7 +359,15 @@ __global__ void k_convert(const S* __restrict__ src, D* __restrict__ dst, size_t
 StageParams make_stage_params(const amrvac_state* s, int k, int epilogue) {
   StageParams sp;
   sp.k = k;
-  stage_coeffs(s->cfg.time, k, &sp.a, &sp.b);
+  const StageCoeffs co = stage_coeffs(s->cfg.time, k);
+  sp.a = co.a;
+  sp.b = co.b;
+  sp.c = co.c;
+  sp.a2 = co.a2;
+  sp.b2 = co.b2;
+  sp.c2 = co.c2;
+  sp.plain = co.a == 0.0 && co.b == 1.0;
+  sp.has2 = co.b2 != 0.0;
   sp.courant = s->cfg.courant;
   sp.glm_alpha = s->cfg.glm_alpha;
   sp.small_density = s->cfg.small_density;
@@ -356,6 +380,8 @@ StageParams make_stage_params(const amrvac_state* s, int k, int epilogue) {
   sp.pressure_ff = s->cfg.precision == AMRVAC_FP32_BULK && s->cfg.pressure == AMRVAC_PRESSURE_FF;
   sp.af = (float)sp.a;
   sp.bf = (float)sp.b;
+  sp.a2f = (float)sp.a2;
+  sp.b2f = (float)sp.b2;
   sp.small_density_f = (float)sp.small_density;
   sp.small_pressure_f = (float)sp.small_pressure;
   return sp;
@@ -363,7 +389,7 @@ StageParams make_stage_params(const amrvac_state* s, int k, int epilogue) {
 
 // per-(instance, level) stage constants of the fused kernels from InstRT and
 // the level's cell size (one thread per level)
-__global__ void k_level_consts(DevMesh M, double glm_alpha, int glm) {
+__global__ void k_level_consts(DevMesh M, double glm_alpha, int glm, double c, double c2) {
   const int q = blockIdx.x, L = threadIdx.x;
   if (q >= M.ninst || L >= MAXLEV) return;
   const InstRT rt = M.rt[q];
@@ -373,13 +399,19 @@ __global__ void k_level_consts(DevMesh M, double glm_alpha, int glm) {
   const double g = M.gamma[q];
   float* f = M.lcf + (q * MAXLEV + L) * LC_N;
   double* d = M.lcd + (q * MAXLEV + L) * LC_N;
-  d[LC_DT] = rt.dt;
-  f[LC_DT] = (float)rt.dt;
+  // the stage's Euler step c dt and its psi damping factor (float bulk: exp of
+  // the float-rounded argument); the same for the second output's c2 dt
+  const double dt1 = c * rt.dt, dt2 = c2 * rt.dt;
+  d[LC_DT] = dt1;
+  f[LC_DT] = (float)dt1;
   d[LC_CH] = rt.ch;
   f[LC_CH] = (float)rt.ch;
-  d[LC_DAMP] = glm ? exp(-glm_alpha * rt.ch * rt.dt / dxmin) : 1.0;
-  // float bulk: the damping factor is the exp of the float-rounded argument
-  f[LC_DAMP] = glm ? expf((float)(-glm_alpha * rt.ch * rt.dt / dxmin)) : 1.0f;
+  d[LC_DAMP] = glm ? exp(-glm_alpha * rt.ch * dt1 / dxmin) : 1.0;
+  f[LC_DAMP] = glm ? expf((float)(-glm_alpha * rt.ch * dt1 / dxmin)) : 1.0f;
+  d[LC_DT2] = dt2;
+  f[LC_DT2] = (float)dt2;
+  d[LC_DAMP2] = glm ? exp(-glm_alpha * rt.ch * dt2 / dxmin) : 1.0;
+  f[LC_DAMP2] = glm ? expf((float)(-glm_alpha * rt.ch * dt2 / dxmin)) : 1.0f;
   for (int e = 0; e < 3; e++) {
     d[LC_DX + e] = dx[e];
     f[LC_DX + e] = (float)dx[e];
@@ -394,14 +426,16 @@ __global__ void k_level_consts(DevMesh M, double glm_alpha, int glm) {
   f[LC_GM1] = (float)(g - 1.0);
 }
 
-int launch_level_consts(amrvac_state* s) {
-  k_level_consts<<<s->ninst, MAXLEV, 0, s->stream>>>(s->mesh, s->cfg.glm_alpha, s->cfg.glm);
+int launch_level_consts(amrvac_state* s, int k) {
+  const StageCoeffs co = stage_coeffs(s->cfg.time, k);
+  k_level_consts<<<s->ninst, MAXLEV, 0, s->stream>>>(s->mesh, s->cfg.glm_alpha, s->cfg.glm,
+                                                      co.c, co.c2);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 template <class T> static int plain_stage_t(amrvac_state* s, int k, int epilogue) {
-  int u0, uin, uout;
-  stage_buffers(s->cfg.time, k, &u0, &uin, &uout);
+  const StageBuffers sb = stage_buffers(s->cfg.time, k);
+  const int uin = sb.uin;
   StageParams sp = make_stage_params(s, k, epilogue);
   const DevMesh& M = s->mesh;
   size_t work = s->npad * s->nblocks;
@@ -411,9 +445,11 @@ template <class T> static int plain_stage_t(amrvac_state* s, int k, int epilogue
     k_flux<T><<<grid_for(s->nface[d] * s->nblocks, 256), 256, 0, s->stream>>>(
         M, (const T*)s->W, (T*)s->F[d], d, s->P[0], s->P[1], s->P[2], sp);
   int grid = s->nblocks < 152 * 16 ? s->nblocks : 152 * 16;
-  k_update<T><<<grid, 256, 0, s->stream>>>(M, (const T*)s->U[u0], (const T*)s->U[uin],
-                                           (T*)s->U[uout], (const T*)s->F[0],
-                                           (const T*)s->F[1], (const T*)s->F[2], sp);
+  k_update<T><<<grid, 256, 0, s->stream>>>(
+      M, (const T*)s->U[sb.u0], (const T*)s->U[uin],
+      sb.u2 >= 0 ? (const T*)s->U[sb.u2] : nullptr, (T*)s->U[sb.out],
+      sb.out2 >= 0 ? (T*)s->U[sb.out2] : nullptr, (const T*)s->F[0], (const T*)s->F[1],
+      (const T*)s->F[2], sp);
   if (cudaPeekAtLastError() != cudaSuccess) return -1;
   return 2 + s->ndim;
 }

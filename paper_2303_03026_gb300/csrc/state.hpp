@@ -50,41 +50,68 @@ struct amrvac_state {
 
 namespace amrvac {
 
-// stage coefficients of the Shu-Osher form: out = a U^n + b (U + dt L(U))
-inline void stage_coeffs(int time, int k, double* a, double* b) {
-  if (k == 0) {
-    *a = 0.0;
-    *b = 1.0;
-  } else if (time == AMRVAC_SSPRK2) {
-    *a = 0.5;
-    *b = 0.5;
-  } else if (k == 1) {
-    *a = 0.75;
-    *b = 0.25;
+// Shu-Osher coefficients of stage k: out = a U0 + b (U_in + c dt L(U_in)) and,
+// for SSPRK(5,4) stage 3 only (b2 != 0), out2 = a2 U2 + b2 (U_in + c2 dt L(U_in)).
+// SSPRK(4,3) and SSPRK(5,4) are the optimal schemes of Spiteri & Ruuth 2002:
+//   SSPRK(4,3): u1 = u0 + dt/2 L(u0), u2 = u1 + dt/2 L(u1),
+//               u3 = 2/3 u0 + 1/3 (u2 + dt/2 L(u2)), u4 = u3 + dt/2 L(u3)
+//   SSPRK(5,4): u1 = u0 + 0.391752226571890 dt L(u0)
+//               u2 = 0.444370493651235 u0 + 0.555629506348765 u1 + 0.368410593050371 dt L(u1)
+//               u3 = 0.620101851488403 u0 + 0.379898148511597 u2 + 0.251891774271694 dt L(u2)
+//               u4 = 0.178079954393132 u0 + 0.821920045606868 u3 + 0.544974750228521 dt L(u3)
+//               u5 = 0.517231671970585 u2 + 0.096059710526147 u3 + 0.063692468666290 dt L(u3)
+//                    + 0.386708617503269 u4 + 0.226007483236906 dt L(u4)
+// with w = the u2, u3, L(u3) part of u5 produced by stage 3.
+struct StageCoeffs {
+  double a, b, c, a2, b2, c2;
+};
+
+inline StageCoeffs stage_coeffs(int time, int k) {
+  StageCoeffs r{0.0, 1.0, 1.0, 0.0, 0.0, 0.0};
+  if (time == AMRVAC_SSPRK2) {
+    if (k == 1) r.a = 0.5, r.b = 0.5;
+  } else if (time == AMRVAC_SSPRK3) {
+    if (k == 1) r.a = 0.75, r.b = 0.25;
+    if (k == 2) r.a = 1.0 / 3.0, r.b = 2.0 / 3.0;
+  } else if (time == AMRVAC_SSPRK43) {
+    r.c = 0.5;
+    if (k == 2) r.a = 2.0 / 3.0, r.b = 1.0 / 3.0;
   } else {
-    *a = 1.0 / 3.0;
-    *b = 2.0 / 3.0;
+    if (k == 0) {
+      r.c = 0.391752226571890;
+    } else if (k == 1) {
+      r.a = 0.444370493651235, r.b = 0.555629506348765, r.c = 0.368410593050371 / r.b;
+    } else if (k == 2) {
+      r.a = 0.620101851488403, r.b = 0.379898148511597, r.c = 0.251891774271694 / r.b;
+    } else if (k == 3) {
+      r.a = 0.178079954393132, r.b = 0.821920045606868, r.c = 0.544974750228521 / r.b;
+      r.a2 = 0.517231671970585, r.b2 = 0.096059710526147, r.c2 = 0.063692468666290 / r.b2;
+    } else {
+      r.a = 1.0, r.b = 0.386708617503269, r.c = 0.226007483236906 / r.b;
+    }
   }
+  return r;
 }
 
-inline int num_stages(int time) { return time == AMRVAC_SSPRK2 ? 2 : 3; }
+inline int num_stages(int time) {
+  return time == AMRVAC_SSPRK2 ? 2 : time == AMRVAC_SSPRK3 ? 3 : time == AMRVAC_SSPRK43 ? 4 : 5;
+}
 
-// buffers read (U0, Uin) and written (out) by stage k
-inline void stage_buffers(int time, int k, int* u0, int* uin, int* out) {
-  *u0 = 0;
-  if (k == 0) {
-    *uin = 0;
-    *out = 1;
-  } else if (time == AMRVAC_SSPRK2) {
-    *uin = 1;
-    *out = 0;
-  } else if (k == 1) {
-    *uin = 1;
-    *out = 2;
-  } else {
-    *uin = 2;
-    *out = 0;
-  }
+// state registers used by stage k: U0, U_in, U2 (-1: none) -> out, out2 (-1)
+struct StageBuffers {
+  int u0, uin, u2, out, out2;
+};
+
+inline StageBuffers stage_buffers(int time, int k) {
+  if (k == 0) return {0, 0, -1, 1, -1};
+  if (time == AMRVAC_SSPRK2) return {0, 1, -1, 0, -1};
+  if (k == 1) return {0, 1, -1, 2, -1};
+  if (time == AMRVAC_SSPRK3) return {0, 2, -1, 0, -1};
+  if (time == AMRVAC_SSPRK43) return k == 2 ? StageBuffers{0, 2, -1, 1, -1}
+                                            : StageBuffers{0, 1, -1, 0, -1};
+  if (k == 2) return {0, 2, -1, 1, -1};
+  if (k == 3) return {0, 1, 2, 2, 0};
+  return {0, 2, -1, 0, -1};
 }
 
 StageParams make_stage_params(const amrvac_state* s, int k, int epilogue);
@@ -95,7 +122,7 @@ int launch_plain_stage(amrvac_state* s, int k, int epilogue);
 int launch_cfl_partials(amrvac_state* s, int buffer);
 int launch_finalize(amrvac_state* s, int advance);
 int launch_sums(amrvac_state* s, int buffer);
-int launch_level_consts(amrvac_state* s);
+int launch_level_consts(amrvac_state* s, int k);
 int launch_fill_ghosts(amrvac_state* s, int buffer, void* out);
 int launch_convert(amrvac_state* s, const void* src, int src_prec, void* dst, int dst_prec,
                    size_t n);
