@@ -93,7 +93,8 @@ def lib():
 
 
 _FLUX = {"hll": 0, "hlld": 1, "tvdlf": 2}
-_LIM = {"minmod": 0, "vanleer": 1, "koren": 2}
+_LIM = {"minmod": 0, "vanleer": 1, "koren": 2, "superbee": 3, "woodward": 4, "mcbeta": 5,
+        "albada": 6}
 _TIME = {"ssprk2": 0, "ssprk3": 1, "ssprk43": 2, "ssprk54": 3}
 _BC = {"periodic": 0, "outflow": 1}
 

@@ -13,9 +13,11 @@
  *    monopole control, option `glm`); psi enters only through the interface
  *    solve and an exponential damping after each Euler sub-step; no
  *    non-conservative sources.
- *  - reconstruction on primitive variables (Sect. 3, "usually on the primitive
- *    variables") with the `minmod`, `vanleer` and `koren` limiters of the
- *    limiter table (orders 2, 2, 3; two ghost cells).
+ *  - reconstruction on primitive variables (Sect. 3 reconstructs primitives by
+ *    default) with the two-ghost-cell limiters `minmod`, `vanleer`, `koren`,
+ *    `superbee`, `woodward`, `mcbeta` (beta = 1.4) and `albada` of the limiter
+ *    table (order 3 for koren, 2 for the others); albada in its TVD form
+ *    (zero slope at extrema, like the others).
  *  - a face whose reconstructed density or pressure is not positive falls back
  *    to first order (cell values) on both sides (Sect. 7.4 mentions checks on
  *    reconstructions; the fallback form is our reading).
@@ -177,10 +179,27 @@ static double minmod2(double a, double b) {
   return 0.0;
 }
 
+/* slope of the symmetric TVD limiters of the limiter table, phi(r) dp with
+ * r = dm/dp > 0 (the caller handles dm dp <= 0):
+ *   3 superbee (Roe 1985):      phi = max(min(2r, 1), min(r, 2))
+ *   4 woodward (van Leer 1977, monotonized central): phi = min(2r, (1+r)/2, 2)
+ *   5 mcbeta (van Leer 1977):   phi = min(beta r, (1+r)/2, beta), beta = 1.4
+ *   6 albada (van Albada 1982): phi = (r^2 + r)/(r^2 + 1) */
+static double sym_slope(int lim, double dm, double dp) {
+  double am = fabs(dm), ap = fabs(dp);
+  switch (lim) {
+    case 3: return sgn(dp) * dmax(dmin(2.0 * am, ap), dmin(am, 2.0 * ap));
+    case 4: return sgn(dp) * dmin(dmin(2.0 * am, 0.5 * (am + ap)), 2.0 * ap);
+    case 5: return sgn(dp) * dmin(dmin(1.4 * am, 0.5 * (am + ap)), 1.4 * ap);
+    default: return dm * dp * (dm + dp) / (dm * dm + dp * dp);
+  }
+}
+
 /* left state at the right face (i+1/2) of the cell with values (a, b, c) */
 static double recon_plus(int lim, double a, double b, double c) {
   double dm = b - a, dp = c - b;
   if (!(dm * dp > 0.0)) return b;
+  if (lim >= 3) return b + 0.5 * sym_slope(lim, dm, dp);
   switch (lim) {
     case 0: return b + 0.5 * minmod2(dm, dp);
     case 1: return b + 0.5 * (2.0 * dm * dp / (dm + dp));
@@ -197,6 +216,7 @@ static double recon_plus(int lim, double a, double b, double c) {
 static double recon_minus(int lim, double a, double b, double c) {
   double dm = b - a, dp = c - b;
   if (!(dm * dp > 0.0)) return b;
+  if (lim >= 3) return b - 0.5 * sym_slope(lim, dm, dp);
   switch (lim) {
     case 0: return b - 0.5 * minmod2(dm, dp);
     case 1: return b - 0.5 * (2.0 * dm * dp / (dm + dp));
