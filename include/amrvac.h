@@ -66,7 +66,18 @@ typedef enum {
 /* flux-scheme table of Sect. 3.2.1: HLL (Harten 1983), HLLD (Miyoshi & Kusano
  * 2005), TVD Lax-Friedrichs (local LF with the fastest signal speed) */
 typedef enum { AMRVAC_FLUX_HLL = 0, AMRVAC_FLUX_HLLD = 1, AMRVAC_FLUX_TVDLF = 2 } amrvac_flux;
-typedef enum { AMRVAC_LIM_MINMOD = 0, AMRVAC_LIM_VANLEER = 1, AMRVAC_LIM_KOREN = 2 } amrvac_limiter;
+/* two-ghost-cell limiters of the limiter table (Sect. 3.1.1): minmod, van Leer
+ * 1974, Koren 1993 (third order), superbee (Roe 1985), woodward (monotonized
+ * central, van Leer 1977), mcbeta (beta = 1.4), van Albada 1982 (TVD form) */
+typedef enum {
+  AMRVAC_LIM_MINMOD = 0,
+  AMRVAC_LIM_VANLEER = 1,
+  AMRVAC_LIM_KOREN = 2,
+  AMRVAC_LIM_SUPERBEE = 3,
+  AMRVAC_LIM_WOODWARD = 4,
+  AMRVAC_LIM_MCBETA = 5,
+  AMRVAC_LIM_ALBADA = 6
+} amrvac_limiter;
 /* time-integration table of Sect. 3: SSPRK(2,2), SSPRK(3,3) (Gottlieb 2005),
  * SSPRK(4,3) and SSPRK(5,4) (Spiteri & Ruuth 2002) */
 typedef enum {

@@ -36,7 +36,8 @@ bool config_ok(const amrvac_config* c, std::string& err) {
   for (int d = 0; d < c->ndim; d++)
     if (c->block_nx[d] < 4 || c->block_nx[d] > 4096) return err = "block_nx must be 4..4096", false;
   if (c->flux < AMRVAC_FLUX_HLL || c->flux > AMRVAC_FLUX_TVDLF) return err = "bad flux", false;
-  if (c->limiter < 0 || c->limiter > 2) return err = "bad limiter", false;
+  if (c->limiter < AMRVAC_LIM_MINMOD || c->limiter > AMRVAC_LIM_ALBADA)
+    return err = "bad limiter", false;
   if (c->time < AMRVAC_SSPRK2 || c->time > AMRVAC_SSPRK54) return err = "bad time", false;
   if (c->precision != AMRVAC_FP64 && c->precision != AMRVAC_FP32_BULK)
     return err = "bad precision", false;

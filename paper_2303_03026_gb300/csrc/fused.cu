@@ -19,7 +19,8 @@ template <class T, int DIM> static int by_limiter(amrvac_state* s, int k, int ep
     case AMRVAC_LIM_VANLEER: return launch_fused_l<T, DIM, AMRVAC_LIM_VANLEER>(s, k, epilogue);
     case AMRVAC_LIM_KOREN: return launch_fused_l<T, DIM, AMRVAC_LIM_KOREN>(s, k, epilogue);
   }
-  return -1;
+  // the other limiters share one instantiation with a runtime limiter
+  return launch_fused_l<T, DIM, -1>(s, k, epilogue);
 }
 
 int launch_fused_stage(amrvac_state* s, int k, int epilogue) {

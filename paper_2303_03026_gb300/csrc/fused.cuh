@@ -166,20 +166,21 @@ template <> __device__ __forceinline__ double over_dx(double a, double dx, doubl
 template <> __device__ __forceinline__ float over_dx(float a, float, float idx) { return a * idx; }
 
 // face flux from a 4-cell stencil accessor S(v, t), t = 0..3 for cells
-// f-2, f-1, f, f+1 around the face f-1/2
+// f-2, f-1, f, f+1 around the face f-1/2; LIM < 0: runtime limiter lim
 template <class T, int D, int LIM, int FLUX, class Acc>
-__device__ __forceinline__ void stencil_flux(Acc S, int glm, T g, T ch, T* f) {
+__device__ __forceinline__ void stencil_flux(Acc S, int glm, T g, T ch, T* f, int lim) {
   if constexpr (sizeof(T) == 4) {
     // FP32 bulk: left/right states packed in float2 lanes (physics_f2.cuh)
-    stencil_flux_f2<D, LIM, FLUX>(S, glm, g, ch, f);
+    stencil_flux_f2<D, LIM, FLUX>(S, glm, g, ch, f, lim);
     return;
   }
+  const int L = LIM >= 0 ? LIM : lim;
   T wl[NV], wr[NV];
 #pragma unroll
   for (int v = 0; v < NV; v++) {
     T a = S(v, 0), b = S(v, 1), c = S(v, 2), e = S(v, 3);
-    wl[v] = recon_plus<T>(LIM, a, b, c);
-    wr[v] = recon_minus<T>(LIM, b, c, e);
+    wl[v] = recon_plus<T>(L, a, b, c);
+    wr[v] = recon_minus<T>(L, b, c, e);
   }
   if (!(wl[0] > T(0)) || !(wl[4] > T(0)) || !(wr[0] > T(0)) || !(wr[4] > T(0))) {
 #pragma unroll
@@ -462,7 +463,7 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
         int s = t == 0 ? s0 : (t == 1 ? s1 : (t == 2 ? s2 : s3));
         return S.plane[s][v][y + NG][x + NG];
       };
-      stencil_flux<T, 2, LIM, FLUX>(acc, sp.glm, g, ch, f);
+      stencil_flux<T, 2, LIM, FLUX>(acc, sp.glm, g, ch, f, sp.limiter);
     };
 
     T fzp[NV];
@@ -504,11 +505,11 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
         const int fyr = owner ? y : FB, fyc = owner ? x : hr;
         T f[NV];
         auto ax = [&](int v, int t) -> T { return S.plane[sl][v][fxr + NG][fxc + t]; };
-        stencil_flux<T, 0, LIM, FLUX>(ax, sp.glm, g, ch, f);
+        stencil_flux<T, 0, LIM, FLUX>(ax, sp.glm, g, ch, f, sp.limiter);
 #pragma unroll
         for (int v = 0; v < NV; v++) S.fx[fb][v][fxr][fxc] = f[v];
         auto ay = [&](int v, int t) -> T { return S.plane[sl][v][fyr + t][fyc + NG]; };
-        stencil_flux<T, 1, LIM, FLUX>(ay, sp.glm, g, ch, f);
+        stencil_flux<T, 1, LIM, FLUX>(ay, sp.glm, g, ch, f, sp.limiter);
 #pragma unroll
         for (int v = 0; v < NV; v++) S.fy[fb][v][fyr][fyc] = f[v];
       }

@@ -206,11 +206,11 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
         const int fyr = owner ? y : FB, fyc = owner ? x : hr;
         T f[NV];
         auto ax = [&](int v, int t) -> T { return S.prim[v][fxr + NG][fxc + t]; };
-        stencil_flux<T, 0, LIM, FLUX>(ax, sp.glm, g, ch, f);
+        stencil_flux<T, 0, LIM, FLUX>(ax, sp.glm, g, ch, f, sp.limiter);
 #pragma unroll
         for (int v = 0; v < NV; v++) S.fx[v][fxr][fxc] = f[v];
         auto ay = [&](int v, int t) -> T { return S.prim[v][fyr + t][fyc + NG]; };
-        stencil_flux<T, 1, LIM, FLUX>(ay, sp.glm, g, ch, f);
+        stencil_flux<T, 1, LIM, FLUX>(ay, sp.glm, g, ch, f, sp.limiter);
 #pragma unroll
         for (int v = 0; v < NV; v++) S.fy[v][fyr][fyc] = f[v];
       }

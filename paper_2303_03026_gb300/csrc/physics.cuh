@@ -130,10 +130,23 @@ template <class T> __device__ __forceinline__ T minmod2(T a, T b) {
   return (a * b > T(0)) ? sgnT(a) * fmin(fabs(a), fabs(b)) : T(0);
 }
 
+// slope phi(r) dp (r = dm/dp > 0) of the symmetric limiters superbee,
+// woodward (monotonized central), mcbeta (beta = 1.4) and van Albada
+template <class T> __device__ __forceinline__ T sym_slope(int lim, T dm, T dp) {
+  const T am = fabs(dm), ap = fabs(dp);
+  if (lim == AMRVAC_LIM_SUPERBEE) return sgnT(dp) * fmax(fmin(T(2) * am, ap), fmin(am, T(2) * ap));
+  if (lim == AMRVAC_LIM_WOODWARD)
+    return sgnT(dp) * fmin(fmin(T(2) * am, T(0.5) * (am + ap)), T(2) * ap);
+  if (lim == AMRVAC_LIM_MCBETA)
+    return sgnT(dp) * fmin(fmin(T(1.4) * am, T(0.5) * (am + ap)), T(1.4) * ap);
+  return dm * dp * (dm + dp) / (dm * dm + dp * dp);
+}
+
 // face value at i+1/2 from the cell with values (a, b, c) = (w_{i-1}, w_i, w_{i+1})
 template <class T> __device__ __forceinline__ T recon_plus(int lim, T a, T b, T c) {
   T dm = b - a, dp = c - b;
   if (!(dm * dp > T(0))) return b;
+  if (lim >= AMRVAC_LIM_SUPERBEE) return b + T(0.5) * sym_slope(lim, dm, dp);
   if (lim == AMRVAC_LIM_MINMOD) return b + T(0.5) * minmod2(dm, dp);
   if (lim == AMRVAC_LIM_VANLEER) return b + T(0.5) * (T(2) * dm * dp / (dm + dp));
   T am = fabs(dm), ap = fabs(dp);
@@ -145,6 +158,7 @@ template <class T> __device__ __forceinline__ T recon_plus(int lim, T a, T b, T 
 template <class T> __device__ __forceinline__ T recon_minus(int lim, T a, T b, T c) {
   T dm = b - a, dp = c - b;
   if (!(dm * dp > T(0))) return b;
+  if (lim >= AMRVAC_LIM_SUPERBEE) return b - T(0.5) * sym_slope(lim, dm, dp);
   if (lim == AMRVAC_LIM_MINMOD) return b - T(0.5) * minmod2(dm, dp);
   if (lim == AMRVAC_LIM_VANLEER) return b - T(0.5) * (T(2) * dm * dp / (dm + dp));
   T am = fabs(dm), ap = fabs(dp);

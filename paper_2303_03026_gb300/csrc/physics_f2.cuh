@@ -224,14 +224,17 @@ __device__ __forceinline__ float2 vanleer_pair(float a, float b, float c, float 
 // Face flux along D from the 4-cell stencils of the 9 primitive variables:
 // st(v, t) for cells f-2, f-1, f, f+1.  Positivity fallback and glm as in
 // face_flux_d.
+// LIM < 0: the limiter is the runtime value lim.
 template <int D, int LIM, int FLUX, class Acc>
-__device__ __forceinline__ void stencil_flux_f2(Acc st, int glm, float g, float ch, float* f) {
+__device__ __forceinline__ void stencil_flux_f2(Acc st, int glm, float g, float ch, float* f,
+                                                int lim) {
+  const int L = LIM >= 0 ? LIM : lim;
   float2 w[NV];
 #pragma unroll
   for (int v = 0; v < NV; v++) {
     float a = st(v, 0), b = st(v, 1), c = st(v, 2), e = st(v, 3);
     if (LIM == AMRVAC_LIM_VANLEER) w[v] = vanleer_pair(a, b, c, e);
-    else w[v] = make_float2(recon_plus<float>(LIM, a, b, c), recon_minus<float>(LIM, b, c, e));
+    else w[v] = make_float2(recon_plus<float>(L, a, b, c), recon_minus<float>(L, b, c, e));
   }
   if (!(w[0].x > 0.f) || !(w[4].x > 0.f) || !(w[0].y > 0.f) || !(w[4].y > 0.f)) {
 #pragma unroll

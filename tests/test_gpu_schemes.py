@@ -1,6 +1,7 @@
 """GPU parity of the wider scheme family against the FP64 CPU oracle: the TVD
-Lax-Friedrichs flux and the SSPRK(4,3) / SSPRK(5,4) time steppers, on the plain
-per-block path and the fused kernels (2D, 3D, block AMR), FP64 and FP32 bulk.
+Lax-Friedrichs flux, the SSPRK(4,3) / SSPRK(5,4) time steppers and the
+superbee / woodward / mcbeta / albada limiters, on the plain per-block path and
+the fused kernels (2D, 3D, block AMR), FP64 and FP32 bulk.
 
 Each stage is checked from identical register contents laid out as the C ABI
 documents the stage buffers (U0, U_in [, U2] -> out [, out2]); full steps are
@@ -165,3 +166,21 @@ def test_full_steps_match_oracle_run(amr, orc, kernel, time, flux):
     scale = np.abs(W.U).max()
     np.testing.assert_allclose(d["sums"], so, rtol=1e-11, atol=1e-13 * scale)
     S.close()
+
+
+NEW_LIMITERS = ["superbee", "woodward", "mcbeta", "albada"]
+
+
+@pytest.mark.parametrize("kernel", ["plain", "auto"])
+@pytest.mark.parametrize("limiter", NEW_LIMITERS)
+def test_new_limiter_stage_parity_fp64(amr, orc, kernel, limiter):
+    for W in _small_cases("fp64"):
+        W.cfg.limiter = limiter
+        _scheme_stage_parity(amr, orc, W, kernel, 1e-12)
+
+
+@pytest.mark.parametrize("limiter", NEW_LIMITERS)
+def test_new_limiter_stage_parity_fp32(amr, orc, limiter):
+    for W in _small_cases("fp32")[:2]:
+        W.cfg.limiter = limiter
+        _scheme_stage_parity(amr, orc, W, "auto", 1e-5)
