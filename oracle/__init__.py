@@ -48,7 +48,8 @@ class _Config(C.Structure):
                 ("limiter", C.c_int), ("time", C.c_int), ("glm", C.c_int),
                 ("glm_alpha", C.c_double), ("courant", C.c_double),
                 ("bc", (C.c_int * 2) * 3), ("small_density", C.c_double),
-                ("small_pressure", C.c_double), ("check_small_values", C.c_int)]
+                ("small_pressure", C.c_double), ("check_small_values", C.c_int),
+                ("fix_small_values", C.c_int)]
 
 
 class _Instance(C.Structure):
@@ -87,6 +88,8 @@ def lib():
                                            C.POINTER(C.c_double)]
             L.orc_stage_coeffs6.argtypes = [C.c_int, C.c_int, dp]
             L.orc_num_stages.argtypes = [C.c_int]
+            L.orc_fix_small.argtypes = [C.c_void_p, dp, C.c_int]
+            L.orc_fix_small.restype = C.c_long
             L.orc_num_stages.restype = C.c_int
             _lib = L
     return _lib
@@ -97,6 +100,7 @@ _LIM = {"minmod": 0, "vanleer": 1, "koren": 2, "superbee": 3, "woodward": 4, "mc
         "albada": 6}
 _TIME = {"ssprk2": 0, "ssprk3": 1, "ssprk43": 2, "ssprk54": 3}
 _BC = {"periodic": 0, "outflow": 1}
+_FIX = {"off": 0, "replace": 1, "average": 2}
 
 
 class Mesh:
@@ -119,6 +123,7 @@ class Mesh:
         c.small_density = float(cfg.small_density)
         c.small_pressure = float(cfg.small_pressure)
         c.check_small_values = int(bool(cfg.check_small_values))
+        c.fix_small_values = _FIX[getattr(cfg, "fix_small_values", "off")]
         arr = (_Instance * len(instances))()
         for q, inst in enumerate(instances):
             for d in range(3):
@@ -192,6 +197,12 @@ class Mesh:
         out2 = np.zeros_like(Uk)
         st = lib().orc_stage2(self._h, k, dt, ch, U0, Uk, U2, out, out2, None, 0)
         return out, out2, st
+
+    def fix_small(self, U, method):
+        """fix_small_values on a copy of U; returns (U, number of cells fixed)."""
+        U = self._u(U).copy()
+        n = lib().orc_fix_small(self._h, U, _FIX[method])
+        return U, n
 
     def cfl(self, U, t=None, t_end=None):
         t = np.zeros(self.ninst) if t is None else np.ascontiguousarray(

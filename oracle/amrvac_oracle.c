@@ -35,6 +35,10 @@
  *    Requires full 2:1 balance (checked at creation).  No refluxing.
  *  - outflow boundary: a ghost takes the value of the nearest in-domain cell of
  *    its own level (zero gradient, Sect. 3.1.1 and Sect. 3.2.1).
+ *  - fix_small_values (Sect. 7.4 bootstrapping, off by default): after every
+ *    stage, cells below small_density / small_pressure are replaced by the
+ *    floors or by the average over their non-small same-level face
+ *    neighbours, on primitive variables, never changing B (orc_fix_small).
  */
 #include "amrvac_oracle.h"
 
@@ -766,9 +770,17 @@ int orc_fill_ghosts(const orc_mesh* m, const double* U, double* padded) {
   return 0;
 }
 
+/* small: density or pressure below its floor, or not positive at all */
+static int small_prim(const orc_mesh* m, const double* w) {
+  return !(w[0] > 0.0 && w[0] >= m->cfg.small_density) ||
+         !(w[4] > 0.0 && w[4] >= m->cfg.small_pressure);
+}
+
+/* check_small_values reports small values unless fix_small_values repairs
+ * them (Sect. 7.4: with the fix on, the bootstrapping replaces the stop) */
 static int small_values(const orc_mesh* m, const double* w) {
-  if (!m->cfg.check_small_values) return 0;
-  return !(w[0] > m->cfg.small_density) || !(w[4] > m->cfg.small_pressure);
+  if (!m->cfg.check_small_values || m->cfg.fix_small_values) return 0;
+  return small_prim(m, w);
 }
 
 /* One stage on one block.  scratch: cons/prim padded (NV*np each) + fluxes. */
@@ -967,6 +979,102 @@ int orc_stage2(const orc_mesh* m, int k, const double* dt, const double* ch, con
 }
 
 /* ------------------------------------------------------------------------ */
+/* bootstrapping: fix_small_values (Sect. 7.4)                               */
+/* ------------------------------------------------------------------------ */
+
+static int is_small(const orc_mesh* m, double gamma, const double* u) {
+  double w[NV];
+  orc_cons_to_prim(gamma, u, w);
+  return small_prim(m, w);
+}
+
+static void cell_of(const orc_mesh* m, const double* U, int b, size_t c, double* u) {
+  const size_t nvb = (size_t)m->nblocks * m->ncell;
+  for (int v = 0; v < NV; v++) u[v] = U[(size_t)v * nvb + (size_t)b * m->ncell + c];
+}
+
+long orc_fix_small(const orc_mesh* m, double* U, int method) {
+  const size_t nvb = (size_t)m->nblocks * m->ncell;
+  const int* nx = m->cfg.nx;
+  unsigned char* flag = (unsigned char*)calloc(nvb, 1);
+  long nfix = 0;
+  /* 1. find every small cell before changing any */
+  for (int b = 0; b < m->nblocks; b++) {
+    const double gamma = m->inst[m->blk[b].inst].gamma;
+    for (int c = 0; c < m->ncell; c++) {
+      double u[NV];
+      cell_of(m, U, b, (size_t)c, u);
+      flag[(size_t)b * m->ncell + c] = (unsigned char)is_small(m, gamma, u);
+    }
+  }
+  /* 2. fix them; averages read only cells that are not small (never changed) */
+  for (int b = 0; b < m->nblocks; b++) {
+    const blockinfo* B = &m->blk[b];
+    const double gamma = m->inst[B->inst].gamma;
+    for (int c = 0; c < m->ncell; c++) {
+      if (!flag[(size_t)b * m->ncell + c]) continue;
+      nfix++;
+      int ijk[3] = {c % nx[0], (c / nx[0]) % nx[1], c / (nx[0] * nx[1])};
+      double u[NV], w[NV];
+      cell_of(m, U, b, (size_t)c, u);
+      double rho, vel[3], p;
+      int n = 0;
+      double sr = 0.0, sv[3] = {0.0, 0.0, 0.0}, sp = 0.0;
+      if (method == 2) {
+        for (int d = 0; d < m->cfg.ndim; d++)
+          for (int side = 0; side < 2; side++) {
+            int q[3] = {ijk[0], ijk[1], ijk[2]};
+            q[d] += side ? 1 : -1;
+            int nb = b;
+            if (q[d] < 0 || q[d] >= nx[d]) {
+              /* same-level face neighbour block (periodic wrap); none across
+               * a physical boundary or a level change */
+              long id[3] = {B->idx[0], B->idx[1], B->idx[2]};
+              id[d] += side ? 1 : -1;
+              long nbl = blocks_at_level(m, B->inst, B->level, d);
+              if (id[d] < 0 || id[d] >= nbl) {
+                if (m->cfg.bc[d][side] != 0) continue;
+                id[d] = (id[d] % nbl + nbl) % nbl;
+              }
+              nb = hget(m, mkkey(B->inst, B->level, id[0], id[1], id[2]));
+              if (nb < 0) continue;
+              q[d] = side ? 0 : nx[d] - 1;
+            }
+            size_t cc = ((size_t)q[2] * nx[1] + q[1]) * nx[0] + q[0];
+            if (flag[(size_t)nb * m->ncell + cc]) continue;
+            double un[NV], wn[NV];
+            cell_of(m, U, nb, cc, un);
+            orc_cons_to_prim(gamma, un, wn);
+            sr += wn[0];
+            sv[0] += wn[1];
+            sv[1] += wn[2];
+            sv[2] += wn[3];
+            sp += wn[4];
+            n++;
+          }
+      }
+      if (n > 0) {
+        rho = sr / n;
+        vel[0] = sv[0] / n, vel[1] = sv[1] / n, vel[2] = sv[2] / n;
+        p = sp / n;
+      } else {
+        /* replace: floors, velocity kept where the density allows */
+        orc_cons_to_prim(gamma, u, w);
+        rho = u[0] > m->cfg.small_density ? u[0] : m->cfg.small_density;
+        for (int e = 0; e < 3; e++) vel[e] = u[0] > 0.0 ? w[1 + e] : 0.0;
+        p = (u[0] > 0.0 && w[4] > m->cfg.small_pressure) ? w[4] : m->cfg.small_pressure;
+      }
+      double wf[NV] = {rho, vel[0], vel[1], vel[2], p, u[5], u[6], u[7], u[8]};
+      double uf[NV];
+      orc_prim_to_cons(gamma, wf, uf);
+      for (int v = 0; v < NV; v++) U[(size_t)v * nvb + (size_t)b * m->ncell + c] = uf[v];
+    }
+  }
+  free(flag);
+  return nfix;
+}
+
+/* ------------------------------------------------------------------------ */
 /* CFL time step, sums, runs                                                 */
 /* ------------------------------------------------------------------------ */
 
@@ -1040,30 +1148,51 @@ int orc_run(orc_mesh* m, double* U, double* t, const double* t_end, int maxsteps
     for (int q = 0; q < m->ninst; q++) any |= dt[q] > 0.0;
     if (!any) break;
     int st[5] = {0, 0, 0, 0, 0};
+    /* with fix_small_values every stage's (first) output is bootstrapped */
+    const int fx = m->cfg.fix_small_values;
+#define ORC_FIX(arr) \
+  do {               \
+    if (fx) orc_fix_small(m, (arr), fx); \
+  } while (0)
     if (m->cfg.time == 0) {
       st[0] = orc_stage(m, 0, dt, ch, U, U, A, NULL, 0);
+      ORC_FIX(A);
       st[1] = orc_stage(m, 1, dt, ch, U, A, Bf, NULL, 0);
+      ORC_FIX(Bf);
       memcpy(U, Bf, sizeof(double) * n);
     } else if (m->cfg.time == 1) {
       st[0] = orc_stage(m, 0, dt, ch, U, U, A, NULL, 0);
+      ORC_FIX(A);
       st[1] = orc_stage(m, 1, dt, ch, U, A, Bf, NULL, 0);
+      ORC_FIX(Bf);
       st[2] = orc_stage(m, 2, dt, ch, U, Bf, A, NULL, 0);
+      ORC_FIX(A);
       memcpy(U, A, sizeof(double) * n);
     } else if (m->cfg.time == 2) {
       /* u1 -> A, u2 -> Bf, u3 -> A, u4 -> U */
       st[0] = orc_stage(m, 0, dt, ch, U, U, A, NULL, 0);
+      ORC_FIX(A);
       st[1] = orc_stage(m, 1, dt, ch, U, A, Bf, NULL, 0);
+      ORC_FIX(Bf);
       st[2] = orc_stage(m, 2, dt, ch, U, Bf, A, NULL, 0);
+      ORC_FIX(A);
       st[3] = orc_stage(m, 3, dt, ch, U, A, U, NULL, 0);
+      ORC_FIX(U);
     } else {
       /* u1 -> A, u2 -> Bf, u3 -> A; stage 3: u4 -> Bf (over u2, its own
        * cells) and w -> U (over u0); stage 4: u5 = w + ... -> U */
       st[0] = orc_stage(m, 0, dt, ch, U, U, A, NULL, 0);
+      ORC_FIX(A);
       st[1] = orc_stage(m, 1, dt, ch, U, A, Bf, NULL, 0);
+      ORC_FIX(Bf);
       st[2] = orc_stage(m, 2, dt, ch, U, Bf, A, NULL, 0);
+      ORC_FIX(A);
       st[3] = orc_stage2(m, 3, dt, ch, U, A, Bf, Bf, U, NULL, 0);
+      ORC_FIX(Bf);
       st[4] = orc_stage(m, 4, dt, ch, U, Bf, U, NULL, 0);
+      ORC_FIX(U);
     }
+#undef ORC_FIX
     for (int e = 0; e < 5; e++)
       if (st[e]) status = st[e];
     for (int q = 0; q < m->ninst; q++) {

@@ -40,6 +40,7 @@ typedef struct {
   int bc[3][2];          /* 0 periodic, 1 outflow (zero gradient) */
   double small_density, small_pressure;
   int check_small_values;
+  int fix_small_values;  /* 0 off, 1 replace, 2 average (Sect. 7.4 bootstrapping) */
 } orc_config;
 
 typedef struct {
@@ -74,6 +75,16 @@ int orc_stage(const orc_mesh* m, int k, const double* dt, const double* ch,
 int orc_stage2(const orc_mesh* m, int k, const double* dt, const double* ch,
                const double* U0, const double* Uk, const double* U2, double* out,
                double* out2, const int32_t* sub, int nsub);
+
+/* Bootstrapping of Sect. 7.4 on the state U in place: a cell is small when
+ * rho < small_density or p < small_pressure, or either is not positive.  method 1 (replace): rho and p
+ * floored to the small values, v = m/rho kept (0 if rho <= 0); method 2
+ * (average): rho, v, p become the mean over the cell's face neighbours of its
+ * own level that are not small themselves (the replace rule when there is
+ * none).  B and psi are never changed; m and e follow from the new primitives.
+ * All small cells are found before any is changed.  Returns the number of
+ * cells fixed. */
+long orc_fix_small(const orc_mesh* m, double* U, int method);
 
 /* CFL: per instance dt = courant / max sum_d (|v_d|+c_f,d)/dx_d and
  * ch = max (|v_d|+c_f,d); dt clipped to t_end - t. */

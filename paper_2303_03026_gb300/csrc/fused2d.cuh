@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
 #pragma unroll
         for (int v = 0; v < NV; v++) u[v] = S.cons[s][v][j + NG][i + NG];
         cons2prim(gammad, u, w, ff, gm1f);
-        if (sp.check_small && (!(w[0] > rho_floor) || !(w[4] > p_floor)))
+        if (sp.check_small && is_small_prim(w[0], w[4], rho_floor, p_floor))
           latch_error(M.err, AMRVAC_E_SMALL_VALUES, b, tid, which);
 #pragma unroll
         for (int v = 0; v < NV; v++) S.prim[v][j + NG][i + NG] = w[v];

@@ -124,6 +124,13 @@ __device__ __forceinline__ T fast_speed(T gamma, const T* w, int d) {
   return sqrt(T(0.5) * (a2 + bb + sqrt(dd * dd + T(4) * a2 * bt2)));
 }
 
+// small values (Sect. 7.4): density or pressure below its floor, or not
+// positive at all (the floors default to 0)
+template <class T> __device__ __forceinline__ bool is_small_prim(T rho, T p, T rho_floor,
+                                                                  T p_floor) {
+  return !(rho > T(0) && rho >= rho_floor) || !(p > T(0) && p >= p_floor);
+}
+
 // ---------------------------------------------------------------- limiters
 
 template <class T> __device__ __forceinline__ T minmod2(T a, T b) {

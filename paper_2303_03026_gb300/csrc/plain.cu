@@ -44,8 +44,9 @@ __global__ void __launch_bounds__(256) k_prim(DevMesh M, const T* __restrict__ U
     T u[NV], w[NV];
     block_cell_value(M, U, vs, b, i, j, k, u);
     cons2prim(M.gamma[bi[0]], u, w);
-    if (sp.check_small && (!(w[0] > (T)sp.small_density) || !(w[4] > (T)sp.small_pressure)))
-      latch_error(M.err, AMRVAC_E_SMALL_VALUES, b, pc, !(w[0] > (T)sp.small_density) ? 0 : 4);
+    if (sp.check_small && is_small_prim(w[0], w[4], (T)sp.small_density, (T)sp.small_pressure))
+      latch_error(M.err, AMRVAC_E_SMALL_VALUES, b, pc,
+                  is_small_prim(w[0], T(1), (T)sp.small_density, T(0)) ? 0 : 4);
     T* dst = W + (size_t)b * NV * np + pc;
 #pragma unroll
     for (int v = 0; v < NV; v++) dst[(size_t)v * np] = w[v];

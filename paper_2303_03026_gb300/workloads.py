@@ -44,6 +44,7 @@ LIMITER = {"minmod": 0, "vanleer": 1, "koren": 2, "superbee": 3, "woodward": 4, 
 TIME = {"ssprk2": 0, "ssprk3": 1, "ssprk43": 2, "ssprk54": 3}
 PRECISION = {"fp64": 0, "fp32": 1}
 BC = {"periodic": 0, "outflow": 1}
+FIX = {"off": 0, "replace": 1, "average": 2}
 
 
 @dataclass
@@ -63,6 +64,7 @@ class Config:
     small_density: float = 0.0
     small_pressure: float = 0.0
     check_small_values: bool = True
+    fix_small_values: str = "off"   # "off", "replace" or "average" (Sect. 7.4)
 
 
 @dataclass
