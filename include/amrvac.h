@@ -104,6 +104,16 @@ typedef enum { AMRVAC_PRESSURE_FP64 = 0, AMRVAC_PRESSURE_FF = 1 } amrvac_pressur
  * and the time-step reduction with shared-memory staging.  AUTO picks FUSED
  * for 16x16 (2D) and 16x16x16 (3D) blocks, PLAIN otherwise. */
 typedef enum { AMRVAC_KERNEL_AUTO = 0, AMRVAC_KERNEL_PLAIN = 1, AMRVAC_KERNEL_FUSED = 2 } amrvac_kernel;
+/* fix_small_values (bootstrapping, Sect. 7.4).  A cell is small when its
+ * density is below small_density or its pressure below small_pressure, or
+ * either is not positive.  OFF: small stage inputs are reported
+ * (check_small_values).  REPLACE: after every stage the small cells of its
+ * output get rho = max(rho, small_density), p = max(p, small_pressure) with the
+ * velocity kept (0 where rho <= 0).  AVERAGE: rho, v and p of a small cell
+ * become the mean over its face neighbours of the same level that are not small
+ * (REPLACE where there is none).  B and psi are never changed; momentum and
+ * energy follow from the new primitives.  Both need positive floors. */
+typedef enum { AMRVAC_FIX_OFF = 0, AMRVAC_FIX_REPLACE = 1, AMRVAC_FIX_AVERAGE = 2 } amrvac_fix;
 
 typedef struct {
   int32_t ndim;           /* 1, 2 or 3                                          */
@@ -123,6 +133,7 @@ typedef struct {
   int32_t check_small_values;
   int32_t kernel;         /* amrvac_kernel                                      */
   int32_t pressure;       /* amrvac_pressure (FP32_BULK only)                   */
+  int32_t fix_small_values; /* amrvac_fix                                       */
 } amrvac_config;
 
 /* One instance = one independent domain with its own gamma and clock. */
@@ -319,6 +330,17 @@ amrvac_status amrvac_clear_error(amrvac_state* s);
 
 /* Number of kernels this library launched on the state since creation. */
 int64_t amrvac_launch_count(const amrvac_state* s);
+
+/*
+ * Bootstrapping (Sect. 7.4) of state register `buffer` (0..2) with the
+ * configuration's fix_small_values method (AMRVAC_E_INVALID when it is OFF):
+ * all small cells are found first, then repaired in place as described at
+ * amrvac_fix.  Stream-ordered; with h_count != NULL the call synchronises and
+ * writes the number of cells repaired.  Stages already apply it to their
+ * output when the method is not OFF; this entry point serves states set by the
+ * caller.
+ */
+amrvac_status amrvac_fix_small_values(amrvac_state* s, int32_t buffer, int64_t* h_count);
 
 const char* amrvac_error_string(amrvac_status st);
 

@@ -28,7 +28,8 @@ SYMBOLS = ("amrvac_workspace_bytes", "amrvac_state_create", "amrvac_state_destro
            "amrvac_fill_ghosts", "amrvac_cfl_dt", "amrvac_set_dt", "amrvac_stage",
            "amrvac_step", "amrvac_get_diag", "amrvac_clear_error", "amrvac_launch_count",
            "amrvac_error_string", "amrvac_cfl_dt_noalloc", "amrvac_state_save",
-           "amrvac_state_load", "amrvac_set_tuning", "amrvac_get_tuning", "amrvac_autotune")
+           "amrvac_state_load", "amrvac_set_tuning", "amrvac_get_tuning", "amrvac_autotune",
+           "amrvac_fix_small_values")
 
 
 class AmrvacError(RuntimeError):
@@ -44,7 +45,8 @@ class Config(C.Structure):
                 ("glm", C.c_int32), ("glm_alpha", C.c_double), ("courant", C.c_double),
                 ("bc", (C.c_int32 * 2) * 3), ("small_density", C.c_double),
                 ("small_pressure", C.c_double), ("check_small_values", C.c_int32),
-                ("kernel", C.c_int32), ("pressure", C.c_int32)]
+                ("kernel", C.c_int32), ("pressure", C.c_int32),
+                ("fix_small_values", C.c_int32)]
 
 
 class InstanceDesc(C.Structure):
@@ -103,6 +105,7 @@ def load(path: str = LIB_PATH):
     L.amrvac_autotune.argtypes = [vp, i32, C.c_char_p, C.POINTER(Tuning)]
     L.amrvac_state_save.argtypes = [vp, C.c_char_p]
     L.amrvac_state_load.argtypes = [vp, C.c_char_p]
+    L.amrvac_fix_small_values.argtypes = [vp, i32, vp]
     L.amrvac_cfl_dt_noalloc.argtypes = [C.POINTER(Config), C.POINTER(InstanceDesc), i32, vp, dbl,
                                         vp, vp]
     _lib = L
@@ -128,6 +131,7 @@ def make_config(cfg: wl.Config, kernel: str = "auto", pressure: str = "fp64") ->
     c.check_small_values = int(bool(cfg.check_small_values))
     c.kernel = KERNEL[kernel]
     c.pressure = PRESSURE[pressure]
+    c.fix_small_values = wl.FIX[getattr(cfg, "fix_small_values", "off")]
     return c
 
 
@@ -324,6 +328,13 @@ class State:
 
     def restore(self, path):
         _check(load().amrvac_state_load(self._h, os.fsencode(path)), "amrvac_state_load")
+
+    def fix_small(self, buffer=0):
+        """fix_small_values on register ``buffer``; returns the cells repaired."""
+        n = C.c_int64(0)
+        _check(load().amrvac_fix_small_values(self._h, int(buffer), C.addressof(n)),
+               "amrvac_fix_small_values")
+        return n.value
 
     def clear_error(self):
         _check(load().amrvac_clear_error(self._h), "amrvac_clear_error")

@@ -27,7 +27,7 @@ struct Tables {
 
 struct Layout {
   size_t U[3], W, F[3], part, blk, nbr, gface, glist, lmap, lmap_off, lnb, gamma, dx, istart,
-      iblocks, rt, sums, err, work, work2, counter, gslab, lcf, lcd, total;
+      iblocks, rt, sums, err, work, work2, counter, gslab, lcf, lcd, flags, fixcount, total;
 };
 
 bool config_ok(const amrvac_config* c, std::string& err) {
@@ -38,6 +38,11 @@ bool config_ok(const amrvac_config* c, std::string& err) {
   if (c->flux < AMRVAC_FLUX_HLL || c->flux > AMRVAC_FLUX_TVDLF) return err = "bad flux", false;
   if (c->limiter < AMRVAC_LIM_MINMOD || c->limiter > AMRVAC_LIM_ALBADA)
     return err = "bad limiter", false;
+  if (c->fix_small_values < AMRVAC_FIX_OFF || c->fix_small_values > AMRVAC_FIX_AVERAGE)
+    return err = "bad fix_small_values", false;
+  if (c->fix_small_values != AMRVAC_FIX_OFF &&
+      !(c->small_density > 0.0 && c->small_pressure > 0.0))
+    return err = "fix_small_values needs positive small_density and small_pressure", false;
   if (c->time < AMRVAC_SSPRK2 || c->time > AMRVAC_SSPRK54) return err = "bad time", false;
   if (c->precision != AMRVAC_FP64 && c->precision != AMRVAC_FP32_BULK)
     return err = "bad precision", false;
@@ -264,6 +269,11 @@ Layout make_layout(const amrvac_config* c, int ninst, int nblocks, const Tables&
   L.work2 = take(sizeof(int) * (size_t)nblocks);
   L.counter = take(sizeof(int) * 4);
   L.gslab = 0;
+  L.flags = L.fixcount = 0;
+  if (c->fix_small_values != AMRVAC_FIX_OFF) {
+    L.flags = take((size_t)ncell * nblocks);
+    L.fixcount = take(sizeof(unsigned long long));
+  }
   L.lcf = take(sizeof(float) * LC_N * MAXLEV * ninst);
   L.lcd = take(sizeof(double) * LC_N * MAXLEV * ninst);
   if (fused) {
@@ -286,6 +296,10 @@ amrvac_status check_launch(amrvac_state* s, int n) {
 
 amrvac_status enqueue_stage(amrvac_state* s, int k, int epilogue, int* count) {
   int n = s->use_fused ? launch_fused_stage(s, k, epilogue) : launch_plain_stage(s, k, epilogue);
+  if (n < 0) return AMRVAC_E_CUDA;
+  *count += n;
+  // bootstrapping of the stage output (fix_small_values, Sect. 7.4)
+  n = launch_fix_small(s, stage_buffers(s->cfg.time, k).out);
   if (n < 0) return AMRVAC_E_CUDA;
   *count += n;
   return AMRVAC_OK;
@@ -396,6 +410,10 @@ amrvac_status amrvac_state_create(const amrvac_config* cfg, int32_t ninst,
   M.part = at<double>(s, L.part);
   M.sums = at<double>(s, L.sums);
   M.err = at<int>(s, L.err);
+  if (cfg->fix_small_values != AMRVAC_FIX_OFF) {
+    s->d_flags = at<unsigned char>(s, L.flags);
+    s->d_fixcount = at<unsigned long long>(s, L.fixcount);
+  }
   M.lcf = at<float>(s, L.lcf);
   M.lcd = at<double>(s, L.lcd);
   s->d_work = at<int>(s, L.work);

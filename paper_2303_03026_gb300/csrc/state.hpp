@@ -32,6 +32,9 @@ struct amrvac_state {
   // fused path: ghost slabs of the level-change faces (2 layers x 16 x 16
   // cells x 9 vars each), rebuilt from the stage input before every stage
   void* gslab = nullptr;
+  // fix_small_values: one flag byte per cell and a count of repaired cells
+  unsigned char* d_flags = nullptr;
+  unsigned long long* d_fixcount = nullptr;
   int* d_glist = nullptr;  // [ngen] b * 6 + face
   int ngen = 0;
   // launch shape of the fused kernel (see amrvac_tuning)
@@ -123,6 +126,7 @@ int launch_cfl_partials(amrvac_state* s, int buffer);
 int launch_finalize(amrvac_state* s, int advance);
 int launch_sums(amrvac_state* s, int buffer);
 int launch_level_consts(amrvac_state* s, int k);
+int launch_fix_small(amrvac_state* s, int buffer);
 int launch_fill_ghosts(amrvac_state* s, int buffer, void* out);
 int launch_convert(amrvac_state* s, const void* src, int src_prec, void* dst, int dst_prec,
                    size_t n);
