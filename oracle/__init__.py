@@ -49,7 +49,7 @@ class _Config(C.Structure):
                 ("glm_alpha", C.c_double), ("courant", C.c_double),
                 ("bc", (C.c_int * 2) * 3), ("small_density", C.c_double),
                 ("small_pressure", C.c_double), ("check_small_values", C.c_int),
-                ("fix_small_values", C.c_int)]
+                ("fix_small_values", C.c_int), ("reflux", C.c_int)]
 
 
 class _Instance(C.Structure):
@@ -124,6 +124,7 @@ class Mesh:
         c.small_pressure = float(cfg.small_pressure)
         c.check_small_values = int(bool(cfg.check_small_values))
         c.fix_small_values = _FIX[getattr(cfg, "fix_small_values", "off")]
+        c.reflux = int(bool(getattr(cfg, "reflux", False)))
         arr = (_Instance * len(instances))()
         for q, inst in enumerate(instances):
             for d in range(3):

@@ -32,7 +32,10 @@
  *  - AMR ghost values (the paper gives no operators): same level -> copy;
  *    finer -> mean of the 2^d children; coarser -> coarse value plus
  *    minmod-limited slopes times +-1/4 coarse cell, on conserved variables.
- *    Requires full 2:1 balance (checked at creation).  No refluxing.
+ *    Requires full 2:1 balance (checked at creation).
+ *  - refluxing (cfg.reflux): after each stage the coarse cell next to a finer
+ *    neighbour replaces that face's coarse flux by the mean of the fine fluxes
+ *    through it (conservative AMR, Sect. 3).
  *  - outflow boundary: a ghost takes the value of the nearest in-domain cell of
  *    its own level (zero gradient, Sect. 3.1.1 and Sect. 3.2.1).
  *  - fix_small_values (Sect. 7.4 bootstrapping, off by default): after every
@@ -70,6 +73,12 @@ struct orc_mesh {
   uint64_t* hkey;
   int* hval;
   unsigned char* hused;
+  /* refluxing: per block and face the kind of neighbour (0 same level or
+   * boundary, 1 finer, 2 coarser) and the stage's face fluxes there,
+   * [block][face][var][tangential cells] */
+  unsigned char* fkind;
+  double* facef;
+  int farea;
 };
 
 /* ------------------------------------------------------------------------ */
@@ -572,6 +581,8 @@ static void value_at(const orc_mesh* m, const double* U, int inst, int L, const 
 
 void orc_destroy(orc_mesh* m) {
   if (!m) return;
+  free(m->fkind);
+  free(m->facef);
   free(m->inst);
   free(m->blk);
   free(m->hkey);
@@ -693,6 +704,34 @@ orc_mesh* orc_create(const orc_config* cfg, int ninst, const orc_instance* inst,
           if (r == -2) FAIL("block %d: neighbour not covered", b);
           if (L < B->level - 1) FAIL("block %d (level %d) touches level %d: not 2:1", b, B->level, L);
         }
+  }
+  if (cfg->reflux) {
+    /* face kinds for refluxing: 1 = the neighbour region is finer (this block
+     * is the coarse side), 2 = coarser, 0 otherwise */
+    m->farea = 1;
+    for (int d = 0; d < cfg->ndim; d++) {
+      int a = 1;
+      for (int e = 0; e < cfg->ndim; e++)
+        if (e != d) a *= m->cfg.nx[e];
+      if (a > m->farea) m->farea = a;
+    }
+    m->fkind = (unsigned char*)calloc((size_t)nblocks * 6, 1);
+    m->facef = (double*)calloc((size_t)nblocks * 6 * NV * m->farea, sizeof(double));
+    for (int b = 0; b < nblocks; b++) {
+      const blockinfo* B = &m->blk[b];
+      for (int d = 0; d < cfg->ndim; d++)
+        for (int side = 0; side < 2; side++) {
+          long id[3] = {B->idx[0], B->idx[1], B->idx[2]};
+          id[d] += side ? 1 : -1;
+          long N = blocks_at_level(m, B->inst, B->level, d);
+          if (id[d] < 0 || id[d] >= N) {
+            if (cfg->bc[d][side] != 0) continue;
+            id[d] = (id[d] % N + N) % N;
+          }
+          int r = hget(m, mkkey(B->inst, B->level, id[0], id[1], id[2]));
+          m->fkind[b * 6 + d * 2 + side] = r >= 0 ? 0 : (r == -1 ? 1 : 2);
+        }
+    }
   }
   return m;
 #undef FAIL
@@ -872,6 +911,29 @@ static int block_stage(const orc_mesh* m, int b, int k, const double* dtv, const
         }
   }
 
+  /* 2b. refluxing: keep the fluxes of this block's level-change faces */
+  if (m->cfg.reflux) {
+    for (int d = 0; d < m->cfg.ndim; d++) {
+      int ext[3] = {nx[0], nx[1], nx[2]};
+      ext[d] += 1;
+      const int ta = d == 0 ? 1 : 0, tb = d == 2 ? 1 : 2; /* tangential dims in order */
+      for (int side = 0; side < 2; side++) {
+        if (!m->fkind[b * 6 + d * 2 + side]) continue;
+        double* dst = m->facef + ((size_t)b * 6 + d * 2 + side) * NV * m->farea;
+        for (int t2 = 0; t2 < nx[tb]; t2++)
+          for (int t1 = 0; t1 < nx[ta]; t1++) {
+            int c[3];
+            c[d] = side ? nx[d] : 0;
+            c[ta] = t1;
+            c[tb] = t2;
+            size_t fi = ((size_t)c[2] * ext[1] + c[1]) * ext[0] + c[0];
+            for (int v = 0; v < NV; v++)
+              dst[(size_t)v * m->farea + (size_t)t2 * nx[ta] + t1] = F[d][v * nf[d] + fi];
+          }
+      }
+    }
+  }
+
   /* 3. update: Euler sub-step, psi damping, convex combination */
   double dx[3];
   cell_dx(m, B->inst, B->level, dx);
@@ -911,6 +973,80 @@ static int block_stage(const orc_mesh* m, int b, int k, const double* dtv, const
         }
       }
   return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* refluxing                                                                 */
+/* ------------------------------------------------------------------------ */
+
+/* Coarse cells next to a finer neighbour: the stage used the coarse flux of
+ * that face; conservation asks for the fine fluxes through it.  One pass over
+ * blocks and their faces in a fixed order (a corner cell is corrected by each
+ * of its faces in turn). */
+static void reflux_pass(const orc_mesh* m, int k, const double* dtv, const double* chv,
+                        double* out, double* out2) {
+  const int* nx = m->cfg.nx;
+  const size_t nvb = (size_t)m->nblocks * m->ncell;
+  double co[6];
+  orc_stage_coeffs6(m->cfg.time, k, co);
+  const int second = out2 != NULL && co[4] != 0.0;
+  for (int b = 0; b < m->nblocks; b++) {
+    const blockinfo* B = &m->blk[b];
+    const double dt = dtv[B->inst], ch = chv[B->inst];
+    if (dt == 0.0) continue;
+    double dx[3];
+    cell_dx(m, B->inst, B->level, dx);
+    double dxmin = dx[0];
+    for (int d = 1; d < m->cfg.ndim; d++) dxmin = dmin(dxmin, dx[d]);
+    const double damp = m->cfg.glm ? exp(-m->cfg.glm_alpha * ch * (co[2] * dt) / dxmin) : 1.0;
+    const double damp2 = m->cfg.glm ? exp(-m->cfg.glm_alpha * ch * (co[5] * dt) / dxmin) : 1.0;
+    for (int d = 0; d < m->cfg.ndim; d++) {
+      const int ta = d == 0 ? 1 : 0, tb = d == 2 ? 1 : 2;
+      for (int side = 0; side < 2; side++) {
+        if (m->fkind[b * 6 + d * 2 + side] != 1) continue;
+        const double* fc = m->facef + ((size_t)b * 6 + d * 2 + side) * NV * m->farea;
+        for (int t2 = 0; t2 < nx[tb]; t2++)
+          for (int t1 = 0; t1 < nx[ta]; t1++) {
+            /* fine cells across the face, level L+1 global indices */
+            long g[3] = {0, 0, 0};
+            g[d] = side ? 2 * ((long)B->idx[d] * nx[d] + nx[d]) : 2 * (long)B->idx[d] * nx[d] - 1;
+            long N = cells_at_level(m, B->inst, B->level + 1, d);
+            g[d] = (g[d] % N + N) % N; /* periodic (a finer neighbour exists) */
+            double fm[NV];
+            for (int v = 0; v < NV; v++) fm[v] = 0.0;
+            int nf = 0;
+            for (int o2 = 0; o2 < (tb < m->cfg.ndim ? 2 : 1); o2++)
+              for (int o1 = 0; o1 < (ta < m->cfg.ndim ? 2 : 1); o1++) {
+                g[ta] = ta < m->cfg.ndim ? 2 * ((long)B->idx[ta] * nx[ta] + t1) + o1 : 0;
+                g[tb] = tb < m->cfg.ndim ? 2 * ((long)B->idx[tb] * nx[tb] + t2) + o2 : 0;
+                long bi[3], ci[3];
+                for (int e = 0; e < 3; e++) {
+                  bi[e] = g[e] / nx[e];
+                  ci[e] = g[e] - bi[e] * nx[e];
+                }
+                int fb = hget(m, mkkey(B->inst, B->level + 1, bi[0], bi[1], bi[2]));
+                const double* ff =
+                    m->facef + ((size_t)fb * 6 + d * 2 + (1 - side)) * NV * m->farea;
+                for (int v = 0; v < NV; v++)
+                  fm[v] += ff[(size_t)v * m->farea + ci[tb] * nx[ta] + ci[ta]];
+                nf++;
+              }
+            int c[3];
+            c[d] = side ? nx[d] - 1 : 0;
+            c[ta] = t1;
+            c[tb] = t2;
+            size_t cell = ((size_t)c[2] * nx[1] + c[1]) * nx[0] + c[0];
+            for (int v = 0; v < NV; v++) {
+              double dF = fc[(size_t)v * m->farea + (size_t)t2 * nx[ta] + t1] - fm[v] / nf;
+              double dL = (side ? dF : -dF) / dx[d];
+              size_t at = (size_t)v * nvb + (size_t)b * m->ncell + cell;
+              out[at] += co[1] * (co[2] * dt) * dL * (v == PSI ? damp : 1.0);
+              if (second) out2[at] += co[4] * (co[5] * dt) * dL * (v == PSI ? damp2 : 1.0);
+            }
+          }
+      }
+    }
+  }
 }
 
 /* ------------------------------------------------------------------------ */
@@ -975,6 +1111,7 @@ int orc_stage2(const orc_mesh* m, int k, const double* dt, const double* ch, con
   }
   free(jobs);
   free(th);
+  if (m->cfg.reflux && sub == NULL) reflux_pass(m, k, dt, ch, out, out2);
   return status;
 }
 

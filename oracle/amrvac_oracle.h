@@ -41,6 +41,8 @@ typedef struct {
   double small_density, small_pressure;
   int check_small_values;
   int fix_small_values;  /* 0 off, 1 replace, 2 average (Sect. 7.4 bootstrapping) */
+  int reflux;            /* 1: coarse fluxes at level changes replaced by the mean
+                            of the fine fluxes (conservative AMR) */
 } orc_config;
 
 typedef struct {
@@ -61,6 +63,14 @@ void orc_set_threads(orc_mesh* m, int nthreads);
 /* Ghost fill: padded [var][block][(nx+4)(ny+4)(nz+4) over active dims];
  * interior and the 2-deep face slabs are written, edge/corner cells are 0. */
 int orc_fill_ghosts(const orc_mesh* m, const double* U, double* padded);
+
+/* Refluxing (with cfg.reflux) is part of every stage over all blocks: after
+ * the update, the coarse cell next to a face whose neighbour is finer gets
+ *   out += b c dt (+-) (F_coarse - mean of the 2^(d-1) fine fluxes) / dx,
+ * + for the high face and - for the low face of the coarse cell (psi of the
+ * Euler part times its damping factor; likewise for out2).  The stored face
+ * fluxes are those of the same stage.  A stage restricted to a block subset
+ * does not reflux. */
 
 /* One SSPRK stage k on the listed blocks (all when sub == NULL):
  * out = a_k U0 + b_k (Uk + c_k dt L(Uk)), psi of the Euler part damped over

@@ -65,6 +65,7 @@ class Config:
     small_pressure: float = 0.0
     check_small_values: bool = True
     fix_small_values: str = "off"   # "off", "replace" or "average" (Sect. 7.4)
+    reflux: bool = False            # conservative flux correction at level changes
 
 
 @dataclass
