@@ -134,6 +134,12 @@ typedef struct {
   int32_t kernel;         /* amrvac_kernel                                      */
   int32_t pressure;       /* amrvac_pressure (FP32_BULK only)                   */
   int32_t fix_small_values; /* amrvac_fix                                       */
+  int32_t reflux;         /* 1: conservative coarse-fine flux correction: after
+                             every stage the coarse cell next to a finer
+                             neighbour replaces that face's flux by the mean of
+                             the fine fluxes through it, so AMR runs conserve
+                             to round-off (off: level changes are not exactly
+                             conservative)                                     */
 } amrvac_config;
 
 /* One instance = one independent domain with its own gamma and clock. */

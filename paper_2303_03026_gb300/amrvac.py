@@ -46,7 +46,7 @@ class Config(C.Structure):
                 ("bc", (C.c_int32 * 2) * 3), ("small_density", C.c_double),
                 ("small_pressure", C.c_double), ("check_small_values", C.c_int32),
                 ("kernel", C.c_int32), ("pressure", C.c_int32),
-                ("fix_small_values", C.c_int32)]
+                ("fix_small_values", C.c_int32), ("reflux", C.c_int32)]
 
 
 class InstanceDesc(C.Structure):
@@ -132,6 +132,7 @@ def make_config(cfg: wl.Config, kernel: str = "auto", pressure: str = "fp64") ->
     c.kernel = KERNEL[kernel]
     c.pressure = PRESSURE[pressure]
     c.fix_small_values = wl.FIX[getattr(cfg, "fix_small_values", "off")]
+    c.reflux = int(bool(getattr(cfg, "reflux", False)))
     return c
 
 

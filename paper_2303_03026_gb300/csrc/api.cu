@@ -20,14 +20,15 @@ constexpr size_t ALIGN = 256;
 size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Tables {
-  std::vector<int> blk, nbr, gface, glist, lmap, lmap_off, lnb, istart, iblocks;
+  std::vector<int> blk, nbr, gface, glist, gkind, rlist, lmap, lmap_off, lnb, istart, iblocks;
   std::vector<double> gamma, dx;
   std::string err;
 };
 
 struct Layout {
   size_t U[3], W, F[3], part, blk, nbr, gface, glist, lmap, lmap_off, lnb, gamma, dx, istart,
-      iblocks, rt, sums, err, work, work2, counter, gslab, lcf, lcd, flags, fixcount, total;
+      iblocks, rt, sums, err, work, work2, counter, gslab, lcf, lcd, flags, fixcount, gkind,
+      rlist, fluxreg, total;
 };
 
 bool config_ok(const amrvac_config* c, std::string& err) {
@@ -38,6 +39,7 @@ bool config_ok(const amrvac_config* c, std::string& err) {
   if (c->flux < AMRVAC_FLUX_HLL || c->flux > AMRVAC_FLUX_TVDLF) return err = "bad flux", false;
   if (c->limiter < AMRVAC_LIM_MINMOD || c->limiter > AMRVAC_LIM_ALBADA)
     return err = "bad limiter", false;
+  if (c->reflux != 0 && c->reflux != 1) return err = "bad reflux", false;
   if (c->fix_small_values < AMRVAC_FIX_OFF || c->fix_small_values > AMRVAC_FIX_AVERAGE)
     return err = "bad fix_small_values", false;
   if (c->fix_small_values != AMRVAC_FIX_OFF &&
@@ -203,17 +205,29 @@ bool build_tables(const amrvac_config* c, int ninst, const amrvac_instance_desc*
         }
         int m = pos(q, L, p[0], p[1], p[2]);
         out = m >= 0 ? m : NBR_GENERAL;
+        if (m == MAP_REFINED) out = NBR_GENERAL_FINER;
       }
   }
-  // level-change faces: one ghost slab each
+  // level-change faces: one ghost slab (and flux register) each; gkind 1 when
+  // the neighbour region is finer, 2 when coarser; rlist: blocks with a finer
+  // neighbour (the coarse side of refluxing)
   T.gface.assign((size_t)nblocks * 6, -1);
   T.glist.clear();
-  for (int b = 0; b < nblocks; b++)
-    for (int f = 0; f < 6; f++)
-      if (T.nbr[b * 6 + f] == NBR_GENERAL) {
-        T.gface[b * 6 + f] = (int)T.glist.size();
-        T.glist.push_back(b * 6 + f);
-      }
+  T.gkind.clear();
+  T.rlist.clear();
+  for (int b = 0; b < nblocks; b++) {
+    bool coarse_side = false;
+    for (int f = 0; f < 6; f++) {
+      int& code = T.nbr[b * 6 + f];
+      if (code != NBR_GENERAL && code != NBR_GENERAL_FINER) continue;
+      T.gface[b * 6 + f] = (int)T.glist.size();
+      T.glist.push_back(b * 6 + f);
+      T.gkind.push_back(code == NBR_GENERAL_FINER ? 1 : 2);
+      coarse_side |= code == NBR_GENERAL_FINER;
+      code = NBR_GENERAL;
+    }
+    if (coarse_side) T.rlist.push_back(b);
+  }
   T.istart.assign(ninst + 1, 0);
   for (int b = 0; b < nblocks; b++) T.istart[meta[5 * b] + 1]++;
   for (int q = 0; q < ninst; q++) T.istart[q + 1] += T.istart[q];
@@ -255,6 +269,8 @@ Layout make_layout(const amrvac_config* c, int ninst, int nblocks, const Tables&
   L.nbr = take(sizeof(int) * T.nbr.size());
   L.gface = take(sizeof(int) * T.gface.size());
   L.glist = take(sizeof(int) * (T.glist.size() + 1));
+  L.gkind = take(sizeof(int) * (T.gkind.size() + 1));
+  L.rlist = take(sizeof(int) * (T.rlist.size() + 1));
   L.lmap = take(sizeof(int) * T.lmap.size());
   L.lmap_off = take(sizeof(int) * T.lmap_off.size());
   L.lnb = take(sizeof(int) * T.lnb.size());
@@ -269,6 +285,18 @@ Layout make_layout(const amrvac_config* c, int ninst, int nblocks, const Tables&
   L.work2 = take(sizeof(int) * (size_t)nblocks);
   L.counter = take(sizeof(int) * 4);
   L.gslab = 0;
+  L.fluxreg = 0;
+  if (c->reflux) {
+    // flux register of every level-change face: NV x the largest face area
+    size_t area = 1;
+    for (int d = 0; d < c->ndim; d++) {
+      size_t a = 1;
+      for (int e = 0; e < c->ndim; e++)
+        if (e != d) a *= (size_t)nx_of(c, e);
+      area = a > area ? a : area;
+    }
+    L.fluxreg = take(rs * NV * area * T.glist.size());
+  }
   L.flags = L.fixcount = 0;
   if (c->fix_small_values != AMRVAC_FIX_OFF) {
     L.flags = take((size_t)ncell * nblocks);
@@ -295,13 +323,26 @@ amrvac_status check_launch(amrvac_state* s, int n) {
 }
 
 amrvac_status enqueue_stage(amrvac_state* s, int k, int epilogue, int* count) {
-  int n = s->use_fused ? launch_fused_stage(s, k, epilogue) : launch_plain_stage(s, k, epilogue);
+  // with refluxing or bootstrapping the output changes after the stage
+  // kernel, so its time-step terms are taken afterwards from the final state
+  const bool post = s->cfg.reflux || s->cfg.fix_small_values != AMRVAC_FIX_OFF;
+  const int out = stage_buffers(s->cfg.time, k).out;
+  int n = s->use_fused ? launch_fused_stage(s, k, epilogue && !post)
+                       : launch_plain_stage(s, k, epilogue && !post);
   if (n < 0) return AMRVAC_E_CUDA;
   *count += n;
-  // bootstrapping of the stage output (fix_small_values, Sect. 7.4)
-  n = launch_fix_small(s, stage_buffers(s->cfg.time, k).out);
+  // conservative coarse-fine correction, then bootstrapping (Sect. 7.4)
+  n = launch_reflux(s, k);
   if (n < 0) return AMRVAC_E_CUDA;
   *count += n;
+  n = launch_fix_small(s, out);
+  if (n < 0) return AMRVAC_E_CUDA;
+  *count += n;
+  if (epilogue && post) {
+    n = launch_cfl_partials(s, out);
+    if (n < 0) return AMRVAC_E_CUDA;
+    *count += n;
+  }
   return AMRVAC_OK;
 }
 
@@ -399,6 +440,7 @@ amrvac_status amrvac_state_create(const amrvac_config* cfg, int32_t ninst,
   M.blk = at<int>(s, L.blk);
   M.nbr = at<int>(s, L.nbr);
   M.gface = at<int>(s, L.gface);
+  M.gkind = at<int>(s, L.gkind);
   M.lmap = at<int>(s, L.lmap);
   M.lmap_off = at<int>(s, L.lmap_off);
   M.lnb = at<int>(s, L.lnb);
@@ -420,10 +462,22 @@ amrvac_status amrvac_state_create(const amrvac_config* cfg, int32_t ninst,
   s->d_work_morton = s->d_work;
   s->d_work_storage = at<int>(s, L.work2);
   s->d_counter = at<int>(s, L.counter);
-  if (fused) {
-    s->gslab = s->ws + L.gslab;
-    s->d_glist = at<int>(s, L.glist);
-    s->ngen = (int)T.glist.size();
+  s->d_glist = at<int>(s, L.glist);
+  s->ngen = (int)T.glist.size();
+  s->d_rlist = at<int>(s, L.rlist);
+  s->nrlist = (int)T.rlist.size();
+  if (fused) s->gslab = s->ws + L.gslab;
+  if (cfg->reflux) {
+    s->fluxreg = s->ws + L.fluxreg;
+    size_t area = 1;
+    for (int d = 0; d < cfg->ndim; d++) {
+      size_t a = 1;
+      for (int e = 0; e < cfg->ndim; e++)
+        if (e != d) a *= (size_t)nx_of(cfg, e);
+      area = a > area ? a : area;
+    }
+    M.farea = (int)area;
+    M.fluxreg = s->fluxreg;
   }
 
   std::vector<InstRT> rt(ninst);
@@ -435,7 +489,9 @@ amrvac_status amrvac_state_create(const amrvac_config* cfg, int32_t ninst,
   up((void*)M.blk, T.blk.data(), sizeof(int) * T.blk.size());
   up((void*)M.nbr, T.nbr.data(), sizeof(int) * T.nbr.size());
   up((void*)M.gface, T.gface.data(), sizeof(int) * T.gface.size());
-  if (fused) up((void*)s->d_glist, T.glist.data(), sizeof(int) * T.glist.size());
+  up((void*)s->d_glist, T.glist.data(), sizeof(int) * T.glist.size());
+  up((void*)M.gkind, T.gkind.data(), sizeof(int) * T.gkind.size());
+  up((void*)s->d_rlist, T.rlist.data(), sizeof(int) * T.rlist.size());
   up((void*)M.lmap, T.lmap.data(), sizeof(int) * T.lmap.size());
   up((void*)M.lmap_off, T.lmap_off.data(), sizeof(int) * T.lmap_off.size());
   up((void*)M.lnb, T.lnb.data(), sizeof(int) * T.lnb.size());

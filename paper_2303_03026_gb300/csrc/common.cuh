@@ -27,6 +27,7 @@ enum {
 // face neighbour codes in DevMesh::nbr
 constexpr int NBR_OUTFLOW = -1;  // physical zero-gradient boundary
 constexpr int NBR_GENERAL = -2;  // level change: use the per-level block maps
+constexpr int NBR_GENERAL_FINER = -4;  // host tables only, while classifying faces
 // per-level block map codes
 constexpr int MAP_REFINED = -1;  // covered by finer leaves
 constexpr int MAP_COARSER = -2;  // covered by a coarser leaf
@@ -45,6 +46,9 @@ struct DevMesh {
   const int* blk;         // [nblocks][5]: inst, level, i, j, k
   const int* nbr;         // [nblocks][6]: face (d, side) -> neighbour code
   const int* gface;       // [nblocks][6]: ghost-slab index of a level-change face, else -1
+  const int* gkind;       // [slab index]: 1 the neighbour region is finer, 2 coarser
+  void* fluxreg;          // refluxing: [slab index][NV][farea] face fluxes of the stage
+  int farea;              // cells of the largest block face
   const int* lmap;        // concatenated dense per-(instance, level) block maps
   const int* lmap_off;    // [ninst][MAXLEV] offset into lmap
   const int* lnb;         // [ninst][MAXLEV][3] blocks per dimension at a level
@@ -83,6 +87,7 @@ struct StageParams {
   int pressure_ff;       // FP32 bulk: float-float pressure recovery and sums
   float af, bf, a2f, b2f;  // a, b, a2, b2, small_density, small_pressure in float
   float small_density_f, small_pressure_f;
+  int reflux;            // keep the fluxes of level-change faces for refluxing
 };
 
 // a StageParams value in the kernel's arithmetic type (no conversion in-kernel)

@@ -161,6 +161,15 @@ __device__ __forceinline__ void cfl_terms(const T* u, double gammad, T g, bool f
   smx = fmax(smx, s);
 }
 
+// refluxing: the flux f of cell `idx` of level-change face `face` of the block
+// into that face's register (nb code -3 - slab index)
+template <class T>
+__device__ __forceinline__ void keep_face_flux(const DevMesh& M, int code, int idx, const T* f) {
+  T* reg = (T*)M.fluxreg + (size_t)(-3 - code) * NV * M.farea + idx;
+#pragma unroll
+  for (int v = 0; v < NV; v++) reg[(size_t)v * M.farea] = f[v];
+}
+
 template <class T> __device__ __forceinline__ T over_dx(T a, T dx, T idx);
 template <> __device__ __forceinline__ double over_dx(double a, double dx, double) { return a / dx; }
 template <> __device__ __forceinline__ float over_dx(float a, float, float idx) { return a * idx; }
@@ -471,6 +480,7 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
     cp_async_wait_all();
     for (int pz = -2; pz <= 1; pz++) convert_plane(pz);
     if (owner) zflux(0, fzp);  // own column only
+    if (sp.reflux && owner && nb[4] <= -3) keep_face_flux(M, nb[4], y * FB + x, fzp);
     __syncthreads();  // the halo copies of planes 0 and 1 are visible
     convert_halo(0);
     __syncthreads();  // plane 0 with its halo in primitives
@@ -508,10 +518,18 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
         stencil_flux<T, 0, LIM, FLUX>(ax, sp.glm, g, ch, f, sp.limiter);
 #pragma unroll
         for (int v = 0; v < NV; v++) S.fx[fb][v][fxr][fxc] = f[v];
+        if (sp.reflux) {  // x faces on the block boundary: face 0 (owners x = 0), 1 (helpers)
+          const int face = owner ? (x == 0 ? 0 : -1) : 1;
+          if (face >= 0 && nb[face] <= -3) keep_face_flux(M, nb[face], z * FB + fxr, f);
+        }
         auto ay = [&](int v, int t) -> T { return S.plane[sl][v][fyr + t][fyc + NG]; };
         stencil_flux<T, 1, LIM, FLUX>(ay, sp.glm, g, ch, f, sp.limiter);
 #pragma unroll
         for (int v = 0; v < NV; v++) S.fy[fb][v][fyr][fyc] = f[v];
+        if (sp.reflux) {  // y faces on the block boundary: face 2 (owners y = 0), 3 (helpers)
+          const int face = owner ? (y == 0 ? 2 : -1) : 3;
+          if (face >= 0 && nb[face] <= -3) keep_face_flux(M, nb[face], z * FB + fyc, f);
+        }
       }
       // owners: own cell of plane z+2 -> primitives (needed by the z face
       // below); owners 128..255 also a halo cell of plane z+1, whose copies
@@ -522,6 +540,8 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
       if (z + 1 < NZ) convert_halo(z + 1);
       T fz[NV];
       if (DIM == 3 && owner) zflux(z + 1, fz);
+      if (sp.reflux && owner && z == NZ - 1 && nb[5] <= -3)
+        keep_face_flux(M, nb[5], y * FB + x, fz);
       __syncthreads();
       if (!owner) continue;  // helpers: no cell of their own
 

@@ -209,10 +209,22 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
         stencil_flux<T, 0, LIM, FLUX>(ax, sp.glm, g, ch, f, sp.limiter);
 #pragma unroll
         for (int v = 0; v < NV; v++) S.fx[v][fxr][fxc] = f[v];
+        if (sp.reflux) {  // block-boundary x faces: 0 (owners x = 0), 1 (helpers)
+          const int face = owner ? (x == 0 ? 0 : -1) : 1;
+          const int code = face >= 0 ? M.nbr[b * 6 + face] : 0;
+          if (code == NBR_GENERAL)
+            keep_face_flux(M, -3 - M.gface[b * 6 + face], fxr, f);
+        }
         auto ay = [&](int v, int t) -> T { return S.prim[v][fyr + t][fyc + NG]; };
         stencil_flux<T, 1, LIM, FLUX>(ay, sp.glm, g, ch, f, sp.limiter);
 #pragma unroll
         for (int v = 0; v < NV; v++) S.fy[v][fyr][fyc] = f[v];
+        if (sp.reflux) {  // block-boundary y faces: 2 (owners y = 0), 3 (helpers)
+          const int face = owner ? (y == 0 ? 2 : -1) : 3;
+          const int code = face >= 0 ? M.nbr[b * 6 + face] : 0;
+          if (code == NBR_GENERAL)
+            keep_face_flux(M, -3 - M.gface[b * 6 + face], fyc, f);
+        }
       }
       __syncthreads();
       wnn = counter ? S.next : wn + gridDim.x;

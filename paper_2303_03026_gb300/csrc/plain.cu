@@ -375,6 +375,7 @@ StageParams make_stage_params(const amrvac_state* s, int k, int epilogue) {
   sp.small_pressure = s->cfg.small_pressure;
   // with fix_small_values the stage outputs are repaired instead of reported
   sp.check_small = s->cfg.check_small_values && s->cfg.fix_small_values == AMRVAC_FIX_OFF;
+  sp.reflux = s->cfg.reflux;
   sp.flux = s->cfg.flux;
   sp.limiter = s->cfg.limiter;
   sp.glm = s->cfg.glm;

@@ -37,6 +37,10 @@ struct amrvac_state {
   unsigned long long* d_fixcount = nullptr;
   int* d_glist = nullptr;  // [ngen] b * 6 + face
   int ngen = 0;
+  // refluxing: blocks with a finer face neighbour, face flux registers
+  int* d_rlist = nullptr;
+  int nrlist = 0;
+  void* fluxreg = nullptr;
   // launch shape of the fused kernel (see amrvac_tuning)
   amrvac_tuning tune{0, 0, 0, 0.0};
   int* d_work_morton = nullptr;
@@ -127,6 +131,7 @@ int launch_finalize(amrvac_state* s, int advance);
 int launch_sums(amrvac_state* s, int buffer);
 int launch_level_consts(amrvac_state* s, int k);
 int launch_fix_small(amrvac_state* s, int buffer);
+int launch_reflux(amrvac_state* s, int k);
 int launch_fill_ghosts(amrvac_state* s, int buffer, void* out);
 int launch_convert(amrvac_state* s, const void* src, int src_prec, void* dst, int dst_prec,
                    size_t n);

@@ -7,7 +7,8 @@ Each stage is checked from identical register contents laid out as the C ABI
 documents the stage buffers (U0, U_in [, U2] -> out [, out2]); full steps are
 checked against the oracle's run.  Tolerances as in test_gpu_parity.py: FP64
 relative L-inf 1e-12 per stage and 1e-10 after several steps; FP32 relative L1
-1e-5 per stage on smooth flows.
+1e-5 per stage on smooth flows, a variable far smaller than the state measured
+against 1% of the state's mean magnitude.
 """
 import numpy as np
 import pytest
@@ -45,13 +46,19 @@ def _err(got, ref, fp32, ch):
             s = np.abs(ref[v]).sum()
             if v == 8:
                 s = max(s, float(np.max(ch)) * bmag.sum())
-            s = max(s, 1e-12 * np.abs(ref).mean() * ref[v].size)
+            # FP32: a variable far smaller than the state (e.g. a momentum
+            # component near zero) is measured against 1% of the state's mean
+            # magnitude, since FP32 rounding of its O(state) fluxes is absolute
+            s = max(s, 1e-2 * np.abs(ref).mean() * ref[v].size)
             out.append(np.abs(got[v] - ref[v]).sum() / s)
         else:
             m = np.abs(ref[v]).max()
             if v == 8:
                 m = max(m, float(np.max(ch)) * bmag.max())
-            m = m if m > 0 else np.abs(ref).max()
+            # a variable at round-off level (identically zero up to rounding) is
+            # measured against the scale of the whole state
+            if m < 1e-9 * np.abs(ref).max():
+                m = np.abs(ref).max()
             out.append(np.abs(got[v] - ref[v]).max() / m)
     return np.array(out)
 
@@ -184,3 +191,62 @@ def test_new_limiter_stage_parity_fp32(amr, orc, limiter):
     for W in _small_cases("fp32")[:2]:
         W.cfg.limiter = limiter
         _scheme_stage_parity(amr, orc, W, "auto", 1e-5)
+
+
+# ----------------------------------------------------------------------------
+# refluxing (conservative coarse-fine correction)
+# ----------------------------------------------------------------------------
+
+def _advected_amr(precision, bnx, ndim):
+    """AMR mesh with a density wave advected across its level changes."""
+    import oracle as orc
+    if ndim == 2:
+        W = wl.small_amr_2d(bnx=bnx, precision=precision)
+    else:
+        W = wl.c4_blast_amr(base=4, levels=3, bnx=bnx, shell=(0.2, 0.26), precision=precision)
+    g = W.instances[0].gamma
+    for b in range(W.U.shape[1]):
+        X, Y, Z = wl.cell_centres(W.cfg, W.instances[0], W.block_meta[b])
+        rho = (1.0 + 0.3 * np.sin(2 * np.pi * (X + Y + (Z if ndim == 3 else 0)))).ravel()
+        for c in range(W.U.shape[2]):
+            w = np.array([rho[c], 0.5, 0.3, 0.2 if ndim == 3 else 0.0, 1.0, 0.5, 0.3, 0.2, 0.0])
+            W.U[:, b, c] = orc.prim_to_cons(g, w)
+    W.cfg.reflux = True
+    return W
+
+
+@pytest.mark.parametrize("ndim,kernel,bnx", [(2, "plain", 8), (2, "auto", 16), (3, "plain", 4),
+                                             (3, "auto", 16)])
+@pytest.mark.parametrize("time", ["ssprk3", "ssprk54"])
+def test_reflux_stage_parity_fp64(amr, orc, ndim, kernel, bnx, time):
+    W = _advected_amr("fp64", bnx, ndim)
+    W.cfg.time = time
+    _scheme_stage_parity(amr, orc, W, kernel, 1e-12)
+
+
+def test_reflux_stage_parity_fp32(amr, orc):
+    for ndim in (2, 3):
+        W = _advected_amr("fp32", 16, ndim)
+        _scheme_stage_parity(amr, orc, W, "auto", 1e-5)
+
+
+@pytest.mark.parametrize("ndim,kernel,bnx", [(2, "auto", 16), (3, "auto", 16), (3, "plain", 4)])
+def test_reflux_conserves_on_gpu(amr, orc, ndim, kernel, bnx):
+    W = _advected_amr("fp64", bnx, ndim)
+    m = orc.mesh_for(W, 8)
+    s0 = m.sums(W.U)
+    S = amr.State.from_workload(W, kernel=kernel)
+    S.set_conserved(W.U)
+    S.step(4)
+    d = S.diag()
+    assert d["status"] == 0, d
+    scale = np.abs(s0).max()
+    drift = np.abs(d["sums"][0, :8] - s0[0, :8]).max() / scale
+    assert drift < 1e-13, drift
+    Uo, t, ns, st = m.run(W.U, 1e30, maxsteps=4)
+    got = S.get_conserved(0)
+    S.close()
+    # per variable; a variable at round-off level against the state's scale
+    sc = np.abs(Uo).max(axis=(1, 2), keepdims=True)
+    sc = np.where(sc < 1e-9 * np.abs(Uo).max(), np.abs(Uo).max(), sc)
+    assert (np.abs(got - Uo) / sc).max() < 1e-10
