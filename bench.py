@@ -393,24 +393,35 @@ def main():
                 "alg_bytes_per_launch": [int(b) for b in alg_bytes],
                 "frac_of_nominal_7900": achieved / NOMINAL_HBM_GBS}
 
-    # variants on the same workload: HLL flux, FP64 pressure recovery
+    # variants on the same workload: other fluxes, time steppers, FP64
+    # pressure recovery; algorithmic bytes per cell-update follow the stage
+    # registers each scheme reads and writes (state passes x 9 x 4 B)
+    passes = {"ssprk2": 5, "ssprk3": 8, "ssprk43": 9, "ssprk54": 16}
     variants = {}
     if not args.no_variants and fused:
-        for name, kw in (("hll_vanleer", {"flux": "hll"}), ("fp64_pressure", {"pressure": "fp64"})):
-            Wv, _ = W, None
-            old_flux = W.cfg.flux
-            if "flux" in kw:
-                W.cfg.flux = kw["flux"]
+        for name, kw in (("hll_vanleer", {"flux": "hll"}), ("tvdlf_vanleer", {"flux": "tvdlf"}),
+                         ("hlld_ssprk43", {"time": "ssprk43"}),
+                         ("hlld_ssprk54", {"time": "ssprk54"}),
+                         ("hlld_woodward", {"limiter": "woodward"}),
+                         ("hlld_reflux", {"reflux": True}),
+                         ("fp64_pressure", {"pressure": "fp64"})):
+            keys = ("flux", "time", "limiter", "reflux")
+            old = {k: getattr(W.cfg, k) for k in keys}
+            for k in keys:
+                setattr(W.cfg, k, kw.get(k, old[k]))
             Sv = amrvac.State.from_workload(W, device=dev, kernel=args.kernel,
                                             pressure=kw.get("pressure", args.pressure))
-            W.cfg.flux = old_flux
+            nbytes = passes[W.cfg.time] * 9 * 4
+            for k in keys:
+                setattr(W.cfg, k, old[k])
             Sv.set_conserved(U32)
             if tuning is not None:
                 Sv.set_tuning(tuning["ctas_per_sm"], tuning["order"], tuning["dynamic"])
             Sv.step(2)
             msv = time_steps(torch, Sv, max(3, min(args.steps, 10)))
             variants[name] = {"value": cells * ws / (msv / 1e3), "ms_per_step": msv,
-                              "frac": 288 * cells / (msv / 1e3) / 1e9 / hbm}
+                              "alg_bytes_per_cell_step": nbytes,
+                              "frac": nbytes * cells / (msv / 1e3) / 1e9 / hbm}
             Sv.close()
 
     # C5 batching: the same instances advanced one at a time

@@ -297,7 +297,10 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-template <class T, int DIM, int LIM, int FLUX>
+// FULL: the SSPRK(5,4) second output and the refluxing face registers are
+// compiled in (they are runtime-uniform branches that still cost the hot loop
+// registers and scheduling freedom, so the lean instantiation runs otherwise)
+template <class T, int DIM, int LIM, int FLUX, bool FULL>
 __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
     k_fused(DevMesh M, const T* U0, const T* __restrict__ Uk, const T* U2, T* out, T* out2,
             const int* __restrict__ work, int nwork, const T* __restrict__ gslab,
@@ -361,7 +364,7 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
           size_t at = (size_t)v * vs + (size_t)b * ncell + c;
           u[v] = Uk[at];
           out[at] = u[v];
-          if (sp.has2) out2[at] = u[v];
+          if (FULL && sp.has2) out2[at] = u[v];
         }
         if (sp.epilogue) cfl_terms<T, DIM>(u, gammad, g, ff, gm1f, idd, smx, cmx);
       }
@@ -480,7 +483,7 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
     cp_async_wait_all();
     for (int pz = -2; pz <= 1; pz++) convert_plane(pz);
     if (owner) zflux(0, fzp);  // own column only
-    if (sp.reflux && owner && nb[4] <= -3) keep_face_flux(M, nb[4], y * FB + x, fzp);
+    if (FULL && sp.reflux && owner && nb[4] <= -3) keep_face_flux(M, nb[4], y * FB + x, fzp);
     __syncthreads();  // the halo copies of planes 0 and 1 are visible
     convert_halo(0);
     __syncthreads();  // plane 0 with its halo in primitives
@@ -518,7 +521,7 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
         stencil_flux<T, 0, LIM, FLUX>(ax, sp.glm, g, ch, f, sp.limiter);
 #pragma unroll
         for (int v = 0; v < NV; v++) S.fx[fb][v][fxr][fxc] = f[v];
-        if (sp.reflux) {  // x faces on the block boundary: face 0 (owners x = 0), 1 (helpers)
+        if (FULL && sp.reflux) {  // x faces on the block boundary: face 0 (owners x = 0), 1 (helpers)
           const int face = owner ? (x == 0 ? 0 : -1) : 1;
           if (face >= 0 && nb[face] <= -3) keep_face_flux(M, nb[face], z * FB + fxr, f);
         }
@@ -526,7 +529,7 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
         stencil_flux<T, 1, LIM, FLUX>(ay, sp.glm, g, ch, f, sp.limiter);
 #pragma unroll
         for (int v = 0; v < NV; v++) S.fy[fb][v][fyr][fyc] = f[v];
-        if (sp.reflux) {  // y faces on the block boundary: face 2 (owners y = 0), 3 (helpers)
+        if (FULL && sp.reflux) {  // y faces on the block boundary: face 2 (owners y = 0), 3 (helpers)
           const int face = owner ? (y == 0 ? 2 : -1) : 3;
           if (face >= 0 && nb[face] <= -3) keep_face_flux(M, nb[face], z * FB + fyc, f);
         }
@@ -540,7 +543,7 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
       if (z + 1 < NZ) convert_halo(z + 1);
       T fz[NV];
       if (DIM == 3 && owner) zflux(z + 1, fz);
-      if (sp.reflux && owner && z == NZ - 1 && nb[5] <= -3)
+      if (FULL && sp.reflux && owner && z == NZ - 1 && nb[5] <= -3)
         keep_face_flux(M, nb[5], y * FB + x, fz);
       __syncthreads();
       if (!owner) continue;  // helpers: no cell of their own
@@ -557,7 +560,7 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
         T ut = uk - dt * acc;
         if (v == 8) ut = ut * damp;
         un[v] = sp.plain ? ut : ca * (PRE0 ? S.u0[v][tid] : U0[at]) + cb * ut;
-        if (sp.has2) {
+        if (FULL && sp.has2) {
           // SSPRK(5,4) stage 3: w = a2 U2 + b2 (Uk + c2 dt L); U2 is out's
           // register and out2 is U0's, both read above before their writes
           T ut2 = uk - lc[LC_DT2] * acc;
@@ -584,10 +587,10 @@ namespace amrvac {
 
 // ---------------------------------------------------------------- launcher
 
-template <class T, int DIM, int LIM, int FLUX>
+template <class T, int DIM, int LIM, int FLUX, bool FULL>
 static int launch_one(amrvac_state* s, const T* U0, const T* Uk, const T* U2, T* out, T* out2,
                       StageParams sp) {
-  auto kern = DIM == 3 ? k_fused<T, 3, LIM, FLUX> : k_fused2d<T, LIM, FLUX>;
+  auto kern = DIM == 3 ? k_fused<T, 3, LIM, FLUX, FULL> : k_fused2d<T, LIM, FLUX, FULL>;
   const int smem = DIM == 3 ? (int)sizeof(FusedSmem<T, 3>) : (int)sizeof(Fused2dSmem<T>);
   static int nsm = 0, per_sm = 0;  // per instantiation, this device
   if (nsm == 0) {
@@ -630,13 +633,17 @@ int launch_fused_l(amrvac_state* s, int k, int epilogue) {
   const T* U2 = sb.u2 >= 0 ? (const T*)s->U[sb.u2] : nullptr;
   T* out = (T*)s->U[sb.out];
   T* out2 = sb.out2 >= 0 ? (T*)s->U[sb.out2] : nullptr;
+  const bool full = sp.has2 || sp.reflux;
   int n;
   if (s->cfg.flux == AMRVAC_FLUX_HLLD)
-    n = launch_one<T, DIM, LIM, AMRVAC_FLUX_HLLD>(s, U0, Uk, U2, out, out2, sp);
+    n = full ? launch_one<T, DIM, LIM, AMRVAC_FLUX_HLLD, true>(s, U0, Uk, U2, out, out2, sp)
+             : launch_one<T, DIM, LIM, AMRVAC_FLUX_HLLD, false>(s, U0, Uk, U2, out, out2, sp);
   else if (s->cfg.flux == AMRVAC_FLUX_HLL)
-    n = launch_one<T, DIM, LIM, AMRVAC_FLUX_HLL>(s, U0, Uk, U2, out, out2, sp);
+    n = full ? launch_one<T, DIM, LIM, AMRVAC_FLUX_HLL, true>(s, U0, Uk, U2, out, out2, sp)
+             : launch_one<T, DIM, LIM, AMRVAC_FLUX_HLL, false>(s, U0, Uk, U2, out, out2, sp);
   else
-    n = launch_one<T, DIM, LIM, AMRVAC_FLUX_TVDLF>(s, U0, Uk, U2, out, out2, sp);
+    n = full ? launch_one<T, DIM, LIM, AMRVAC_FLUX_TVDLF, true>(s, U0, Uk, U2, out, out2, sp)
+             : launch_one<T, DIM, LIM, AMRVAC_FLUX_TVDLF, false>(s, U0, Uk, U2, out, out2, sp);
   return n < 0 ? -1 : n + 1;
 }
 

@@ -46,7 +46,7 @@ template <class T> struct Fused2dSmem {
   int next;
 };
 
-template <class T, int LIM, int FLUX>
+template <class T, int LIM, int FLUX, bool FULL>
 __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
     k_fused2d(DevMesh M, const T* U0, const T* __restrict__ Uk, const T* U2, T* out, T* out2,
               const int* __restrict__ work, int nwork, const T* __restrict__ gslab,
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
         for (int v = 0; v < NV; v++) {
           u[v] = S.cons[s][v][y + NG][x + NG];
           out[(size_t)v * vs + (size_t)b * ncell + y * FB + x] = u[v];
-          if (sp.has2) out2[(size_t)v * vs + (size_t)b * ncell + y * FB + x] = u[v];
+          if (FULL && sp.has2) out2[(size_t)v * vs + (size_t)b * ncell + y * FB + x] = u[v];
         }
         if (sp.epilogue) cfl_terms<T, 2>(u, gammad, g, ff, gm1f, idd, smx, cmx);
       }
@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
         stencil_flux<T, 0, LIM, FLUX>(ax, sp.glm, g, ch, f, sp.limiter);
 #pragma unroll
         for (int v = 0; v < NV; v++) S.fx[v][fxr][fxc] = f[v];
-        if (sp.reflux) {  // block-boundary x faces: 0 (owners x = 0), 1 (helpers)
+        if (FULL && sp.reflux) {  // block-boundary x faces: 0 (owners x = 0), 1 (helpers)
           const int face = owner ? (x == 0 ? 0 : -1) : 1;
           const int code = face >= 0 ? M.nbr[b * 6 + face] : 0;
           if (code == NBR_GENERAL)
@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
         stencil_flux<T, 1, LIM, FLUX>(ay, sp.glm, g, ch, f, sp.limiter);
 #pragma unroll
         for (int v = 0; v < NV; v++) S.fy[v][fyr][fyc] = f[v];
-        if (sp.reflux) {  // block-boundary y faces: 2 (owners y = 0), 3 (helpers)
+        if (FULL && sp.reflux) {  // block-boundary y faces: 2 (owners y = 0), 3 (helpers)
           const int face = owner ? (y == 0 ? 2 : -1) : 3;
           const int code = face >= 0 ? M.nbr[b * 6 + face] : 0;
           if (code == NBR_GENERAL)
@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
           if (v == 8) ut = ut * damp;
           un[v] = sp.plain ? ut : ca * S.u0[s][v][tid] + cb * ut;
           const size_t at = (size_t)v * vs + (size_t)b * ncell + c;
-          if (sp.has2) {
+          if (FULL && sp.has2) {
             // SSPRK(5,4) stage 3: w = a2 U2 + b2 (Uk + c2 dt L); U2 is out's
             // register (read here before its write), out2 is U0's (in smem)
             T ut2 = uk - lc[LC_DT2] * acc;

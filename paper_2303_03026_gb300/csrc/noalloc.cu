@@ -40,7 +40,7 @@ double* g_partials_addr[kMaxDevices] = {nullptr};
 template <class T>
 __global__ void __launch_bounds__(256) k_cfl_partials_static(DevMesh M, const T* __restrict__ U,
                                                              double gamma, double dx0,
-                                                             double dx1, double dx2,
+                                                             double dx1, double dx2, int ff,
                                                              double* __restrict__ partials) {
   const size_t vs = (size_t)M.nblocks * M.ncell;
   const double dx[3] = {dx0, dx1, dx2};
@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(256) k_cfl_partials_static(DevMesh M, const T*
       const T* src = U + (size_t)b * M.ncell + c;
 #pragma unroll
       for (int v = 0; v < NV; v++) u[v] = src[(size_t)v * vs];
-      accumulate_cell(M, u, gamma, dx, p);
+      accumulate_cell(M, u, gamma, dx, p, ff != 0);
     }
     // block maximum: warp shuffles, then the warps' maxima in a fixed order
     __shared__ double sh[32][2];
@@ -165,12 +165,14 @@ extern "C" amrvac_status amrvac_cfl_dt_noalloc(const amrvac_config* cfg,
   if (st) return st;
   cudaStream_t s = (cudaStream_t)cuda_stream;
   const int grid = nblocks < 152 * 16 ? nblocks : 152 * 16;
+  // float-float pressure recovery for FP32-bulk states configured with it
+  const int ff = cfg->precision == AMRVAC_FP32_BULK && cfg->pressure == AMRVAC_PRESSURE_FF;
   if (cfg->precision == AMRVAC_FP64)
     k_cfl_partials_static<double><<<grid, 256, 0, s>>>(M, (const double*)d_U, inst->gamma, dx[0],
-                                                       dx[1], dx[2], partials);
+                                                       dx[1], dx[2], 0, partials);
   else
     k_cfl_partials_static<float><<<grid, 256, 0, s>>>(M, (const float*)d_U, inst->gamma, dx[0],
-                                                      dx[1], dx[2], partials);
+                                                      dx[1], dx[2], ff, partials);
   k_cfl_finish_static<<<1, 256, 0, s>>>(partials, nblocks, cfg->courant, t, inst->t_end, d_out);
   return cudaPeekAtLastError() == cudaSuccess ? AMRVAC_OK : AMRVAC_E_CUDA;
 }

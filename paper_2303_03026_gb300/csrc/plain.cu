@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(256) k_update(DevMesh M, const T* U0,
         out[(size_t)v * vs + (size_t)b * M.ncell + c] = un[v];
         if (sp.has2) out2[(size_t)v * vs + (size_t)b * M.ncell + c] = u2n[v];
       }
-      if (sp.epilogue) accumulate_cell(M, un, gamma, dx, p);
+      if (sp.epilogue) accumulate_cell(M, un, gamma, dx, p, sp.pressure_ff != 0);
     }
     if (sp.epilogue) block_reduce_store(p, M.part + (size_t)b * NPART);
   }
@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(256) k_update(DevMesh M, const T* U0,
 // ------------------------------------------------------------------ k_cfl
 
 template <class T>
-__global__ void __launch_bounds__(256) k_cfl(DevMesh M, const T* __restrict__ U) {
+__global__ void __launch_bounds__(256) k_cfl(DevMesh M, const T* __restrict__ U, int ff) {
   const size_t vs = (size_t)M.nblocks * M.ncell;
   for (int b = blockIdx.x; b < M.nblocks; b += gridDim.x) {
     const int* bi = M.blk + b * 5;
@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(256) k_cfl(DevMesh M, const T* __restrict__ U)
     for (int c = threadIdx.x; c < M.ncell; c += blockDim.x) {
       T u[NV];
       read_cell(M, U, vs, b, c, u);
-      accumulate_cell(M, u, M.gamma[q], dx, p);
+      accumulate_cell(M, u, M.gamma[q], dx, p, ff != 0);
     }
     block_reduce_store(p, M.part + (size_t)b * NPART);
   }
@@ -464,10 +464,11 @@ int launch_plain_stage(amrvac_state* s, int k, int epilogue) {
 
 int launch_cfl_partials(amrvac_state* s, int buffer) {
   int grid = s->nblocks < 152 * 16 ? s->nblocks : 152 * 16;
+  const int ff = s->cfg.precision == AMRVAC_FP32_BULK && s->cfg.pressure == AMRVAC_PRESSURE_FF;
   if (s->cfg.precision == AMRVAC_FP64)
-    k_cfl<double><<<grid, 256, 0, s->stream>>>(s->mesh, (const double*)s->U[buffer]);
+    k_cfl<double><<<grid, 256, 0, s->stream>>>(s->mesh, (const double*)s->U[buffer], 0);
   else
-    k_cfl<float><<<grid, 256, 0, s->stream>>>(s->mesh, (const float*)s->U[buffer]);
+    k_cfl<float><<<grid, 256, 0, s->stream>>>(s->mesh, (const float*)s->U[buffer], ff);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 

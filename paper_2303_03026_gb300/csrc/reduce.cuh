@@ -52,9 +52,11 @@ static __device__ void block_reduce_store(Partial& p, double* part_b) {
 // bulk precision (inverse cell sizes precomputed); conservation sums in double
 template <class T>
 __device__ __forceinline__ void accumulate_cell(const DevMesh& M, const T* u, double gamma,
-                                                const double* dx, Partial& p) {
+                                                const double* dx, Partial& p, bool ff = false) {
+  // CFL terms only (the conservation sums are reduced on demand by k_sums);
+  // ff: float-float pressure recovery of FP32-bulk states
   T w[NV];
-  cons2prim(gamma, u, w);
+  cons2prim(gamma, u, w, ff, (float)(gamma - 1.0));
   T s = T(0), cm = T(0);
   for (int d = 0; d < M.ndim; d++) {
     T spd = fabs(w[1 + d]) + fast_speed((T)gamma, w, d);
@@ -63,8 +65,6 @@ __device__ __forceinline__ void accumulate_cell(const DevMesh& M, const T* u, do
   }
   p.smax = fmax(p.smax, (double)s);
   p.chm = fmax(p.chm, (double)cm);
-#pragma unroll
-  for (int v = 0; v < NV; v++) p.sum[v] += (double)u[v];
 }
 
 // same reduction with caller-provided shared scratch red[>= nwarps][NPART]
