@@ -221,6 +221,40 @@ __device__ __forceinline__ float2 vanleer_pair(float a, float b, float c, float 
   return make_float2(prod.x > 0.f ? v.x : b, prod.y > 0.f ? v.y : c);
 }
 
+// The symmetric limiters of the runtime-limiter instantiation, both face
+// states of the face between cells b and c at once (x: left state from cell b
+// with stencil (a, b, c); y: right state from cell c with (b, c, e)); slope =
+// sgn(dp) G(|dm|, |dp|) where dm dp > 0, else first order.
+//   monotonized central family: G = min(beta |dm|, (|dm| + |dp|)/2, beta |dp|)
+//     (woodward beta = 2, mcbeta beta = 1.4)
+//   superbee: G = max(min(2 |dm|, |dp|), min(|dm|, 2 |dp|))
+//   albada:   slope = dm dp (dm + dp) / (dm^2 + dp^2)
+template <int KIND>  // 0 monotonized central (beta), 1 superbee, 2 albada
+__device__ __forceinline__ float2 sym_pair(float a, float b, float c, float e, float beta) {
+  const float2 X = make_float2(b, c);
+  const float2 dm = sub2(X, make_float2(a, b));
+  const float2 dp = sub2(make_float2(c, e), X);
+  const float2 prod = mul2(dm, dp);
+  float2 s;
+  if (KIND == 2) {
+    const float2 den = fma2(dm, dm, mul2(dp, dp));
+    s = mul2(mul2(prod, add2(dm, dp)), rcp2(den));
+  } else {
+    const float am0 = fabsf(dm.x), ap0 = fabsf(dp.x), am1 = fabsf(dm.y), ap1 = fabsf(dp.y);
+    float g0, g1;
+    if (KIND == 1) {
+      g0 = fmaxf(fminf(2.f * am0, ap0), fminf(am0, 2.f * ap0));
+      g1 = fmaxf(fminf(2.f * am1, ap1), fminf(am1, 2.f * ap1));
+    } else {
+      g0 = fminf(fminf(beta * am0, 0.5f * (am0 + ap0)), beta * ap0);
+      g1 = fminf(fminf(beta * am1, 0.5f * (am1 + ap1)), beta * ap1);
+    }
+    s = make_float2(copysignf(g0, dp.x), copysignf(g1, dp.y));
+  }
+  const float2 v = fma2(make_float2(0.5f, -0.5f), s, X);
+  return make_float2(prod.x > 0.f ? v.x : b, prod.y > 0.f ? v.y : c);
+}
+
 // Face flux along D from the 4-cell stencils of the 9 primitive variables:
 // st(v, t) for cells f-2, f-1, f, f+1.  Positivity fallback and glm as in
 // face_flux_d.
@@ -228,13 +262,28 @@ __device__ __forceinline__ float2 vanleer_pair(float a, float b, float c, float 
 template <int D, int LIM, int FLUX, class Acc>
 __device__ __forceinline__ void stencil_flux_f2(Acc st, int glm, float g, float ch, float* f,
                                                 int lim) {
-  const int L = LIM >= 0 ? LIM : lim;
   float2 w[NV];
+  if constexpr (LIM >= 0) {
 #pragma unroll
-  for (int v = 0; v < NV; v++) {
-    float a = st(v, 0), b = st(v, 1), c = st(v, 2), e = st(v, 3);
-    if (LIM == AMRVAC_LIM_VANLEER) w[v] = vanleer_pair(a, b, c, e);
-    else w[v] = make_float2(recon_plus<float>(L, a, b, c), recon_minus<float>(L, b, c, e));
+    for (int v = 0; v < NV; v++) {
+      float a = st(v, 0), b = st(v, 1), c = st(v, 2), e = st(v, 3);
+      if (LIM == AMRVAC_LIM_VANLEER) w[v] = vanleer_pair(a, b, c, e);
+      else w[v] = make_float2(recon_plus<float>(LIM, a, b, c), recon_minus<float>(LIM, b, c, e));
+    }
+  } else {
+    // runtime limiter: one switch per face, the variable loop inside
+    if (lim == AMRVAC_LIM_SUPERBEE) {
+#pragma unroll
+      for (int v = 0; v < NV; v++) w[v] = sym_pair<1>(st(v, 0), st(v, 1), st(v, 2), st(v, 3), 0.f);
+    } else if (lim == AMRVAC_LIM_ALBADA) {
+#pragma unroll
+      for (int v = 0; v < NV; v++) w[v] = sym_pair<2>(st(v, 0), st(v, 1), st(v, 2), st(v, 3), 0.f);
+    } else {
+      const float beta = lim == AMRVAC_LIM_WOODWARD ? 2.f : 1.4f;
+#pragma unroll
+      for (int v = 0; v < NV; v++)
+        w[v] = sym_pair<0>(st(v, 0), st(v, 1), st(v, 2), st(v, 3), beta);
+    }
   }
   if (!(w[0].x > 0.f) || !(w[4].x > 0.f) || !(w[0].y > 0.f) || !(w[4].y > 0.f)) {
 #pragma unroll
