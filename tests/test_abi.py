@@ -80,3 +80,37 @@ def test_workspace_matches_precision(lib):
     _, n64 = _bytes(lib, W64)
     _, n32 = _bytes(lib, W32)
     assert n32 < n64
+
+
+def test_scheme_options_validated(lib):
+    # the wider scheme family is accepted; values outside the enums are not
+    for flux, time, lim in (("tvdlf", "ssprk43", "superbee"), ("hll", "ssprk54", "albada"),
+                            ("hlld", "ssprk3", "mcbeta"), ("hlld", "ssprk2", "woodward")):
+        W = wl.small_amr_2d()
+        W.cfg.flux, W.cfg.time, W.cfg.limiter = flux, time, lim
+        assert _bytes(lib, W)[0] == 0, (flux, time, lim)
+    from paper_2303_03026_gb300 import amrvac
+    W = wl.small_amr_2d()
+    for field, value in (("flux", 3), ("time", 4), ("limiter", 7), ("reflux", 2),
+                         ("fix_small_values", 3)):
+        c = amrvac.make_config(W.cfg)
+        setattr(c, field, value)
+        ins = amrvac.make_instances(W.instances)
+        meta = np.ascontiguousarray(W.block_meta, np.int32)
+        n = C.c_size_t(0)
+        st = lib.amrvac_workspace_bytes(C.byref(c), len(W.instances), ins, meta.shape[0],
+                                        meta.ctypes.data, C.byref(n))
+        assert st == 1, field
+
+
+def test_fix_and_reflux_need_their_workspace(lib):
+    W = wl.small_amr_2d()
+    _, n0 = _bytes(lib, W)
+    W.cfg.reflux = True
+    st, n1 = _bytes(lib, W)
+    assert st == 0 and n1 > n0  # flux registers of the level-change faces
+    W.cfg.fix_small_values = "average"
+    assert _bytes(lib, W)[0] == 1  # needs positive floors
+    W.cfg.small_density, W.cfg.small_pressure = 1e-6, 1e-6
+    st, n2 = _bytes(lib, W)
+    assert st == 0 and n2 >= n1 + W.nblocks * W.ncell  # one flag byte per cell
