@@ -49,7 +49,8 @@ class _Config(C.Structure):
                 ("glm_alpha", C.c_double), ("courant", C.c_double),
                 ("bc", (C.c_int * 2) * 3), ("small_density", C.c_double),
                 ("small_pressure", C.c_double), ("check_small_values", C.c_int),
-                ("fix_small_values", C.c_int), ("reflux", C.c_int)]
+                ("fix_small_values", C.c_int), ("reflux", C.c_int),
+                ("level_flux", C.c_int * 16), ("level_limiter", C.c_int * 16)]
 
 
 class _Instance(C.Structure):
@@ -125,6 +126,11 @@ class Mesh:
         c.check_small_values = int(bool(cfg.check_small_values))
         c.fix_small_values = _FIX[getattr(cfg, "fix_small_values", "off")]
         c.reflux = int(bool(getattr(cfg, "reflux", False)))
+        lf = getattr(cfg, "level_flux", None) or {}
+        ll = getattr(cfg, "level_limiter", None) or {}
+        for lev in range(16):
+            c.level_flux[lev] = _FLUX[lf[lev]] if lev in lf else -1
+            c.level_limiter[lev] = _LIM[ll[lev]] if lev in ll else -1
         arr = (_Instance * len(instances))()
         for q, inst in enumerate(instances):
             for d in range(3):

@@ -33,6 +33,8 @@
  *    finer -> mean of the 2^d children; coarser -> coarse value plus
  *    minmod-limited slopes times +-1/4 coarse cell, on conserved variables.
  *    Requires full 2:1 balance (checked at creation).
+ *  - per-level schemes (Sect. 3): a block's faces use the flux and limiter of
+ *    its level (level_flux / level_limiter, -1 = the global choice).
  *  - refluxing (cfg.reflux): after each stage the coarse cell next to a finer
  *    neighbour replaces that face's coarse flux by the mean of the fine fluxes
  *    through it (conservative AMR, Sect. 3).
@@ -876,7 +878,12 @@ static int block_stage(const orc_mesh* m, int b, int k, const double* dtv, const
         for (int v = 0; v < NV; v++) W[v * pi.np + pc] = w[v];
       }
 
-  /* 2. faces: reconstruction, positivity fallback, glm + Riemann flux */
+  /* 2. faces: reconstruction, positivity fallback, glm + Riemann flux, with
+   * the scheme of this block's level (every face of a block is computed with
+   * the block's scheme) */
+  const int flux = m->cfg.level_flux[B->level] >= 0 ? m->cfg.level_flux[B->level] : m->cfg.flux;
+  const int lim =
+      m->cfg.level_limiter[B->level] >= 0 ? m->cfg.level_limiter[B->level] : m->cfg.limiter;
   for (int d = 0; d < m->cfg.ndim; d++) {
     int ext[3] = {nx[0], nx[1], nx[2]};
     ext[d] += 1;
@@ -893,8 +900,8 @@ static int block_stage(const orc_mesh* m, int b, int k, const double* dtv, const
               cc[d] += t - 2;
               s[t] = W[v * pi.np + pidx(&pi, cc[0], cc[1], cc[2])];
             }
-            wl[v] = recon_plus(m->cfg.limiter, s[0], s[1], s[2]);
-            wr[v] = recon_minus(m->cfg.limiter, s[1], s[2], s[3]);
+            wl[v] = recon_plus(lim, s[0], s[1], s[2]);
+            wr[v] = recon_minus(lim, s[1], s[2], s[3]);
             w0[v] = s[1];
             w1[v] = s[2];
           }
@@ -905,7 +912,7 @@ static int block_stage(const orc_mesh* m, int b, int k, const double* dtv, const
             }
           }
           double f[NV];
-          orc_face_flux(m->cfg.flux, m->cfg.glm, gamma, ch, d, wl, wr, f);
+          orc_face_flux(flux, m->cfg.glm, gamma, ch, d, wl, wr, f);
           size_t fi = ((size_t)kk * ext[1] + j) * ext[0] + i;
           for (int v = 0; v < NV; v++) F[d][v * nf[d] + fi] = f[v];
         }

@@ -43,6 +43,9 @@ typedef struct {
   int fix_small_values;  /* 0 off, 1 replace, 2 average (Sect. 7.4 bootstrapping) */
   int reflux;            /* 1: coarse fluxes at level changes replaced by the mean
                             of the fine fluxes (conservative AMR) */
+  int level_flux[16];    /* per AMR level: flux scheme of that level's blocks,
+                            -1 = flux (Sect. 3: schemes may differ per level) */
+  int level_limiter[16]; /* per AMR level: limiter, -1 = limiter */
 } orc_config;
 
 typedef struct {

@@ -66,6 +66,8 @@ class Config:
     check_small_values: bool = True
     fix_small_values: str = "off"   # "off", "replace" or "average" (Sect. 7.4)
     reflux: bool = False            # conservative flux correction at level changes
+    level_flux: dict = None         # {level: flux} overrides per AMR level (Sect. 3)
+    level_limiter: dict = None      # {level: limiter} overrides per AMR level
 
 
 @dataclass
