@@ -140,6 +140,12 @@ typedef struct {
                              the fine fluxes through it, so AMR runs conserve
                              to round-off (off: level changes are not exactly
                              conservative)                                     */
+  /* per AMR level (Sect. 3: the scheme may differ between levels): flux and
+   * limiter of that level's blocks, every face of a block computed with its
+   * block's scheme; 0 = the global flux / limiter above, v + 1 = amrvac_flux /
+   * amrvac_limiter v (so a zero-initialised config has no overrides) */
+  int32_t level_flux[AMRVAC_MAX_LEVELS];
+  int32_t level_limiter[AMRVAC_MAX_LEVELS];
 } amrvac_config;
 
 /* One instance = one independent domain with its own gamma and clock. */

@@ -46,7 +46,8 @@ class Config(C.Structure):
                 ("bc", (C.c_int32 * 2) * 3), ("small_density", C.c_double),
                 ("small_pressure", C.c_double), ("check_small_values", C.c_int32),
                 ("kernel", C.c_int32), ("pressure", C.c_int32),
-                ("fix_small_values", C.c_int32), ("reflux", C.c_int32)]
+                ("fix_small_values", C.c_int32), ("reflux", C.c_int32),
+                ("level_flux", C.c_int32 * 16), ("level_limiter", C.c_int32 * 16)]
 
 
 class InstanceDesc(C.Structure):
@@ -133,6 +134,11 @@ def make_config(cfg: wl.Config, kernel: str = "auto", pressure: str = "fp64") ->
     c.pressure = PRESSURE[pressure]
     c.fix_small_values = wl.FIX[getattr(cfg, "fix_small_values", "off")]
     c.reflux = int(bool(getattr(cfg, "reflux", False)))
+    lf = getattr(cfg, "level_flux", None) or {}
+    ll = getattr(cfg, "level_limiter", None) or {}
+    for lev in range(16):
+        c.level_flux[lev] = wl.FLUX[lf[lev]] + 1 if lev in lf else 0
+        c.level_limiter[lev] = wl.LIMITER[ll[lev]] + 1 if lev in ll else 0
     return c
 
 

@@ -40,6 +40,12 @@ bool config_ok(const amrvac_config* c, std::string& err) {
   if (c->limiter < AMRVAC_LIM_MINMOD || c->limiter > AMRVAC_LIM_ALBADA)
     return err = "bad limiter", false;
   if (c->reflux != 0 && c->reflux != 1) return err = "bad reflux", false;
+  for (int L = 0; L < AMRVAC_MAX_LEVELS; L++) {
+    if (c->level_flux[L] < 0 || c->level_flux[L] > AMRVAC_FLUX_TVDLF + 1)
+      return err = "bad level_flux", false;
+    if (c->level_limiter[L] < 0 || c->level_limiter[L] > AMRVAC_LIM_ALBADA + 1)
+      return err = "bad level_limiter", false;
+  }
   if (c->fix_small_values < AMRVAC_FIX_OFF || c->fix_small_values > AMRVAC_FIX_AVERAGE)
     return err = "bad fix_small_values", false;
   if (c->fix_small_values != AMRVAC_FIX_OFF &&
@@ -283,7 +289,7 @@ Layout make_layout(const amrvac_config* c, int ninst, int nblocks, const Tables&
   L.err = take(sizeof(int) * 4);
   L.work = take(sizeof(int) * (size_t)nblocks);
   L.work2 = take(sizeof(int) * (size_t)nblocks);
-  L.counter = take(sizeof(int) * 4);
+  L.counter = take(sizeof(int) * (MAXLEV + 4));  // one per scheme group
   L.gslab = 0;
   L.fluxreg = 0;
   if (c->reflux) {
@@ -530,13 +536,44 @@ amrvac_status amrvac_state_create(const amrvac_config* cfg, int32_t ninst,
   }
   std::vector<int> work_storage(nblocks);
   for (int b = 0; b < nblocks; b++) work_storage[b] = b;
+  // scheme groups of the fused path: levels with the same (flux, limiter) share
+  // one launch; both work lists become contiguous per group (order kept inside)
+  {
+    int gof[MAXLEV];
+    s->ngroups = 0;
+    for (int L = 0; L < MAXLEV; L++) {
+      const int fl = cfg->level_flux[L] > 0 ? cfg->level_flux[L] - 1 : cfg->flux;
+      const int li = cfg->level_limiter[L] > 0 ? cfg->level_limiter[L] - 1 : cfg->limiter;
+      int g = 0;
+      while (g < s->ngroups && !(s->grp_flux[g] == fl && s->grp_lim[g] == li)) g++;
+      if (g == s->ngroups) {
+        s->grp_flux[g] = fl;
+        s->grp_lim[g] = li;
+        s->ngroups++;
+      }
+      gof[L] = g;
+    }
+    auto regroup = [&](std::vector<int>& list) {
+      std::vector<int> out;
+      out.reserve(list.size());
+      for (int g = 0; g < s->ngroups; g++) {
+        s->grp_off[g] = (int)out.size();
+        for (int b : list)
+          if (gof[block_meta[5 * b + 1]] == g) out.push_back(b);
+        s->grp_cnt[g] = (int)out.size() - s->grp_off[g];
+      }
+      list.swap(out);
+    };
+    regroup(work);
+    regroup(work_storage);
+  }
   up((void*)s->d_work_storage, work_storage.data(), sizeof(int) * work_storage.size());
   s->nwork = nblocks;
   up((void*)s->d_work, work.data(), sizeof(int) * work.size());
   if (e == cudaSuccess) e = cudaMemsetAsync(M.part, 0, sizeof(double) * NPART * nblocks, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(M.sums, 0, sizeof(double) * NV * ninst, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(M.err, 0, sizeof(int) * 4, s->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(s->d_counter, 0, sizeof(int) * 4, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->d_counter, 0, sizeof(int) * (MAXLEV + 4), s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);  // host vectors die here
   if (e != cudaSuccess) {
     delete s;

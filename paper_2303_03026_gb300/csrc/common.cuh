@@ -88,6 +88,7 @@ struct StageParams {
   float af, bf, a2f, b2f;  // a, b, a2, b2, small_density, small_pressure in float
   float small_density_f, small_pressure_f;
   int reflux;            // keep the fluxes of level-change faces for refluxing
+  signed char lflux[MAXLEV], llim[MAXLEV];  // flux and limiter of each level
 };
 
 // a StageParams value in the kernel's arithmetic type (no conversion in-kernel)

@@ -5,7 +5,8 @@
 
 namespace amrvac {
 
-template <class T, int DIM, int LIM> int launch_fused_l(amrvac_state* s, int k, int epilogue);
+template <class T, int DIM, int LIM>
+int launch_fused_l(amrvac_state* s, int k, int epilogue, int g);
 
 bool fused_supported(const amrvac_config* c) {
   if (c->ndim == 2) return c->block_nx[0] == 16 && c->block_nx[1] == 16;
@@ -13,21 +14,29 @@ bool fused_supported(const amrvac_config* c) {
   return false;
 }
 
-template <class T, int DIM> static int by_limiter(amrvac_state* s, int k, int epilogue) {
-  switch (s->cfg.limiter) {
-    case AMRVAC_LIM_MINMOD: return launch_fused_l<T, DIM, AMRVAC_LIM_MINMOD>(s, k, epilogue);
-    case AMRVAC_LIM_VANLEER: return launch_fused_l<T, DIM, AMRVAC_LIM_VANLEER>(s, k, epilogue);
-    case AMRVAC_LIM_KOREN: return launch_fused_l<T, DIM, AMRVAC_LIM_KOREN>(s, k, epilogue);
+template <class T, int DIM> static int by_limiter(amrvac_state* s, int k, int epilogue, int g) {
+  switch (s->grp_lim[g]) {
+    case AMRVAC_LIM_MINMOD: return launch_fused_l<T, DIM, AMRVAC_LIM_MINMOD>(s, k, epilogue, g);
+    case AMRVAC_LIM_VANLEER: return launch_fused_l<T, DIM, AMRVAC_LIM_VANLEER>(s, k, epilogue, g);
+    case AMRVAC_LIM_KOREN: return launch_fused_l<T, DIM, AMRVAC_LIM_KOREN>(s, k, epilogue, g);
   }
   // the other limiters share one instantiation with a runtime limiter
-  return launch_fused_l<T, DIM, -1>(s, k, epilogue);
+  return launch_fused_l<T, DIM, -1>(s, k, epilogue, g);
 }
 
+// one launch per scheme group (levels sharing flux and limiter), in order
 int launch_fused_stage(amrvac_state* s, int k, int epilogue) {
   const bool f64 = s->cfg.precision == AMRVAC_FP64;
-  if (s->ndim == 2) return f64 ? by_limiter<double, 2>(s, k, epilogue) : by_limiter<float, 2>(s, k, epilogue);
-  if (s->ndim == 3) return f64 ? by_limiter<double, 3>(s, k, epilogue) : by_limiter<float, 3>(s, k, epilogue);
-  return -1;
+  int total = 0;
+  for (int g = 0; g < s->ngroups; g++) {
+    int n;
+    if (s->ndim == 2) n = f64 ? by_limiter<double, 2>(s, k, epilogue, g) : by_limiter<float, 2>(s, k, epilogue, g);
+    else if (s->ndim == 3) n = f64 ? by_limiter<double, 3>(s, k, epilogue, g) : by_limiter<float, 3>(s, k, epilogue, g);
+    else return -1;
+    if (n < 0) return -1;
+    total += n;
+  }
+  return total;
 }
 
 }  // namespace amrvac

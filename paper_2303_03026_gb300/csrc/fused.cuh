@@ -589,7 +589,7 @@ namespace amrvac {
 
 template <class T, int DIM, int LIM, int FLUX, bool FULL>
 static int launch_one(amrvac_state* s, const T* U0, const T* Uk, const T* U2, T* out, T* out2,
-                      StageParams sp) {
+                      const int* work, int nwork, int* counter, StageParams sp) {
   auto kern = DIM == 3 ? k_fused<T, 3, LIM, FLUX, FULL> : k_fused2d<T, LIM, FLUX, FULL>;
   const int smem = DIM == 3 ? (int)sizeof(FusedSmem<T, 3>) : (int)sizeof(Fused2dSmem<T>);
   static int nsm = 0, per_sm = 0;  // per instantiation, this device
@@ -603,48 +603,67 @@ static int launch_one(amrvac_state* s, const T* U0, const T* Uk, const T* U2, T*
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, FT, smem);
     if (per_sm < 1) per_sm = 1;
   }
+  if (nwork <= 0) return 0;
   int ctas = s->tune.ctas_per_sm > 0 && s->tune.ctas_per_sm < per_sm ? s->tune.ctas_per_sm : per_sm;
   int grid = nsm * ctas;
-  if (grid > s->nwork) grid = s->nwork;
-  int n = 1;
-  if (s->ngen > 0) {
-    // ghost slabs of the level-change faces of the stage input
-    const int g = s->ngen < nsm * 8 ? s->ngen : nsm * 8;
-    k_ghost_slabs<T, DIM><<<g, 256, 0, s->stream>>>(s->mesh, Uk, (T*)s->gslab, s->d_glist,
-                                                     s->ngen);
-    n++;
-  }
+  if (grid > nwork) grid = nwork;
   if (s->tune.dynamic) {
-    if (cudaMemsetAsync(s->d_counter, 0, sizeof(int), s->stream) != cudaSuccess) return -1;
+    if (cudaMemsetAsync(counter, 0, sizeof(int), s->stream) != cudaSuccess) return -1;
   }
-  kern<<<grid, FT, smem, s->stream>>>(s->mesh, U0, Uk, U2, out, out2, s->d_work, s->nwork,
-                                       (const T*)s->gslab,
-                                       s->tune.dynamic ? s->d_counter : nullptr, sp);
-  return cudaPeekAtLastError() == cudaSuccess ? n : -1;
+  kern<<<grid, FT, smem, s->stream>>>(s->mesh, U0, Uk, U2, out, out2, work, nwork,
+                                       (const T*)s->gslab, s->tune.dynamic ? counter : nullptr,
+                                       sp);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
+// Stage k for scheme group g (the blocks of the levels sharing this
+// limiter and the group's flux); group 0 also launches the per-stage passes
+// every group shares: the stage constants and the ghost slabs.
 template <class T, int DIM, int LIM>
-int launch_fused_l(amrvac_state* s, int k, int epilogue) {
+int launch_fused_l(amrvac_state* s, int k, int epilogue, int g) {
   const StageBuffers sb = stage_buffers(s->cfg.time, k);
   StageParams sp = make_stage_params(s, k, epilogue);
-  if (launch_level_consts(s, k) < 0) return -1;
+  sp.flux = s->grp_flux[g];
+  sp.limiter = s->grp_lim[g];
   const T* U0 = (const T*)s->U[sb.u0];
   const T* Uk = (const T*)s->U[sb.uin];
   const T* U2 = sb.u2 >= 0 ? (const T*)s->U[sb.u2] : nullptr;
   T* out = (T*)s->U[sb.out];
   T* out2 = sb.out2 >= 0 ? (T*)s->U[sb.out2] : nullptr;
+  int n = 0;
+  if (g == 0) {
+    if (launch_level_consts(s, k) < 0) return -1;
+    n++;
+    if (s->ngen > 0) {
+      // ghost slabs of the level-change faces of the stage input
+      const int gs = s->ngen < 152 * 8 ? s->ngen : 152 * 8;
+      k_ghost_slabs<T, DIM><<<gs, 256, 0, s->stream>>>(s->mesh, Uk, (T*)s->gslab, s->d_glist,
+                                                        s->ngen);
+      n++;
+    }
+  }
+  const int* work = s->d_work + s->grp_off[g];
+  const int nwork = s->grp_cnt[g];
+  int* counter = s->d_counter + g;
   const bool full = sp.has2 || sp.reflux;
-  int n;
-  if (s->cfg.flux == AMRVAC_FLUX_HLLD)
-    n = full ? launch_one<T, DIM, LIM, AMRVAC_FLUX_HLLD, true>(s, U0, Uk, U2, out, out2, sp)
-             : launch_one<T, DIM, LIM, AMRVAC_FLUX_HLLD, false>(s, U0, Uk, U2, out, out2, sp);
-  else if (s->cfg.flux == AMRVAC_FLUX_HLL)
-    n = full ? launch_one<T, DIM, LIM, AMRVAC_FLUX_HLL, true>(s, U0, Uk, U2, out, out2, sp)
-             : launch_one<T, DIM, LIM, AMRVAC_FLUX_HLL, false>(s, U0, Uk, U2, out, out2, sp);
+  const int flux = s->grp_flux[g];
+  int m;
+  if (flux == AMRVAC_FLUX_HLLD)
+    m = full ? launch_one<T, DIM, LIM, AMRVAC_FLUX_HLLD, true>(s, U0, Uk, U2, out, out2, work,
+                                                               nwork, counter, sp)
+             : launch_one<T, DIM, LIM, AMRVAC_FLUX_HLLD, false>(s, U0, Uk, U2, out, out2, work,
+                                                                nwork, counter, sp);
+  else if (flux == AMRVAC_FLUX_HLL)
+    m = full ? launch_one<T, DIM, LIM, AMRVAC_FLUX_HLL, true>(s, U0, Uk, U2, out, out2, work,
+                                                              nwork, counter, sp)
+             : launch_one<T, DIM, LIM, AMRVAC_FLUX_HLL, false>(s, U0, Uk, U2, out, out2, work,
+                                                               nwork, counter, sp);
   else
-    n = full ? launch_one<T, DIM, LIM, AMRVAC_FLUX_TVDLF, true>(s, U0, Uk, U2, out, out2, sp)
-             : launch_one<T, DIM, LIM, AMRVAC_FLUX_TVDLF, false>(s, U0, Uk, U2, out, out2, sp);
-  return n < 0 ? -1 : n + 1;
+    m = full ? launch_one<T, DIM, LIM, AMRVAC_FLUX_TVDLF, true>(s, U0, Uk, U2, out, out2, work,
+                                                                nwork, counter, sp)
+             : launch_one<T, DIM, LIM, AMRVAC_FLUX_TVDLF, false>(s, U0, Uk, U2, out, out2, work,
+                                                                 nwork, counter, sp);
+  return m < 0 ? -1 : n + m;
 }
 
 }  // namespace amrvac

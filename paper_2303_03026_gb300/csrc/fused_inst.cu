@@ -10,5 +10,5 @@
 #endif
 
 namespace amrvac {
-template int launch_fused_l<AMRVAC_FT, AMRVAC_FD, AMRVAC_FL>(amrvac_state*, int, int);
+template int launch_fused_l<AMRVAC_FT, AMRVAC_FD, AMRVAC_FL>(amrvac_state*, int, int, int);
 }  // namespace amrvac

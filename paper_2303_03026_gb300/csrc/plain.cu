@@ -72,6 +72,8 @@ __global__ void __launch_bounds__(256) k_flux(DevMesh M, const T* __restrict__ W
     const int q = M.blk[b * 5];
     const InstRT rt = M.rt[q];
     if (rt.dt == 0.0) continue;
+    const int lev = M.blk[b * 5 + 1];
+    const int lim = sp.llim[lev], flux = sp.lflux[lev];  // the block's level's scheme
     int i = fi % e0, j = (fi / e0) % e1, k = fi / (e0 * e1);
     // padded index of the cell right of the face
     int pc = ((k + g2) * P1 + (j + g1)) * P0 + (i + g0);
@@ -81,8 +83,8 @@ __global__ void __launch_bounds__(256) k_flux(DevMesh M, const T* __restrict__ W
     for (int v = 0; v < NV; v++) {
       const T* s = src + (size_t)v * np;
       T s0 = s[-2 * stride], s1 = s[-stride], s2 = s[0], s3 = s[stride];
-      wl[v] = recon_plus(sp.limiter, s0, s1, s2);
-      wr[v] = recon_minus(sp.limiter, s1, s2, s3);
+      wl[v] = recon_plus(lim, s0, s1, s2);
+      wr[v] = recon_minus(lim, s1, s2, s3);
       w0[v] = s1;
       w1[v] = s2;
     }
@@ -94,7 +96,7 @@ __global__ void __launch_bounds__(256) k_flux(DevMesh M, const T* __restrict__ W
       }
     }
     T f[NV];
-    face_flux(sp.flux, sp.glm, (T)M.gamma[q], (T)rt.ch, d, wl, wr, f);
+    face_flux(flux, sp.glm, (T)M.gamma[q], (T)rt.ch, d, wl, wr, f);
     T* dst = F + (size_t)b * NV * nf + fi;
 #pragma unroll
     for (int v = 0; v < NV; v++) dst[(size_t)v * nf] = f[v];
@@ -378,6 +380,12 @@ StageParams make_stage_params(const amrvac_state* s, int k, int epilogue) {
   sp.reflux = s->cfg.reflux;
   sp.flux = s->cfg.flux;
   sp.limiter = s->cfg.limiter;
+  for (int L = 0; L < MAXLEV; L++) {
+    sp.lflux[L] =
+        (signed char)(s->cfg.level_flux[L] > 0 ? s->cfg.level_flux[L] - 1 : s->cfg.flux);
+    sp.llim[L] =
+        (signed char)(s->cfg.level_limiter[L] > 0 ? s->cfg.level_limiter[L] - 1 : s->cfg.limiter);
+  }
   sp.glm = s->cfg.glm;
   sp.epilogue = epilogue;
   sp.pressure_ff = s->cfg.precision == AMRVAC_FP32_BULK && s->cfg.pressure == AMRVAC_PRESSURE_FF;

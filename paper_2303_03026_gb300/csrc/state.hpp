@@ -45,7 +45,12 @@ struct amrvac_state {
   amrvac_tuning tune{0, 0, 0, 0.0};
   int* d_work_morton = nullptr;
   int* d_work_storage = nullptr;
-  int* d_counter = nullptr;
+  int* d_counter = nullptr;  // one dynamic-schedule counter per scheme group
+  // fused path: scheme groups (levels sharing a flux and limiter), each a
+  // contiguous range [grp_off, grp_off + grp_cnt) of the work lists
+  int ngroups = 1;
+  int grp_flux[amrvac::MAXLEV] = {0}, grp_lim[amrvac::MAXLEV] = {0};
+  int grp_off[amrvac::MAXLEV] = {0}, grp_cnt[amrvac::MAXLEV] = {0};
   // host copies
   std::vector<int32_t> meta;
   std::vector<amrvac_instance_desc> inst;

@@ -92,9 +92,13 @@ def test_scheme_options_validated(lib):
     from paper_2303_03026_gb300 import amrvac
     W = wl.small_amr_2d()
     for field, value in (("flux", 3), ("time", 4), ("limiter", 7), ("reflux", 2),
-                         ("fix_small_values", 3)):
+                         ("fix_small_values", 3), ("level_flux", 4), ("level_limiter", 8),
+                         ("level_flux", -1)):
         c = amrvac.make_config(W.cfg)
-        setattr(c, field, value)
+        if field.startswith("level_"):
+            getattr(c, field)[2] = value
+        else:
+            setattr(c, field, value)
         ins = amrvac.make_instances(W.instances)
         meta = np.ascontiguousarray(W.block_meta, np.int32)
         n = C.c_size_t(0)

@@ -250,3 +250,38 @@ def test_reflux_conserves_on_gpu(amr, orc, ndim, kernel, bnx):
     sc = np.abs(Uo).max(axis=(1, 2), keepdims=True)
     sc = np.where(sc < 1e-9 * np.abs(Uo).max(), np.abs(Uo).max(), sc)
     assert (np.abs(got - Uo) / sc).max() < 1e-10
+
+
+# ----------------------------------------------------------------------------
+# per-level schemes (Sect. 3: flux and reconstruction may differ per level)
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("ndim,kernel,bnx", [(2, "plain", 8), (2, "auto", 16), (3, "auto", 16)])
+def test_per_level_schemes_stage_parity(amr, orc, ndim, kernel, bnx):
+    if ndim == 2:
+        W = wl.small_amr_2d(bnx=bnx)
+    else:
+        W = wl.c4_blast_amr(base=4, levels=3, bnx=bnx, shell=(0.2, 0.26), precision="fp64")
+    W.cfg.level_flux = {1: "hll", 2: "tvdlf"}
+    W.cfg.level_limiter = {2: "woodward"}
+    _scheme_stage_parity(amr, orc, W, kernel, 1e-12)
+
+
+def test_per_level_schemes_with_reflux_conserve(amr, orc):
+    W = _advected_amr("fp64", 16, 3)
+    W.cfg.level_flux = {2: "hll"}
+    W.cfg.level_limiter = {1: "minmod"}
+    m = orc.mesh_for(W, 8)
+    s0 = m.sums(W.U)
+    S = amr.State.from_workload(W, kernel="auto")
+    S.set_conserved(W.U)
+    S.step(3)
+    d = S.diag()
+    assert d["status"] == 0, d
+    assert np.abs(d["sums"][0, :8] - s0[0, :8]).max() / np.abs(s0).max() < 1e-13
+    Uo, *_ = m.run(W.U, 1e30, maxsteps=3)
+    got = S.get_conserved(0)
+    S.close()
+    sc = np.abs(Uo).max(axis=(1, 2), keepdims=True)
+    sc = np.where(sc < 1e-9 * np.abs(Uo).max(), np.abs(Uo).max(), sc)
+    assert (np.abs(got - Uo) / sc).max() < 1e-10
