@@ -96,7 +96,7 @@ def lib():
     return _lib
 
 
-_FLUX = {"hll": 0, "hlld": 1, "tvdlf": 2}
+_FLUX = {"hll": 0, "hlld": 1, "tvdlf": 2, "hllc": 3}
 _LIM = {"minmod": 0, "vanleer": 1, "koren": 2, "superbee": 3, "woodward": 4, "mcbeta": 5,
         "albada": 6}
 _TIME = {"ssprk2": 0, "ssprk3": 1, "ssprk43": 2, "ssprk54": 3}

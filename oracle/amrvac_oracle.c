@@ -26,7 +26,8 @@
  *  - SSPRK(2,2), SSPRK(3,3) (Gottlieb 2005), SSPRK(4,3) and SSPRK(5,4)
  *    (Spiteri & Ruuth 2002) in Shu-Osher form (Sect. 3, time-integration
  *    table); psi is damped over each Euler part's time step.
- *  - TVD Lax-Friedrichs flux with the fastest local signal speed.
+ *  - TVD Lax-Friedrichs flux with the fastest local signal speed; HLLC for
+ *    MHD in the three-wave form of Li 2005 (see hllc_local).
  *  - CFL: dt = C / max over cells of sum_d (|v_d| + c_f,d)/dx_d, from U^n,
  *    global per instance, no subcycling; c_h = max (|v_d| + c_f,d).
  *  - AMR ghost values (the paper gives no operators): same level -> copy;
@@ -318,6 +319,58 @@ static void tvdlf_local(double g, const double* ql, const double* qr, double bx,
   for (int c = 0; c < 8; c++) f[c] = 0.5 * (FL[c] + FR[c]) - 0.5 * cmax * (UR[c] - UL[c]);
 }
 
+/* HLLC for MHD (the `hllc' flux of the flux-scheme table; the paper prints no
+ * formulas and cites a review, so this restates the three-wave solver of
+ * Li 2005): HLL speeds; the HLL state U* = (S_R U_R - S_L U_L - F_R + F_L) /
+ * (S_R - S_L) gives the contact speed S_M (its momentum over its density),
+ * the star magnetic field B* (normal component B_x) and the star velocity v*
+ * (its momentum over its density);
+ * p_T* = rho_L (S_L - u_L)(S_M - u_L) + p_TL; per side K
+ *   rho*_K = rho_K (S_K - u_K)/(S_K - S_M),  (rho u)*_K = rho*_K S_M,
+ *   (rho v_t)*_K = [rho_K v_tK (S_K - u_K) - (B_x B*_t - B_x B_tK)]/(S_K - S_M),
+ *   e*_K = [e_K (S_K - u_K) + p_T* S_M - p_TK u_K - B_x (v*.B* - v_K.B_K)]/(S_K - S_M),
+ * flux F*_K = F_K + S_K (U*_K - U_K), region by S_L, S_M, S_R. */
+static void hllc_local(double g, const double* ql, const double* qr, double bx, double* f) {
+  double UL[8], UR[8], FL[8], FR[8], ptl, ptr;
+  local_cons_flux(g, ql, bx, UL, FL, &ptl);
+  local_cons_flux(g, qr, bx, UR, FR, &ptr);
+  double cfl = local_fast(g, ql, bx), cfr = local_fast(g, qr, bx);
+  double sl = dmin(ql[1] - cfl, qr[1] - cfr);
+  double sr = dmax(ql[1] + cfl, qr[1] + cfr);
+  if (sl >= 0.0) {
+    for (int c = 0; c < 8; c++) f[c] = FL[c];
+    return;
+  }
+  if (sr <= 0.0) {
+    for (int c = 0; c < 8; c++) f[c] = FR[c];
+    return;
+  }
+  double uh[8];
+  for (int c = 0; c < 8; c++) uh[c] = (sr * UR[c] - sl * UL[c] - FR[c] + FL[c]) / (sr - sl);
+  const double sm = uh[1] / uh[0];
+  const double vs[3] = {sm, uh[2] / uh[0], uh[3] / uh[0]};
+  const double bs[3] = {bx, uh[6], uh[7]};
+  const double pts = ql[0] * (sl - ql[1]) * (sm - ql[1]) + ptl;
+  const double vbs = vs[0] * bs[0] + vs[1] * bs[1] + vs[2] * bs[2];
+  const double* q = sm >= 0.0 ? ql : qr;
+  const double* U = sm >= 0.0 ? UL : UR;
+  const double* F = sm >= 0.0 ? FL : FR;
+  const double S = sm >= 0.0 ? sl : sr;
+  const double pt = sm >= 0.0 ? ptl : ptr;
+  const double su = S - q[1], ssm = S - sm;
+  const double vb = q[1] * bx + q[2] * q[6] + q[3] * q[7];
+  double Us[8];
+  Us[0] = q[0] * su / ssm;
+  Us[1] = Us[0] * sm;
+  Us[2] = (q[0] * q[2] * su - (bx * bs[1] - bx * q[6])) / ssm;
+  Us[3] = (q[0] * q[3] * su - (bx * bs[2] - bx * q[7])) / ssm;
+  Us[4] = (U[4] * su + pts * sm - pt * q[1] - bx * (vbs - vb)) / ssm;
+  Us[5] = bx;
+  Us[6] = bs[1];
+  Us[7] = bs[2];
+  for (int c = 0; c < 8; c++) f[c] = F[c] + S * (Us[c] - U[c]);
+}
+
 /* one side of the HLLD single-star state, Miyoshi & Kusano 2005 */
 typedef struct {
   double rs, vs, ws, bys, bzs, es;
@@ -424,7 +477,8 @@ void orc_face_flux(int flux, int glm, double gamma, double ch, int dir, const do
   double fl[8];
   if (flux == 0) hll_local(gamma, ql, qr, bns, fl);
   else if (flux == 1) hlld_local(gamma, ql, qr, bns, fl);
-  else tvdlf_local(gamma, ql, qr, bns, fl);
+  else if (flux == 2) tvdlf_local(gamma, ql, qr, bns, fl);
+  else hllc_local(gamma, ql, qr, bns, fl);
   f[RHO] = fl[0];
   f[MX + dir] = fl[1];
   f[MX + t1] = fl[2];

@@ -30,7 +30,7 @@ extern "C" {
 typedef struct {
   int ndim;              /* 1, 2 or 3 */
   int nx[3];             /* cells per block per dimension (1 for unused dims) */
-  int flux;              /* 0 hll, 1 hlld, 2 tvdlf */
+  int flux;              /* 0 hll, 1 hlld, 2 tvdlf, 3 hllc */
   int limiter;           /* 0 minmod, 1 vanleer, 2 koren, 3 superbee, 4 woodward,
                             5 mcbeta, 6 albada */
   int time;              /* 0 ssprk(2,2), 1 ssprk(3,3), 2 ssprk(4,3), 3 ssprk(5,4) */

@@ -38,7 +38,7 @@ RHO, MX, MY, MZ, EN, BX, BY, BZ, PSI = range(NVAR)
 VAR_NAMES = ("rho", "m_x", "m_y", "m_z", "e", "B_x", "B_y", "B_z", "psi")
 
 # option values shared by the C ABI (include/amrvac.h) and the oracle
-FLUX = {"hll": 0, "hlld": 1, "tvdlf": 2}
+FLUX = {"hll": 0, "hlld": 1, "tvdlf": 2, "hllc": 3}
 LIMITER = {"minmod": 0, "vanleer": 1, "koren": 2, "superbee": 3, "woodward": 4, "mcbeta": 5,
            "albada": 6}
 TIME = {"ssprk2": 0, "ssprk3": 1, "ssprk43": 2, "ssprk54": 3}

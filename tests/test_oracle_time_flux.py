@@ -253,3 +253,61 @@ def test_higher_stage_schemes_on_cp_wave(orc, time):
     e32, e64 = err(32, time), err(64, time)
     assert math.log2(e32 / e64) > 1.7, (e32, e64)
     assert e64 < 1.2 * err(64, "ssprk3")
+
+
+# ----------------------------------------------------------------------------
+# HLLC (Li 2005 three-wave solver for MHD)
+# ----------------------------------------------------------------------------
+
+def test_hllc_consistency_and_rotation(orc):
+    rng = np.random.Generator(np.random.PCG64(31))
+    perm = lambda w: np.array([w[0], w[3], w[1], w[2], w[4], w[7], w[5], w[6], w[8]])
+    for _ in range(40):
+        w = _rand_state(rng)
+        for d in range(3):
+            np.testing.assert_allclose(orc.face_flux("hllc", 1, 5 / 3, 1.3, d, w, w),
+                                       orc.face_flux("hll", 1, 5 / 3, 1.3, d, w, w),
+                                       rtol=1e-12, atol=1e-13)
+        a, b = _rand_state(rng), _rand_state(rng)
+        fx = orc.face_flux("hllc", 1, 5 / 3, 2.0, 0, a, b)
+        fy = orc.face_flux("hllc", 1, 5 / 3, 2.0, 1, perm(a), perm(b))
+        np.testing.assert_allclose(fy, perm(fx), rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("bx", [0.0, 0.7])
+def test_hllc_resolves_stationary_contact(orc, bx):
+    # density jump at rest with continuous p and B: the contact must not move
+    # (zero mass flux, momentum flux p_T - B_x^2); HLL smears it
+    wl_ = _state(1.0, 0.0, 0, 0, 1.0, bx, 0.4, -0.2)
+    wr_ = _state(0.1, 0.0, 0, 0, 1.0, bx, 0.4, -0.2)
+    f = orc.face_flux("hllc", 0, 1.4, 1.0, 0, wl_, wr_)
+    assert abs(f[0]) < 1e-14
+    pt = 1.0 + 0.5 * (bx * bx + 0.16 + 0.04)
+    assert abs(f[1] - (pt - bx * bx)) < 1e-13
+    assert abs(orc.face_flux("hll", 0, 1.4, 1.0, 0, wl_, wr_)[0]) > 1e-3
+
+
+def test_hllc_moving_contact_b0(orc):
+    # B = 0: HLLC is the Euler HLLC of Toro, exact for an isolated moving contact
+    wl_ = _state(1.0, 0.4, 0.1, -0.3, 0.8, 0, 0, 0)
+    wr_ = _state(0.3, 0.4, 0.1, -0.3, 0.8, 0, 0, 0)
+    f = orc.face_flux("hllc", 0, 1.4, 1.0, 0, wl_, wr_)
+    np.testing.assert_allclose(f[:5], [0.4, 0.4 * 0.4 + 0.8, 0.4 * 0.1, 0.4 * -0.3,
+                                       (0.8 / 0.4 + 0.5 * (0.16 + 0.01 + 0.09) + 0.8) * 0.4],
+                               rtol=1e-13)
+
+
+def test_hllc_sod_converges_and_beats_hll(orc):
+    errs = {}
+    for flux in ("hllc", "hll"):
+        e = []
+        for n in (200, 400, 800):
+            W = wl.riemann_1d((1.0, 0, 0, 0, 1.0, 0, 0), (0.125, 0, 0, 0, 0.1, 0, 0), n=n,
+                              gamma=1.4, bx=0.0, t_end=0.2, flux=flux, time="ssprk3")
+            U, t, ns, st = orc.mesh_for(W).run(W.U, 0.2)
+            x = (np.arange(n) + 0.5) / n
+            ex = euler_exact((1.0, 0, 1.0), (0.125, 0, 0.1), 1.4, x, 0.2, x0=0.5)
+            e.append(np.abs(U[0, 0] - ex[0]).mean())
+        errs[flux] = e
+    assert errs["hllc"][-1] < 4e-3 and errs["hllc"][0] / errs["hllc"][-1] > 2.5
+    assert errs["hllc"][-1] < errs["hll"][-1]  # the contact is sharper
