@@ -46,9 +46,11 @@ def parse():
     p.add_argument("--size", type=int, default=0,
                    help="workload size (c4: level-0 blocks per dim; c3/c2: cells per dim; "
                         "c5: instance count); 0 = the full configuration")
-    p.add_argument("--flux", default=None, choices=["hll", "hlld"],
+    p.add_argument("--flux", default=None, choices=["hll", "hlld", "tvdlf", "hllc"],
                    help="override the workload's flux scheme")
-    p.add_argument("--limiter", default=None, choices=["minmod", "vanleer", "koren"],
+    p.add_argument("--limiter", default=None,
+                   choices=["minmod", "vanleer", "koren", "superbee", "woodward", "mcbeta",
+                            "albada"],
                    help="override the workload's limiter")
     p.add_argument("--no-variants", action="store_true",
                    help="skip the HLL and FP64-pressure variant timings")
@@ -400,6 +402,7 @@ def main():
     variants = {}
     if not args.no_variants and fused:
         for name, kw in (("hll_vanleer", {"flux": "hll"}), ("tvdlf_vanleer", {"flux": "tvdlf"}),
+                         ("hllc_vanleer", {"flux": "hllc"}),
                          ("hlld_ssprk43", {"time": "ssprk43"}),
                          ("hlld_ssprk54", {"time": "ssprk54"}),
                          ("hlld_woodward", {"limiter": "woodward"}),

@@ -64,8 +64,14 @@ typedef enum {
 } amrvac_status;
 
 /* flux-scheme table of Sect. 3.2.1: HLL (Harten 1983), HLLD (Miyoshi & Kusano
- * 2005), TVD Lax-Friedrichs (local LF with the fastest signal speed) */
-typedef enum { AMRVAC_FLUX_HLL = 0, AMRVAC_FLUX_HLLD = 1, AMRVAC_FLUX_TVDLF = 2 } amrvac_flux;
+ * 2005), TVD Lax-Friedrichs (local LF with the fastest signal speed), HLLC for
+ * MHD (the three-wave solver of Li 2005) */
+typedef enum {
+  AMRVAC_FLUX_HLL = 0,
+  AMRVAC_FLUX_HLLD = 1,
+  AMRVAC_FLUX_TVDLF = 2,
+  AMRVAC_FLUX_HLLC = 3
+} amrvac_flux;
 /* two-ghost-cell limiters of the limiter table (Sect. 3.1.1): minmod, van Leer
  * 1974, Koren 1993 (third order), superbee (Roe 1985), woodward (monotonized
  * central, van Leer 1977), mcbeta (beta = 1.4), van Albada 1982 (TVD form) */

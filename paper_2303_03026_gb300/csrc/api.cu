@@ -36,12 +36,12 @@ bool config_ok(const amrvac_config* c, std::string& err) {
   if (c->ndim < 1 || c->ndim > 3) return err = "ndim must be 1..3", false;
   for (int d = 0; d < c->ndim; d++)
     if (c->block_nx[d] < 4 || c->block_nx[d] > 4096) return err = "block_nx must be 4..4096", false;
-  if (c->flux < AMRVAC_FLUX_HLL || c->flux > AMRVAC_FLUX_TVDLF) return err = "bad flux", false;
+  if (c->flux < AMRVAC_FLUX_HLL || c->flux > AMRVAC_FLUX_HLLC) return err = "bad flux", false;
   if (c->limiter < AMRVAC_LIM_MINMOD || c->limiter > AMRVAC_LIM_ALBADA)
     return err = "bad limiter", false;
   if (c->reflux != 0 && c->reflux != 1) return err = "bad reflux", false;
   for (int L = 0; L < AMRVAC_MAX_LEVELS; L++) {
-    if (c->level_flux[L] < 0 || c->level_flux[L] > AMRVAC_FLUX_TVDLF + 1)
+    if (c->level_flux[L] < 0 || c->level_flux[L] > AMRVAC_FLUX_HLLC + 1)
       return err = "bad level_flux", false;
     if (c->level_limiter[L] < 0 || c->level_limiter[L] > AMRVAC_LIM_ALBADA + 1)
       return err = "bad level_limiter", false;

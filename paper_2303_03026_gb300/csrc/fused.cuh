@@ -658,11 +658,16 @@ int launch_fused_l(amrvac_state* s, int k, int epilogue, int g) {
                                                               nwork, counter, sp)
              : launch_one<T, DIM, LIM, AMRVAC_FLUX_HLL, false>(s, U0, Uk, U2, out, out2, work,
                                                                nwork, counter, sp);
-  else
+  else if (flux == AMRVAC_FLUX_TVDLF)
     m = full ? launch_one<T, DIM, LIM, AMRVAC_FLUX_TVDLF, true>(s, U0, Uk, U2, out, out2, work,
                                                                 nwork, counter, sp)
              : launch_one<T, DIM, LIM, AMRVAC_FLUX_TVDLF, false>(s, U0, Uk, U2, out, out2, work,
                                                                  nwork, counter, sp);
+  else
+    m = full ? launch_one<T, DIM, LIM, AMRVAC_FLUX_HLLC, true>(s, U0, Uk, U2, out, out2, work,
+                                                               nwork, counter, sp)
+             : launch_one<T, DIM, LIM, AMRVAC_FLUX_HLLC, false>(s, U0, Uk, U2, out, out2, work,
+                                                                nwork, counter, sp);
   return m < 0 ? -1 : n + m;
 }
 

@@ -241,6 +241,58 @@ __device__ __forceinline__ void tvdlf_local(T g, T ig1, const T* ql, const T* qr
   for (int c = 0; c < 8; c++) f[c] = T(0.5) * (FL[c] + FR[c]) - T(0.5) * cmax * (UR[c] - UL[c]);
 }
 
+// HLLC for MHD (Li 2005): HLL speeds; the HLL state gives the contact speed
+// S_M, the star field B* (normal component bx) and star velocity v*; total
+// pressure p_T* = rho_L (S_L - u_L)(S_M - u_L) + p_TL; the upwind side K of
+// S_M: rho* = rho (S - u)/(S - S_M), m* = (rho* S_M, [rho v_t (S - u) -
+// bx (B*_t - B_t)]/(S - S_M)), e* = [e (S - u) + p_T* S_M - p_T u -
+// bx (v*.B* - v.B)]/(S - S_M); flux F_K + S_K (U*_K - U_K)
+template <class T>
+__device__ __forceinline__ void hllc_local(T g, T ig1, const T* ql, const T* qr, T bx, T* f) {
+  T UL[8], UR[8], FL[8], FR[8], ptl, ptr;
+  local_cons_flux(ig1, ql, bx, UL, FL, ptl);
+  local_cons_flux(ig1, qr, bx, UR, FR, ptr);
+  const T cfl = local_fast(g, ql, bx), cfr = local_fast(g, qr, bx);
+  const T sl = fmin(ql[1] - cfl, qr[1] - cfr);
+  const T sr = fmax(ql[1] + cfl, qr[1] + cfr);
+  if (sl >= T(0)) {
+#pragma unroll
+    for (int c = 0; c < 8; c++) f[c] = FL[c];
+    return;
+  }
+  if (sr <= T(0)) {
+#pragma unroll
+    for (int c = 0; c < 8; c++) f[c] = FR[c];
+    return;
+  }
+  T uh[8];
+#pragma unroll
+  for (int c = 0; c < 8; c++) uh[c] = (sr * UR[c] - sl * UL[c] - FR[c] + FL[c]) / (sr - sl);
+  const T sm = uh[1] / uh[0];
+  const T vy = uh[2] / uh[0], vz = uh[3] / uh[0];
+  const T by = uh[6], bz = uh[7];
+  const T pts = ql[0] * (sl - ql[1]) * (sm - ql[1]) + ptl;
+  const T vbs = sm * bx + vy * by + vz * bz;
+  const bool left = sm >= T(0);
+  const T* q = left ? ql : qr;
+  const T* U = left ? UL : UR;
+  const T* F = left ? FL : FR;
+  const T S = left ? sl : sr, pt = left ? ptl : ptr;
+  const T su = S - q[1], ssm = S - sm;
+  const T vb = q[1] * bx + q[2] * q[6] + q[3] * q[7];
+  T Us[8];
+  Us[0] = q[0] * su / ssm;
+  Us[1] = Us[0] * sm;
+  Us[2] = (q[0] * q[2] * su - (bx * by - bx * q[6])) / ssm;
+  Us[3] = (q[0] * q[3] * su - (bx * bz - bx * q[7])) / ssm;
+  Us[4] = (U[4] * su + pts * sm - pt * q[1] - bx * (vbs - vb)) / ssm;
+  Us[5] = bx;
+  Us[6] = by;
+  Us[7] = bz;
+#pragma unroll
+  for (int c = 0; c < 8; c++) f[c] = F[c] + S * (Us[c] - U[c]);
+}
+
 template <class T> struct StarState {
   T rs, vs, ws, bys, bzs, es;
 };
@@ -384,7 +436,8 @@ __device__ __forceinline__ void face_flux_d(int flux, int glm, T g, T ch, const 
   const T ig1 = T(1) / (g - T(1));
   if (flux == AMRVAC_FLUX_HLL) hll_local(g, ig1, ql, qr, bns, fl);
   else if (flux == AMRVAC_FLUX_HLLD) hlld_local(g, ig1, ql, qr, bns, fl);
-  else tvdlf_local(g, ig1, ql, qr, bns, fl);
+  else if (flux == AMRVAC_FLUX_TVDLF) tvdlf_local(g, ig1, ql, qr, bns, fl);
+  else hllc_local(g, ig1, ql, qr, bns, fl);
   f[0] = fl[0];
   f[1 + D] = fl[1];
   f[1 + t1] = fl[2];

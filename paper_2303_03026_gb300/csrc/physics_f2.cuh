@@ -311,7 +311,13 @@ __device__ __forceinline__ void stencil_flux_f2(Acc st, int glm, float g, float 
   const float ig1 = 1.f / (g - 1.f);
   if (FLUX == AMRVAC_FLUX_HLL) hll_pair(g, ig1, q, bns, fl);
   else if (FLUX == AMRVAC_FLUX_HLLD) hlld_pair(g, ig1, q, bns, fl);
-  else tvdlf_pair(g, ig1, q, bns, fl);
+  else if (FLUX == AMRVAC_FLUX_TVDLF) tvdlf_pair(g, ig1, q, bns, fl);
+  else {
+    // HLLC: the scalar three-wave solver on the unpacked face states
+    const float ql[8] = {q.rho.x, q.u.x, q.v.x, q.w.x, q.p.x, bns, q.by.x, q.bz.x};
+    const float qr[8] = {q.rho.y, q.u.y, q.v.y, q.w.y, q.p.y, bns, q.by.y, q.bz.y};
+    hllc_local<float>(g, ig1, ql, qr, bns, fl);
+  }
   f[0] = fl[0];
   f[1 + D] = fl[1];
   f[1 + t1] = fl[2];

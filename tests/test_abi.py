@@ -84,15 +84,15 @@ def test_workspace_matches_precision(lib):
 
 def test_scheme_options_validated(lib):
     # the wider scheme family is accepted; values outside the enums are not
-    for flux, time, lim in (("tvdlf", "ssprk43", "superbee"), ("hll", "ssprk54", "albada"),
+    for flux, time, lim in (("tvdlf", "ssprk43", "superbee"), ("hllc", "ssprk54", "albada"),
                             ("hlld", "ssprk3", "mcbeta"), ("hlld", "ssprk2", "woodward")):
         W = wl.small_amr_2d()
         W.cfg.flux, W.cfg.time, W.cfg.limiter = flux, time, lim
         assert _bytes(lib, W)[0] == 0, (flux, time, lim)
     from paper_2303_03026_gb300 import amrvac
     W = wl.small_amr_2d()
-    for field, value in (("flux", 3), ("time", 4), ("limiter", 7), ("reflux", 2),
-                         ("fix_small_values", 3), ("level_flux", 4), ("level_limiter", 8),
+    for field, value in (("flux", 4), ("time", 4), ("limiter", 7), ("reflux", 2),
+                         ("fix_small_values", 3), ("level_flux", 5), ("level_limiter", 8),
                          ("level_flux", -1)):
         c = amrvac.make_config(W.cfg)
         if field.startswith("level_"):

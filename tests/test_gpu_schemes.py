@@ -19,6 +19,7 @@ pytestmark = pytest.mark.gpu
 
 # stage register schedule of the C ABI: (U0, U_in, U2, out, out2) per stage
 SCHED = {
+    "ssprk2": [(0, 0, None, 1, None), (0, 1, None, 0, None)],
     "ssprk3": [(0, 0, None, 1, None), (0, 1, None, 2, None), (0, 2, None, 0, None)],
     "ssprk43": [(0, 0, None, 1, None), (0, 1, None, 2, None), (0, 2, None, 1, None),
                 (0, 1, None, 0, None)],
@@ -285,3 +286,19 @@ def test_per_level_schemes_with_reflux_conserve(amr, orc):
     sc = np.abs(Uo).max(axis=(1, 2), keepdims=True)
     sc = np.where(sc < 1e-9 * np.abs(Uo).max(), np.abs(Uo).max(), sc)
     assert (np.abs(got - Uo) / sc).max() < 1e-10
+
+
+@pytest.mark.parametrize("kernel", ["plain", "auto"])
+def test_hllc_stage_parity_fp64(amr, orc, kernel):
+    for W in _small_cases("fp64"):
+        W.cfg.flux = "hllc"
+        _scheme_stage_parity(amr, orc, W, kernel, 1e-12)
+    W = wl.c1_riemann(seed=5)
+    W.cfg.flux = "hllc"
+    _scheme_stage_parity(amr, orc, W, "plain", 1e-12)
+
+
+def test_hllc_stage_parity_fp32(amr, orc):
+    for W in _small_cases("fp32")[:2]:
+        W.cfg.flux = "hllc"
+        _scheme_stage_parity(amr, orc, W, "auto", 1e-5)
