@@ -360,6 +360,59 @@ int64_t amrvac_launch_count(const amrvac_state* s);
  */
 amrvac_status amrvac_fix_small_values(amrvac_state* s, int32_t buffer, int64_t* h_count);
 
+/*
+ * Dynamic regridding (Sect. 1 and 3: blocks are refined and coarsened
+ * automatically where chosen plasma quantities vary).  The paper prints no
+ * criterion; the library uses Loehner's normalised second derivative of the
+ * density, per cell
+ *   E = sqrt( sum_d (r_{+} - 2 r_0 + r_{-})^2 /
+ *             sum_d (|r_{+} - r_0| + |r_0 - r_{-}|
+ *                    + 0.01 (|r_{+}| + 2 |r_0| + |r_{-}|))^2 )
+ * with r_{+-} the face neighbours along d (ghost values of the level across
+ * block faces, as amrvac_fill_ghosts), and a regrid in three calls:
+ *
+ * amrvac_regrid_estimate: per block of register `buffer`, the maximum of E
+ *   over its cells into h_est[nblocks] (double, may be NULL) and the flag
+ *   h_flags[nblocks] (int8, may be NULL): 1 (refine) when E > refine_threshold
+ *   and the block's level < max_level, -1 (coarsen) when
+ *   E < derefine_ratio * refine_threshold and the level > 0, else 0.  The
+ *   estimator is evaluated in double from the stored values.  Synchronises.
+ *   AMRVAC_E_INVALID for a bad buffer, threshold or max_level (0..15).
+ *
+ * amrvac_regrid_plan (host only, no device work): the block list after one
+ *   regrid of the mesh (cfg, inst, block_meta as amrvac_workspace_bytes) with
+ *   the given flags.  Flagged blocks are split in 2^ndim children; then every
+ *   leaf that would touch (across faces, edges or corners) a leaf two levels
+ *   finer is split too, until the mesh is 2:1 balanced.  A family of 2^ndim
+ *   sibling leaves is merged into its parent only when every sibling has flag
+ *   -1, none was split, and the parent keeps the mesh 2:1 balanced; families
+ *   are tried in increasing (instance, level, k, j, i) order of the parent.
+ *   The result is sorted by (instance, level, k, j, i) and written to
+ *   new_meta[capacity][5]; *new_nblocks gets its length.  AMRVAC_E_INVALID for
+ *   an invalid mesh, flags outside {-1, 0, 1}, a split beyond level 15 or
+ *   capacity too small (*new_nblocks then holds the length needed).
+ *
+ * amrvac_regrid_transfer: fills register dst_buffer of `dst` (a state created
+ *   with the planned block list and the same config and instances as `src`)
+ *   from register src_buffer of `src`: a block present in both is copied; the
+ *   children of a split block get its conserved value plus minmod-limited
+ *   slopes times +-1/4 (the prolongation of the ghost fill, slopes across the
+ *   block's faces from its ghost values); a merged parent gets the mean of the
+ *   2^ndim children cells it covers.  Every conserved variable's integral is
+ *   kept.  Needs even block_nx in every dimension.  Enqueued on dst's stream
+ *   after the work enqueued so far on src's stream.  AMRVAC_E_INVALID when the
+ *   states do not match or dst's blocks are not one regrid away from src's.
+ */
+amrvac_status amrvac_regrid_estimate(amrvac_state* s, int32_t buffer, double refine_threshold,
+                                     double derefine_ratio, int32_t max_level, double* h_est,
+                                     int8_t* h_flags);
+amrvac_status amrvac_regrid_plan(const amrvac_config* cfg, int32_t ninst,
+                                 const amrvac_instance_desc* inst, int32_t nblocks,
+                                 const int32_t* block_meta, const int8_t* flags,
+                                 int32_t capacity, int32_t* new_meta, int32_t* new_nblocks);
+amrvac_status amrvac_regrid_transfer(amrvac_state* src, int32_t src_buffer, amrvac_state* dst,
+                                     int32_t dst_buffer);
+
 const char* amrvac_error_string(amrvac_status st);
 
 #ifdef __cplusplus

@@ -196,8 +196,9 @@ def plan(cfg, instances, meta, fl):
     return np.array(sorted(newset), np.int32)
 
 
-def transfer(cfg, instances, old_meta, Uold, orc_mesh, new_meta):
-    """State of the new mesh from the old one (copy / prolongation / restriction)."""
+def transfer(cfg, instances, old_meta, Uold, orc_mesh, new_meta, only=None):
+    """State of the new mesh from the old one (copy / prolongation / restriction).
+    ``only``: indices of the new blocks to compute (the others stay 0)."""
     nd = cfg.ndim
     nx = _nx(cfg)
     ncell = nx[0] * nx[1] * nx[2]
@@ -205,6 +206,8 @@ def transfer(cfg, instances, old_meta, Uold, orc_mesh, new_meta):
     Up = orc_mesh.fill_ghosts(Uold)
     out = np.zeros((9, len(new_meta), ncell))
     for nb, r in enumerate(new_meta):
+        if only is not None and nb not in only:
+            continue
         key = tuple(int(v) for v in r)
         q, L, i, j, k = key
         if key in old:

@@ -29,7 +29,8 @@ SYMBOLS = ("amrvac_workspace_bytes", "amrvac_state_create", "amrvac_state_destro
            "amrvac_step", "amrvac_get_diag", "amrvac_clear_error", "amrvac_launch_count",
            "amrvac_error_string", "amrvac_cfl_dt_noalloc", "amrvac_state_save",
            "amrvac_state_load", "amrvac_set_tuning", "amrvac_get_tuning", "amrvac_autotune",
-           "amrvac_fix_small_values")
+           "amrvac_fix_small_values", "amrvac_regrid_estimate", "amrvac_regrid_plan",
+           "amrvac_regrid_transfer")
 
 
 class AmrvacError(RuntimeError):
@@ -107,6 +108,10 @@ def load(path: str = LIB_PATH):
     L.amrvac_state_save.argtypes = [vp, C.c_char_p]
     L.amrvac_state_load.argtypes = [vp, C.c_char_p]
     L.amrvac_fix_small_values.argtypes = [vp, i32, vp]
+    L.amrvac_regrid_estimate.argtypes = [vp, i32, dbl, dbl, i32, vp, vp]
+    L.amrvac_regrid_plan.argtypes = [C.POINTER(Config), i32, C.POINTER(InstanceDesc), i32, vp,
+                                     vp, i32, vp, vp]
+    L.amrvac_regrid_transfer.argtypes = [vp, i32, vp, i32]
     L.amrvac_cfl_dt_noalloc.argtypes = [C.POINTER(Config), C.POINTER(InstanceDesc), i32, vp, dbl,
                                         vp, vp]
     _lib = L
@@ -340,8 +345,44 @@ class State:
         """fix_small_values on register ``buffer``; returns the cells repaired."""
         n = C.c_int64(0)
         _check(load().amrvac_fix_small_values(self._h, int(buffer), C.addressof(n)),
-               "amrvac_fix_small_values")
+               "amrvac_fix_small_values", "amrvac_regrid_estimate", "amrvac_regrid_plan",
+           "amrvac_regrid_transfer")
         return n.value
+
+    # -------------------------------------------------------- regridding
+    def regrid_estimate(self, refine_threshold, derefine_ratio=0.125, max_level=15, buffer=0):
+        """Per-block estimator and flags of register ``buffer`` (numpy float64
+        [nblocks], int8 [nblocks]); see amrvac_regrid_estimate."""
+        est = np.zeros(self.nblocks, np.float64)
+        flags = np.zeros(self.nblocks, np.int8)
+        _check(load().amrvac_regrid_estimate(self._h, int(buffer), float(refine_threshold),
+                                             float(derefine_ratio), int(max_level),
+                                             est.ctypes.data, flags.ctypes.data),
+               "amrvac_regrid_estimate")
+        return est, flags
+
+    def regrid_transfer(self, dst, buffer=0, dst_buffer=0):
+        """Fill register ``dst_buffer`` of State ``dst`` (built on a planned block
+        list) from register ``buffer`` of this state."""
+        _check(load().amrvac_regrid_transfer(self._h, int(buffer), dst._h, int(dst_buffer)),
+               "amrvac_regrid_transfer")
+
+    def regrid(self, refine_threshold, derefine_ratio=0.125, max_level=15, buffer=0,
+               kernel="auto", pressure="fp64"):
+        """One regrid of register ``buffer``: estimator, plan and transfer into a
+        new State (returned; this one is left as it is).  Each instance's clock
+        continues from this state's time."""
+        _, flags = self.regrid_estimate(refine_threshold, derefine_ratio, max_level, buffer)
+        meta = regrid_plan(self.cfg, self.instances, self.meta, flags)
+        d = self.diag()
+        insts = []
+        for q, inst in enumerate(self.instances):
+            i2 = wl.Instance(**{**inst.__dict__, "t0": float(d["t"][q])})
+            insts.append(i2)
+        new = State(self.cfg, insts, meta, device=self.device, kernel=kernel,
+                    pressure=pressure)
+        self.regrid_transfer(new, buffer, 0)
+        return new
 
     def clear_error(self):
         _check(load().amrvac_clear_error(self._h), "amrvac_clear_error")
@@ -349,6 +390,24 @@ class State:
     @property
     def launches(self) -> int:
         return int(load().amrvac_launch_count(self._h))
+
+
+def regrid_plan(cfg, instances, block_meta, flags):
+    """Block list after one regrid with per-block ``flags`` (1 refine, -1
+    coarsen, 0 keep); host logic of the library (amrvac_regrid_plan)."""
+    L = load()
+    c = make_config(cfg)
+    inst = make_instances(instances)
+    meta = np.ascontiguousarray(block_meta, np.int32)
+    fl = np.ascontiguousarray(flags, np.int8)
+    assert fl.shape == (meta.shape[0],)
+    cap = meta.shape[0] * (1 << cfg.ndim) + 16
+    out = np.zeros((cap, 5), np.int32)
+    n = C.c_int32(0)
+    st = L.amrvac_regrid_plan(C.byref(c), len(instances), inst, meta.shape[0], meta.ctypes.data,
+                              fl.ctypes.data, cap, out.ctypes.data, C.byref(n))
+    _check(st, "amrvac_regrid_plan")
+    return out[:n.value].copy()
 
 
 def cfl_dt_noalloc(cfg, instance, U, out, t=0.0, stream=None):

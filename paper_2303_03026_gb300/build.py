@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libamrvac_gb300.so")
-SOURCES = ["api.cu", "plain.cu", "fused.cu", "noalloc.cu", "fix.cu", "reflux.cu"]
+SOURCES = ["api.cu", "plain.cu", "fused.cu", "noalloc.cu", "fix.cu", "reflux.cu", "regrid.cu"]
 # the fused kernel source is compiled once per (precision, dimension, limiter)
 # limiter groups: minmod, vanleer, koren as compile-time limiters, -1 = runtime
 # limiter (superbee, woodward, mcbeta, albada)

@@ -28,7 +28,7 @@ struct Tables {
 struct Layout {
   size_t U[3], W, F[3], part, blk, nbr, gface, glist, lmap, lmap_off, lnb, gamma, dx, istart,
       iblocks, rt, sums, err, work, work2, counter, gslab, lcf, lcd, flags, fixcount, gkind,
-      rlist, fluxreg, total;
+      rlist, fluxreg, est, eflags, rtab, total;
 };
 
 bool config_ok(const amrvac_config* c, std::string& err) {
@@ -310,6 +310,10 @@ Layout make_layout(const amrvac_config* c, int ninst, int nblocks, const Tables&
   }
   L.lcf = take(sizeof(float) * LC_N * MAXLEV * ninst);
   L.lcd = take(sizeof(double) * LC_N * MAXLEV * ninst);
+  // regridding: per-block estimator and flag, and the transfer table
+  L.est = take(sizeof(double) * nblocks);
+  L.eflags = take((size_t)nblocks);
+  L.rtab = take(sizeof(int) * RTAB_N * (size_t)nblocks);
   if (fused) {
     size_t per = (size_t)NV * 2 * 16 * (c->ndim == 3 ? 16 : 1);  // one face
     L.gslab = take(rs * per * T.glist.size());
@@ -468,6 +472,9 @@ amrvac_status amrvac_state_create(const amrvac_config* cfg, int32_t ninst,
   s->d_work_morton = s->d_work;
   s->d_work_storage = at<int>(s, L.work2);
   s->d_counter = at<int>(s, L.counter);
+  s->d_est = at<double>(s, L.est);
+  s->d_eflags = at<signed char>(s, L.eflags);
+  s->d_rtab = at<int>(s, L.rtab);
   s->d_glist = at<int>(s, L.glist);
   s->ngen = (int)T.glist.size();
   s->d_rlist = at<int>(s, L.rlist);

@@ -1,0 +1,434 @@
+// Dynamic regridding of the block-AMR mesh (Sect. 1 and 3: automatic
+// refinement and coarsening where chosen quantities vary).
+//
+//   k_regrid_estimate: per block, the maximum over its cells of Loehner's
+//       normalised second derivative of the density (face neighbours across
+//       block faces from the ghost operators of the update), and the block's
+//       refine / coarsen flag.  The arithmetic is double with explicit
+//       round-to-nearest operations, so the flags follow the estimator bit
+//       for bit on any state held in double.
+//   amrvac_regrid_plan (host): the new block list, closed under 2:1 balance.
+//   k_regrid_transfer: fills a state built on the new list from the old one:
+//       copy, prolongation (coarse value plus minmod-limited slopes times
+//       +-1/4) or restriction (mean of the 2^d children cells).  Sums are
+//       formed in double in a fixed order and rounded once to the state's
+//       precision.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <map>
+#include <set>
+#include <vector>
+
+#include "ghost.cuh"
+#include "state.hpp"
+
+namespace amrvac {
+
+namespace {
+
+constexpr double LOEHNER_EPS = 0.01;  // noise filter of the estimator's denominator
+
+// density of block-local cell (i, j, k) with at most one index outside the
+// block: interior load, else the ghost value of the level
+template <class T>
+__device__ __forceinline__ double rho_at(const DevMesh& M, const T* U, size_t vs, int b, int i,
+                                         int j, int k) {
+  if (i >= 0 && i < M.nx[0] && j >= 0 && j < M.nx[1] && k >= 0 && k < M.nx[2])
+    return (double)U[(size_t)b * M.ncell + ((size_t)k * M.nx[1] + j) * M.nx[0] + i];
+  T u[NV];
+  block_cell_value(M, U, vs, b, i, j, k, u);
+  return (double)u[0];
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_regrid_estimate(DevMesh M, const T* __restrict__ U,
+                                                         double thr, double dthr, int maxlev,
+                                                         double* est, signed char* flags) {
+  __shared__ double red[256 / 32];
+  const size_t vs = (size_t)M.nblocks * M.ncell;
+  for (int b = blockIdx.x; b < M.nblocks; b += gridDim.x) {
+    double rmax = 0.0;
+    for (int c = threadIdx.x; c < M.ncell; c += blockDim.x) {
+      const int ci[3] = {c % M.nx[0], (c / M.nx[0]) % M.nx[1], c / (M.nx[0] * M.nx[1])};
+      const double r0 = (double)U[(size_t)b * M.ncell + c];
+      double num = 0.0, den = 0.0;
+      for (int d = 0; d < M.ndim; d++) {
+        int p[3] = {ci[0], ci[1], ci[2]}, m[3] = {ci[0], ci[1], ci[2]};
+        p[d] += 1;
+        m[d] -= 1;
+        const double rp = rho_at(M, U, vs, b, p[0], p[1], p[2]);
+        const double rm = rho_at(M, U, vs, b, m[0], m[1], m[2]);
+        const double s2 = __dadd_rn(__dsub_rn(rp, 2.0 * r0), rm);
+        num = __dadd_rn(num, __dmul_rn(s2, s2));
+        const double a = __dadd_rn(fabs(__dsub_rn(rp, r0)), fabs(__dsub_rn(r0, rm)));
+        const double f = __dadd_rn(__dadd_rn(fabs(rp), 2.0 * fabs(r0)), fabs(rm));
+        const double dd = __dadd_rn(a, __dmul_rn(LOEHNER_EPS, f));
+        den = __dadd_rn(den, __dmul_rn(dd, dd));
+      }
+      const double ratio = num / den;
+      rmax = ratio > rmax ? ratio : rmax;  // a NaN ratio (den 0) never wins
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double other = __shfl_xor_sync(0xffffffffu, rmax, o);
+      rmax = other > rmax ? other : rmax;
+    }
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = rmax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < (int)(blockDim.x >> 5); w++) rmax = red[w] > rmax ? red[w] : rmax;
+      const double e = sqrt(rmax);
+      const int L = M.blk[b * 5 + 1];
+      est[b] = e;
+      flags[b] = (e > thr && L < maxlev) ? 1 : ((e < dthr && L > 0) ? -1 : 0);
+    }
+    __syncthreads();  // red is reused by the next block
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_regrid_transfer(DevMesh Ms, const T* __restrict__ Us,
+                                                         DevMesh Md, T* __restrict__ Ud,
+                                                         const int* __restrict__ tab) {
+  const size_t vss = (size_t)Ms.nblocks * Ms.ncell, vsd = (size_t)Md.nblocks * Md.ncell;
+  const int nd = Md.ndim;
+  const int nx[3] = {Md.nx[0], Md.nx[1], Md.nx[2]};
+  const int h[3] = {nx[0] / 2, nd > 1 ? nx[1] / 2 : 1, nd > 2 ? nx[2] / 2 : 1};
+  for (int b = blockIdx.x; b < Md.nblocks; b += gridDim.x) {
+    const int* t = tab + (size_t)b * RTAB_N;
+    const int kind = t[0], sb = t[1];
+    const int idx[3] = {Md.blk[b * 5 + 2], Md.blk[b * 5 + 3], Md.blk[b * 5 + 4]};
+    for (int c = threadIdx.x; c < Md.ncell; c += blockDim.x) {
+      const size_t dst = (size_t)b * Md.ncell + c;
+      if (kind == 0) {
+        const size_t src = (size_t)sb * Ms.ncell + c;
+#pragma unroll
+        for (int v = 0; v < NV; v++) Ud[(size_t)v * vsd + dst] = Us[(size_t)v * vss + src];
+        continue;
+      }
+      const int ci[3] = {c % nx[0], (c / nx[0]) % nx[1], c / (nx[0] * nx[1])};
+      double out[NV];
+      if (kind == 1) {
+        // child cell ci lies in parent cell pc of the split block sb
+        int pc[3];
+#pragma unroll
+        for (int d = 0; d < 3; d++) pc[d] = d < nd ? (idx[d] & 1) * h[d] + ci[d] / 2 : 0;
+        T ub[NV];
+        read_cell(Ms, Us, vss, sb, (pc[2] * nx[1] + pc[1]) * nx[0] + pc[0], ub);
+        double base[NV];
+#pragma unroll
+        for (int v = 0; v < NV; v++) out[v] = base[v] = (double)ub[v];
+        for (int d = 0; d < nd; d++) {
+          int p[3] = {pc[0], pc[1], pc[2]}, m[3] = {pc[0], pc[1], pc[2]};
+          p[d] += 1;
+          m[d] -= 1;
+          T up[NV], um[NV];
+          block_cell_value(Ms, Us, vss, sb, p[0], p[1], p[2], up);
+          block_cell_value(Ms, Us, vss, sb, m[0], m[1], m[2], um);
+          const double w = (ci[d] & 1) ? 0.25 : -0.25;
+#pragma unroll
+          for (int v = 0; v < NV; v++) {
+            const double a = base[v] - (double)um[v], bb = (double)up[v] - base[v];
+            const double sl = a * bb > 0.0 ? (a > 0.0 ? fmin(a, bb) : fmax(a, bb)) : 0.0;
+            out[v] = out[v] + w * sl;
+          }
+        }
+      } else {
+        // merged parent: its cell ci covers 2^d cells of one child
+        int o[3], f0[3];
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+          o[d] = d < nd ? ci[d] / h[d] : 0;
+          f0[d] = d < nd ? 2 * ci[d] - o[d] * nx[d] : 0;
+        }
+        const int cb = t[2 + (o[2] * 2 + o[1]) * 2 + o[0]];
+#pragma unroll
+        for (int v = 0; v < NV; v++) out[v] = 0.0;
+        for (int fz = 0; fz < (nd > 2 ? 2 : 1); fz++)
+          for (int fy = 0; fy < (nd > 1 ? 2 : 1); fy++)
+            for (int fx = 0; fx < 2; fx++) {
+              const size_t src = (size_t)cb * Ms.ncell +
+                                 ((size_t)(f0[2] + fz) * nx[1] + (f0[1] + fy)) * nx[0] + f0[0] + fx;
+#pragma unroll
+              for (int v = 0; v < NV; v++) out[v] += (double)Us[(size_t)v * vss + src];
+            }
+        const double inv = nd == 3 ? 0.125 : (nd == 2 ? 0.25 : 0.5);  // exact
+#pragma unroll
+        for (int v = 0; v < NV; v++) out[v] *= inv;
+      }
+#pragma unroll
+      for (int v = 0; v < NV; v++) Ud[(size_t)v * vsd + dst] = (T)out[v];
+    }
+  }
+}
+
+int grid_for(int nblocks) { return nblocks < 152 * 8 ? nblocks : 152 * 8; }
+
+using Key = std::array<int, 5>;  // instance, level, i, j, k
+
+struct Planner {
+  int nd;
+  bool periodic[3];
+  std::vector<std::array<int, 3>> base;
+  int nblk(int q, int L, int d) const { return d < nd ? base[q][d] << L : 1; }
+
+  // level-L positions around (i, j, k) (faces, edges, corners), wrapped on
+  // periodic dimensions, dropped outside the others
+  std::vector<std::array<int, 3>> neighbours(int q, int L, int i, int j, int k) const {
+    std::vector<std::array<int, 3>> out;
+    const int lo[3] = {-1, nd > 1 ? -1 : 0, nd > 2 ? -1 : 0};
+    for (int dz = lo[2]; dz <= -lo[2]; dz++)
+      for (int dy = lo[1]; dy <= -lo[1]; dy++)
+        for (int dx = -1; dx <= 1; dx++) {
+          if (!dx && !dy && !dz) continue;
+          std::array<int, 3> p{i + dx, j + dy, k + dz};
+          bool ok = true;
+          for (int d = 0; d < nd; d++) {
+            const int n = nblk(q, L, d);
+            if (p[d] < 0 || p[d] >= n) {
+              if (periodic[d]) p[d] = ((p[d] % n) + n) % n;
+              else ok = false;
+            }
+          }
+          if (ok) out.push_back(p);
+        }
+    return out;
+  }
+
+  // level of the leaf of s covering level-L position p (walking up), -1 when
+  // finer leaves cover it
+  static int covering(const std::set<Key>& s, int q, int L, std::array<int, 3> p) {
+    for (int LL = L; LL >= 0; LL--) {
+      if (s.count(Key{q, LL, p[0], p[1], p[2]})) return LL;
+      for (int d = 0; d < 3; d++) p[d] >>= 1;
+    }
+    return -1;
+  }
+
+  std::vector<Key> children(const Key& k) const {
+    std::vector<Key> out;
+    for (int oz = 0; oz < (nd > 2 ? 2 : 1); oz++)
+      for (int oy = 0; oy < (nd > 1 ? 2 : 1); oy++)
+        for (int ox = 0; ox < 2; ox++)
+          out.push_back(Key{k[0], k[1] + 1, 2 * k[2] + ox, nd > 1 ? 2 * k[3] + oy : 0,
+                            nd > 2 ? 2 * k[4] + oz : 0});
+    return out;
+  }
+
+  // deepest leaf level of s around the parent position (q, L, i, j, k)
+  int finest_near(const std::set<Key>& s, int q, int L, int i, int j, int k) const {
+    int best = L;
+    for (const auto& p : neighbours(q, L, i, j, k)) {
+      const int lev = covering(s, q, L, p);
+      if (lev >= 0) {
+        best = std::max(best, lev);
+        continue;
+      }
+      for (const Key& c : children(Key{q, L, p[0], p[1], p[2]})) {
+        const int l2 = covering(s, q, L + 1, {c[2], c[3], c[4]});
+        best = std::max(best, l2 < 0 ? L + 2 : l2);
+      }
+    }
+    return best;
+  }
+};
+
+}  // namespace
+
+}  // namespace amrvac
+
+using namespace amrvac;
+
+extern "C" amrvac_status amrvac_regrid_plan(const amrvac_config* cfg, int32_t ninst,
+                                            const amrvac_instance_desc* inst, int32_t nblocks,
+                                            const int32_t* block_meta, const int8_t* flags,
+                                            int32_t capacity, int32_t* new_meta,
+                                            int32_t* new_nblocks) {
+  size_t bytes = 0;
+  if (!flags || !new_nblocks || capacity < 0 || (capacity > 0 && !new_meta))
+    return AMRVAC_E_INVALID;
+  const amrvac_status st = amrvac_workspace_bytes(cfg, ninst, inst, nblocks, block_meta, &bytes);
+  if (st != AMRVAC_OK) return st;
+  Planner P;
+  P.nd = cfg->ndim;
+  for (int d = 0; d < 3; d++) P.periodic[d] = cfg->bc[d][0] == AMRVAC_BC_PERIODIC;
+  for (int q = 0; q < ninst; q++)
+    P.base.push_back({inst[q].base_blocks[0], inst[q].base_blocks[1], inst[q].base_blocks[2]});
+  std::set<Key> cur, refine, want;
+  for (int b = 0; b < nblocks; b++) {
+    const int32_t* r = block_meta + 5 * b;
+    const Key k{r[0], r[1], r[2], P.nd > 1 ? r[3] : 0, P.nd > 2 ? r[4] : 0};
+    cur.insert(k);
+    if (flags[b] < -1 || flags[b] > 1) return AMRVAC_E_INVALID;
+    if (flags[b] == 1) {
+      if (r[1] + 1 >= AMRVAC_MAX_LEVELS) return AMRVAC_E_INVALID;
+      refine.insert(k);
+    }
+    if (flags[b] == -1 && r[1] > 0) want.insert(k);
+  }
+  // 2:1 closure of the splits: a split level-L leaf forces every coarser
+  // leaf around it to split too
+  std::vector<Key> todo(refine.begin(), refine.end());
+  while (!todo.empty()) {
+    const Key k = todo.back();
+    todo.pop_back();
+    for (const auto& p : P.neighbours(k[0], k[1], k[2], k[3], k[4])) {
+      const int lev = Planner::covering(cur, k[0], k[1], p);
+      if (lev < 0 || lev >= k[1]) continue;
+      std::array<int, 3> pp = p;
+      for (int s = 0; s < k[1] - lev; s++)
+        for (int d = 0; d < 3; d++) pp[d] >>= 1;
+      const Key c{k[0], lev, pp[0], pp[1], pp[2]};
+      if (refine.insert(c).second) todo.push_back(c);
+    }
+  }
+  std::set<Key> next;
+  for (const Key& k : cur) {
+    if (refine.count(k)) {
+      for (const Key& c : P.children(k)) next.insert(c);
+    } else {
+      next.insert(k);
+    }
+  }
+  // merges: complete families asking for it, in increasing parent order
+  std::map<Key, std::vector<Key>> parents;
+  for (const Key& k : want) {
+    if (refine.count(k)) continue;
+    parents[Key{k[0], k[1] - 1, k[2] >> 1, k[3] >> 1, k[4] >> 1}].push_back(k);
+  }
+  const size_t nchild = (size_t)1 << P.nd;
+  for (const auto& it : parents) {
+    const Key& par = it.first;
+    const std::vector<Key>& kids = it.second;
+    if (kids.size() != nchild) continue;
+    bool all = true;
+    for (const Key& c : kids) all = all && next.count(c);
+    if (!all) continue;
+    std::set<Key> trial = next;
+    for (const Key& c : kids) trial.erase(c);
+    trial.insert(par);
+    if (P.finest_near(trial, par[0], par[1], par[2], par[3], par[4]) <= par[1] + 1)
+      next.swap(trial);
+  }
+  *new_nblocks = (int32_t)next.size();
+  if ((size_t)capacity < next.size()) return AMRVAC_E_INVALID;
+  size_t b = 0;
+  for (const Key& k : next) {
+    for (int e = 0; e < 5; e++) new_meta[5 * b + e] = k[e];
+    b++;
+  }
+  return AMRVAC_OK;
+}
+
+extern "C" amrvac_status amrvac_regrid_estimate(amrvac_state* s, int32_t buffer,
+                                                double refine_threshold, double derefine_ratio,
+                                                int32_t max_level, double* h_est,
+                                                int8_t* h_flags) {
+  if (!s || buffer < 0 || buffer > 2 || !(refine_threshold >= 0.0) || !(derefine_ratio >= 0.0) ||
+      max_level < 0 || max_level >= AMRVAC_MAX_LEVELS)
+    return AMRVAC_E_INVALID;
+  const double dthr = derefine_ratio * refine_threshold;
+  const int g = grid_for(s->nblocks);
+  if (s->cfg.precision == AMRVAC_FP64)
+    k_regrid_estimate<double><<<g, 256, 0, s->stream>>>(s->mesh, (const double*)s->U[buffer],
+                                                         refine_threshold, dthr, max_level,
+                                                         s->d_est, s->d_eflags);
+  else
+    k_regrid_estimate<float><<<g, 256, 0, s->stream>>>(s->mesh, (const float*)s->U[buffer],
+                                                        refine_threshold, dthr, max_level,
+                                                        s->d_est, s->d_eflags);
+  if (cudaPeekAtLastError() != cudaSuccess) return AMRVAC_E_CUDA;
+  s->launches++;
+  if (h_est && cudaMemcpyAsync(h_est, s->d_est, sizeof(double) * s->nblocks,
+                               cudaMemcpyDeviceToHost, s->stream) != cudaSuccess)
+    return AMRVAC_E_CUDA;
+  if (h_flags && cudaMemcpyAsync(h_flags, s->d_eflags, (size_t)s->nblocks,
+                                 cudaMemcpyDeviceToHost, s->stream) != cudaSuccess)
+    return AMRVAC_E_CUDA;
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess) return AMRVAC_E_CUDA;
+  int err = 0;  // a ghost lookup that found no leaf latches the device error
+  if (cudaMemcpy(&err, s->mesh.err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return AMRVAC_E_CUDA;
+  return err ? (amrvac_status)err : AMRVAC_OK;
+}
+
+extern "C" amrvac_status amrvac_regrid_transfer(amrvac_state* src, int32_t src_buffer,
+                                                amrvac_state* dst, int32_t dst_buffer) {
+  if (!src || !dst || src_buffer < 0 || src_buffer > 2 || dst_buffer < 0 || dst_buffer > 2)
+    return AMRVAC_E_INVALID;
+  const amrvac_config &a = src->cfg, &c = dst->cfg;
+  if (a.ndim != c.ndim || a.precision != c.precision || src->ninst != dst->ninst)
+    return AMRVAC_E_INVALID;
+  const int nd = a.ndim;
+  for (int d = 0; d < nd; d++)
+    if (a.block_nx[d] != c.block_nx[d] || (c.block_nx[d] & 1) || a.bc[d][0] != c.bc[d][0] ||
+        a.bc[d][1] != c.bc[d][1])
+      return AMRVAC_E_INVALID;
+  for (int q = 0; q < src->ninst; q++)
+    for (int d = 0; d < nd; d++)
+      if (src->inst[q].base_blocks[d] != dst->inst[q].base_blocks[d]) return AMRVAC_E_INVALID;
+  std::map<Key, int> old;
+  for (int b = 0; b < src->nblocks; b++) {
+    const int32_t* r = &src->meta[5 * b];
+    old[Key{r[0], r[1], r[2], nd > 1 ? r[3] : 0, nd > 2 ? r[4] : 0}] = b;
+  }
+  std::vector<int> tab((size_t)dst->nblocks * RTAB_N, -1);
+  for (int b = 0; b < dst->nblocks; b++) {
+    const int32_t* r = &dst->meta[5 * b];
+    const Key k{r[0], r[1], r[2], nd > 1 ? r[3] : 0, nd > 2 ? r[4] : 0};
+    int* t = &tab[(size_t)b * RTAB_N];
+    auto it = old.find(k);
+    if (it != old.end()) {
+      t[0] = 0;
+      t[1] = it->second;
+      continue;
+    }
+    if (k[1] > 0) {
+      it = old.find(Key{k[0], k[1] - 1, k[2] >> 1, k[3] >> 1, k[4] >> 1});
+      if (it != old.end()) {
+        t[0] = 1;
+        t[1] = it->second;
+        continue;
+      }
+    }
+    t[0] = 2;
+    int n = 0;
+    for (int oz = 0; oz < (nd > 2 ? 2 : 1); oz++)
+      for (int oy = 0; oy < (nd > 1 ? 2 : 1); oy++)
+        for (int ox = 0; ox < 2; ox++) {
+          it = old.find(Key{k[0], k[1] + 1, 2 * k[2] + ox, nd > 1 ? 2 * k[3] + oy : 0,
+                            nd > 2 ? 2 * k[4] + oz : 0});
+          if (it == old.end()) return AMRVAC_E_INVALID;
+          t[2 + (oz * 2 + oy) * 2 + ox] = it->second;
+          n++;
+        }
+    t[1] = t[2];
+    (void)n;
+  }
+  // the transfer runs on dst's stream after the work already on src's
+  cudaEvent_t ev;
+  if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return AMRVAC_E_CUDA;
+  cudaError_t e = cudaEventRecord(ev, src->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(dst->stream, ev, 0);
+  cudaEventDestroy(ev);
+  if (e != cudaSuccess) return AMRVAC_E_CUDA;
+  if (cudaMemcpyAsync(dst->d_rtab, tab.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice,
+                      dst->stream) != cudaSuccess)
+    return AMRVAC_E_CUDA;
+  const int g = grid_for(dst->nblocks);
+  if (c.precision == AMRVAC_FP64)
+    k_regrid_transfer<double><<<g, 256, 0, dst->stream>>>(
+        src->mesh, (const double*)src->U[src_buffer], dst->mesh, (double*)dst->U[dst_buffer],
+        dst->d_rtab);
+  else
+    k_regrid_transfer<float><<<g, 256, 0, dst->stream>>>(
+        src->mesh, (const float*)src->U[src_buffer], dst->mesh, (float*)dst->U[dst_buffer],
+        dst->d_rtab);
+  if (cudaPeekAtLastError() != cudaSuccess) return AMRVAC_E_CUDA;
+  dst->launches++;
+  // the host table must outlive the asynchronous upload
+  if (cudaStreamSynchronize(dst->stream) != cudaSuccess) return AMRVAC_E_CUDA;
+  return AMRVAC_OK;
+}

@@ -9,6 +9,13 @@
 
 #include "common.cuh"
 
+namespace amrvac {
+// transfer table of a regrid, per destination block: kind (0 copy,
+// 1 prolongation from a parent, 2 restriction of children), source block, and
+// the 2^ndim source children of a merged parent in (z, y, x) order
+constexpr int RTAB_N = 10;
+}  // namespace amrvac
+
 struct amrvac_state {
   amrvac_config cfg;
   int ninst = 0, nblocks = 0, ncell = 0;
@@ -51,6 +58,10 @@ struct amrvac_state {
   int ngroups = 1;
   int grp_flux[amrvac::MAXLEV] = {0}, grp_lim[amrvac::MAXLEV] = {0};
   int grp_off[amrvac::MAXLEV] = {0}, grp_cnt[amrvac::MAXLEV] = {0};
+  // regridding: per-block estimator and flag, transfer table [nblocks][RTAB_N]
+  double* d_est = nullptr;
+  signed char* d_eflags = nullptr;
+  int* d_rtab = nullptr;
   // host copies
   std::vector<int32_t> meta;
   std::vector<amrvac_instance_desc> inst;
