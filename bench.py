@@ -278,6 +278,72 @@ def time_steps(torch, S, k):
     return e0.elapsed_time(e1) / k
 
 
+def bench_regrid(torch, amrvac, W, S, dev, args, hbm, thr=0.05, ratio=0.2):
+    """Times one regrid of S's current state (register 0), refining on density
+    and pressure (weights 1/2 each).  Algorithmic bytes: the estimator reads
+    every conserved variable of a cell once (36 B a cell); the transfer reads
+    each source cell it needs once (a split block's cells once for all its
+    children) and writes every destination cell (36 B a cell each way)."""
+    maxlev = int(W.block_meta[:, 1].max())
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    est_ms = []
+    for _ in range(3):
+        e0, e1 = ev(), ev()
+        e0.record(S.stream)
+        _, flags = S.regrid_estimate(thr, ratio, max_level=maxlev,
+                                     weights=[0.5, 0, 0, 0, 0.5, 0, 0, 0, 0])
+        e1.record(S.stream)
+        S.stream.synchronize()
+        est_ms.append(e0.elapsed_time(e1))
+    t0 = time.perf_counter()
+    new = amrvac.regrid_plan(W.cfg, W.instances, S.meta, flags)
+    plan_ms = (time.perf_counter() - t0) * 1e3
+    t0 = time.perf_counter()
+    D = amrvac.State(W.cfg, W.instances, new, device=dev, kernel=args.kernel,
+                     pressure=args.pressure, stream=S.stream)
+    torch.cuda.synchronize(dev)
+    create_ms = (time.perf_counter() - t0) * 1e3
+    tr_ms = []
+    for _ in range(3):
+        e0, e1 = ev(), ev()
+        e0.record(S.stream)
+        S.regrid_transfer(D, 0, 0)
+        e1.record(S.stream)
+        S.stream.synchronize()
+        tr_ms.append(e0.elapsed_time(e1))
+    s0 = S.diag()["sums"][0]
+    s1 = D.diag()["sums"][0]
+    old = {tuple(r) for r in S.meta.tolist()}
+    kept = sum(1 for r in new.tolist() if tuple(r) in old)
+    nd = W.cfg.ndim
+    parents = {(r[0], r[1] - 1, r[2] >> 1, r[3] >> 1, r[4] >> 1) for r in new.tolist()
+               if tuple(r) not in old}
+    n_split = sum(1 for p in parents if p in old)
+    n_merged = sum(1 for r in new.tolist()
+                   if tuple(r) not in old and
+                   (r[0], r[1] - 1, r[2] >> 1, r[3] >> 1, r[4] >> 1) not in old)
+    ncell = W.ncell
+    src_cells = (kept + n_split + n_merged * (1 << nd)) * ncell
+    dst_cells = len(new) * ncell
+    est_s = float(np.median(est_ms)) / 1e3
+    tr_s = float(np.median(tr_ms)) / 1e3
+    est_bytes = 36 * S.nblocks * ncell
+    tr_bytes = 36 * (src_cells + dst_cells)
+    scale = np.abs(s0).max()
+    D.close()
+    return {"refine_threshold": thr, "derefine_ratio": ratio, "max_level": maxlev,
+            "weights": "rho 0.5, p 0.5",
+            "blocks_before": int(S.nblocks), "blocks_after": int(len(new)),
+            "split": int(n_split), "merged_parents": int(n_merged), "kept": int(kept),
+            "estimate_ms": est_s * 1e3, "plan_ms": plan_ms, "state_create_ms": create_ms,
+            "transfer_ms": tr_s * 1e3,
+            "estimate_gbs": est_bytes / est_s / 1e9, "transfer_gbs": tr_bytes / tr_s / 1e9,
+            "transfer_frac": tr_bytes / tr_s / 1e9 / hbm,
+            "estimate_alg_bytes": est_bytes, "transfer_alg_bytes": tr_bytes,
+            "max_rel_change_of_integrals": float(np.abs(s1 - s0).max() / max(scale, 1e-300)),
+            "cells_per_s": dst_cells / (est_s + tr_s)}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -364,8 +430,9 @@ def main():
     achieved = sum(alg_bytes) / (sum(stage_ms) / 1e3) / 1e9
     fused = args.kernel != "plain" and (W.cfg.block_nx[0] == 16)
     digest = libbuild._digest()[:16]
+    kdigest = libbuild.kernel_digest()[:16]
     kv = counters_from_profile(args.workload + (str(args.size) if args.size else ""),
-                               digest) if fused and W.cfg.flux == "hlld" else {}
+                               kdigest) if fused and W.cfg.flux == "hlld" else {}
     tr = float(kv["dram_bytes_per_cell_step"]) if "dram_bytes_per_cell_step" in kv else None
     # issue ceiling beside the HBM bound: one warp instruction per cycle per
     # SM sub-partition (4 per SM) at the SM clock sampled during the timed steps
@@ -426,6 +493,12 @@ def main():
                               "alg_bytes_per_cell_step": nbytes,
                               "frac": nbytes * cells / (msv / 1e3) / 1e9 / hbm}
             Sv.close()
+
+    # dynamic regridding of the evolved state: estimator + flags (device),
+    # plan (host), new state tables (host + upload), transfer (device)
+    regrid = None
+    if not args.no_variants and W.cfg.ndim == 3 and len(np.unique(W.block_meta[:, 1])) > 1:
+        regrid = bench_regrid(torch, amrvac, W, S, dev, args, hbm)
 
     # C5 batching: the same instances advanced one at a time
     one_at_a_time = None
@@ -525,10 +598,12 @@ def main():
                                precision="fp32 bulk; pressure recovery in %s; fp64 dt, c_h "
                                          "and conservation sums" %
                                          ("float-float" if args.pressure == "ff" else "fp64"),
-                               kernel=args.kernel, build=digest, tuning=tuning,
+                               kernel=args.kernel, build=digest, kernel_build=kdigest,
+                               tuning=tuning,
                                parallelism="replicas" if ws > 1 else "1 GPU"),
                 "clocks": clocks, "gpu_launches": launches, "roofline": roofline,
-                "e2e": e2e, "variants": variants or None, "one_at_a_time": one_at_a_time,
+                "e2e": e2e, "variants": variants or None, "regrid": regrid,
+                "one_at_a_time": one_at_a_time,
                 "fp64_plain": fp64, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     S.close()

@@ -362,22 +362,26 @@ amrvac_status amrvac_fix_small_values(amrvac_state* s, int32_t buffer, int64_t* 
 
 /*
  * Dynamic regridding (Sect. 1 and 3: blocks are refined and coarsened
- * automatically where chosen plasma quantities vary).  The paper prints no
- * criterion; the library uses Loehner's normalised second derivative of the
- * density, per cell
- *   E = sqrt( sum_d (r_{+} - 2 r_0 + r_{-})^2 /
- *             sum_d (|r_{+} - r_0| + |r_0 - r_{-}|
- *                    + 0.01 (|r_{+}| + 2 |r_0| + |r_{-}|))^2 )
- * with r_{+-} the face neighbours along d (ghost values of the level across
- * block faces, as amrvac_fill_ghosts), and a regrid in three calls:
+ * automatically on weighted, user-chosen plasma quantities).  The paper
+ * prints no criterion; the library uses Loehner's normalised second
+ * derivative.  For a quantity q and a cell, with q_{+-} its face neighbours
+ * along d (ghost values of the level across block faces, as
+ * amrvac_fill_ghosts):
+ *   E(q) = sqrt( sum_d (q_{+} - 2 q_0 + q_{-})^2 /
+ *                sum_d (|q_{+} - q_0| + |q_0 - q_{-}|
+ *                       + 0.01 (|q_{+}| + 2 |q_0| + |q_{-}|))^2 )
+ * (0 where the denominator vanishes), and the cell's estimate is
+ * sum_v weights[v] E(w_v) over the primitive variables w = (rho, v_x, v_y,
+ * v_z, p, B_x, B_y, B_z, psi).  A regrid takes three calls:
  *
- * amrvac_regrid_estimate: per block of register `buffer`, the maximum of E
- *   over its cells into h_est[nblocks] (double, may be NULL) and the flag
- *   h_flags[nblocks] (int8, may be NULL): 1 (refine) when E > refine_threshold
- *   and the block's level < max_level, -1 (coarsen) when
- *   E < derefine_ratio * refine_threshold and the level > 0, else 0.  The
- *   estimator is evaluated in double from the stored values.  Synchronises.
- *   AMRVAC_E_INVALID for a bad buffer, threshold or max_level (0..15).
+ * amrvac_regrid_estimate: per block of register `buffer`, the maximum of the
+ *   estimate over its cells into h_est[nblocks] (double, may be NULL) and the
+ *   flag h_flags[nblocks] (int8, may be NULL): 1 (refine) when it exceeds
+ *   refine_threshold and the block's level < max_level, -1 (coarsen) when it
+ *   is below derefine_ratio * refine_threshold and the level > 0, else 0.
+ *   weights: host double[9], >= 0, not all 0; NULL = the density alone.
+ *   Evaluated in double from the stored values.  Synchronises.
+ *   AMRVAC_E_INVALID for a bad buffer, weight, threshold or max_level (0..15).
  *
  * amrvac_regrid_plan (host only, no device work): the block list after one
  *   regrid of the mesh (cfg, inst, block_meta as amrvac_workspace_bytes) with
@@ -403,9 +407,9 @@ amrvac_status amrvac_fix_small_values(amrvac_state* s, int32_t buffer, int64_t* 
  *   after the work enqueued so far on src's stream.  AMRVAC_E_INVALID when the
  *   states do not match or dst's blocks are not one regrid away from src's.
  */
-amrvac_status amrvac_regrid_estimate(amrvac_state* s, int32_t buffer, double refine_threshold,
-                                     double derefine_ratio, int32_t max_level, double* h_est,
-                                     int8_t* h_flags);
+amrvac_status amrvac_regrid_estimate(amrvac_state* s, int32_t buffer, const double* weights,
+                                     double refine_threshold, double derefine_ratio,
+                                     int32_t max_level, double* h_est, int8_t* h_flags);
 amrvac_status amrvac_regrid_plan(const amrvac_config* cfg, int32_t ninst,
                                  const amrvac_instance_desc* inst, int32_t nblocks,
                                  const int32_t* block_meta, const int8_t* flags,

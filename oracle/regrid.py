@@ -7,12 +7,14 @@ blocks and cells, no code shared with the GPU library.
 The paper names the capability but no criterion or operator, so this follows
 the readings of the library:
   * estimator (Loehner 1987, the normalised second derivative, per direction):
-      E_i = sqrt( sum_d (w_{i+1} - 2 w_i + w_{i-1})^2 /
-                  sum_d (|w_{i+1} - w_i| + |w_i - w_{i-1}|
-                         + eps (|w_{i+1}| + 2 |w_i| + |w_{i-1}|))^2 )
-    on the density, eps = 0.01, neighbours across block faces from the
-    conserved ghost values of the level (same operators as the update);
-    a block's estimator is the maximum over its cells;
+      E_i(q) = sqrt( sum_d (q_{i+1} - 2 q_i + q_{i-1})^2 /
+                     sum_d (|q_{i+1} - q_i| + |q_i - q_{i-1}|
+                            + eps (|q_{i+1}| + 2 |q_i| + |q_{i-1}|))^2 )
+    with eps = 0.01, summed over the primitive quantities q the caller
+    weights (the paper's weighted, user-chosen quantities; default the
+    density alone), neighbours across block faces from the conserved ghost
+    values of the level (same operators as the update); a block's estimator
+    is the maximum over its cells;
   * flags: refine when E > refine_threshold (and the level is below
     max_level), coarsen when E < derefine_ratio * refine_threshold (level > 0);
   * plan: refined blocks, then every block closer than one block (faces, edges,
@@ -46,29 +48,62 @@ def _padded_block(m, Up, b, cfg):
     return Up[:, b, :].reshape(9, P[2], P[1], P[0]), g
 
 
-def estimator(orc_mesh, U, cfg):
-    """Per-block maximum of the Loehner estimator on the density."""
+def _primitive(Pb, gamma):
+    """Primitive (rho, v, p, B, psi) of conserved cells (ideal MHD, magnetic
+    pressure B^2/2), numpy over whole arrays."""
+    rho = Pb[0]
+    with np.errstate(all="ignore"):  # unused zero edge/corner ghosts
+        v = Pb[1:4] / rho
+        ke = 0.5 * (Pb[1] * Pb[1] + Pb[2] * Pb[2] + Pb[3] * Pb[3]) / rho
+    me = 0.5 * (Pb[5] * Pb[5] + Pb[6] * Pb[6] + Pb[7] * Pb[7])
+    p = (gamma - 1.0) * (Pb[4] - ke - me)
+    return np.concatenate([rho[None], v, p[None], Pb[5:9]])
+
+
+def estimator(orc_mesh, U, cfg, weights=None):
+    """Per-block maximum over cells of the weighted sum of Loehner estimators
+    of the primitive variables (weights[9] over rho, v_x, v_y, v_z, p, B_x, B_y,
+    B_z, psi; default the density alone).  A variable whose denominator
+    vanishes (flat and zero) contributes 0."""
+    w = np.zeros(9)
+    if weights is None:
+        w[0] = 1.0
+    else:
+        w[:] = weights
     Up = orc_mesh.fill_ghosts(U)
     nb = U.shape[1]
     nx = _nx(cfg)
     out = np.zeros(nb)
     for b in range(nb):
         Pb, g = _padded_block(orc_mesh, Up, b, cfg)
-        rho = Pb[0]
-        num = np.zeros((nx[2], nx[1], nx[0]))
-        den = np.zeros_like(num)
-        for d in range(cfg.ndim):
-            sl = [slice(g[2], g[2] + nx[2]), slice(g[1], g[1] + nx[1]), slice(g[0], g[0] + nx[0])]
-            ax = 2 - d
-            c = rho[tuple(sl)]
-            slp = list(sl)
-            slp[ax] = slice(sl[ax].start + 1, sl[ax].stop + 1)
-            slm = list(sl)
-            slm[ax] = slice(sl[ax].start - 1, sl[ax].stop - 1)
-            p, mm = rho[tuple(slp)], rho[tuple(slm)]
-            num += (p - 2 * c + mm) ** 2
-            den += (np.abs(p - c) + np.abs(c - mm) + EPS * (np.abs(p) + 2 * np.abs(c) + np.abs(mm))) ** 2
-        out[b] = np.sqrt((num / den).max())
+        if np.any(w[1:] != 0):
+            Wb = _primitive(Pb, orc_mesh.instances[int(orc_mesh.meta[b][0])].gamma)
+        else:
+            Wb = Pb  # density only: the conserved density is the primitive one
+        E = np.zeros((nx[2], nx[1], nx[0]))
+        for var in range(9):
+            if w[var] == 0:
+                continue
+            q = Wb[var]
+            num = np.zeros((nx[2], nx[1], nx[0]))
+            den = np.zeros_like(num)
+            for d in range(cfg.ndim):
+                sl = [slice(g[2], g[2] + nx[2]), slice(g[1], g[1] + nx[1]),
+                      slice(g[0], g[0] + nx[0])]
+                ax = 2 - d
+                c = q[tuple(sl)]
+                slp = list(sl)
+                slp[ax] = slice(sl[ax].start + 1, sl[ax].stop + 1)
+                slm = list(sl)
+                slm[ax] = slice(sl[ax].start - 1, sl[ax].stop - 1)
+                p, mm = q[tuple(slp)], q[tuple(slm)]
+                num += (p - 2 * c + mm) ** 2
+                den += (np.abs(p - c) + np.abs(c - mm) +
+                        EPS * (np.abs(p) + 2 * np.abs(c) + np.abs(mm))) ** 2
+            with np.errstate(all="ignore"):
+                r = np.where(den > 0, num / den, 0.0)
+            E += w[var] * np.sqrt(r)
+        out[b] = E.max()
     return out
 
 

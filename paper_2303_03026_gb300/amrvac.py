@@ -108,7 +108,7 @@ def load(path: str = LIB_PATH):
     L.amrvac_state_save.argtypes = [vp, C.c_char_p]
     L.amrvac_state_load.argtypes = [vp, C.c_char_p]
     L.amrvac_fix_small_values.argtypes = [vp, i32, vp]
-    L.amrvac_regrid_estimate.argtypes = [vp, i32, dbl, dbl, i32, vp, vp]
+    L.amrvac_regrid_estimate.argtypes = [vp, i32, vp, dbl, dbl, i32, vp, vp]
     L.amrvac_regrid_plan.argtypes = [C.POINTER(Config), i32, C.POINTER(InstanceDesc), i32, vp,
                                      vp, i32, vp, vp]
     L.amrvac_regrid_transfer.argtypes = [vp, i32, vp, i32]
@@ -350,12 +350,20 @@ class State:
         return n.value
 
     # -------------------------------------------------------- regridding
-    def regrid_estimate(self, refine_threshold, derefine_ratio=0.125, max_level=15, buffer=0):
+    def regrid_estimate(self, refine_threshold, derefine_ratio=0.125, max_level=15, buffer=0,
+                        weights=None):
         """Per-block estimator and flags of register ``buffer`` (numpy float64
-        [nblocks], int8 [nblocks]); see amrvac_regrid_estimate."""
+        [nblocks], int8 [nblocks]); ``weights``: 9 weights of the primitive
+        variables (rho, v, p, B, psi), default the density alone.  See
+        amrvac_regrid_estimate."""
         est = np.zeros(self.nblocks, np.float64)
         flags = np.zeros(self.nblocks, np.int8)
-        _check(load().amrvac_regrid_estimate(self._h, int(buffer), float(refine_threshold),
+        wp = None
+        if weights is not None:
+            wv = np.ascontiguousarray(weights, np.float64)
+            assert wv.shape == (9,)
+            wp = wv.ctypes.data
+        _check(load().amrvac_regrid_estimate(self._h, int(buffer), wp, float(refine_threshold),
                                              float(derefine_ratio), int(max_level),
                                              est.ctypes.data, flags.ctypes.data),
                "amrvac_regrid_estimate")
@@ -368,11 +376,12 @@ class State:
                "amrvac_regrid_transfer")
 
     def regrid(self, refine_threshold, derefine_ratio=0.125, max_level=15, buffer=0,
-               kernel="auto", pressure="fp64"):
+               weights=None, kernel="auto", pressure="fp64"):
         """One regrid of register ``buffer``: estimator, plan and transfer into a
         new State (returned; this one is left as it is).  Each instance's clock
         continues from this state's time."""
-        _, flags = self.regrid_estimate(refine_threshold, derefine_ratio, max_level, buffer)
+        _, flags = self.regrid_estimate(refine_threshold, derefine_ratio, max_level, buffer,
+                                        weights)
         meta = regrid_plan(self.cfg, self.instances, self.meta, flags)
         d = self.diag()
         insts = []

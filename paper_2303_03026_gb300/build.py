@@ -45,6 +45,25 @@ def _digest() -> str:
     return h.hexdigest()
 
 
+# the translation unit of the fused stage kernels and everything it includes
+FUSED_KERNEL_FILES = ["fused_inst.cu", "fused.cuh", "fused2d.cuh", "ghost.cuh", "physics.cuh",
+                      "physics_f2.cuh", "reduce.cuh", "state.hpp", "common.cuh"]
+
+
+def kernel_digest() -> str:
+    """Fingerprint of the fused stage kernels alone (their sources, the public
+    header, flags and host machine): hardware counters taken on one build stay
+    valid for another with the same fingerprint."""
+    h = hashlib.sha256()
+    for name in FUSED_KERNEL_FILES:
+        with open(os.path.join(CSRC, name), "rb") as f:
+            h.update(name.encode() + f.read())
+    with open(os.path.join(ROOT, "include", "amrvac.h"), "rb") as f:
+        h.update(f.read())
+    h.update(" ".join(ARCH + NVCC_FLAGS + [os.uname().machine]).encode())
+    return h.hexdigest()
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
     stamp = os.path.join(OUT_DIR, "build.stamp")

@@ -1,12 +1,11 @@
 // Dynamic regridding of the block-AMR mesh (Sect. 1 and 3: automatic
 // refinement and coarsening where chosen quantities vary).
 //
-//   k_regrid_estimate: per block, the maximum over its cells of Loehner's
-//       normalised second derivative of the density (face neighbours across
-//       block faces from the ghost operators of the update), and the block's
-//       refine / coarsen flag.  The arithmetic is double with explicit
-//       round-to-nearest operations, so the flags follow the estimator bit
-//       for bit on any state held in double.
+//   k_regrid_estimate: per block, the maximum over its cells of the weighted
+//       sum of Loehner's normalised second derivatives of the chosen primitive
+//       quantities (face neighbours across block faces from the ghost
+//       operators of the update), and the block's refine / coarsen flag.
+//       The arithmetic is double with explicit round-to-nearest operations.
 //   amrvac_regrid_plan (host): the new block list, closed under 2:1 balance.
 //   k_regrid_transfer: fills a state built on the new list from the old one:
 //       copy, prolongation (coarse value plus minmod-limited slopes times
@@ -17,11 +16,13 @@
 
 #include <algorithm>
 #include <array>
+#include <cmath>
 #include <map>
 #include <set>
 #include <vector>
 
 #include "ghost.cuh"
+#include "physics.cuh"
 #include "state.hpp"
 
 namespace amrvac {
@@ -30,59 +31,88 @@ namespace {
 
 constexpr double LOEHNER_EPS = 0.01;  // noise filter of the estimator's denominator
 
-// density of block-local cell (i, j, k) with at most one index outside the
-// block: interior load, else the ghost value of the level
+struct EstWeights {
+  double w[NV];  // weight of each primitive variable (rho, v, p, B, psi)
+  int prim;      // 1 when a variable other than rho is weighted
+};
+
+// the weighted quantities of block-local cell (i, j, k) with at most one
+// index outside the block (ghost values of the level there), in double
 template <class T>
-__device__ __forceinline__ double rho_at(const DevMesh& M, const T* U, size_t vs, int b, int i,
-                                         int j, int k) {
-  if (i >= 0 && i < M.nx[0] && j >= 0 && j < M.nx[1] && k >= 0 && k < M.nx[2])
-    return (double)U[(size_t)b * M.ncell + ((size_t)k * M.nx[1] + j) * M.nx[0] + i];
+__device__ __forceinline__ void est_cell(const DevMesh& M, const T* U, size_t vs, int b, int i,
+                                         int j, int k, const EstWeights& ew, double g,
+                                         double* q) {
+  const bool inside = i >= 0 && i < M.nx[0] && j >= 0 && j < M.nx[1] && k >= 0 && k < M.nx[2];
+  if (!ew.prim && inside) {
+    q[0] = (double)U[(size_t)b * M.ncell + ((size_t)k * M.nx[1] + j) * M.nx[0] + i];
+    return;
+  }
   T u[NV];
   block_cell_value(M, U, vs, b, i, j, k, u);
-  return (double)u[0];
+  double ud[NV];
+#pragma unroll
+  for (int v = 0; v < NV; v++) ud[v] = (double)u[v];
+  if (ew.prim) {
+    cons2prim(g, ud, q);
+  } else {
+    q[0] = ud[0];
+  }
 }
 
 template <class T>
 __global__ void __launch_bounds__(256) k_regrid_estimate(DevMesh M, const T* __restrict__ U,
-                                                         double thr, double dthr, int maxlev,
-                                                         double* est, signed char* flags) {
+                                                         EstWeights ew, double thr, double dthr,
+                                                         int maxlev, double* est,
+                                                         signed char* flags) {
   __shared__ double red[256 / 32];
   const size_t vs = (size_t)M.nblocks * M.ncell;
+  const int nq = ew.prim ? NV : 1;
   for (int b = blockIdx.x; b < M.nblocks; b += gridDim.x) {
-    double rmax = 0.0;
+    const double g = M.gamma[M.blk[b * 5]];
+    double emax = 0.0;
     for (int c = threadIdx.x; c < M.ncell; c += blockDim.x) {
       const int ci[3] = {c % M.nx[0], (c / M.nx[0]) % M.nx[1], c / (M.nx[0] * M.nx[1])};
-      const double r0 = (double)U[(size_t)b * M.ncell + c];
-      double num = 0.0, den = 0.0;
+      double q0[NV], num[NV], den[NV];
+      est_cell(M, U, vs, b, ci[0], ci[1], ci[2], ew, g, q0);
+      for (int v = 0; v < nq; v++) num[v] = den[v] = 0.0;
       for (int d = 0; d < M.ndim; d++) {
         int p[3] = {ci[0], ci[1], ci[2]}, m[3] = {ci[0], ci[1], ci[2]};
         p[d] += 1;
         m[d] -= 1;
-        const double rp = rho_at(M, U, vs, b, p[0], p[1], p[2]);
-        const double rm = rho_at(M, U, vs, b, m[0], m[1], m[2]);
-        const double s2 = __dadd_rn(__dsub_rn(rp, 2.0 * r0), rm);
-        num = __dadd_rn(num, __dmul_rn(s2, s2));
-        const double a = __dadd_rn(fabs(__dsub_rn(rp, r0)), fabs(__dsub_rn(r0, rm)));
-        const double f = __dadd_rn(__dadd_rn(fabs(rp), 2.0 * fabs(r0)), fabs(rm));
-        const double dd = __dadd_rn(a, __dmul_rn(LOEHNER_EPS, f));
-        den = __dadd_rn(den, __dmul_rn(dd, dd));
+        double qp[NV], qm[NV];
+        est_cell(M, U, vs, b, p[0], p[1], p[2], ew, g, qp);
+        est_cell(M, U, vs, b, m[0], m[1], m[2], ew, g, qm);
+        for (int v = 0; v < nq; v++) {
+          if (ew.w[v] == 0.0) continue;
+          const double rp = qp[v], r0 = q0[v], rm = qm[v];
+          const double s2 = __dadd_rn(__dsub_rn(rp, 2.0 * r0), rm);
+          num[v] = __dadd_rn(num[v], __dmul_rn(s2, s2));
+          const double a = __dadd_rn(fabs(__dsub_rn(rp, r0)), fabs(__dsub_rn(r0, rm)));
+          const double f = __dadd_rn(__dadd_rn(fabs(rp), 2.0 * fabs(r0)), fabs(rm));
+          const double dd = __dadd_rn(a, __dmul_rn(LOEHNER_EPS, f));
+          den[v] = __dadd_rn(den[v], __dmul_rn(dd, dd));
+        }
       }
-      const double ratio = num / den;
-      rmax = ratio > rmax ? ratio : rmax;  // a NaN ratio (den 0) never wins
+      double e = 0.0;
+      for (int v = 0; v < nq; v++) {
+        if (ew.w[v] == 0.0) continue;
+        const double r = den[v] > 0.0 ? num[v] / den[v] : 0.0;
+        e = __dadd_rn(e, __dmul_rn(ew.w[v], sqrt(r)));
+      }
+      emax = e > emax ? e : emax;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      const double other = __shfl_xor_sync(0xffffffffu, rmax, o);
-      rmax = other > rmax ? other : rmax;
+      const double other = __shfl_xor_sync(0xffffffffu, emax, o);
+      emax = other > emax ? other : emax;
     }
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = rmax;
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = emax;
     __syncthreads();
     if (threadIdx.x == 0) {
-      for (int w = 1; w < (int)(blockDim.x >> 5); w++) rmax = red[w] > rmax ? red[w] : rmax;
-      const double e = sqrt(rmax);
+      for (int w = 1; w < (int)(blockDim.x >> 5); w++) emax = red[w] > emax ? red[w] : emax;
       const int L = M.blk[b * 5 + 1];
-      est[b] = e;
-      flags[b] = (e > thr && L < maxlev) ? 1 : ((e < dthr && L > 0) ? -1 : 0);
+      est[b] = emax;
+      flags[b] = (emax > thr && L < maxlev) ? 1 : ((emax < dthr && L > 0) ? -1 : 0);
     }
     __syncthreads();  // red is reused by the next block
   }
@@ -306,11 +336,13 @@ extern "C" amrvac_status amrvac_regrid_plan(const amrvac_config* cfg, int32_t ni
     bool all = true;
     for (const Key& c : kids) all = all && next.count(c);
     if (!all) continue;
-    std::set<Key> trial = next;
-    for (const Key& c : kids) trial.erase(c);
-    trial.insert(par);
-    if (P.finest_near(trial, par[0], par[1], par[2], par[3], par[4]) <= par[1] + 1)
-      next.swap(trial);
+    // merge in place; undo it when the parent would touch a leaf two levels finer
+    for (const Key& c : kids) next.erase(c);
+    next.insert(par);
+    if (P.finest_near(next, par[0], par[1], par[2], par[3], par[4]) > par[1] + 1) {
+      next.erase(par);
+      for (const Key& c : kids) next.insert(c);
+    }
   }
   *new_nblocks = (int32_t)next.size();
   if ((size_t)capacity < next.size()) return AMRVAC_E_INVALID;
@@ -323,20 +355,32 @@ extern "C" amrvac_status amrvac_regrid_plan(const amrvac_config* cfg, int32_t ni
 }
 
 extern "C" amrvac_status amrvac_regrid_estimate(amrvac_state* s, int32_t buffer,
-                                                double refine_threshold, double derefine_ratio,
-                                                int32_t max_level, double* h_est,
-                                                int8_t* h_flags) {
+                                                const double* weights, double refine_threshold,
+                                                double derefine_ratio, int32_t max_level,
+                                                double* h_est, int8_t* h_flags) {
   if (!s || buffer < 0 || buffer > 2 || !(refine_threshold >= 0.0) || !(derefine_ratio >= 0.0) ||
       max_level < 0 || max_level >= AMRVAC_MAX_LEVELS)
     return AMRVAC_E_INVALID;
+  EstWeights ew{};
+  ew.w[0] = 1.0;
+  if (weights) {
+    bool any = false;
+    for (int v = 0; v < NV; v++) {
+      if (!(weights[v] >= 0.0) || !std::isfinite(weights[v])) return AMRVAC_E_INVALID;
+      ew.w[v] = weights[v];
+      any = any || weights[v] > 0.0;
+      if (v > 0 && weights[v] > 0.0) ew.prim = 1;
+    }
+    if (!any) return AMRVAC_E_INVALID;
+  }
   const double dthr = derefine_ratio * refine_threshold;
   const int g = grid_for(s->nblocks);
   if (s->cfg.precision == AMRVAC_FP64)
-    k_regrid_estimate<double><<<g, 256, 0, s->stream>>>(s->mesh, (const double*)s->U[buffer],
+    k_regrid_estimate<double><<<g, 256, 0, s->stream>>>(s->mesh, (const double*)s->U[buffer], ew,
                                                          refine_threshold, dthr, max_level,
                                                          s->d_est, s->d_eflags);
   else
-    k_regrid_estimate<float><<<g, 256, 0, s->stream>>>(s->mesh, (const float*)s->U[buffer],
+    k_regrid_estimate<float><<<g, 256, 0, s->stream>>>(s->mesh, (const float*)s->U[buffer], ew,
                                                         refine_threshold, dthr, max_level,
                                                         s->d_est, s->d_eflags);
   if (cudaPeekAtLastError() != cudaSuccess) return AMRVAC_E_CUDA;

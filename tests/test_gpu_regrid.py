@@ -84,17 +84,29 @@ def _thresholds(E):
     return thr, dthr / thr
 
 
+WEIGHTS = {
+    "rho": None,
+    # density and pressure (the blast quantities), and every primitive
+    "rho_p": [0.5, 0, 0, 0, 0.5, 0, 0, 0, 0],
+    "all": [1.0, 0.3, 0.3, 0.3, 1.0, 0.2, 0.2, 0.2, 0.1],
+}
+
+
 @pytest.mark.parametrize("name", ["1d", "2d", "2d_outflow", "3d"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_estimator_parity(amr, orc, name, precision):
+@pytest.mark.parametrize("weights", ["rho", "rho_p", "all"])
+def test_estimator_parity(amr, orc, name, precision, weights):
     W = _as(_cases()[name], precision)
-    Eo = rg.estimator(orc.mesh_for(W), W.U, W.cfg)
+    wts = WEIGHTS[weights]
+    Eo = rg.estimator(orc.mesh_for(W), W.U, W.cfg, weights=wts)
     thr, ratio = _thresholds(Eo)
     S = amr.State.from_workload(W, kernel="plain")
     S.set_conserved(W.U.astype(np.float32) if precision == "fp32" else W.U)
-    E, f = S.regrid_estimate(thr, ratio, max_level=3)
+    E, f = S.regrid_estimate(thr, ratio, max_level=3, weights=wts)
     S.close()
-    tol = 1e-13 if precision == "fp64" else 2e-5
+    # FP64: rounding of the primitive recovery and of the level-change ghost
+    # operators; FP32 bulk: the ghost operators run in float
+    tol = (1e-13 if weights == "rho" else 1e-12) if precision == "fp64" else 2e-5
     assert np.abs(E - Eo).max() <= tol, np.abs(E - Eo).max()
     fo = rg.flags(Eo, W.block_meta, thr, ratio, 3)
     far = (np.abs(Eo - thr) > tol) & (np.abs(Eo - ratio * thr) > tol)
@@ -190,7 +202,7 @@ def test_regrid_fused_3d_conserves(amr, orc, precision):
     S.set_conserved(W.U.astype(np.float32) if precision == "fp32" else W.U)
     S.step(3)
     s0 = S.diag()["sums"][0]
-    E, f = S.regrid_estimate(0.05, 0.2, max_level=3)
+    E, f = S.regrid_estimate(0.05, 0.2, max_level=3, weights=WEIGHTS["rho_p"])
     assert (f == 1).any() and (f == -1).any()
     U1 = S.get_conserved(0, precision=0)
     new = amr.regrid_plan(W.cfg, W.instances, W.block_meta, f)

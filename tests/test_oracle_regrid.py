@@ -66,6 +66,43 @@ def test_estimator_jump_across_block_face_2d(orc):
         assert E[b] == pytest.approx(lo if r[2] == 0 else hi, rel=1e-14), (b, E)
 
 
+def _prim_case(rho_fn, vx_fn, p_fn):
+    def prim(inst, x, y, z):
+        zero = np.zeros_like(x)
+        return wl.conserved_from_primitive(inst.gamma, rho_fn(x), vx_fn(x), zero, zero,
+                                           p_fn(x), 0.5 + zero, zero, zero)
+    return _case(2, (2, 2, 1), (8, 8, 1), wl.uniform_meta((2, 2, 1)), prim)
+
+
+def test_estimator_weighted_primitives(orc):
+    step = lambda lo, hi: (lambda x: np.where(x < 0.5, lo, hi))  # noqa: E731
+    lo = 1.0 / np.sqrt(1.05 ** 2 + 0.04 ** 2)
+    hi = 1.0 / np.sqrt(1.07 ** 2 + 0.08 ** 2)
+    # a pressure jump at the block face under uniform density: the pressure
+    # weight sees the closed form of the density case, the density weight 0
+    W = _prim_case(lambda x: 1.0 + 0 * x, lambda x: 0 * x, step(1.0, 2.0))
+    wp = np.zeros(9)
+    wp[4] = 1.0
+    E = rg.estimator(orc.mesh_for(W), W.U, W.cfg, weights=wp)
+    for b, r in enumerate(W.block_meta):
+        assert E[b] == pytest.approx(lo if r[2] == 0 else hi, rel=1e-13)
+    assert np.all(_est(orc, W) == 0.0)
+    wmix = np.zeros(9)
+    wmix[0] = wmix[4] = 0.5
+    np.testing.assert_allclose(rg.estimator(orc.mesh_for(W), W.U, W.cfg, weights=wmix),
+                               0.5 * E, rtol=1e-15)
+    # uniform momentum across a density jump: the velocity (a derived
+    # quantity) jumps 1 -> 0.5.  Low side, last cell (p, c, m) = (0.5, 1, 1):
+    # 0.5 / sqrt((0.5 + 0.01 * 3.5)^2 + (0.01 * 4)^2); the momentum is flat
+    W = _prim_case(step(1.0, 2.0), step(1.0, 0.5), lambda x: 1.0 + 0 * x)
+    wv = np.zeros(9)
+    wv[1] = 1.0
+    E = rg.estimator(orc.mesh_for(W), W.U, W.cfg, weights=wv)
+    want_lo = 0.5 / np.sqrt(0.535 ** 2 + 0.04 ** 2)
+    assert E[0] == pytest.approx(want_lo, rel=1e-13)
+    assert np.all(W.U[1] == 1.0)
+
+
 def test_estimator_zero_on_uniform_and_scale_invariant(orc):
     W = _case(2, (2, 2, 1), (8, 8, 1), wl.uniform_meta((2, 2, 1)),
               _rho_prim(lambda x, y, z: 1.3 + 0 * x), bc="periodic")
