@@ -83,6 +83,9 @@ def lib():
             L.orc_fast_speed.restype = C.c_double
             L.orc_fast_speed.argtypes = [C.c_double, dp, C.c_int]
             L.orc_reconstruct.argtypes = [C.c_int, dp, C.c_int, dp, dp]
+            L.orc_reconstruct5.argtypes = [C.c_int, dp, C.c_int, dp, dp]
+            L.orc_ghost_width.argtypes = [C.c_void_p]
+            L.orc_ghost_width.restype = C.c_int
             L.orc_face_flux.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_int,
                                         dp, dp, dp]
             L.orc_stage_coeffs.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_double),
@@ -98,7 +101,7 @@ def lib():
 
 _FLUX = {"hll": 0, "hlld": 1, "tvdlf": 2, "hllc": 3}
 _LIM = {"minmod": 0, "vanleer": 1, "koren": 2, "superbee": 3, "woodward": 4, "mcbeta": 5,
-        "albada": 6}
+        "albada": 6, "mp5": 7, "weno5": 8, "wenoz5": 9}
 _TIME = {"ssprk2": 0, "ssprk3": 1, "ssprk43": 2, "ssprk54": 3}
 _BC = {"periodic": 0, "outflow": 1}
 _FIX = {"off": 0, "replace": 1, "average": 2}
@@ -166,10 +169,15 @@ class Mesh:
         assert U.shape == (NVAR, self.nblocks, self.ncell), U.shape
         return U
 
+    @property
+    def ng(self):
+        """Ghost cells per block face (3 with a five-point limiter, else 2)."""
+        return lib().orc_ghost_width(self._h)
+
     def padded_shape(self):
         P = 1
         for d in range(self.cfg.ndim):
-            P *= self.cfg.block_nx[d] + 4
+            P *= self.cfg.block_nx[d] + 2 * self.ng
         return (NVAR, self.nblocks, P)
 
     def fill_ghosts(self, U):
@@ -263,7 +271,11 @@ def reconstruct(limiter, w):
     w = np.ascontiguousarray(w, np.float64)
     wl = np.full_like(w, np.nan)
     wr = np.full_like(w, np.nan)
-    lib().orc_reconstruct(_LIM[limiter], w, w.shape[0], wl, wr)
+    lim = _LIM[limiter]
+    if lim >= 7:
+        lib().orc_reconstruct5(lim, w, w.shape[0], wl, wr)
+    else:
+        lib().orc_reconstruct(lim, w, w.shape[0], wl, wr)
     return wl, wr
 
 

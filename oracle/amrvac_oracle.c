@@ -17,7 +17,8 @@
  *    default) with the two-ghost-cell limiters `minmod`, `vanleer`, `koren`,
  *    `superbee`, `woodward`, `mcbeta` (beta = 1.4) and `albada` of the limiter
  *    table (order 3 for koren, 2 for the others); albada in its TVD form
- *    (zero slope at extrema, like the others).
+ *    (zero slope at extrema, like the others); and the three-ghost-cell
+ *    five-point `mp5`, `weno5` and `wenoz5` (see mp5_plus, weno5_plus).
  *  - a face whose reconstructed density or pressure is not positive falls back
  *    to first order (cell values) on both sides (Sect. 7.4 mentions checks on
  *    reconstructions; the fallback form is our reading).
@@ -55,7 +56,10 @@
 #include <string.h>
 
 #define NV ORC_NVAR
+/* ghost cells per block face: 2 for the two-ghost-cell limiters, 3 for the
+ * five-point ones (mp5, weno5, wenoz5); per mesh in orc_mesh.ng */
 #define NG 2
+#define NG5 3
 enum { RHO = 0, MX = 1, MY = 2, MZ = 3, EN = 4, BXV = 5, BYV = 6, BZV = 7, PSI = 8 };
 enum { ST_OK = 0, ST_SMALL = 4 };
 
@@ -82,6 +86,7 @@ struct orc_mesh {
   unsigned char* fkind;
   double* facef;
   int farea;
+  int ng; /* ghost width: NG5 when any level uses a five-point limiter, else NG */
 };
 
 /* ------------------------------------------------------------------------ */
@@ -250,6 +255,94 @@ void orc_reconstruct(int limiter, const double* w, int n, double* wl, double* wr
     wr[i] = recon_minus(limiter, w[i - 1], w[i], w[i + 1]);
   }
 }
+
+/* Five-point limiters of the limiter table (3 ghost cells), each giving the
+ * left state at the face i+1/2 of cell i from v = (v_{i-2}, ..., v_{i+2}); the
+ * right state at i-1/2 is the same formula on the mirrored stencil.
+ *   7 mp5 (Suresh & Huynh 1997): the fifth-order interface polynomial
+ *     (2 v_{i-2} - 13 v_{i-1} + 47 v_i + 27 v_{i+1} - 3 v_{i+2}) / 60, kept when
+ *     it lies between v_i and the monotonicity bound v_i + minmod(v_{i+1} - v_i,
+ *     4 (v_i - v_{i-1})); otherwise clipped to the interval built from the
+ *     upper limit v_i + 4 (v_i - v_{i-1}), the median and the large-curvature
+ *     values with the minmod4 of the second differences.
+ *   8 weno5 (Jiang & Shu 1996): convex combination of the three third-order
+ *     candidates with the smoothness indicators beta_k and the linear weights
+ *     (1, 6, 3)/10, alpha_k = d_k / (eps + beta_k)^2, eps = 1e-6.
+ *   9 wenoz5 (Borges et al. 2008): the same candidates with
+ *     alpha_k = d_k (1 + tau5 / (beta_k + eps)), tau5 = |beta_0 - beta_2|,
+ *     exponent 1, eps = 1e-40. */
+static double minmod4(double w, double x, double y, double z) {
+  if (w > 0.0 && x > 0.0 && y > 0.0 && z > 0.0) return dmin(dmin(w, x), dmin(y, z));
+  if (w < 0.0 && x < 0.0 && y < 0.0 && z < 0.0) return dmax(dmax(w, x), dmax(y, z));
+  return 0.0;
+}
+
+static double mp5_plus(const double* v) {
+  const double a = 4.0;
+  const double vm2 = v[0], vm1 = v[1], v0 = v[2], vp1 = v[3], vp2 = v[4];
+  const double vor = (2.0 * vm2 - 13.0 * vm1 + 47.0 * v0 + 27.0 * vp1 - 3.0 * vp2) / 60.0;
+  const double vmp = v0 + minmod2(vp1 - v0, a * (v0 - vm1));
+  if ((vor - v0) * (vor - vmp) <= 0.0) return vor;
+  const double djm1 = vm2 - 2.0 * vm1 + v0;
+  const double dj = vm1 - 2.0 * v0 + vp1;
+  const double djp1 = v0 - 2.0 * vp1 + vp2;
+  const double dp = minmod4(4.0 * dj - djp1, 4.0 * djp1 - dj, dj, djp1);
+  const double dm = minmod4(4.0 * dj - djm1, 4.0 * djm1 - dj, dj, djm1);
+  const double vul = v0 + a * (v0 - vm1);
+  const double vav = 0.5 * (v0 + vp1);
+  const double vmd = vav - 0.5 * dp;
+  const double vlc = v0 + 0.5 * (v0 - vm1) + 4.0 / 3.0 * dm;
+  const double vmin = dmax(dmin(dmin(v0, vp1), vmd), dmin(dmin(v0, vul), vlc));
+  const double vmax = dmin(dmax(dmax(v0, vp1), vmd), dmax(dmax(v0, vul), vlc));
+  return vor + minmod2(vmin - vor, vmax - vor);
+}
+
+static double weno5_plus(int z, const double* v) {
+  const double vm2 = v[0], vm1 = v[1], v0 = v[2], vp1 = v[3], vp2 = v[4];
+  const double c13 = 13.0 / 12.0;
+  const double t0 = vm2 - 2.0 * vm1 + v0, u0 = vm2 - 4.0 * vm1 + 3.0 * v0;
+  const double t1 = vm1 - 2.0 * v0 + vp1, u1 = vm1 - vp1;
+  const double t2 = v0 - 2.0 * vp1 + vp2, u2 = 3.0 * v0 - 4.0 * vp1 + vp2;
+  const double b0 = c13 * t0 * t0 + 0.25 * u0 * u0;
+  const double b1 = c13 * t1 * t1 + 0.25 * u1 * u1;
+  const double b2 = c13 * t2 * t2 + 0.25 * u2 * u2;
+  const double q0 = (2.0 * vm2 - 7.0 * vm1 + 11.0 * v0) / 6.0;
+  const double q1 = (-vm1 + 5.0 * v0 + 2.0 * vp1) / 6.0;
+  const double q2 = (2.0 * v0 + 5.0 * vp1 - vp2) / 6.0;
+  double a0, a1, a2;
+  if (z) {
+    const double eps = 1e-40, tau = fabs(b0 - b2);
+    a0 = 0.1 * (1.0 + tau / (b0 + eps));
+    a1 = 0.6 * (1.0 + tau / (b1 + eps));
+    a2 = 0.3 * (1.0 + tau / (b2 + eps));
+  } else {
+    const double eps = 1e-6;
+    a0 = 0.1 / ((eps + b0) * (eps + b0));
+    a1 = 0.6 / ((eps + b1) * (eps + b1));
+    a2 = 0.3 / ((eps + b2) * (eps + b2));
+  }
+  const double sa = a0 + a1 + a2;
+  return (a0 * q0 + a1 * q1 + a2 * q2) / sa;
+}
+
+static double recon5_plus(int lim, const double* v) {
+  return lim == 7 ? mp5_plus(v) : weno5_plus(lim == 9, v);
+}
+
+/* right state at i-1/2 of cell i from v = (v_{i-2}, ..., v_{i+2}) */
+static double recon5_minus(int lim, const double* v) {
+  const double r[5] = {v[4], v[3], v[2], v[1], v[0]};
+  return recon5_plus(lim, r);
+}
+
+void orc_reconstruct5(int limiter, const double* w, int n, double* wl, double* wr) {
+  for (int i = 2; i + 2 < n; i++) {
+    wl[i] = recon5_plus(limiter, w + i - 2);
+    wr[i] = recon5_minus(limiter, w + i - 2);
+  }
+}
+
+int orc_ghost_width(const orc_mesh* m) { return m->ng; }
 
 /* ------------------------------------------------------------------------ */
 /* Riemann solvers in the face frame: x = face normal                        */
@@ -664,9 +757,15 @@ orc_mesh* orc_create(const orc_config* cfg, int ninst, const orc_instance* inst,
   m->nblocks = nblocks;
   m->nthreads = 1;
   if (cfg->ndim < 1 || cfg->ndim > 3) FAIL("ndim must be 1..3");
+  if (cfg->limiter < 0 || cfg->limiter > 9) FAIL("limiter must be 0..9");
+  m->ng = cfg->limiter >= 7 ? NG5 : NG;
+  for (int L = 0; L < 16; L++) {
+    if (cfg->level_limiter[L] > 9) FAIL("level_limiter must be -1..9");
+    if (cfg->level_limiter[L] >= 7) m->ng = NG5;
+  }
   for (int d = 0; d < 3; d++) {
     if (d >= cfg->ndim) m->cfg.nx[d] = 1;
-    else if (cfg->nx[d] < NG) FAIL("block must have at least 2 cells per active dim");
+    else if (cfg->nx[d] < m->ng) FAIL("block must have at least as many cells as ghost cells");
   }
   m->ncell = m->cfg.nx[0] * m->cfg.nx[1] * m->cfg.nx[2];
   m->inst = (orc_instance*)malloc(sizeof(orc_instance) * (size_t)ninst);
@@ -807,7 +906,7 @@ static padinfo pad_of(const orc_mesh* m) {
   padinfo p;
   p.np = 1;
   for (int d = 0; d < 3; d++) {
-    p.g[d] = is_active(m, d) ? NG : 0;
+    p.g[d] = is_active(m, d) ? m->ng : 0;
     p.P[d] = m->cfg.nx[d] + 2 * p.g[d];
     p.np *= (size_t)p.P[d];
   }
@@ -948,16 +1047,22 @@ static int block_stage(const orc_mesh* m, int b, int k, const double* dtv, const
           int c[3] = {i, j, kk};
           double wl[NV], wr[NV], w1[NV], w0[NV];
           for (int v = 0; v < NV; v++) {
-            double s[4];
-            for (int t = 0; t < 4; t++) {
+            /* s[t] = cell f - 3 + t along d (the outer two only with 3 ghosts) */
+            double s[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+            for (int t = m->ng == NG5 ? 0 : 1; t < (m->ng == NG5 ? 6 : 5); t++) {
               int cc[3] = {c[0], c[1], c[2]};
-              cc[d] += t - 2;
+              cc[d] += t - 3;
               s[t] = W[v * pi.np + pidx(&pi, cc[0], cc[1], cc[2])];
             }
-            wl[v] = recon_plus(lim, s[0], s[1], s[2]);
-            wr[v] = recon_minus(lim, s[1], s[2], s[3]);
-            w0[v] = s[1];
-            w1[v] = s[2];
+            if (lim >= 7) {
+              wl[v] = recon5_plus(lim, s);
+              wr[v] = recon5_minus(lim, s + 1);
+            } else {
+              wl[v] = recon_plus(lim, s[1], s[2], s[3]);
+              wr[v] = recon_minus(lim, s[2], s[3], s[4]);
+            }
+            w0[v] = s[2];
+            w1[v] = s[3];
           }
           if (!(wl[0] > 0.0) || !(wl[4] > 0.0) || !(wr[0] > 0.0) || !(wr[4] > 0.0)) {
             for (int v = 0; v < NV; v++) {

@@ -32,7 +32,8 @@ typedef struct {
   int nx[3];             /* cells per block per dimension (1 for unused dims) */
   int flux;              /* 0 hll, 1 hlld, 2 tvdlf, 3 hllc */
   int limiter;           /* 0 minmod, 1 vanleer, 2 koren, 3 superbee, 4 woodward,
-                            5 mcbeta, 6 albada */
+                            5 mcbeta, 6 albada; 7 mp5, 8 weno5, 9 wenoz5 (five-
+                            point, 3 ghost cells) */
   int time;              /* 0 ssprk(2,2), 1 ssprk(3,3), 2 ssprk(4,3), 3 ssprk(5,4) */
   int glm;               /* 1: Dedner glm cleaning; 0: none (psi stays 0) */
   double glm_alpha;      /* psi damping parameter alpha_p */
@@ -63,9 +64,11 @@ orc_mesh* orc_create(const orc_config* cfg, int ninst, const orc_instance* inst,
 void orc_destroy(orc_mesh* m);
 void orc_set_threads(orc_mesh* m, int nthreads);
 
-/* Ghost fill: padded [var][block][(nx+4)(ny+4)(nz+4) over active dims];
- * interior and the 2-deep face slabs are written, edge/corner cells are 0. */
+/* Ghost fill: padded [var][block][(nx+2g)(ny+2g)(nz+2g) over active dims],
+ * g = orc_ghost_width (3 when a level uses a five-point limiter, else 2);
+ * interior and the g-deep face slabs are written, edge/corner cells are 0. */
 int orc_fill_ghosts(const orc_mesh* m, const double* U, double* padded);
+int orc_ghost_width(const orc_mesh* m);
 
 /* Refluxing (with cfg.reflux) is part of every stage over all blocks: after
  * the update, the coarse cell next to a face whose neighbour is finer gets
@@ -119,6 +122,8 @@ double orc_fast_speed(double gamma, const double* w, int dir);
 /* reconstruction of a 1D array: left state at i+1/2 (wl[i]) and right state at
  * i-1/2 (wr[i]) from cell i, for 1 <= i <= n-2 */
 void orc_reconstruct(int limiter, const double* w, int n, double* wl, double* wr);
+/* the same for the five-point limiters (7..9), for 2 <= i <= n-3 */
+void orc_reconstruct5(int limiter, const double* w, int n, double* wl, double* wr);
 /* face flux along dir from primitive face states (global frame) */
 void orc_face_flux(int flux, int glm, double gamma, double ch, int dir,
                    const double* wl, const double* wr, double* f);

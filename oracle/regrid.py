@@ -40,10 +40,10 @@ def _nx(cfg):
 
 
 def _padded_block(m, Up, b, cfg):
-    """Conserved values of block b with one ghost layer per active face from the
-    oracle's ghost fill (padded with 2 ghosts; edges/corners unused)."""
+    """Conserved values of block b with its ghost layers from the oracle's ghost
+    fill (m.ng per active face; edges/corners unused)."""
     nx = _nx(cfg)
-    g = [2 if d < cfg.ndim else 0 for d in range(3)]
+    g = [m.ng if d < cfg.ndim else 0 for d in range(3)]
     P = [nx[d] + 2 * g[d] for d in range(3)]
     return Up[:, b, :].reshape(9, P[2], P[1], P[0]), g
 
