@@ -474,22 +474,26 @@ def main():
                          ("hlld_ssprk54", {"time": "ssprk54"}),
                          ("hlld_woodward", {"limiter": "woodward"}),
                          ("hlld_reflux", {"reflux": True}),
-                         ("fp64_pressure", {"pressure": "fp64"})):
+                         ("fp64_pressure", {"pressure": "fp64"}),
+                         # five-point limiters: three ghost cells, plain kernels
+                         ("hlld_mp5_plain", {"limiter": "mp5", "kernel": "plain"}),
+                         ("hlld_wenoz5_plain", {"limiter": "wenoz5", "kernel": "plain"})):
             keys = ("flux", "time", "limiter", "reflux")
             old = {k: getattr(W.cfg, k) for k in keys}
             for k in keys:
                 setattr(W.cfg, k, kw.get(k, old[k]))
-            Sv = amrvac.State.from_workload(W, device=dev, kernel=args.kernel,
+            Sv = amrvac.State.from_workload(W, device=dev, kernel=kw.get("kernel", args.kernel),
                                             pressure=kw.get("pressure", args.pressure))
             nbytes = passes[W.cfg.time] * 9 * 4
             for k in keys:
                 setattr(W.cfg, k, old[k])
             Sv.set_conserved(U32)
-            if tuning is not None:
+            if tuning is not None and kw.get("kernel") != "plain":
                 Sv.set_tuning(tuning["ctas_per_sm"], tuning["order"], tuning["dynamic"])
             Sv.step(2)
             msv = time_steps(torch, Sv, max(3, min(args.steps, 10)))
             variants[name] = {"value": cells * ws / (msv / 1e3), "ms_per_step": msv,
+                              "kernel": kw.get("kernel", args.kernel),
                               "alg_bytes_per_cell_step": nbytes,
                               "frac": nbytes * cells / (msv / 1e3) / 1e9 / hbm}
             Sv.close()

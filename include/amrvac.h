@@ -72,9 +72,14 @@ typedef enum {
   AMRVAC_FLUX_TVDLF = 2,
   AMRVAC_FLUX_HLLC = 3
 } amrvac_flux;
-/* two-ghost-cell limiters of the limiter table (Sect. 3.1.1): minmod, van Leer
- * 1974, Koren 1993 (third order), superbee (Roe 1985), woodward (monotonized
- * central, van Leer 1977), mcbeta (beta = 1.4), van Albada 1982 (TVD form) */
+/* limiters of the limiter table (Sect. 3.1.1).  Two ghost cells: minmod, van
+ * Leer 1974, Koren 1993 (third order), superbee (Roe 1985), woodward
+ * (monotonized central, van Leer 1977), mcbeta (beta = 1.4), van Albada 1982
+ * (TVD form).  Three ghost cells (five-point, fifth order on smooth data): mp5
+ * (Suresh & Huynh 1997), weno5 (Jiang & Shu 1996, eps = 1e-6), wenoz5 (Borges
+ * et al. 2008, exponent 1); these run on the PLAIN kernels only (AUTO picks
+ * PLAIN, FUSED is rejected) whenever the limiter or a level's limiter is one
+ * of them. */
 typedef enum {
   AMRVAC_LIM_MINMOD = 0,
   AMRVAC_LIM_VANLEER = 1,
@@ -82,7 +87,10 @@ typedef enum {
   AMRVAC_LIM_SUPERBEE = 3,
   AMRVAC_LIM_WOODWARD = 4,
   AMRVAC_LIM_MCBETA = 5,
-  AMRVAC_LIM_ALBADA = 6
+  AMRVAC_LIM_ALBADA = 6,
+  AMRVAC_LIM_MP5 = 7,
+  AMRVAC_LIM_WENO5 = 8,
+  AMRVAC_LIM_WENOZ5 = 9
 } amrvac_limiter;
 /* time-integration table of Sect. 3: SSPRK(2,2), SSPRK(3,3) (Gottlieb 2005),
  * SSPRK(4,3) and SSPRK(5,4) (Spiteri & Ruuth 2002) */
@@ -216,8 +224,9 @@ amrvac_status amrvac_set_time(amrvac_state* s, const double* h_t, const double* 
 
 /*
  * Ghost fill of buffer into d_padded_out (device, state precision):
- * [var][block][padded cell] with (n_d + 4) cells per active dimension; the
- * interior and the 2-deep face slabs are written, edge and corner cells are
+ * [var][block][padded cell] with (n_d + 2 g) cells per active dimension, g = 3
+ * when the limiter or a level's limiter is a five-point one, else 2; the
+ * interior and the g-deep face slabs are written, edge and corner cells are
  * set to 0 (the unsplit scheme reads face ghosts only).  Same-level copy,
  * periodic wrap, zero-gradient outflow, restriction (mean of the 2^d children)
  * and prolongation (coarse value plus minmod-limited slopes times 1/4 of a

@@ -272,10 +272,18 @@ class State:
             self.stream.synchronize()
         return out
 
+    @property
+    def ng(self):
+        """Ghost cells per block face of the ghost export: 3 when the limiter
+        or a level's limiter is a five-point one (mp5, weno5, wenoz5), else 2."""
+        five = {"mp5", "weno5", "wenoz5"}
+        lims = {self.cfg.limiter} | set((self.cfg.level_limiter or {}).values())
+        return 3 if lims & five else 2
+
     def fill_ghosts(self, buffer=0):
         P = 1
         for d in range(self.cfg.ndim):
-            P *= self.cfg.block_nx[d] + 4
+            P *= self.cfg.block_nx[d] + 2 * self.ng
         out = self.torch.zeros((9, self.nblocks, P), dtype=self.dtype, device=self.device)
         self.torch.cuda.current_stream(self.device).synchronize()
         _check(load().amrvac_fill_ghosts(self._h, buffer, out.data_ptr()), "amrvac_fill_ghosts")

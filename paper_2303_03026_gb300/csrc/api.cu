@@ -37,13 +37,13 @@ bool config_ok(const amrvac_config* c, std::string& err) {
   for (int d = 0; d < c->ndim; d++)
     if (c->block_nx[d] < 4 || c->block_nx[d] > 4096) return err = "block_nx must be 4..4096", false;
   if (c->flux < AMRVAC_FLUX_HLL || c->flux > AMRVAC_FLUX_HLLC) return err = "bad flux", false;
-  if (c->limiter < AMRVAC_LIM_MINMOD || c->limiter > AMRVAC_LIM_ALBADA)
+  if (c->limiter < AMRVAC_LIM_MINMOD || c->limiter > AMRVAC_LIM_WENOZ5)
     return err = "bad limiter", false;
   if (c->reflux != 0 && c->reflux != 1) return err = "bad reflux", false;
   for (int L = 0; L < AMRVAC_MAX_LEVELS; L++) {
     if (c->level_flux[L] < 0 || c->level_flux[L] > AMRVAC_FLUX_HLLC + 1)
       return err = "bad level_flux", false;
-    if (c->level_limiter[L] < 0 || c->level_limiter[L] > AMRVAC_LIM_ALBADA + 1)
+    if (c->level_limiter[L] < 0 || c->level_limiter[L] > AMRVAC_LIM_WENOZ5 + 1)
       return err = "bad level_limiter", false;
   }
   if (c->fix_small_values < AMRVAC_FIX_OFF || c->fix_small_values > AMRVAC_FIX_AVERAGE)
@@ -69,6 +69,15 @@ bool config_ok(const amrvac_config* c, std::string& err) {
 }
 
 int nx_of(const amrvac_config* c, int d) { return d < c->ndim ? c->block_nx[d] : 1; }
+
+// ghost cells per block face of the plain path: 3 when the limiter or a
+// level's limiter is a five-point one, else 2
+int ghost_width(const amrvac_config* c) {
+  int g = c->limiter >= AMRVAC_LIM_MP5 ? NG5 : NG;
+  for (int L = 0; L < AMRVAC_MAX_LEVELS; L++)
+    if (c->level_limiter[L] - 1 >= AMRVAC_LIM_MP5) g = NG5;
+  return g;
+}
 
 // Build and validate the block tables.  Per instance and level a dense map of
 // block positions: leaf id, MAP_REFINED or MAP_COARSER.
@@ -244,7 +253,7 @@ bool build_tables(const amrvac_config* c, int ninst, const amrvac_instance_desc*
 }
 
 bool use_fused_for(const amrvac_config* c) {
-  if (c->kernel == AMRVAC_KERNEL_PLAIN) return false;
+  if (c->kernel == AMRVAC_KERNEL_PLAIN || ghost_width(c) != NG) return false;
   if (c->kernel == AMRVAC_KERNEL_FUSED) return true;
   return fused_supported(c);
 }
@@ -262,7 +271,8 @@ Layout make_layout(const amrvac_config* c, int ninst, int nblocks, const Tables&
   for (int i = 0; i < 3; i++) L.U[i] = take(rs * NV * ncell * nblocks);
   if (!fused) {
     size_t np = 1;
-    for (int d = 0; d < 3; d++) np *= (size_t)(nx_of(c, d) + (d < c->ndim ? 2 * NG : 0));
+    for (int d = 0; d < 3; d++)
+      np *= (size_t)(nx_of(c, d) + (d < c->ndim ? 2 * ghost_width(c) : 0));
     L.W = take(rs * NV * np * nblocks);
     for (int d = 0; d < 3; d++) {
       size_t nf = 0;
@@ -390,6 +400,8 @@ amrvac_status amrvac_workspace_bytes(const amrvac_config* cfg, int32_t ninst,
                                      const int32_t* block_meta, size_t* bytes) {
   std::string err;
   if (!bytes || !config_ok(cfg, err)) return AMRVAC_E_INVALID;
+  if (cfg->kernel == AMRVAC_KERNEL_FUSED && (!fused_supported(cfg) || ghost_width(cfg) != NG))
+    return AMRVAC_E_INVALID;
   Tables T;
   if (!build_tables(cfg, ninst, inst, nblocks, block_meta, T)) return AMRVAC_E_INVALID;
   *bytes = make_layout(cfg, ninst, nblocks, T, use_fused_for(cfg)).total;
@@ -404,7 +416,8 @@ amrvac_status amrvac_state_create(const amrvac_config* cfg, int32_t ninst,
   std::string err;
   if (!out || !config_ok(cfg, err)) return AMRVAC_E_INVALID;
   *out = nullptr;
-  if (cfg->kernel == AMRVAC_KERNEL_FUSED && !fused_supported(cfg)) return AMRVAC_E_INVALID;
+  if (cfg->kernel == AMRVAC_KERNEL_FUSED && (!fused_supported(cfg) || ghost_width(cfg) != NG))
+    return AMRVAC_E_INVALID;
   Tables T;
   if (!build_tables(cfg, ninst, inst, nblocks, block_meta, T)) return AMRVAC_E_INVALID;
   bool fused = use_fused_for(cfg);
@@ -429,7 +442,7 @@ amrvac_status amrvac_state_create(const amrvac_config* cfg, int32_t ninst,
   for (int i = 0; i < 3; i++) s->U[i] = s->ws + L.U[i];
   s->npad = 1;
   for (int d = 0; d < 3; d++) {
-    s->P[d] = nx_of(cfg, d) + (d < cfg->ndim ? 2 * NG : 0);
+    s->P[d] = nx_of(cfg, d) + (d < cfg->ndim ? 2 * ghost_width(cfg) : 0);
     s->npad *= (size_t)s->P[d];
     s->nface[d] = d < cfg->ndim ? (size_t)s->ncell / nx_of(cfg, d) * (nx_of(cfg, d) + 1) : 0;
   }
@@ -439,6 +452,7 @@ amrvac_status amrvac_state_create(const amrvac_config* cfg, int32_t ninst,
   }
   DevMesh& M = s->mesh;
   M.ndim = cfg->ndim;
+  M.ng = ghost_width(cfg);
   for (int d = 0; d < 3; d++) {
     M.nx[d] = nx_of(cfg, d);
     M.bc[d][0] = cfg->bc[d][0];

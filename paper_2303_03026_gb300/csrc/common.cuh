@@ -11,7 +11,8 @@
 namespace amrvac {
 
 constexpr int NV = 9;       // rho, m_x, m_y, m_z, e, B_x, B_y, B_z, psi
-constexpr int NG = 2;       // ghost cells per face (vanleer/koren/minmod: limiter table)
+constexpr int NG = 2;       // ghost cells per face of the two-ghost-cell limiters
+constexpr int NG5 = 3;      // ghost cells per face of the five-point limiters (plain path)
 constexpr int MAXLEV = AMRVAC_MAX_LEVELS;
 constexpr int NPART = 12;   // per-block partials: smax, chmax, sums[9], pad
 // per-(instance, level) stage constants of the fused kernels, refreshed from
@@ -38,6 +39,7 @@ struct InstRT {      // per-instance clock and step parameters (device resident)
 
 struct DevMesh {
   int ndim;
+  int ng;                 // ghost cells per face of the plain path (NG or NG5)
   int nx[3];
   int ncell;
   int nblocks;

@@ -173,6 +173,78 @@ template <class T> __device__ __forceinline__ T recon_minus(int lim, T a, T b, T
   return b - T(0.5) * sgnT(dm) * l3;
 }
 
+// Five-point limiters of the limiter table (3 ghost cells), face value at
+// i+1/2 from v = (v_{i-2}, ..., v_{i+2}); the value at i-1/2 is the same
+// formula on the mirrored stencil.
+//   mp5 (Suresh & Huynh 1997): fifth-order interface polynomial, kept when it
+//     lies between v_i and v_i + minmod(v_{i+1} - v_i, 4 (v_i - v_{i-1})),
+//     else clipped into [v_min, v_max] built from the upper limit, the median
+//     and the large-curvature values (minmod4 of second differences).
+//   weno5 (Jiang & Shu 1996): linear weights (1, 6, 3)/10, alpha_k = d_k /
+//     (1e-6 + beta_k)^2.
+//   wenoz5 (Borges et al. 2008): alpha_k = d_k (1 + tau5 / (beta_k + eps)),
+//     tau5 = |beta_0 - beta_2|, eps = 1e-40 (double) / 1e-36 (float).
+template <class T> __device__ __forceinline__ T minmod4g(T w, T x, T y, T z) {
+  if (w > T(0) && x > T(0) && y > T(0) && z > T(0)) return fmin(fmin(w, x), fmin(y, z));
+  if (w < T(0) && x < T(0) && y < T(0) && z < T(0)) return fmax(fmax(w, x), fmax(y, z));
+  return T(0);
+}
+
+template <class T> __device__ __forceinline__ T mp5_face(T vm2, T vm1, T v0, T vp1, T vp2) {
+  const T a = T(4);
+  const T vor = (T(2) * vm2 - T(13) * vm1 + T(47) * v0 + T(27) * vp1 - T(3) * vp2) / T(60);
+  const T vmp = v0 + minmod2(vp1 - v0, a * (v0 - vm1));
+  if ((vor - v0) * (vor - vmp) <= T(0)) return vor;
+  const T djm1 = vm2 - T(2) * vm1 + v0, dj = vm1 - T(2) * v0 + vp1, djp1 = v0 - T(2) * vp1 + vp2;
+  const T dp = minmod4g(T(4) * dj - djp1, T(4) * djp1 - dj, dj, djp1);
+  const T dm = minmod4g(T(4) * dj - djm1, T(4) * djm1 - dj, dj, djm1);
+  const T vul = v0 + a * (v0 - vm1);
+  const T vmd = T(0.5) * (v0 + vp1) - T(0.5) * dp;
+  const T vlc = v0 + T(0.5) * (v0 - vm1) + T(4) / T(3) * dm;
+  const T vmin = fmax(fmin(fmin(v0, vp1), vmd), fmin(fmin(v0, vul), vlc));
+  const T vmax = fmin(fmax(fmax(v0, vp1), vmd), fmax(fmax(v0, vul), vlc));
+  return vor + minmod2(vmin - vor, vmax - vor);
+}
+
+template <class T>
+__device__ __forceinline__ T weno5_face(bool z, T vm2, T vm1, T v0, T vp1, T vp2) {
+  const T c13 = T(13) / T(12);
+  const T t0 = vm2 - T(2) * vm1 + v0, u0 = vm2 - T(4) * vm1 + T(3) * v0;
+  const T t1 = vm1 - T(2) * v0 + vp1, u1 = vm1 - vp1;
+  const T t2 = v0 - T(2) * vp1 + vp2, u2 = T(3) * v0 - T(4) * vp1 + vp2;
+  const T b0 = c13 * t0 * t0 + T(0.25) * u0 * u0;
+  const T b1 = c13 * t1 * t1 + T(0.25) * u1 * u1;
+  const T b2 = c13 * t2 * t2 + T(0.25) * u2 * u2;
+  const T q0 = (T(2) * vm2 - T(7) * vm1 + T(11) * v0) / T(6);
+  const T q1 = (-vm1 + T(5) * v0 + T(2) * vp1) / T(6);
+  const T q2 = (T(2) * v0 + T(5) * vp1 - vp2) / T(6);
+  T a0, a1, a2;
+  if (z) {
+    const T eps = sizeof(T) == 8 ? T(1e-40) : T(1e-36), tau = fabs(b0 - b2);
+    a0 = T(0.1) * (T(1) + tau / (b0 + eps));
+    a1 = T(0.6) * (T(1) + tau / (b1 + eps));
+    a2 = T(0.3) * (T(1) + tau / (b2 + eps));
+  } else {
+    const T eps = T(1e-6);
+    a0 = T(0.1) / ((eps + b0) * (eps + b0));
+    a1 = T(0.6) / ((eps + b1) * (eps + b1));
+    a2 = T(0.3) / ((eps + b2) * (eps + b2));
+  }
+  return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+}
+
+// left state at i+1/2 of cell i, v = (v_{i-2}, ..., v_{i+2})
+template <class T> __device__ __forceinline__ T recon5_plus(int lim, const T* v) {
+  return lim == AMRVAC_LIM_MP5 ? mp5_face(v[0], v[1], v[2], v[3], v[4])
+                               : weno5_face(lim == AMRVAC_LIM_WENOZ5, v[0], v[1], v[2], v[3], v[4]);
+}
+
+// right state at i-1/2 of cell i, v = (v_{i-2}, ..., v_{i+2})
+template <class T> __device__ __forceinline__ T recon5_minus(int lim, const T* v) {
+  return lim == AMRVAC_LIM_MP5 ? mp5_face(v[4], v[3], v[2], v[1], v[0])
+                               : weno5_face(lim == AMRVAC_LIM_WENOZ5, v[4], v[3], v[2], v[1], v[0]);
+}
+
 // ---------------------------------------------------------------- Riemann
 // local frame: q = (rho, u, v, w, p, -, By, Bz), normal field bx shared.
 

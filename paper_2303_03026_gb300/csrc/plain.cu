@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(256) k_prim(DevMesh M, const T* __restrict__ U
   const size_t np = (size_t)P0 * P1 * P2;
   const size_t total = np * M.nblocks;
   const size_t vs = (size_t)M.nblocks * M.ncell;
-  const int g0 = NG, g1 = M.ndim > 1 ? NG : 0, g2 = M.ndim > 2 ? NG : 0;
+  const int g0 = M.ng, g1 = M.ndim > 1 ? M.ng : 0, g2 = M.ndim > 2 ? M.ng : 0;
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (size_t)gridDim.x * blockDim.x) {
     int b = (int)(t / np);
@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(256) k_flux(DevMesh M, const T* __restrict__ W
   int e0 = M.nx[0] + (d == 0), e1 = M.nx[1] + (d == 1), e2 = M.nx[2] + (d == 2);
   const size_t nf = (size_t)e0 * e1 * e2;
   const size_t total = nf * M.nblocks;
-  const int g0 = NG, g1 = M.ndim > 1 ? NG : 0, g2 = M.ndim > 2 ? NG : 0;
+  const int g0 = M.ng, g1 = M.ndim > 1 ? M.ng : 0, g2 = M.ndim > 2 ? M.ng : 0;
   const int stride = d == 0 ? 1 : (d == 1 ? P0 : P0 * P1);
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (size_t)gridDim.x * blockDim.x) {
@@ -79,14 +79,28 @@ __global__ void __launch_bounds__(256) k_flux(DevMesh M, const T* __restrict__ W
     int pc = ((k + g2) * P1 + (j + g1)) * P0 + (i + g0);
     const T* src = W + (size_t)b * NV * np + pc;
     T wl[NV], wr[NV], w0[NV], w1[NV];
+    if (lim >= AMRVAC_LIM_MP5) {
+      // five-point limiters: cells f-3 .. f+2 (three ghost layers)
 #pragma unroll
-    for (int v = 0; v < NV; v++) {
-      const T* s = src + (size_t)v * np;
-      T s0 = s[-2 * stride], s1 = s[-stride], s2 = s[0], s3 = s[stride];
-      wl[v] = recon_plus(lim, s0, s1, s2);
-      wr[v] = recon_minus(lim, s1, s2, s3);
-      w0[v] = s1;
-      w1[v] = s2;
+      for (int v = 0; v < NV; v++) {
+        const T* s = src + (size_t)v * np;
+        const T c[6] = {s[-3 * stride], s[-2 * stride], s[-stride], s[0], s[stride],
+                        s[2 * stride]};
+        wl[v] = recon5_plus(lim, c);
+        wr[v] = recon5_minus(lim, c + 1);
+        w0[v] = c[2];
+        w1[v] = c[3];
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < NV; v++) {
+        const T* s = src + (size_t)v * np;
+        T s0 = s[-2 * stride], s1 = s[-stride], s2 = s[0], s3 = s[stride];
+        wl[v] = recon_plus(lim, s0, s1, s2);
+        wr[v] = recon_minus(lim, s1, s2, s3);
+        w0[v] = s1;
+        w1[v] = s2;
+      }
     }
     if (!(wl[0] > T(0)) || !(wl[4] > T(0)) || !(wr[0] > T(0)) || !(wr[4] > T(0))) {
 #pragma unroll
@@ -331,7 +345,7 @@ __global__ void k_fill_ghosts(DevMesh M, const T* __restrict__ U, T* __restrict_
   const size_t np = (size_t)P0 * P1 * P2;
   const size_t total = np * M.nblocks;
   const size_t vs = (size_t)M.nblocks * M.ncell;
-  const int g0 = NG, g1 = M.ndim > 1 ? NG : 0, g2 = M.ndim > 2 ? NG : 0;
+  const int g0 = M.ng, g1 = M.ndim > 1 ? M.ng : 0, g2 = M.ndim > 2 ? M.ng : 0;
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (size_t)gridDim.x * blockDim.x) {
     int b = (int)(t / np);

@@ -85,15 +85,17 @@ def test_workspace_matches_precision(lib):
 def test_scheme_options_validated(lib):
     # the wider scheme family is accepted; values outside the enums are not
     for flux, time, lim in (("tvdlf", "ssprk43", "superbee"), ("hllc", "ssprk54", "albada"),
-                            ("hlld", "ssprk3", "mcbeta"), ("hlld", "ssprk2", "woodward")):
+                            ("hlld", "ssprk3", "mcbeta"), ("hlld", "ssprk2", "woodward"),
+                            ("hll", "ssprk3", "mp5"), ("hlld", "ssprk3", "weno5"),
+                            ("hllc", "ssprk43", "wenoz5")):
         W = wl.small_amr_2d()
         W.cfg.flux, W.cfg.time, W.cfg.limiter = flux, time, lim
         assert _bytes(lib, W)[0] == 0, (flux, time, lim)
     from paper_2303_03026_gb300 import amrvac
     W = wl.small_amr_2d()
-    for field, value in (("flux", 4), ("time", 4), ("limiter", 7), ("reflux", 2),
-                         ("fix_small_values", 3), ("level_flux", 5), ("level_limiter", 8),
-                         ("level_flux", -1)):
+    for field, value in (("flux", 4), ("time", 4), ("limiter", 10), ("limiter", -1),
+                         ("reflux", 2), ("fix_small_values", 3), ("level_flux", 5),
+                         ("level_limiter", 11), ("level_flux", -1)):
         c = amrvac.make_config(W.cfg)
         if field.startswith("level_"):
             getattr(c, field)[2] = value
@@ -105,6 +107,21 @@ def test_scheme_options_validated(lib):
         st = lib.amrvac_workspace_bytes(C.byref(c), len(W.instances), ins, meta.shape[0],
                                         meta.ctypes.data, C.byref(n))
         assert st == 1, field
+
+
+def test_five_point_limiters_widen_the_plain_scratch(lib):
+    # three ghost layers in the plain path's padded scratch; the fused kernels
+    # (two ghost layers) are not used for them, and asking for them fails
+    W = wl.c3_turbulence(n=32, bnx=16, precision="fp32")
+    st, n2 = _bytes(lib, W, kernel="plain")
+    W.cfg.limiter = "weno5"
+    st5, n3 = _bytes(lib, W, kernel="plain")
+    assert st == 0 and st5 == 0 and n3 > n2
+    assert _bytes(lib, W, kernel="auto") == (0, n3)  # AUTO falls back to PLAIN
+    assert _bytes(lib, W, kernel="fused")[0] == 1
+    W.cfg.limiter = "vanleer"
+    W.cfg.level_limiter = {0: "mp5"}
+    assert _bytes(lib, W, kernel="fused")[0] == 1
 
 
 def test_fix_and_reflux_need_their_workspace(lib):

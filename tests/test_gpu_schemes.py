@@ -302,3 +302,66 @@ def test_hllc_stage_parity_fp32(amr, orc):
     for W in _small_cases("fp32")[:2]:
         W.cfg.flux = "hllc"
         _scheme_stage_parity(amr, orc, W, "auto", 1e-5)
+
+
+# ----------------------------------------------------------------------------
+# five-point limiters (mp5, weno5, wenoz5: three ghost cells, plain kernels)
+# ----------------------------------------------------------------------------
+
+FIVE_POINT = ["mp5", "weno5", "wenoz5"]
+
+
+@pytest.mark.parametrize("limiter", FIVE_POINT)
+def test_five_point_stage_parity_fp64(amr, orc, limiter):
+    cases = _small_cases("fp64") + [wl.small_amr_2d(periodic=False), wl.c1_riemann(seed=3)]
+    for W in cases:
+        W.cfg.limiter = limiter
+        _scheme_stage_parity(amr, orc, W, "auto", 1e-12)  # AUTO runs the plain kernels
+
+
+@pytest.mark.parametrize("limiter", FIVE_POINT)
+def test_five_point_stage_parity_fp32(amr, orc, limiter):
+    for W in _small_cases("fp32")[:2]:
+        W.cfg.limiter = limiter
+        _scheme_stage_parity(amr, orc, W, "plain", 1e-5)
+
+
+def test_five_point_on_one_level_and_ghost_export(amr, orc):
+    # a five-point limiter on one AMR level widens every block's ghost layers
+    W = wl.small_amr_2d(bnx=8)
+    W.cfg.level_limiter = {1: "wenoz5", 2: "mp5"}
+    _scheme_stage_parity(amr, orc, W, "auto", 1e-12)
+    S = amr.State.from_workload(W, kernel="auto")
+    S.set_conserved(W.U)
+    got = S.fill_ghosts(0)
+    S.close()
+    ref = orc.mesh_for(W).fill_ghosts(W.U)
+    assert got.shape == ref.shape == (9, W.nblocks, 14 * 14)
+    assert np.abs(got - ref).max() <= 1e-15 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("limiter", FIVE_POINT)
+def test_five_point_full_run(amr, orc, limiter):
+    # a shock tube to t_end with every stage and the final dt clip
+    W = wl.riemann_1d((1.0, 0, 0, 0, 1.0, 1.0, 0), (0.125, 0, 0, 0, 0.1, -1.0, 0), n=256,
+                      gamma=2.0, bx=0.75, t_end=0.1, flux="hll", time="ssprk3", nblocks=4)
+    W.cfg.limiter = limiter
+    Uo, t, ns, st = orc.mesh_for(W).run(W.U, 0.1)
+    assert st == 0
+    S = amr.State.from_workload(W, kernel="auto")
+    S.set_conserved(W.U)
+    S.set_time(t=0.0, t_end=0.1)
+    S.step(ns)
+    d = S.diag()
+    got = S.get_conserved(0)
+    S.close()
+    assert d["status"] == 0 and abs(d["t"][0] - t[0]) < 1e-14
+    sc = np.maximum(np.abs(Uo).max(axis=(1, 2), keepdims=True), 1e-300)
+    assert (np.abs(got - Uo) / sc).max() < 1e-10
+
+
+def test_fused_rejects_five_point(amr):
+    W = wl.c3_turbulence(n=32, bnx=16, precision="fp32")
+    W.cfg.limiter = "weno5"
+    with pytest.raises(amr.AmrvacError):
+        amr.State.from_workload(W, kernel="fused")
