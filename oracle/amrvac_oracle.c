@@ -42,6 +42,9 @@
  *    through it (conservative AMR, Sect. 3).
  *  - outflow boundary: a ghost takes the value of the nearest in-domain cell of
  *    its own level (zero gradient, Sect. 3.1.1 and Sect. 3.2.1).
+ *  - symmetric (reflecting) wall: a ghost takes the mirror cell across the
+ *    boundary with the normal momentum and normal magnetic field negated
+ *    (scalars, tangential components and psi even; see value_at).
  *  - fix_small_values (Sect. 7.4 bootstrapping, off by default): after every
  *    stage, cells below small_density / small_pressure are replaced by the
  *    floors or by the average over their non-small same-level face
@@ -656,9 +659,18 @@ static int is_active(const orc_mesh* m, int d) { return d < m->cfg.ndim; }
 
 /* Conserved value of the level-L cell p of instance inst (p may lie outside
  * the domain).  Recursive definition of the AMR ghost value. */
+static void value_in(const orc_mesh* m, const double* U, int inst, int L, const long* p,
+                     double* out);
+
+/* value of the level-L cell p of an instance, p anywhere up to a few cells
+ * outside the domain: periodic wrap; outflow takes the nearest in-domain cell
+ * of the level (zero gradient); a symmetric (reflecting) wall takes the
+ * mirror cell across the boundary with the normal momentum and the normal
+ * magnetic field negated */
 static void value_at(const orc_mesh* m, const double* U, int inst, int L, const long* pin,
                      double* out) {
   long p[3] = {pin[0], pin[1], pin[2]};
+  int flip[3] = {0, 0, 0};
   for (int d = 0; d < 3; d++) {
     if (!is_active(m, d)) {
       p[d] = 0;
@@ -666,13 +678,29 @@ static void value_at(const orc_mesh* m, const double* U, int inst, int L, const 
     }
     long N = cells_at_level(m, inst, L, d);
     if (p[d] < 0 || p[d] >= N) {
-      if (m->cfg.bc[d][p[d] < 0 ? 0 : 1] == 0) {
+      const int bc = m->cfg.bc[d][p[d] < 0 ? 0 : 1];
+      if (bc == 0) {
         p[d] = ((p[d] % N) + N) % N;
+      } else if (bc == 2) {
+        p[d] = p[d] < 0 ? -1 - p[d] : 2 * N - 1 - p[d];
+        flip[d] = 1;
       } else {
         p[d] = p[d] < 0 ? 0 : N - 1;
       }
     }
   }
+  value_in(m, U, inst, L, p, out);
+  for (int d = 0; d < 3; d++)
+    if (flip[d]) {
+      out[MX + d] = -out[MX + d];
+      out[BXV + d] = -out[BXV + d];
+    }
+}
+
+/* value of the in-domain level-L cell p: leaf copy, restriction or
+ * prolongation */
+static void value_in(const orc_mesh* m, const double* U, int inst, int L, const long* p,
+                     double* out) {
   long bp[3], c[3];
   for (int d = 0; d < 3; d++) {
     bp[d] = p[d] / m->cfg.nx[d];
@@ -758,6 +786,9 @@ orc_mesh* orc_create(const orc_config* cfg, int ninst, const orc_instance* inst,
   m->nthreads = 1;
   if (cfg->ndim < 1 || cfg->ndim > 3) FAIL("ndim must be 1..3");
   if (cfg->limiter < 0 || cfg->limiter > 9) FAIL("limiter must be 0..9");
+  for (int d = 0; d < cfg->ndim; d++)
+    for (int side = 0; side < 2; side++)
+      if (cfg->bc[d][side] < 0 || cfg->bc[d][side] > 2) FAIL("bc must be 0..2");
   m->ng = cfg->limiter >= 7 ? NG5 : NG;
   for (int L = 0; L < 16; L++) {
     if (cfg->level_limiter[L] > 9) FAIL("level_limiter must be -1..9");

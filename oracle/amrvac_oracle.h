@@ -38,7 +38,8 @@ typedef struct {
   int glm;               /* 1: Dedner glm cleaning; 0: none (psi stays 0) */
   double glm_alpha;      /* psi damping parameter alpha_p */
   double courant;
-  int bc[3][2];          /* 0 periodic, 1 outflow (zero gradient) */
+  int bc[3][2];          /* 0 periodic, 1 outflow (zero gradient), 2 symmetric
+                            (reflecting wall: mirror, normal m and B negated) */
   double small_density, small_pressure;
   int check_small_values;
   int fix_small_values;  /* 0 off, 1 replace, 2 average (Sect. 7.4 bootstrapping) */

@@ -43,7 +43,7 @@ LIMITER = {"minmod": 0, "vanleer": 1, "koren": 2, "superbee": 3, "woodward": 4, 
            "albada": 6, "mp5": 7, "weno5": 8, "wenoz5": 9}
 TIME = {"ssprk2": 0, "ssprk3": 1, "ssprk43": 2, "ssprk54": 3}
 PRECISION = {"fp64": 0, "fp32": 1}
-BC = {"periodic": 0, "outflow": 1}
+BC = {"periodic": 0, "outflow": 1, "symmetric": 2}
 FIX = {"off": 0, "replace": 1, "average": 2}
 
 
