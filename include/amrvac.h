@@ -104,7 +104,17 @@ typedef enum {
  * arithmetic in float; thermal pressure recovered from the total energy in
  * double; conservation sums and the time step in double. */
 typedef enum { AMRVAC_FP64 = 0, AMRVAC_FP32_BULK = 1 } amrvac_precision;
-typedef enum { AMRVAC_BC_PERIODIC = 0, AMRVAC_BC_OUTFLOW = 1 } amrvac_bc;
+/* Boundaries: PERIODIC (both sides of a dimension); OUTFLOW (zero gradient: a
+ * ghost takes the nearest in-domain cell of its level); SYMMETRIC (reflecting
+ * wall: a ghost takes the mirror cell across the boundary with the normal
+ * momentum and the normal magnetic field negated; density, pressure,
+ * tangential components and psi are even).  Meshes with a SYMMETRIC side run
+ * on the PLAIN kernels (AUTO picks PLAIN, FUSED is rejected). */
+typedef enum {
+  AMRVAC_BC_PERIODIC = 0,
+  AMRVAC_BC_OUTFLOW = 1,
+  AMRVAC_BC_SYMMETRIC = 2
+} amrvac_bc;
 /* Thermal-pressure recovery in FP32_BULK: the subtraction e - m^2/(2 rho) -
  * B^2/2 (and the per-thread conservation sums) in double (FP64), or in
  * float-float (FF, a pair of floats with a ~48-bit significand: the B_i^2 are

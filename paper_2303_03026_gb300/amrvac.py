@@ -353,8 +353,7 @@ class State:
         """fix_small_values on register ``buffer``; returns the cells repaired."""
         n = C.c_int64(0)
         _check(load().amrvac_fix_small_values(self._h, int(buffer), C.addressof(n)),
-               "amrvac_fix_small_values", "amrvac_regrid_estimate", "amrvac_regrid_plan",
-           "amrvac_regrid_transfer")
+               "amrvac_fix_small_values")
         return n.value
 
     # -------------------------------------------------------- regridding

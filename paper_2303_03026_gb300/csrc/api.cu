@@ -57,7 +57,8 @@ bool config_ok(const amrvac_config* c, std::string& err) {
   if (!(c->courant > 0.0) || !(c->glm_alpha >= 0.0)) return err = "bad courant/glm_alpha", false;
   for (int d = 0; d < 3; d++)
     for (int s = 0; s < 2; s++)
-      if (c->bc[d][s] != AMRVAC_BC_PERIODIC && c->bc[d][s] != AMRVAC_BC_OUTFLOW)
+      if (c->bc[d][s] != AMRVAC_BC_PERIODIC && c->bc[d][s] != AMRVAC_BC_OUTFLOW &&
+          c->bc[d][s] != AMRVAC_BC_SYMMETRIC)
         return err = "bad bc", false;
   for (int d = 0; d < c->ndim; d++)
     if ((c->bc[d][0] == AMRVAC_BC_PERIODIC) != (c->bc[d][1] == AMRVAC_BC_PERIODIC))
@@ -69,6 +70,14 @@ bool config_ok(const amrvac_config* c, std::string& err) {
 }
 
 int nx_of(const amrvac_config* c, int d) { return d < c->ndim ? c->block_nx[d] : 1; }
+
+// a symmetric wall on some side (plain kernels only)
+bool has_wall(const amrvac_config* c) {
+  for (int d = 0; d < c->ndim; d++)
+    for (int s = 0; s < 2; s++)
+      if (c->bc[d][s] == AMRVAC_BC_SYMMETRIC) return true;
+  return false;
+}
 
 // ghost cells per block face of the plain path: 3 when the limiter or a
 // level's limiter is a five-point one, else 2
@@ -214,7 +223,7 @@ bool build_tables(const amrvac_config* c, int ninst, const amrvac_instance_desc*
         if (p[d] < 0 || p[d] >= n) {
           if (c->bc[d][side] == AMRVAC_BC_PERIODIC) p[d] = ((p[d] % n) + n) % n;
           else {
-            out = NBR_OUTFLOW;
+            out = c->bc[d][side] == AMRVAC_BC_SYMMETRIC ? NBR_WALL : NBR_OUTFLOW;
             continue;
           }
         }
@@ -253,7 +262,7 @@ bool build_tables(const amrvac_config* c, int ninst, const amrvac_instance_desc*
 }
 
 bool use_fused_for(const amrvac_config* c) {
-  if (c->kernel == AMRVAC_KERNEL_PLAIN || ghost_width(c) != NG) return false;
+  if (c->kernel == AMRVAC_KERNEL_PLAIN || ghost_width(c) != NG || has_wall(c)) return false;
   if (c->kernel == AMRVAC_KERNEL_FUSED) return true;
   return fused_supported(c);
 }
@@ -400,7 +409,8 @@ amrvac_status amrvac_workspace_bytes(const amrvac_config* cfg, int32_t ninst,
                                      const int32_t* block_meta, size_t* bytes) {
   std::string err;
   if (!bytes || !config_ok(cfg, err)) return AMRVAC_E_INVALID;
-  if (cfg->kernel == AMRVAC_KERNEL_FUSED && (!fused_supported(cfg) || ghost_width(cfg) != NG))
+  if (cfg->kernel == AMRVAC_KERNEL_FUSED &&
+      (!fused_supported(cfg) || ghost_width(cfg) != NG || has_wall(cfg)))
     return AMRVAC_E_INVALID;
   Tables T;
   if (!build_tables(cfg, ninst, inst, nblocks, block_meta, T)) return AMRVAC_E_INVALID;
@@ -416,7 +426,8 @@ amrvac_status amrvac_state_create(const amrvac_config* cfg, int32_t ninst,
   std::string err;
   if (!out || !config_ok(cfg, err)) return AMRVAC_E_INVALID;
   *out = nullptr;
-  if (cfg->kernel == AMRVAC_KERNEL_FUSED && (!fused_supported(cfg) || ghost_width(cfg) != NG))
+  if (cfg->kernel == AMRVAC_KERNEL_FUSED &&
+      (!fused_supported(cfg) || ghost_width(cfg) != NG || has_wall(cfg)))
     return AMRVAC_E_INVALID;
   Tables T;
   if (!build_tables(cfg, ninst, inst, nblocks, block_meta, T)) return AMRVAC_E_INVALID;

@@ -18,9 +18,12 @@
 
 namespace amrvac {
 
-// wrap or clamp p at level L of instance q; returns false if a dimension is
-// unusable (never with a validated mesh)
-__device__ __forceinline__ void wrap_level(const DevMesh& M, int q, int L, int* p) {
+// bring p into the domain at level L of instance q: periodic wrap, outflow
+// clamp (zero gradient), or the mirror cell across a symmetric wall; returns
+// the mask of the dimensions mirrored (their normal momentum and field are to
+// be negated, see wall_flip)
+__device__ __forceinline__ int wrap_level(const DevMesh& M, int q, int L, int* p) {
+  int mask = 0;
 #pragma unroll
   for (int d = 0; d < 3; d++) {
     if (d >= M.ndim) {
@@ -29,13 +32,29 @@ __device__ __forceinline__ void wrap_level(const DevMesh& M, int q, int L, int* 
     }
     int N = M.lnb[(q * MAXLEV + L) * 3 + d] * M.nx[d];
     if (p[d] < 0 || p[d] >= N) {
-      if (M.bc[d][p[d] < 0 ? 0 : 1] == AMRVAC_BC_PERIODIC) {
+      const int bc = M.bc[d][p[d] < 0 ? 0 : 1];
+      if (bc == AMRVAC_BC_PERIODIC) {
         p[d] = ((p[d] % N) + N) % N;
+      } else if (bc == AMRVAC_BC_SYMMETRIC) {
+        p[d] = p[d] < 0 ? -1 - p[d] : 2 * N - 1 - p[d];
+        mask |= 1 << d;
       } else {
         p[d] = p[d] < 0 ? 0 : N - 1;
       }
     }
   }
+  return mask;
+}
+
+// symmetric wall: negate the normal momentum and normal field of the
+// dimensions in mask
+template <class T> __device__ __forceinline__ void wall_flip(int mask, T* u) {
+#pragma unroll
+  for (int d = 0; d < 3; d++)
+    if (mask & (1 << d)) {
+      u[1 + d] = -u[1 + d];
+      u[5 + d] = -u[5 + d];
+    }
 }
 
 // map code of the level-L block containing the (in-domain) cell p; cell index
@@ -56,12 +75,11 @@ __device__ __forceinline__ void read_cell(const DevMesh& M, const T* U, size_t v
   for (int v = 0; v < NV; v++) out[v] = src[(size_t)v * vs];
 }
 
-// level-L value of cell p where p is covered at level L or finer (depth <= 2)
+// level-L value of the in-domain cell p where p is covered at level L or finer
+// (depth <= 2)
 template <class T>
-__device__ void level_value_down(const DevMesh& M, const T* U, size_t vs, int q, int L,
-                                 const int* pin, T* out) {
-  int p[3] = {pin[0], pin[1], pin[2]};
-  wrap_level(M, q, L, p);
+__device__ void level_value_in(const DevMesh& M, const T* U, size_t vs, int q, int L,
+                               const int* p, T* out) {
   int cell;
   int r = map_at(M, q, L, p, &cell);
   if (r >= 0) {
@@ -156,12 +174,22 @@ template <class T> __device__ __forceinline__ T minmod_g(T a, T b) {
   return (a * b > T(0)) ? ((a > T(0)) ? fmin(a, b) : fmax(a, b)) : T(0);
 }
 
-// General ghost value of the level-L cell p of instance q (any coverage).
+// level-L value of cell p (anywhere near the domain) where p is covered at
+// level L or finer
 template <class T>
-__device__ void ghost_value(const DevMesh& M, const T* U, size_t vs, int q, int L,
-                            const int* pin, T* out) {
+__device__ void level_value_down(const DevMesh& M, const T* U, size_t vs, int q, int L,
+                                 const int* pin, T* out) {
   int p[3] = {pin[0], pin[1], pin[2]};
-  wrap_level(M, q, L, p);
+  const int mask = wrap_level(M, q, L, p);
+  level_value_in(M, U, vs, q, L, p, out);
+  if (mask) wall_flip(mask, out);
+}
+
+// General ghost value of the in-domain level-L cell p of instance q (any
+// coverage).
+template <class T>
+__device__ void ghost_value_in(const DevMesh& M, const T* U, size_t vs, int q, int L,
+                               const int* p, T* out) {
   int cell;
   int r = map_at(M, q, L, p, &cell);
   if (r >= 0) {
@@ -169,7 +197,7 @@ __device__ void ghost_value(const DevMesh& M, const T* U, size_t vs, int q, int 
     return;
   }
   if (r == MAP_REFINED) {
-    level_value_down(M, U, vs, q, L, p, out);
+    level_value_in(M, U, vs, q, L, p, out);
     return;
   }
   if (L == 0) {
@@ -202,9 +230,20 @@ __device__ void ghost_value(const DevMesh& M, const T* U, size_t vs, int q, int 
   }
 }
 
+// General ghost value of the level-L cell p of instance q, p anywhere near the
+// domain (wrapped, clamped or mirrored first).
+template <class T>
+__device__ void ghost_value(const DevMesh& M, const T* U, size_t vs, int q, int L,
+                            const int* pin, T* out) {
+  int p[3] = {pin[0], pin[1], pin[2]};
+  const int mask = wrap_level(M, q, L, p);
+  ghost_value_in(M, U, vs, q, L, p, out);
+  if (mask) wall_flip(mask, out);
+}
+
 // Conserved values of cell (i, j, k) (block-local, at most one index outside
 // [0, n)) of block b: interior read, same-level neighbour read, outflow clamp,
-// or the general AMR lookup.
+// mirror across a symmetric wall, or the general AMR lookup.
 template <class T>
 __device__ __forceinline__ void block_cell_value(const DevMesh& M, const T* U, size_t vs, int b,
                                                  int i, int j, int k, T* out) {
@@ -225,6 +264,10 @@ __device__ __forceinline__ void block_cell_value(const DevMesh& M, const T* U, s
   } else if (nb == NBR_OUTFLOW) {
     c[d] = side ? M.nx[d] - 1 : 0;
     read_cell(M, U, vs, b, (c[2] * M.nx[1] + c[1]) * M.nx[0] + c[0], out);
+  } else if (nb == NBR_WALL) {
+    c[d] = side ? 2 * M.nx[d] - 1 - c[d] : -1 - c[d];
+    read_cell(M, U, vs, b, (c[2] * M.nx[1] + c[1]) * M.nx[0] + c[0], out);
+    wall_flip(1 << d, out);
   } else {
     const int* bi = M.blk + b * 5;
     int p[3] = {bi[2] * M.nx[0] + i, bi[3] * M.nx[1] + j, bi[4] * M.nx[2] + k};
