@@ -5,18 +5,23 @@
  * the blocks of a block-structured adaptive mesh, with the explicit
  * finite-volume scheme of MPI-AMRVAC 3.0 (Keppens et al. 2023):
  *   - conserved cell averages updated by interface fluxes in every substep of
- *     an SSPRK(2,2) or SSPRK(3,3) scheme (Sect. 3, time-integration table);
+ *     an SSPRK(2,2), (3,3), (4,3) or (5,4) scheme (Sect. 3, time-integration
+ *     table);
  *   - limited reconstruction of primitive variables to two face states per
- *     interface with the `minmod`, `vanleer` or `koren` limiter, two ghost cells
- *     per block face (Sect. 3 and the limiter table of Sect. 3.1.1);
- *   - HLL (Harten 1983) or HLLD (Miyoshi & Kusano 2005) interface fluxes
- *     (flux-scheme table of Sect. 3; Sect. 3.2.1);
+ *     interface with a limiter of the limiter table (Sect. 3.1.1): seven
+ *     two-ghost-cell ones and three five-point ones (amrvac_limiter);
+ *   - HLL (Harten 1983), HLLD (Miyoshi & Kusano 2005), TVDLF or HLLC interface
+ *     fluxes (flux-scheme table of Sect. 3; Sect. 3.2.1), per AMR level if
+ *     asked (level_flux / level_limiter);
  *   - `glm` monopole control (Dedner 2002; table of Sect. 3.2.2);
  *   - the CFL-limited explicit time step (Sect. 3);
  *   - ghost cells filled from same-level neighbours, from finer neighbours by
  *     restriction and from coarser neighbours by limited prolongation, i.e. the
  *     internal boundary exchange of the AMR hierarchy (Sect. 8 describes its
- *     MPI form; here it is a read from the device block pool).
+ *     MPI form; here it is a read from the device block pool); periodic,
+ *     outflow or reflecting domain boundaries;
+ *   - optional refluxing at level changes, bootstrapping of small values
+ *     (Sect. 7.4) and dynamic regridding (amrvac_regrid_*).
  * One explicit substep is the paper's advect1(alpha dt, t_a, u^a, t_b, u^b) of
  * Sect. 4.2: u^b <- u^b + alpha dt F_ex(u^a) together with its boundary update.
  *
