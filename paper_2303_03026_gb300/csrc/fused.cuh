@@ -494,7 +494,8 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
     // readers were the faces of plane z-2 and this thread's own z face of
     // iteration z-1); x/y faces of plane z into the flux buffer of parity z;
     // wait for and convert the own cells of plane z+2, convert the halo of
-    // plane z+1 (owners 128..255); z face z+1/2; barrier; update of plane z.  The buffer of parity z is rewritten at
+    // plane z+1 (owners 128..255); load U_k of the own cell of plane z; z face
+    // z+1/2; barrier; update of plane z.  The buffer of parity z is rewritten at
     // iteration z+2, after the barrier of iteration z+1, which every thread
     // passes only after its update of plane z.
     constexpr bool PRE0 = sizeof(T) == 4;
@@ -541,6 +542,15 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
       cp_async_wait_all();
       convert_plane(z + 2);
       if (z + 1 < NZ) convert_halo(z + 1);
+      // float path: the stage input of the own cell, loaded before the z face
+      // and the barrier so that its L2 latency overlaps them (the double path
+      // has no registers to spare and loads it in the update)
+      const int c = (z * FB + y) * FB + x;
+      T ukr[PRE0 ? NV : 1];
+      if (PRE0 && owner) {
+#pragma unroll
+        for (int v = 0; v < NV; v++) ukr[v] = Uk[(size_t)v * vs + (size_t)b * ncell + c];
+      }
       T fz[NV];
       if (DIM == 3 && owner) zflux(z + 1, fz);
       if (FULL && sp.reflux && owner && z == NZ - 1 && nb[5] <= -3)
@@ -548,7 +558,6 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
       __syncthreads();
       if (!owner) continue;  // helpers: no cell of their own
 
-      const int c = (z * FB + y) * FB + x;
       T un[NV];
 #pragma unroll
       for (int v = 0; v < NV; v++) {
@@ -556,7 +565,7 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
         acc += over_dx<T>(S.fy[fb][v][y + 1][x] - S.fy[fb][v][y][x], dx1, idx1);
         if (DIM == 3) acc += over_dx<T>(fz[v] - fzp[v], dx2, idx2);
         const size_t at = (size_t)v * vs + (size_t)b * ncell + c;
-        const T uk = Uk[at];
+        const T uk = PRE0 ? ukr[PRE0 ? v : 0] : Uk[at];
         T ut = uk - dt * acc;
         if (v == 8) ut = ut * damp;
         un[v] = sp.plain ? ut : ca * (PRE0 ? S.u0[v][tid] : U0[at]) + cb * ut;
