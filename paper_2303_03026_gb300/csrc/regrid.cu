@@ -1,11 +1,12 @@
 // Dynamic regridding of the block-AMR mesh (Sect. 1 and 3: automatic
 // refinement and coarsening where chosen quantities vary).
 //
-//   k_regrid_estimate: per block, the maximum over its cells of the weighted
-//       sum of Loehner's normalised second derivatives of the chosen primitive
-//       quantities (face neighbours across block faces from the ghost
-//       operators of the update), and the block's refine / coarsen flag.
-//       The arithmetic is double with explicit round-to-nearest operations.
+//   k_regrid_estimate(_tiled): per block, the maximum over its cells of the
+//       weighted sum of Loehner's normalised second derivatives of the chosen
+//       primitive quantities (face neighbours across block faces from the
+//       ghost operators of the update), and the block's refine / coarsen flag.
+//       The arithmetic is double with explicit round-to-nearest operations;
+//       the tiled form stages the quantities in shared memory.
 //   amrvac_regrid_plan (host): the new block list, closed under 2:1 balance.
 //   k_regrid_transfer: fills a state built on the new list from the old one:
 //       copy, prolongation (coarse value plus minmod-limited slopes times
@@ -30,6 +31,8 @@ namespace amrvac {
 namespace {
 
 constexpr double LOEHNER_EPS = 0.01;  // noise filter of the estimator's denominator
+
+int grid_for(int nblocks) { return nblocks < 152 * 8 ? nblocks : 152 * 8; }
 
 struct EstWeights {
   double w[NV];  // weight of each primitive variable (rho, v, p, B, psi)
@@ -118,6 +121,122 @@ __global__ void __launch_bounds__(256) k_regrid_estimate(DevMesh M, const T* __r
   }
 }
 
+// The same estimator, tiled: per block, the weighted quantities of its cells
+// and of its one-cell face halo are formed once per chunk of variables into
+// shared memory [chunk var][padded cell] (primitives recovered once per cell,
+// not once per stencil use), the cells' estimates accumulate in shared memory
+// over the chunks in ascending variable order, then the block maximum is
+// taken.  Every value and every operation order equals k_regrid_estimate's.
+constexpr int EST_TILED_THREADS = 512;
+
+template <class T>
+__global__ void __launch_bounds__(EST_TILED_THREADS)
+    k_regrid_estimate_tiled(DevMesh M, const T* __restrict__ U, EstWeights ew, int nch,
+                            double thr, double dthr, int maxlev, double* est,
+                            signed char* flags) {
+  extern __shared__ double tile[];
+  __shared__ double red[EST_TILED_THREADS / 32];
+  const size_t vs = (size_t)M.nblocks * M.ncell;
+  const int h1 = M.ndim > 1 ? 1 : 0, h2 = M.ndim > 2 ? 1 : 0;
+  const int P0 = M.nx[0] + 2, P1 = M.nx[1] + 2 * h1, P2 = M.nx[2] + 2 * h2;
+  const int np = P0 * P1 * P2;
+  double* ecell = tile + (size_t)nch * np;
+  int vars[NV], nw = 0;
+  for (int v = 0; v < (ew.prim ? NV : 1); v++)
+    if (ew.w[v] != 0.0) vars[nw++] = v;
+  const int stride[3] = {1, P0, P0 * P1};
+  for (int b = blockIdx.x; b < M.nblocks; b += gridDim.x) {
+    const double g = M.gamma[M.blk[b * 5]];
+    for (int c = threadIdx.x; c < M.ncell; c += blockDim.x) ecell[c] = 0.0;
+    for (int c0 = 0; c0 < nw; c0 += nch) {
+      const int cn = nw - c0 < nch ? nw - c0 : nch;
+      __syncthreads();  // the previous chunk's (or block's) readers are done
+      for (int t = threadIdx.x; t < np; t += blockDim.x) {
+        const int i = t % P0 - 1, j = (t / P0) % P1 - h1, k = t / (P0 * P1) - h2;
+        const int outside =
+            (i < 0 || i >= M.nx[0]) + (j < 0 || j >= M.nx[1]) + (k < 0 || k >= M.nx[2]);
+        if (outside > 1) continue;  // edge and corner cells are never read
+        double q[NV];
+        est_cell(M, U, vs, b, i, j, k, ew, g, q);
+        for (int cc = 0; cc < cn; cc++) tile[(size_t)cc * np + t] = q[vars[c0 + cc]];
+      }
+      __syncthreads();
+      for (int c = threadIdx.x; c < M.ncell; c += blockDim.x) {
+        const int ci[3] = {c % M.nx[0], (c / M.nx[0]) % M.nx[1], c / (M.nx[0] * M.nx[1])};
+        const int t0 = ((ci[2] + h2) * P1 + (ci[1] + h1)) * P0 + ci[0] + 1;
+        double e = ecell[c];
+        for (int cc = 0; cc < cn; cc++) {
+          const double* q = tile + (size_t)cc * np;
+          const double r0 = q[t0];
+          double num = 0.0, den = 0.0;
+          for (int d = 0; d < M.ndim; d++) {
+            const double rp = q[t0 + stride[d]], rm = q[t0 - stride[d]];
+            const double s2 = __dadd_rn(__dsub_rn(rp, 2.0 * r0), rm);
+            num = __dadd_rn(num, __dmul_rn(s2, s2));
+            const double a = __dadd_rn(fabs(__dsub_rn(rp, r0)), fabs(__dsub_rn(r0, rm)));
+            const double f = __dadd_rn(__dadd_rn(fabs(rp), 2.0 * fabs(r0)), fabs(rm));
+            const double dd = __dadd_rn(a, __dmul_rn(LOEHNER_EPS, f));
+            den = __dadd_rn(den, __dmul_rn(dd, dd));
+          }
+          const double r = den > 0.0 ? num / den : 0.0;
+          e = __dadd_rn(e, __dmul_rn(ew.w[vars[c0 + cc]], sqrt(r)));
+        }
+        ecell[c] = e;
+      }
+    }
+    __syncthreads();
+    double emax = 0.0;
+    for (int c = threadIdx.x; c < M.ncell; c += blockDim.x) emax = ecell[c] > emax ? ecell[c] : emax;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double other = __shfl_xor_sync(0xffffffffu, emax, o);
+      emax = other > emax ? other : emax;
+    }
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = emax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < (int)(blockDim.x >> 5); w++) emax = red[w] > emax ? red[w] : emax;
+      const int L = M.blk[b * 5 + 1];
+      est[b] = emax;
+      flags[b] = (emax > thr && L < maxlev) ? 1 : ((emax < dthr && L > 0) ? -1 : 0);
+    }
+  }
+}
+
+template <class T>
+int launch_estimate(amrvac_state* s, const T* U, const EstWeights& ew, double thr, double dthr,
+                    int maxlev) {
+  // tiled when one variable's padded block and the cell estimates fit
+  constexpr size_t SMEM_MAX = 200 * 1024;
+  const amrvac::DevMesh& M = s->mesh;
+  size_t np = 1;
+  for (int d = 0; d < 3; d++) np *= (size_t)(M.nx[d] + (d < M.ndim ? 2 : 0));
+  const size_t cells = sizeof(double) * (size_t)M.ncell;
+  int nw = 0;
+  for (int v = 0; v < (ew.prim ? NV : 1); v++) nw += ew.w[v] != 0.0;
+  if (cells + sizeof(double) * np <= SMEM_MAX) {
+    int nch = (int)((SMEM_MAX - cells) / (sizeof(double) * np));
+    if (nch > nw) nch = nw;
+    const size_t smem = cells + sizeof(double) * np * (size_t)nch;
+    if (cudaFuncSetAttribute(k_regrid_estimate_tiled<T>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      return -1;
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return -1;
+    const int g = s->nblocks < nsm * 2 ? s->nblocks : nsm * 2;
+    k_regrid_estimate_tiled<T><<<g, EST_TILED_THREADS, smem, s->stream>>>(
+        M, U, ew, nch, thr, dthr, maxlev, s->d_est, s->d_eflags);
+  } else {
+    k_regrid_estimate<T><<<grid_for(s->nblocks), 256, 0, s->stream>>>(M, U, ew, thr, dthr,
+                                                                        maxlev, s->d_est,
+                                                                        s->d_eflags);
+  }
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
 template <class T>
 __global__ void __launch_bounds__(256) k_regrid_transfer(DevMesh Ms, const T* __restrict__ Us,
                                                          DevMesh Md, T* __restrict__ Ud,
@@ -193,8 +312,6 @@ __global__ void __launch_bounds__(256) k_regrid_transfer(DevMesh Ms, const T* __
     }
   }
 }
-
-int grid_for(int nblocks) { return nblocks < 152 * 8 ? nblocks : 152 * 8; }
 
 using Key = std::array<int, 5>;  // instance, level, i, j, k
 
@@ -374,17 +491,13 @@ extern "C" amrvac_status amrvac_regrid_estimate(amrvac_state* s, int32_t buffer,
     if (!any) return AMRVAC_E_INVALID;
   }
   const double dthr = derefine_ratio * refine_threshold;
-  const int g = grid_for(s->nblocks);
-  if (s->cfg.precision == AMRVAC_FP64)
-    k_regrid_estimate<double><<<g, 256, 0, s->stream>>>(s->mesh, (const double*)s->U[buffer], ew,
-                                                         refine_threshold, dthr, max_level,
-                                                         s->d_est, s->d_eflags);
-  else
-    k_regrid_estimate<float><<<g, 256, 0, s->stream>>>(s->mesh, (const float*)s->U[buffer], ew,
-                                                        refine_threshold, dthr, max_level,
-                                                        s->d_est, s->d_eflags);
-  if (cudaPeekAtLastError() != cudaSuccess) return AMRVAC_E_CUDA;
-  s->launches++;
+  const int n = s->cfg.precision == AMRVAC_FP64
+                    ? launch_estimate<double>(s, (const double*)s->U[buffer], ew,
+                                              refine_threshold, dthr, max_level)
+                    : launch_estimate<float>(s, (const float*)s->U[buffer], ew,
+                                             refine_threshold, dthr, max_level);
+  if (n < 0) return AMRVAC_E_CUDA;
+  s->launches += n;
   if (h_est && cudaMemcpyAsync(h_est, s->d_est, sizeof(double) * s->nblocks,
                                cudaMemcpyDeviceToHost, s->stream) != cudaSuccess)
     return AMRVAC_E_CUDA;
