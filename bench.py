@@ -478,9 +478,8 @@ def main():
                          # five-point limiters: three ghost cells, plain kernels
                          ("hlld_mp5_plain", {"limiter": "mp5", "kernel": "plain"}),
                          ("hlld_wenoz5_plain", {"limiter": "wenoz5", "kernel": "plain"}),
-                         # reflecting walls on every side: plain kernels
-                         ("hlld_walls_plain", {"bc": (("symmetric", "symmetric"),) * 3,
-                                               "kernel": "plain"})):
+                         # reflecting walls on every side (FULL fused kernels)
+                         ("hlld_walls", {"bc": (("symmetric", "symmetric"),) * 3})):
             keys = ("flux", "time", "limiter", "reflux", "bc")
             old = {k: getattr(W.cfg, k) for k in keys}
             for k in keys:

@@ -113,8 +113,7 @@ typedef enum { AMRVAC_FP64 = 0, AMRVAC_FP32_BULK = 1 } amrvac_precision;
  * ghost takes the nearest in-domain cell of its level); SYMMETRIC (reflecting
  * wall: a ghost takes the mirror cell across the boundary with the normal
  * momentum and the normal magnetic field negated; density, pressure,
- * tangential components and psi are even).  Meshes with a SYMMETRIC side run
- * on the PLAIN kernels (AUTO picks PLAIN, FUSED is rejected). */
+ * tangential components and psi are even). */
 typedef enum {
   AMRVAC_BC_PERIODIC = 0,
   AMRVAC_BC_OUTFLOW = 1,

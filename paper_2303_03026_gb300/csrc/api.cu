@@ -71,14 +71,6 @@ bool config_ok(const amrvac_config* c, std::string& err) {
 
 int nx_of(const amrvac_config* c, int d) { return d < c->ndim ? c->block_nx[d] : 1; }
 
-// a symmetric wall on some side (plain kernels only)
-bool has_wall(const amrvac_config* c) {
-  for (int d = 0; d < c->ndim; d++)
-    for (int s = 0; s < 2; s++)
-      if (c->bc[d][s] == AMRVAC_BC_SYMMETRIC) return true;
-  return false;
-}
-
 // ghost cells per block face of the plain path: 3 when the limiter or a
 // level's limiter is a five-point one, else 2
 int ghost_width(const amrvac_config* c) {
@@ -262,7 +254,7 @@ bool build_tables(const amrvac_config* c, int ninst, const amrvac_instance_desc*
 }
 
 bool use_fused_for(const amrvac_config* c) {
-  if (c->kernel == AMRVAC_KERNEL_PLAIN || ghost_width(c) != NG || has_wall(c)) return false;
+  if (c->kernel == AMRVAC_KERNEL_PLAIN || ghost_width(c) != NG) return false;
   if (c->kernel == AMRVAC_KERNEL_FUSED) return true;
   return fused_supported(c);
 }
@@ -409,8 +401,7 @@ amrvac_status amrvac_workspace_bytes(const amrvac_config* cfg, int32_t ninst,
                                      const int32_t* block_meta, size_t* bytes) {
   std::string err;
   if (!bytes || !config_ok(cfg, err)) return AMRVAC_E_INVALID;
-  if (cfg->kernel == AMRVAC_KERNEL_FUSED &&
-      (!fused_supported(cfg) || ghost_width(cfg) != NG || has_wall(cfg)))
+  if (cfg->kernel == AMRVAC_KERNEL_FUSED && (!fused_supported(cfg) || ghost_width(cfg) != NG))
     return AMRVAC_E_INVALID;
   Tables T;
   if (!build_tables(cfg, ninst, inst, nblocks, block_meta, T)) return AMRVAC_E_INVALID;
@@ -426,8 +417,7 @@ amrvac_status amrvac_state_create(const amrvac_config* cfg, int32_t ninst,
   std::string err;
   if (!out || !config_ok(cfg, err)) return AMRVAC_E_INVALID;
   *out = nullptr;
-  if (cfg->kernel == AMRVAC_KERNEL_FUSED &&
-      (!fused_supported(cfg) || ghost_width(cfg) != NG || has_wall(cfg)))
+  if (cfg->kernel == AMRVAC_KERNEL_FUSED && (!fused_supported(cfg) || ghost_width(cfg) != NG))
     return AMRVAC_E_INVALID;
   Tables T;
   if (!build_tables(cfg, ninst, inst, nblocks, block_meta, T)) return AMRVAC_E_INVALID;

@@ -29,7 +29,7 @@ enum {
 constexpr int NBR_OUTFLOW = -1;  // physical zero-gradient boundary
 constexpr int NBR_GENERAL = -2;  // level change: use the per-level block maps
 constexpr int NBR_GENERAL_FINER = -4;  // host tables only, while classifying faces
-constexpr int NBR_WALL = -5;     // symmetric (reflecting) wall; plain kernels only
+constexpr int NBR_WALL = -5;     // symmetric (reflecting) wall (fused: FULL kernels only)
 // per-level block map codes
 constexpr int MAP_REFINED = -1;  // covered by finer leaves
 constexpr int MAP_COARSER = -2;  // covered by a coarser leaf

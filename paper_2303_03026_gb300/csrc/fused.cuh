@@ -297,9 +297,10 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// FULL: the SSPRK(5,4) second output and the refluxing face registers are
-// compiled in (they are runtime-uniform branches that still cost the hot loop
-// registers and scheduling freedom, so the lean instantiation runs otherwise)
+// FULL: the SSPRK(5,4) second output, the refluxing face registers and the
+// mirrored reads of symmetric walls are compiled in (they are runtime-uniform
+// branches that still cost the hot loop registers and scheduling freedom, so
+// the lean instantiation runs otherwise)
 template <class T, int DIM, int LIM, int FLUX, bool FULL>
 __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
     k_fused(DevMesh M, const T* U0, const T* __restrict__ Uk, const T* U2, T* out, T* out2,
@@ -380,10 +381,17 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
 
     // face neighbour codes; a level-change face reads its ghost slab, built
     // from the stage input by k_ghost_slabs: code -3 - (slab index)
+    // (FULL) a symmetric wall reads the block's own mirrored cells: bit f of
+    // wmask marks face f, whose code becomes the outflow one
     int nb[6];
+    int wmask = 0;
 #pragma unroll
     for (int f = 0; f < 6; f++) {
       nb[f] = f < 2 * DIM ? M.nbr[b * 6 + f] : NBR_OUTFLOW;
+      if (FULL && nb[f] == NBR_WALL) {  // before slab codes, which reach -5 too
+        nb[f] = NBR_OUTFLOW;
+        wmask |= 1 << f;
+      }
       if (nb[f] == NBR_GENERAL) nb[f] = -3 - M.gface[b * 6 + f];
     }
 
@@ -407,7 +415,8 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
         vstride = 2 * NT2 * FB;
         return;
       }
-      const int nn = code >= 0 ? (n < 0 ? n + FB : n - FB) : (n < 0 ? 0 : FB - 1);
+      int nn = code >= 0 ? (n < 0 ? n + FB : n - FB) : (n < 0 ? 0 : FB - 1);
+      if (FULL && ((wmask >> f) & 1)) nn = n < 0 ? -1 - n : 2 * FB - 1 - n;
       const int src = code >= 0 ? code : b;
       int ii = i, jj = j, kk = k;
       if (f < 2) ii = nn;
@@ -416,12 +425,14 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
       ptr = Uk + (size_t)src * ncell + (kk * FB + jj) * FB + ii;
     };
 
-    auto to_prim = [&](T* cell, int which) {
-      // cell: the 9 values of one cell in a plane slot (stride FPW*FPW), in place
+    auto to_prim = [&](T* cell, int which, int flip) {
+      // cell: the 9 values of one cell in a plane slot (stride FPW*FPW), in
+      // place; flip: (FULL) dimensions whose wall mirrored this cell
       T u[NV], w[NV];
 #pragma unroll
       for (int v = 0; v < NV; v++) u[v] = cell[v * FPW * FPW];
       cons2prim(gammad, u, w, ff, gm1f);
+      if (FULL && flip) wall_flip(flip, w);
       if (sp.check_small && is_small_prim(w[0], w[4], rho_floor, p_floor))
         latch_error(M.err, AMRVAC_E_SMALL_VALUES, b, tid, which);
 #pragma unroll
@@ -454,7 +465,8 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
     // conversion of its own cell ...
     auto convert_plane = [&](int pz) {
       const int slot = ((pz % NSLOT) + NSLOT) % NSLOT;
-      if (owner) to_prim(&S.plane[slot][0][y + NG][x + NG], 0);
+      const int flip = FULL && ((pz < 0 && (wmask & 16)) || (pz >= NZ && (wmask & 32))) ? 4 : 0;
+      if (owner) to_prim(&S.plane[slot][0][y + NG][x + NG], 0, flip);
     };
     // ... and, one barrier after their copies landed, the conversion of the
     // halo cells of plane pz by owners 128..255 (one cell each)
@@ -463,7 +475,12 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
       if (tid >= 128 && tid < 256) {
         int hx, hy;
         halo_xy(tid - 128, hx, hy);
-        to_prim(&S.plane[slot][0][hy + NG][hx + NG], 1);
+        int flip = 0;
+        if (FULL) {
+          if ((hx < 0 && (wmask & 1)) || (hx >= FB && (wmask & 2))) flip |= 1;
+          if ((hy < 0 && (wmask & 4)) || (hy >= FB && (wmask & 8))) flip |= 2;
+        }
+        to_prim(&S.plane[slot][0][hy + NG][hx + NG], 1, flip);
       }
     };
 
@@ -654,7 +671,10 @@ int launch_fused_l(amrvac_state* s, int k, int epilogue, int g) {
   const int* work = s->d_work + s->grp_off[g];
   const int nwork = s->grp_cnt[g];
   int* counter = s->d_counter + g;
-  const bool full = sp.has2 || sp.reflux;
+  bool wall = false;  // symmetric walls are handled by the FULL instantiations
+  for (int d = 0; d < s->cfg.ndim; d++)
+    wall = wall || s->cfg.bc[d][0] == AMRVAC_BC_SYMMETRIC || s->cfg.bc[d][1] == AMRVAC_BC_SYMMETRIC;
+  const bool full = sp.has2 || sp.reflux || wall;
   const int flux = s->grp_flux[g];
   int m;
   if (flux == AMRVAC_FLUX_HLLD)

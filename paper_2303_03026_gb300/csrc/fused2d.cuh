@@ -95,7 +95,8 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
       vstride = 2 * FB;
       return;
     }
-    const int nn = code >= 0 ? (n < 0 ? n + FB : n - FB) : (n < 0 ? 0 : FB - 1);
+    int nn = code >= 0 ? (n < 0 ? n + FB : n - FB) : (n < 0 ? 0 : FB - 1);
+    if (FULL && code == NBR_WALL) nn = n < 0 ? -1 - n : 2 * FB - 1 - n;  // mirror
     const int src = code >= 0 ? code : bb;
     const int ii = f < 2 ? nn : i, jj = f < 2 ? j : nn;
     ptr = Uk + (size_t)src * ncell + jj * FB + ii;
@@ -186,6 +187,11 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
 #pragma unroll
         for (int v = 0; v < NV; v++) u[v] = S.cons[s][v][j + NG][i + NG];
         cons2prim(gammad, u, w, ff, gm1f);
+        if (FULL && which) {
+          // a halo cell mirrored by a symmetric wall of this block
+          const int f = i < 0 ? 0 : (i >= FB ? 1 : (j < 0 ? 2 : 3));
+          if (M.nbr[b * 6 + f] == NBR_WALL) wall_flip(1 << (f >> 1), w);
+        }
         if (sp.check_small && is_small_prim(w[0], w[4], rho_floor, p_floor))
           latch_error(M.err, AMRVAC_E_SMALL_VALUES, b, tid, which);
 #pragma unroll

@@ -1,8 +1,8 @@
 """GPU parity of symmetric (reflecting) walls with the oracle: stage outputs
 (FP64 and FP32 bulk; 1D, 2D, 3D; uniform and AMR; with five-point limiters),
 the ghost export across walls, a closed box with refluxing run to the same
-state and conserving mass and energy on the device, and the fused kernels
-refusing wall meshes.
+state and conserving mass and energy on the device, on the plain and on the
+fused kernels.
 """
 import numpy as np
 import pytest
@@ -93,9 +93,44 @@ def test_closed_box_run(amr, orc):
     assert (np.abs(got - Uo) / sc).max() < 1e-10
 
 
-def test_fused_refuses_walls(amr):
-    W = _walled(wl.c3_turbulence(n=32, bnx=16, precision="fp32"))
-    with pytest.raises(amr.AmrvacError):
-        amr.State.from_workload(W, kernel="fused")
-    S = amr.State.from_workload(W, kernel="auto")  # falls back to the plain kernels
+def _fused_cases(precision):
+    mixed = (("symmetric", "outflow"), ("symmetric", "symmetric"), ("periodic", "periodic"))
+    return [
+        _walled(wl.c3_turbulence(n=32, bnx=16, precision=precision)),
+        _walled(wl.cp_alfven(32, precision=precision), mixed),
+        _walled(wl.small_amr_2d(bnx=16, periodic=False, precision=precision)),
+        _walled(wl.c4_blast_amr(base=4, levels=3, bnx=16, shell=(0.2, 0.26),
+                                precision=precision)),
+    ]
+
+
+def test_fused_walls_stage_parity_fp64(amr, orc):
+    # 16^3 and 16^2 blocks: the fused kernels' mirrored reads (FULL instantiations)
+    for W in _fused_cases("fp64"):
+        _scheme_stage_parity(amr, orc, W, "fused", 1e-12)
+
+
+def test_fused_walls_stage_parity_fp32(amr, orc):
+    for W in _fused_cases("fp32")[:3]:
+        _scheme_stage_parity(amr, orc, W, "fused", 1e-5)
+
+
+def test_fused_closed_box_run(amr, orc):
+    W = _walled(wl.small_amr_2d(bnx=16, periodic=False))
+    W.cfg.reflux = True
+    m = orc.mesh_for(W)
+    s0 = m.sums(W.U)
+    Uo, t, ns, st = m.run(W.U, 1e30, maxsteps=6)
+    assert st == 0
+    S = amr.State.from_workload(W, kernel="fused")
+    S.set_conserved(W.U)
+    S.step(6)
+    d = S.diag()
+    got = S.get_conserved(0)
     S.close()
+    assert d["status"] == 0 and abs(d["t"][0] - t[0]) < 1e-14
+    rel = np.abs(d["sums"][0] - s0[0]) / np.abs(s0).max()
+    assert rel[0] < 1e-14 and rel[4] < 1e-14, rel
+    sc = np.maximum(np.abs(Uo).max(axis=(1, 2), keepdims=True), 1e-300)
+    sc = np.where(sc < 1e-9 * np.abs(Uo).max(), np.abs(Uo).max(), sc)
+    assert (np.abs(got - Uo) / sc).max() < 1e-10
