@@ -551,7 +551,6 @@ extern "C" amrvac_status amrvac_regrid_transfer(amrvac_state* src, int32_t src_b
       }
     }
     t[0] = 2;
-    int n = 0;
     for (int oz = 0; oz < (nd > 2 ? 2 : 1); oz++)
       for (int oy = 0; oy < (nd > 1 ? 2 : 1); oy++)
         for (int ox = 0; ox < 2; ox++) {
@@ -559,10 +558,8 @@ extern "C" amrvac_status amrvac_regrid_transfer(amrvac_state* src, int32_t src_b
                             nd > 2 ? 2 * k[4] + oz : 0});
           if (it == old.end()) return AMRVAC_E_INVALID;
           t[2 + (oz * 2 + oy) * 2 + ox] = it->second;
-          n++;
         }
     t[1] = t[2];
-    (void)n;
   }
   // the transfer runs on dst's stream after the work already on src's
   cudaEvent_t ev;

@@ -153,6 +153,40 @@ def test_transfer_parity(amr, orc, name, precision):
     assert err.max() <= tol, err.max(axis=(1, 2))
 
 
+def test_multi_instance_regrid_and_steps(amr, orc):
+    # independent instances (own gamma, own clock) regridded together, then
+    # stepped on the new mesh: estimator, plan, transfer and the step match
+    W = wl.c5_instances(count=5, nmin=32, nmax=96, precision="fp64")
+    m = orc.mesh_for(W)
+    wts = [0.5, 0, 0, 0, 0.5, 0, 0, 0, 0]
+    Eo = rg.estimator(m, W.U, W.cfg, weights=wts)
+    thr, ratio = _thresholds(Eo)
+    fo = rg.flags(Eo, W.block_meta, thr, ratio, 2)
+    new = rg.plan(W.cfg, W.instances, W.block_meta, fo)
+    Un = rg.transfer(W.cfg, W.instances, W.block_meta, W.U, m, new)
+    assert len(new) != W.nblocks and len(set(new[:, 0].tolist())) == 5
+    S = amr.State.from_workload(W, kernel="auto")
+    S.set_conserved(W.U)
+    E, f = S.regrid_estimate(thr, ratio, max_level=2, weights=wts)
+    assert np.abs(E - Eo).max() <= 1e-12 and np.array_equal(f, fo)
+    N = S.regrid(thr, ratio, max_level=2, weights=wts)
+    S.close()
+    assert np.array_equal(N.meta, new)
+    got = N.get_conserved(0)
+    scale = np.abs(W.U).max(axis=(1, 2), keepdims=True)
+    assert (np.abs(got - Un) / scale).max() <= 1e-14
+    Wn = wl.Workload("regridded", W.cfg, W.instances, new, Un)
+    Uo, t, ns, st = orc.mesh_for(Wn).run(Un, 1e30, maxsteps=2)
+    assert st == 0
+    N.set_time(t=0.0, t_end=1e30)
+    N.step(2)
+    d = N.diag()
+    got = N.get_conserved(0)
+    N.close()
+    assert d["status"] == 0 and np.abs(d["t"] - t).max() < 1e-14
+    assert (np.abs(got - Uo) / scale).max() < 1e-10
+
+
 def test_transfer_without_flags_is_a_copy(amr, orc):
     W = wl.small_amr_2d()
     new, ref, got = _transfer_pair(amr, orc, W, np.zeros(W.nblocks, np.int32), "fp64")

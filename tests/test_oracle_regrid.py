@@ -243,6 +243,7 @@ def test_library_plan_matches_oracle():
     rng = np.random.Generator(np.random.PCG64(7))
     for W in (wl.small_amr_2d(base=(3, 4, 1), maxlevel=2),
               wl.small_amr_2d(periodic=False),
+              wl.c5_instances(count=5, nmin=32, nmax=96, precision="fp64"),
               wl.c4_blast_amr(base=2, levels=3, bnx=4, shell=(0.2, 0.26)),
               _case(1, (5, 1, 1), (8, 1, 1), wl.uniform_meta((5, 1, 1)),
                     _rho_prim(lambda x, y, z: 1 + x))):
