@@ -479,14 +479,21 @@ def main():
                          ("hlld_mp5_plain", {"limiter": "mp5", "kernel": "plain"}),
                          ("hlld_wenoz5_plain", {"limiter": "wenoz5", "kernel": "plain"}),
                          # reflecting walls on every side (FULL fused kernels)
-                         ("hlld_walls", {"bc": (("symmetric", "symmetric"),) * 3})):
-            keys = ("flux", "time", "limiter", "reflux", "bc")
+                         ("hlld_walls", {"bc": (("symmetric", "symmetric"),) * 3}),
+                         # fix_small_values after every stage (flag pass + repair)
+                         ("hlld_fix_average", {"fix_small_values": "average",
+                                               "small_density": 1e-8,
+                                               "small_pressure": 1e-8})):
+            keys = ("flux", "time", "limiter", "reflux", "bc", "fix_small_values",
+                    "small_density", "small_pressure")
             old = {k: getattr(W.cfg, k) for k in keys}
             for k in keys:
                 setattr(W.cfg, k, kw.get(k, old[k]))
             Sv = amrvac.State.from_workload(W, device=dev, kernel=kw.get("kernel", args.kernel),
                                             pressure=kw.get("pressure", args.pressure))
             nbytes = passes[W.cfg.time] * 9 * 4
+            if W.cfg.fix_small_values != "off":
+                nbytes += 3 * (9 * 4 + 1)  # per stage: the state read once, a flag byte
             for k in keys:
                 setattr(W.cfg, k, old[k])
             Sv.set_conserved(U32)
