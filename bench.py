@@ -596,6 +596,9 @@ def main():
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline(W)
+        # the same oracle on one core (a smaller bounded sample)
+        one = cpu_baseline(W, seconds_target=4.0, threads=1)
+        cpu["single_thread"] = {"value": one["value"], "cores": 1, "sample": one["sample"]}
 
     if rank == 0:
         l2 = ("inputs larger than L2 (%.2f GB per state register)" % (state_bytes / 1e9)
