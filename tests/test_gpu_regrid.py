@@ -283,3 +283,22 @@ def test_regrid_rejects_mismatched_states(amr):
         S.regrid_transfer(D2)
     D2.close()
     S.close()
+
+
+def test_regrid_with_walls(amr, orc):
+    # the estimator's and the prolongation's ghost values across reflecting
+    # walls are the mirrored cells with the normal components negated
+    W = wl.small_amr_2d(periodic=False)
+    W.cfg.bc = (("symmetric", "symmetric"),) * 3
+    wts = [0.5, 0.2, 0.2, 0, 0.5, 0.1, 0.1, 0, 0]
+    Eo = rg.estimator(orc.mesh_for(W), W.U, W.cfg, weights=wts)
+    thr, ratio = _thresholds(Eo)
+    S = amr.State.from_workload(W, kernel="auto")
+    S.set_conserved(W.U)
+    E, f = S.regrid_estimate(thr, ratio, max_level=3, weights=wts)
+    S.close()
+    assert np.abs(E - Eo).max() <= 1e-12
+    f = _random_flags(W, 33)
+    new, ref, got = _transfer_pair(amr, orc, W, f, "fp64")
+    scale = np.maximum(np.abs(W.U).max(axis=(1, 2)), 1e-300)[:, None, None]
+    assert (np.abs(got - ref) / scale).max() <= 1e-14

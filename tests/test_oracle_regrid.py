@@ -362,3 +362,21 @@ def test_split_then_merge_is_identity(orc):
             assert np.abs(Ub[:, b] - W.U[:, ref[tuple(r)]]).max() <= 4e-15 * scale
             merged += tuple(r) in split
     assert merged >= 8
+
+
+def test_library_plan_level_limit():
+    # a 1D chain refined towards x = 0 through all 16 levels: splitting a
+    # level-15 block is refused, splitting the coarser ones is not
+    from paper_2303_03026_gb300 import amrvac, build
+    build.build()
+    meta = wl.amr_meta(1, (2, 1, 1), 15, lambda L, i, j, k: i == 0, periodic=False)
+    cfg = wl.Config(ndim=1, block_nx=(8, 1, 1), bc=(("outflow", "outflow"),) * 3)
+    inst = [wl.Instance(base_blocks=(2, 1, 1))]
+    assert meta[:, 1].max() == 15
+    f = np.where(meta[:, 1] == 15, 1, 0).astype(np.int8)
+    with pytest.raises(amrvac.AmrvacError):
+        amrvac.regrid_plan(cfg, inst, meta, f)
+    f = np.where(meta[:, 1] == 14, 1, 0).astype(np.int8)
+    got = amrvac.regrid_plan(cfg, inst, meta, f)
+    assert np.array_equal(got, rg.plan(cfg, inst, meta, f.astype(np.int32)))
+    _check_mesh(cfg, inst[0], got)
