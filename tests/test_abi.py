@@ -135,3 +135,23 @@ def test_fix_and_reflux_need_their_workspace(lib):
     W.cfg.small_density, W.cfg.small_pressure = 1e-6, 1e-6
     st, n2 = _bytes(lib, W)
     assert st == 0 and n2 >= n1 + W.nblocks * W.ncell  # one flag byte per cell
+
+
+def test_wall_boundaries_validated(lib):
+    from paper_2303_03026_gb300 import amrvac
+    W = wl.c3_turbulence(n=32, bnx=16, precision="fp32")
+    W.cfg.bc = (("symmetric", "symmetric"), ("symmetric", "outflow"), ("periodic", "periodic"))
+    assert _bytes(lib, W, kernel="fused")[0] == 0   # walls run on the fused kernels too
+    assert _bytes(lib, W, kernel="plain")[0] == 0
+    c = amrvac.make_config(W.cfg, "plain")
+    ins = amrvac.make_instances(W.instances)
+    meta = np.ascontiguousarray(W.block_meta, np.int32)
+    n = C.c_size_t(0)
+    for d, side, value in ((0, 0, 3), (1, 1, -1), (2, 0, 1)):
+        c2 = amrvac.make_config(W.cfg, "plain")
+        c2.bc[d][side] = value   # out of range, or periodic on one side only
+        st = lib.amrvac_workspace_bytes(C.byref(c2), 1, ins, meta.shape[0], meta.ctypes.data,
+                                        C.byref(n))
+        assert st == 1, (d, side, value)
+    assert lib.amrvac_workspace_bytes(C.byref(c), 1, ins, meta.shape[0], meta.ctypes.data,
+                                      C.byref(n)) == 0
