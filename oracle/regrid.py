@@ -20,8 +20,9 @@ the readings of the library:
   * plan: refined blocks, then every block closer than one block (faces, edges,
     corners) to a block two levels finer is refined too until the mesh is 2:1
     balanced; a family of 2^d sibling leaves is coarsened only when all of
-    them ask for it, none is refined, and the parent would stay 2:1 balanced;
-    the new list is sorted by (instance, level, k, j, i);
+    them ask for it, none is refined, and the parent would stay 2:1 balanced,
+    families tried in (instance, level, k, j, i) order of the parent; the new
+    list is sorted by (instance, level, k, j, i);
   * transfer: a block kept is copied; a refined block's children get the
     coarse value plus minmod-limited slopes times +-1/4 (the slopes from the
     block's own neighbours at its level, ghost values across its faces); a
@@ -116,6 +117,13 @@ def flags(E, meta, refine_threshold, derefine_ratio, max_level):
         elif e < derefine_ratio * refine_threshold and L > 0:
             f[b] = -1
     return f
+
+
+def block_order(key):
+    """Sort key of a block (instance, level, i, j, k): instance, level, then
+    k, j, i (the last index fastest, like cells in a block)."""
+    q, L, i, j, k = key
+    return (q, L, k, j, i)
 
 
 def plan(cfg, instances, meta, fl):
@@ -220,7 +228,7 @@ def plan(cfg, instances, meta, fl):
                 best = max(best, lev)
         return best
 
-    for par in sorted(parents):
+    for par in sorted(parents, key=block_order):
         kids = parents[par]
         if len(kids) != nchild or any(c not in newset for c in kids):
             continue
@@ -228,7 +236,7 @@ def plan(cfg, instances, meta, fl):
         q, L, i, j, k = par
         if finest_near(trial, q, L, i, j, k) <= L + 1:
             newset = trial
-    return np.array(sorted(newset), np.int32)
+    return np.array(sorted(newset, key=block_order), np.int32)
 
 
 def transfer(cfg, instances, old_meta, Uold, orc_mesh, new_meta, only=None):

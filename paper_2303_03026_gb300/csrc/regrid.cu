@@ -19,7 +19,7 @@
 #include <array>
 #include <cmath>
 #include <map>
-#include <set>
+#include <unordered_set>
 #include <vector>
 
 #include "ghost.cuh"
@@ -315,6 +315,26 @@ __global__ void __launch_bounds__(256) k_regrid_transfer(DevMesh Ms, const T* __
 
 using Key = std::array<int, 5>;  // instance, level, i, j, k
 
+struct KeyHash {  // FNV-1a over the five ints
+  size_t operator()(const Key& k) const {
+    uint64_t h = 1469598103934665603ull;
+    for (int v : k) {
+      h ^= (uint32_t)v;
+      h *= 1099511628211ull;
+    }
+    return (size_t)h;
+  }
+};
+using KeySet = std::unordered_set<Key, KeyHash>;
+
+// (instance, level, k, j, i) order: the last block index fastest
+struct KeyBlockOrder {
+  bool operator()(const Key& a, const Key& b) const {
+    const std::array<int, 5> x{a[0], a[1], a[4], a[3], a[2]}, y{b[0], b[1], b[4], b[3], b[2]};
+    return x < y;
+  }
+};
+
 struct Planner {
   int nd;
   bool periodic[3];
@@ -346,7 +366,7 @@ struct Planner {
 
   // level of the leaf of s covering level-L position p (walking up), -1 when
   // finer leaves cover it
-  static int covering(const std::set<Key>& s, int q, int L, std::array<int, 3> p) {
+  static int covering(const KeySet& s, int q, int L, std::array<int, 3> p) {
     for (int LL = L; LL >= 0; LL--) {
       if (s.count(Key{q, LL, p[0], p[1], p[2]})) return LL;
       for (int d = 0; d < 3; d++) p[d] >>= 1;
@@ -365,7 +385,7 @@ struct Planner {
   }
 
   // deepest leaf level of s around the parent position (q, L, i, j, k)
-  int finest_near(const std::set<Key>& s, int q, int L, int i, int j, int k) const {
+  int finest_near(const KeySet& s, int q, int L, int i, int j, int k) const {
     int best = L;
     for (const auto& p : neighbours(q, L, i, j, k)) {
       const int lev = covering(s, q, L, p);
@@ -403,7 +423,9 @@ extern "C" amrvac_status amrvac_regrid_plan(const amrvac_config* cfg, int32_t ni
   for (int d = 0; d < 3; d++) P.periodic[d] = cfg->bc[d][0] == AMRVAC_BC_PERIODIC;
   for (int q = 0; q < ninst; q++)
     P.base.push_back({inst[q].base_blocks[0], inst[q].base_blocks[1], inst[q].base_blocks[2]});
-  std::set<Key> cur, refine, want;
+  KeySet cur, refine;
+  std::vector<Key> want;
+  cur.reserve((size_t)nblocks * 2);
   for (int b = 0; b < nblocks; b++) {
     const int32_t* r = block_meta + 5 * b;
     const Key k{r[0], r[1], r[2], P.nd > 1 ? r[3] : 0, P.nd > 2 ? r[4] : 0};
@@ -413,7 +435,7 @@ extern "C" amrvac_status amrvac_regrid_plan(const amrvac_config* cfg, int32_t ni
       if (r[1] + 1 >= AMRVAC_MAX_LEVELS) return AMRVAC_E_INVALID;
       refine.insert(k);
     }
-    if (flags[b] == -1 && r[1] > 0) want.insert(k);
+    if (flags[b] == -1 && r[1] > 0) want.push_back(k);
   }
   // 2:1 closure of the splits: a split level-L leaf forces every coarser
   // leaf around it to split too
@@ -431,7 +453,8 @@ extern "C" amrvac_status amrvac_regrid_plan(const amrvac_config* cfg, int32_t ni
       if (refine.insert(c).second) todo.push_back(c);
     }
   }
-  std::set<Key> next;
+  KeySet next;
+  next.reserve(cur.size() + refine.size() * ((size_t)1 << P.nd));
   for (const Key& k : cur) {
     if (refine.count(k)) {
       for (const Key& c : P.children(k)) next.insert(c);
@@ -439,8 +462,9 @@ extern "C" amrvac_status amrvac_regrid_plan(const amrvac_config* cfg, int32_t ni
       next.insert(k);
     }
   }
-  // merges: complete families asking for it, in increasing parent order
-  std::map<Key, std::vector<Key>> parents;
+  // merges: complete families asking for it, parents in (instance, level,
+  // k, j, i) order
+  std::map<Key, std::vector<Key>, KeyBlockOrder> parents;
   for (const Key& k : want) {
     if (refine.count(k)) continue;
     parents[Key{k[0], k[1] - 1, k[2] >> 1, k[3] >> 1, k[4] >> 1}].push_back(k);
@@ -463,11 +487,10 @@ extern "C" amrvac_status amrvac_regrid_plan(const amrvac_config* cfg, int32_t ni
   }
   *new_nblocks = (int32_t)next.size();
   if ((size_t)capacity < next.size()) return AMRVAC_E_INVALID;
-  size_t b = 0;
-  for (const Key& k : next) {
-    for (int e = 0; e < 5; e++) new_meta[5 * b + e] = k[e];
-    b++;
-  }
+  std::vector<Key> out(next.begin(), next.end());
+  std::sort(out.begin(), out.end(), KeyBlockOrder());
+  for (size_t b = 0; b < out.size(); b++)
+    for (int e = 0; e < 5; e++) new_meta[5 * b + e] = out[b][e];
   return AMRVAC_OK;
 }
 

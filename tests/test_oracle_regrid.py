@@ -170,7 +170,8 @@ def test_plan_identity_and_counts():
     inst = W.instances[0]
     nb = W.nblocks
     same = rg.plan(W.cfg, W.instances, W.block_meta, np.zeros(nb, np.int32))
-    assert np.array_equal(same, np.array(sorted(map(tuple, W.block_meta)), np.int32))
+    assert np.array_equal(same, np.array(sorted(map(tuple, W.block_meta), key=rg.block_order),
+                                         np.int32))
     # split one level-1 block whose neighbours are all level >= 1: +3 blocks
     f = np.zeros(nb, np.int32)
     b = [i for i, r in enumerate(W.block_meta) if r[1] == 1][0]
@@ -185,7 +186,7 @@ def test_plan_identity_and_counts():
     assert len(ones) == 4 * len(base) and np.all(ones[:, 1] == 1)
     back = rg.plan(W.cfg, [wl.Instance(base_blocks=(3, 2, 1))], ones,
                    -np.ones(len(ones), np.int32))
-    assert np.array_equal(back, np.array(sorted(map(tuple, base)), np.int32))
+    assert np.array_equal(back, np.array(sorted(map(tuple, base), key=rg.block_order), np.int32))
     # one sibling not asking: that family stays
     f = -np.ones(len(ones), np.int32)
     f[0] = 0
