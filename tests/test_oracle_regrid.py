@@ -381,3 +381,19 @@ def test_library_plan_level_limit():
     got = amrvac.regrid_plan(cfg, inst, meta, f)
     assert np.array_equal(got, rg.plan(cfg, inst, meta, f.astype(np.int32)))
     _check_mesh(cfg, inst[0], got)
+
+
+def test_library_plan_at_full_3d_size():
+    # the 3D AMR blast mesh of the benchmark (18,304 blocks over 4 levels) with
+    # random flags: the library's plan equals the oracle's and is a 2:1-balanced
+    # tiling of the domain
+    from paper_2303_03026_gb300 import amrvac, build
+    build.build()
+    W = wl.c4_blast_amr(base=6, precision="fp32")
+    rng = np.random.Generator(np.random.PCG64(3))
+    f = rng.integers(-1, 2, W.nblocks).astype(np.int8)
+    f[(W.block_meta[:, 1] == 0) & (f == -1)] = 0
+    got = amrvac.regrid_plan(W.cfg, W.instances, W.block_meta, f)
+    assert np.array_equal(got, rg.plan(W.cfg, W.instances, W.block_meta, f.astype(np.int32)))
+    _check_mesh(W.cfg, W.instances[0], got)
+    assert len(got) > W.nblocks
