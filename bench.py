@@ -9,8 +9,10 @@ recovery, HLLD + vanleer, glm.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Prints one JSON line (rank 0).  Under torchrun each rank advances its own
-replica (the update shards by block but the halo exchange between GPUs is not
-built, so N > 1 runs independent replicas: weak scaling).
+replica of a single-domain workload (the update shards by block but the halo
+exchange between GPUs is not built: weak scaling); the batched independent
+instances (--workload c5) are partitioned over the ranks instead (no exchange:
+strong scaling).
 """
 from __future__ import annotations
 
