@@ -4,8 +4,10 @@ and coarsened automatically on chosen plasma quantities).
 TEST INFRASTRUCTURE ONLY (like the rest of oracle/): plain numpy loops over
 blocks and cells, no code shared with the GPU library.
 
-The paper names the capability but no criterion or operator, so this follows
-the readings of the library:
+The paper names the capability (automatic (de)refinement on weighted,
+user-chosen plasma quantities, Sect. 1 and 3) but prints no criterion or
+operator.  This restates the published methods below, with these readings of
+the paper where it is silent:
   * estimator (Loehner 1987, the normalised second derivative, per direction):
       E_i(q) = sqrt( sum_d (q_{i+1} - 2 q_i + q_{i-1})^2 /
                      sum_d (|q_{i+1} - q_i| + |q_i - q_{i-1}|
@@ -21,7 +23,8 @@ the readings of the library:
     corners) to a block two levels finer is refined too until the mesh is 2:1
     balanced; a family of 2^d sibling leaves is coarsened only when all of
     them ask for it, none is refined, and the parent would stay 2:1 balanced,
-    families tried in (instance, level, k, j, i) order of the parent; the new
+    families tried in (instance, level, k, j, i) order of the parent and one
+    level per regrid (a deterministic order: the paper gives none); the new
     list is sorted by (instance, level, k, j, i);
   * transfer: a block kept is copied; a refined block's children get the
     coarse value plus minmod-limited slopes times +-1/4 (the slopes from the
