@@ -352,6 +352,10 @@ def main():
         return run_reference(args)
     import torch
     ws, rank, local = dist_env()
+    if args.workload == "c5" and ws > 1:
+        # every rank refuses an empty shard before any collective
+        from paper_2303_03026_gb300 import shard
+        shard.check_ranks(args.size or 256, ws)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if ws > 1:

@@ -56,6 +56,9 @@ extern "C" {
 #define AMRVAC_NVAR 9
 #define AMRVAC_MAX_LEVELS 16
 #define AMRVAC_NOALLOC_MAX_BLOCKS 65536
+/* largest block: interior cells per block (product of block_nx over the active
+ * dimensions, each 4..4096); larger blocks are rejected with AMRVAC_E_INVALID */
+#define AMRVAC_MAX_BLOCK_CELLS (1 << 24)
 
 typedef enum {
   AMRVAC_OK = 0,
@@ -145,8 +148,9 @@ typedef enum { AMRVAC_FIX_OFF = 0, AMRVAC_FIX_REPLACE = 1, AMRVAC_FIX_AVERAGE = 
 
 typedef struct {
   int32_t ndim;           /* 1, 2 or 3                                          */
-  int32_t block_nx[3];    /* interior cells per block and dimension (>= 4 in
-                             active dims; entries of unused dims are ignored)  */
+  int32_t block_nx[3];    /* interior cells per block and dimension (4..4096 in
+                             active dims, at most AMRVAC_MAX_BLOCK_CELLS cells
+                             per block; entries of unused dims are ignored)    */
   int32_t flux;           /* amrvac_flux                                        */
   int32_t limiter;        /* amrvac_limiter                                     */
   int32_t time;           /* amrvac_time                                        */
@@ -318,8 +322,12 @@ amrvac_status amrvac_get_diag(amrvac_state* s, double* h_t, double* h_dt, double
  * (1 MiB) that every device loading the library holds until exit.  More blocks
  * than AMRVAC_NOALLOC_MAX_BLOCKS: AMRVAC_E_INVALID.  The first call on a device
  * looks up the array's device address with cudaGetSymbolAddress (make it
- * before any stream capture).  Calls share the array: calls overlapping on
- * the GPU race.  No allocation of any kind is made.
+ * before any stream capture).  The looked-up address is kept per device for
+ * the life of the process: after cudaDeviceReset on a device it is stale, so
+ * do not call this entry point on that device again.  Calls share the array:
+ * calls overlapping on the GPU race.  A block larger than
+ * AMRVAC_MAX_BLOCK_CELLS: AMRVAC_E_INVALID.  No allocation of any kind is
+ * made.
  */
 amrvac_status amrvac_cfl_dt_noalloc(const amrvac_config* cfg, const amrvac_instance_desc* inst,
                                     int32_t nblocks, const void* d_U, double t, double* d_out,

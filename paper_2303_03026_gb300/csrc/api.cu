@@ -34,8 +34,12 @@ struct Layout {
 bool config_ok(const amrvac_config* c, std::string& err) {
   if (!c) return err = "null config", false;
   if (c->ndim < 1 || c->ndim > 3) return err = "ndim must be 1..3", false;
-  for (int d = 0; d < c->ndim; d++)
+  long long cells = 1;  // 64-bit: 4096^3 overflows an int
+  for (int d = 0; d < c->ndim; d++) {
     if (c->block_nx[d] < 4 || c->block_nx[d] > 4096) return err = "block_nx must be 4..4096", false;
+    cells *= c->block_nx[d];
+  }
+  if (cells > AMRVAC_MAX_BLOCK_CELLS) return err = "block larger than AMRVAC_MAX_BLOCK_CELLS", false;
   if (c->flux < AMRVAC_FLUX_HLL || c->flux > AMRVAC_FLUX_HLLC) return err = "bad flux", false;
   if (c->limiter < AMRVAC_LIM_MINMOD || c->limiter > AMRVAC_LIM_WENOZ5)
     return err = "bad limiter", false;

@@ -14,7 +14,8 @@
 // exits.  Host code cannot use the array's name as a device address, so the
 // first call on each device looks the address up with cudaGetSymbolAddress
 // (with that device current) and caches it; that first call on a device should
-// therefore come before any stream capture.  All calls share the array: calls
+// therefore come before any stream capture, and the cached address is stale
+// once the caller resets that device (cudaDeviceReset).  All calls share the array: calls
 // that overlap on the GPU (other streams, other host threads) race on it.
 // Every slot a call reads is written by the same call first, so nothing has to
 // be cleared between calls.
@@ -141,7 +142,7 @@ extern "C" amrvac_status amrvac_cfl_dt_noalloc(const amrvac_config* cfg,
   if (cfg->precision != AMRVAC_FP64 && cfg->precision != AMRVAC_FP32_BULK) return AMRVAC_E_INVALID;
   if (!(cfg->courant > 0.0) || !(inst->gamma > 1.0)) return AMRVAC_E_INVALID;
   if (nblocks < 1 || nblocks > AMRVAC_NOALLOC_MAX_BLOCKS) return AMRVAC_E_INVALID;
-  long long blocks = 1;
+  long long blocks = 1, cells = 1;  // 64-bit products: 4096^3 overflows an int
   DevMesh M{};
   M.ndim = cfg->ndim;
   double dx[3] = {1.0, 1.0, 1.0};
@@ -153,10 +154,12 @@ extern "C" amrvac_status amrvac_cfl_dt_noalloc(const amrvac_config* cfg,
         return AMRVAC_E_INVALID;
       if (!(inst->xmax[d] > inst->xmin[d])) return AMRVAC_E_INVALID;
       blocks *= inst->base_blocks[d];
+      cells *= cfg->block_nx[d];
       dx[d] = (inst->xmax[d] - inst->xmin[d]) / ((double)inst->base_blocks[d] * cfg->block_nx[d]);
     }
   }
   if (blocks != nblocks) return AMRVAC_E_INVALID;  // one uniform level-0 instance only
+  if (cells > AMRVAC_MAX_BLOCK_CELLS) return AMRVAC_E_INVALID;
   M.ncell = M.nx[0] * M.nx[1] * M.nx[2];
   M.nblocks = nblocks;
   M.ninst = 1;

@@ -18,11 +18,22 @@ import numpy as np
 from . import workloads as wl
 
 
+def check_ranks(n_instances, nranks):
+    """Refuses a partition that would leave a rank without an instance (more
+    ranks than instances).  Every rank evaluates this from its own inputs
+    before any collective, so all ranks stop together instead of the empty
+    one failing while the others wait in a barrier."""
+    if nranks < 1:
+        raise ValueError("nranks must be >= 1")
+    if nranks > n_instances:
+        raise ValueError("%d ranks for %d independent instances: every rank needs at "
+                         "least one instance" % (nranks, n_instances))
+
+
 def partition_instances(cells_per_instance, nranks):
     """Instance indices of each rank (ascending), balanced by cells."""
     cells = [int(c) for c in cells_per_instance]
-    if nranks < 1:
-        raise ValueError("nranks must be >= 1")
+    check_ranks(len(cells), nranks)
     order = sorted(range(len(cells)), key=lambda q: (-cells[q], q))
     load = [0] * nranks
     parts = [[] for _ in range(nranks)]

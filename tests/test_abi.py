@@ -72,6 +72,16 @@ def test_workspace_bytes_and_mesh_validation(lib):
     assert _bytes(lib, unbalanced)[0] == 1
     W.cfg.courant = -1.0
     assert _bytes(lib, W)[0] == 1
+    # one 4096^3 block: 2^36 cells overflow a 32-bit count; rejected, not wrapped
+    big = wl.Workload("big", wl.Config(ndim=3, block_nx=(4096, 4096, 4096)),
+                      [wl.Instance(base_blocks=(1, 1, 1))], np.zeros((1, 5), np.int32),
+                      np.zeros((9, 1, 1)))
+    assert _bytes(lib, big)[0] == 1
+    # the largest accepted block: 4096^2 cells in 2D
+    ok2 = wl.Workload("ok2", wl.Config(ndim=2, block_nx=(4096, 4096, 1)),
+                      [wl.Instance(base_blocks=(1, 1, 1))], np.zeros((1, 5), np.int32),
+                      np.zeros((9, 1, 1)))
+    assert _bytes(lib, ok2)[0] == 0
 
 
 def test_workspace_matches_precision(lib):

@@ -123,3 +123,37 @@ def test_ranks_agree_on_the_partition_gloo_world2():
     assert seen0 == seen1                                 # same view on both ranks
     assert seen0[0][0] == seen0[1][0]                      # computed independently, equal
     assert seen0[0][1] + seen0[1][1] == _c5(32).interior_cells()
+
+
+def _empty_shard_worker(rank, world, port, out):
+    import sys
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    from paper_2303_03026_gb300 import shard
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    W = _c5(1)
+    # the check runs on every rank before the process group exists: no rank
+    # is left waiting in a collective for one that failed
+    try:
+        shard.check_ranks(len(W.instances), world)
+        out[rank] = "accepted"
+    except ValueError as e:
+        out[rank] = "refused: " + str(e)
+        return
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_more_ranks_than_instances_refused_on_every_rank_gloo_world2():
+    port = _free_port()
+    mgr = mp.Manager()
+    out = mgr.dict()
+    mp.spawn(_empty_shard_worker, args=(2, port, out), nprocs=2, join=True)
+    assert out[0].startswith("refused") and out[1].startswith("refused")
+    import sys
+    sys.path.insert(0, ROOT)
+    from paper_2303_03026_gb300 import shard
+    with pytest.raises(ValueError):
+        shard.partition_instances([100], 2)
+    assert shard.partition_instances([100, 50], 2) == [[0], [1]]
