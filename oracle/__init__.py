@@ -83,7 +83,7 @@ def lib():
             L.orc_fast_speed.restype = C.c_double
             L.orc_fast_speed.argtypes = [C.c_double, dp, C.c_int]
             L.orc_reconstruct.argtypes = [C.c_int, dp, C.c_int, dp, dp]
-            L.orc_reconstruct5.argtypes = [C.c_int, dp, C.c_int, dp, dp]
+            L.orc_reconstruct5.argtypes = [C.c_int, dp, C.c_int, C.c_double, dp, dp]
             L.orc_ghost_width.argtypes = [C.c_void_p]
             L.orc_ghost_width.restype = C.c_int
             L.orc_face_flux.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_int,
@@ -101,7 +101,8 @@ def lib():
 
 _FLUX = {"hll": 0, "hlld": 1, "tvdlf": 2, "hllc": 3}
 _LIM = {"minmod": 0, "vanleer": 1, "koren": 2, "superbee": 3, "woodward": 4, "mcbeta": 5,
-        "albada": 6, "mp5": 7, "weno5": 8, "wenoz5": 9}
+        "albada": 6, "mp5": 7, "weno5": 8, "wenoz5": 9, "cada3": 10, "wenozp5": 11}
+_FIVE = (7, 8, 9, 11)
 _TIME = {"ssprk2": 0, "ssprk3": 1, "ssprk43": 2, "ssprk54": 3}
 _BC = {"periodic": 0, "outflow": 1, "symmetric": 2}
 _FIX = {"off": 0, "replace": 1, "average": 2}
@@ -267,13 +268,16 @@ def fast_speed(gamma, w, d):
     return lib().orc_fast_speed(gamma, np.ascontiguousarray(w, np.float64), d)
 
 
-def reconstruct(limiter, w):
+def reconstruct(limiter, w, dx=1.0):
+    """Face states of a 1D row of cell values: wl[i] at i+1/2 and wr[i] at
+    i-1/2 (NaN where the stencil leaves the row); dx: the cell width, used by
+    wenozp5 only."""
     w = np.ascontiguousarray(w, np.float64)
     wl = np.full_like(w, np.nan)
     wr = np.full_like(w, np.nan)
     lim = _LIM[limiter]
-    if lim >= 7:
-        lib().orc_reconstruct5(lim, w, w.shape[0], wl, wr)
+    if lim in _FIVE:
+        lib().orc_reconstruct5(lim, w, w.shape[0], float(dx), wl, wr)
     else:
         lib().orc_reconstruct(lim, w, w.shape[0], wl, wr)
     return wl, wr

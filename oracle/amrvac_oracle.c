@@ -17,8 +17,10 @@
  *    default) with the two-ghost-cell limiters `minmod`, `vanleer`, `koren`,
  *    `superbee`, `woodward`, `mcbeta` (beta = 1.4) and `albada` of the limiter
  *    table (order 3 for koren, 2 for the others); albada in its TVD form
- *    (zero slope at extrema, like the others); and the three-ghost-cell
- *    five-point `mp5`, `weno5` and `wenoz5` (see mp5_plus, weno5_plus).
+ *    (zero slope at extrema, like the others); `cada3` (Cada & Torrilhon
+ *    2009, third order, two ghost cells, see cada3_phi); and the
+ *    three-ghost-cell five-point `mp5`, `weno5`, `wenoz5` and `wenozp5` (see
+ *    mp5_plus, weno5_plus).
  *  - a face whose reconstructed density or pressure is not positive falls back
  *    to first order (cell values) on both sides (Sect. 7.4 mentions checks on
  *    reconstructions; the fallback form is our reading).
@@ -219,9 +221,27 @@ static double sym_slope(int lim, double dm, double dp) {
   }
 }
 
+/* 10 cada3 (Cada & Torrilhon 2009, the compact third-order limiter LimO3):
+ * with theta = dm/dp and the third-order (kappa = 1/3) polynomial
+ * phi3 = (2 + theta)/3,
+ *   phi(theta) = max(0, min(phi3, max(-theta/2, min(2 theta, phi3, 1.6)))),
+ * and the face value b + phi(theta) dp / 2 (b where dp = 0, the limit of
+ * phi dp).  Unlike the TVD limiters it keeps a slope at extrema (theta < 0),
+ * where it follows phi3 as long as phi3 <= -theta/2. */
+static double cada3_phi(double theta) {
+  const double p3 = (2.0 + theta) / 3.0;
+  return dmax(0.0, dmin(p3, dmax(-0.5 * theta, dmin(dmin(2.0 * theta, p3), 1.6))));
+}
+
+static double cada3_face(double dm, double dp) {
+  if (dp == 0.0) return 0.0;
+  return 0.5 * cada3_phi(dm / dp) * dp;
+}
+
 /* left state at the right face (i+1/2) of the cell with values (a, b, c) */
 static double recon_plus(int lim, double a, double b, double c) {
   double dm = b - a, dp = c - b;
+  if (lim == 10) return b + cada3_face(dm, dp);
   if (!(dm * dp > 0.0)) return b;
   if (lim >= 3) return b + 0.5 * sym_slope(lim, dm, dp);
   switch (lim) {
@@ -239,6 +259,8 @@ static double recon_plus(int lim, double a, double b, double c) {
 /* right state at the left face (i-1/2) of the cell with values (a, b, c) */
 static double recon_minus(int lim, double a, double b, double c) {
   double dm = b - a, dp = c - b;
+  /* cada3: the same rule on the mirrored stencil (c, b, a) */
+  if (lim == 10) return b + cada3_face(-dp, -dm);
   if (!(dm * dp > 0.0)) return b;
   if (lim >= 3) return b - 0.5 * sym_slope(lim, dm, dp);
   switch (lim) {
@@ -273,7 +295,12 @@ void orc_reconstruct(int limiter, const double* w, int n, double* wl, double* wr
  *     (1, 6, 3)/10, alpha_k = d_k / (eps + beta_k)^2, eps = 1e-6.
  *   9 wenoz5 (Borges et al. 2008): the same candidates with
  *     alpha_k = d_k (1 + tau5 / (beta_k + eps)), tau5 = |beta_0 - beta_2|,
- *     exponent 1, eps = 1e-40. */
+ *     exponent 1, eps = 1e-40.
+ *  11 wenozp5 (WENO-Z+, Acker, Borges & Costa 2016): the same candidates with
+ *     alpha_k = d_k (1 + (tau5 / (beta_k + eps))^2
+ *                      + lambda (beta_k + eps) / (tau5 + eps)),
+ *     eps = 1e-40, lambda = dx^(2/3) with dx the cell width along the
+ *     reconstruction (the value the authors recommend). */
 static double minmod4(double w, double x, double y, double z) {
   if (w > 0.0 && x > 0.0 && y > 0.0 && z > 0.0) return dmin(dmin(w, x), dmin(y, z));
   if (w < 0.0 && x < 0.0 && y < 0.0 && z < 0.0) return dmax(dmax(w, x), dmax(y, z));
@@ -300,7 +327,9 @@ static double mp5_plus(const double* v) {
   return vor + minmod2(vmin - vor, vmax - vor);
 }
 
-static double weno5_plus(int z, const double* v) {
+/* kind: 0 weno5, 1 wenoz5, 2 wenozp5; dx: cell width along the
+ * reconstruction (wenozp5's lambda) */
+static double weno5_plus(int kind, const double* v, double dx) {
   const double vm2 = v[0], vm1 = v[1], v0 = v[2], vp1 = v[3], vp2 = v[4];
   const double c13 = 13.0 / 12.0;
   const double t0 = vm2 - 2.0 * vm1 + v0, u0 = vm2 - 4.0 * vm1 + 3.0 * v0;
@@ -313,7 +342,16 @@ static double weno5_plus(int z, const double* v) {
   const double q1 = (-vm1 + 5.0 * v0 + 2.0 * vp1) / 6.0;
   const double q2 = (2.0 * v0 + 5.0 * vp1 - vp2) / 6.0;
   double a0, a1, a2;
-  if (z) {
+  if (kind == 2) {
+    /* WENO-Z+ (Acker, Borges & Costa 2016): the Z weights with exponent 2
+     * plus lambda (beta_k + eps)/(tau5 + eps), which raises the weight of
+     * the less smooth candidates; lambda = dx^(2/3) */
+    const double eps = 1e-40, tau = fabs(b0 - b2), lam = pow(dx, 2.0 / 3.0);
+    const double r0 = tau / (b0 + eps), r1 = tau / (b1 + eps), r2 = tau / (b2 + eps);
+    a0 = 0.1 * (1.0 + r0 * r0 + lam * (b0 + eps) / (tau + eps));
+    a1 = 0.6 * (1.0 + r1 * r1 + lam * (b1 + eps) / (tau + eps));
+    a2 = 0.3 * (1.0 + r2 * r2 + lam * (b2 + eps) / (tau + eps));
+  } else if (kind == 1) {
     const double eps = 1e-40, tau = fabs(b0 - b2);
     a0 = 0.1 * (1.0 + tau / (b0 + eps));
     a1 = 0.6 * (1.0 + tau / (b1 + eps));
@@ -328,22 +366,25 @@ static double weno5_plus(int z, const double* v) {
   return (a0 * q0 + a1 * q1 + a2 * q2) / sa;
 }
 
-static double recon5_plus(int lim, const double* v) {
-  return lim == 7 ? mp5_plus(v) : weno5_plus(lim == 9, v);
+static double recon5_plus(int lim, const double* v, double dx) {
+  return lim == 7 ? mp5_plus(v) : weno5_plus(lim == 9 ? 1 : (lim == 11 ? 2 : 0), v, dx);
 }
 
 /* right state at i-1/2 of cell i from v = (v_{i-2}, ..., v_{i+2}) */
-static double recon5_minus(int lim, const double* v) {
+static double recon5_minus(int lim, const double* v, double dx) {
   const double r[5] = {v[4], v[3], v[2], v[1], v[0]};
-  return recon5_plus(lim, r);
+  return recon5_plus(lim, r, dx);
 }
 
-void orc_reconstruct5(int limiter, const double* w, int n, double* wl, double* wr) {
+void orc_reconstruct5(int limiter, const double* w, int n, double dx, double* wl, double* wr) {
   for (int i = 2; i + 2 < n; i++) {
-    wl[i] = recon5_plus(limiter, w + i - 2);
-    wr[i] = recon5_minus(limiter, w + i - 2);
+    wl[i] = recon5_plus(limiter, w + i - 2, dx);
+    wr[i] = recon5_minus(limiter, w + i - 2, dx);
   }
 }
+
+/* the five-point limiters (three ghost cells): mp5, weno5, wenoz5, wenozp5 */
+static int five_point(int lim) { return lim == 7 || lim == 8 || lim == 9 || lim == 11; }
 
 int orc_ghost_width(const orc_mesh* m) { return m->ng; }
 
@@ -785,14 +826,14 @@ orc_mesh* orc_create(const orc_config* cfg, int ninst, const orc_instance* inst,
   m->nblocks = nblocks;
   m->nthreads = 1;
   if (cfg->ndim < 1 || cfg->ndim > 3) FAIL("ndim must be 1..3");
-  if (cfg->limiter < 0 || cfg->limiter > 9) FAIL("limiter must be 0..9");
+  if (cfg->limiter < 0 || cfg->limiter > 11) FAIL("limiter must be 0..11");
   for (int d = 0; d < cfg->ndim; d++)
     for (int side = 0; side < 2; side++)
       if (cfg->bc[d][side] < 0 || cfg->bc[d][side] > 2) FAIL("bc must be 0..2");
-  m->ng = cfg->limiter >= 7 ? NG5 : NG;
+  m->ng = five_point(cfg->limiter) ? NG5 : NG;
   for (int L = 0; L < 16; L++) {
-    if (cfg->level_limiter[L] > 9) FAIL("level_limiter must be -1..9");
-    if (cfg->level_limiter[L] >= 7) m->ng = NG5;
+    if (cfg->level_limiter[L] > 11) FAIL("level_limiter must be -1..11");
+    if (cfg->level_limiter[L] >= 0 && five_point(cfg->level_limiter[L])) m->ng = NG5;
   }
   for (int d = 0; d < 3; d++) {
     if (d >= cfg->ndim) m->cfg.nx[d] = 1;
@@ -1068,6 +1109,8 @@ static int block_stage(const orc_mesh* m, int b, int k, const double* dtv, const
   const int flux = m->cfg.level_flux[B->level] >= 0 ? m->cfg.level_flux[B->level] : m->cfg.flux;
   const int lim =
       m->cfg.level_limiter[B->level] >= 0 ? m->cfg.level_limiter[B->level] : m->cfg.limiter;
+  double dxl[3]; /* this level's cell widths (wenozp5's lambda) */
+  cell_dx(m, B->inst, B->level, dxl);
   for (int d = 0; d < m->cfg.ndim; d++) {
     int ext[3] = {nx[0], nx[1], nx[2]};
     ext[d] += 1;
@@ -1085,9 +1128,9 @@ static int block_stage(const orc_mesh* m, int b, int k, const double* dtv, const
               cc[d] += t - 3;
               s[t] = W[v * pi.np + pidx(&pi, cc[0], cc[1], cc[2])];
             }
-            if (lim >= 7) {
-              wl[v] = recon5_plus(lim, s);
-              wr[v] = recon5_minus(lim, s + 1);
+            if (five_point(lim)) {
+              wl[v] = recon5_plus(lim, s, dxl[d]);
+              wr[v] = recon5_minus(lim, s + 1, dxl[d]);
             } else {
               wl[v] = recon_plus(lim, s[1], s[2], s[3]);
               wr[v] = recon_minus(lim, s[2], s[3], s[4]);

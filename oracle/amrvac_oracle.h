@@ -32,8 +32,8 @@ typedef struct {
   int nx[3];             /* cells per block per dimension (1 for unused dims) */
   int flux;              /* 0 hll, 1 hlld, 2 tvdlf, 3 hllc */
   int limiter;           /* 0 minmod, 1 vanleer, 2 koren, 3 superbee, 4 woodward,
-                            5 mcbeta, 6 albada; 7 mp5, 8 weno5, 9 wenoz5 (five-
-                            point, 3 ghost cells) */
+                            5 mcbeta, 6 albada, 10 cada3; 7 mp5, 8 weno5,
+                            9 wenoz5, 11 wenozp5 (five-point, 3 ghost cells) */
   int time;              /* 0 ssprk(2,2), 1 ssprk(3,3), 2 ssprk(4,3), 3 ssprk(5,4) */
   int glm;               /* 1: Dedner glm cleaning; 0: none (psi stays 0) */
   double glm_alpha;      /* psi damping parameter alpha_p */
@@ -123,8 +123,9 @@ double orc_fast_speed(double gamma, const double* w, int dir);
 /* reconstruction of a 1D array: left state at i+1/2 (wl[i]) and right state at
  * i-1/2 (wr[i]) from cell i, for 1 <= i <= n-2 */
 void orc_reconstruct(int limiter, const double* w, int n, double* wl, double* wr);
-/* the same for the five-point limiters (7..9), for 2 <= i <= n-3 */
-void orc_reconstruct5(int limiter, const double* w, int n, double* wl, double* wr);
+/* the same for the five-point limiters (7, 8, 9, 11), for 2 <= i <= n-3; dx:
+ * the cell width (wenozp5's lambda = dx^(2/3)) */
+void orc_reconstruct5(int limiter, const double* w, int n, double dx, double* wl, double* wr);
 /* face flux along dir from primitive face states (global frame) */
 void orc_face_flux(int flux, int glm, double gamma, double ch, int dir,
                    const double* wl, const double* wr, double* f);

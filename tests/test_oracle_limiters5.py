@@ -1,5 +1,5 @@
 """Pins of the oracle's five-point limiters of the limiter table (mp5, weno5,
-wenoz5; three ghost cells) against facts fixed by their definitions: exact
+wenoz5, wenozp5; three ghost cells) against facts fixed by their definitions: exact
 interface values of quadratics (any convex combination of the exact
 third-order candidates) and, for mp5's fifth-order interface polynomial, of
 monotone quartics; measured fifth order on smooth monotone data; no new
@@ -12,7 +12,7 @@ import pytest
 
 from paper_2303_03026_gb300 import workloads as wl
 
-LIMS5 = ["mp5", "weno5", "wenoz5"]
+LIMS5 = ["mp5", "weno5", "wenoz5", "wenozp5"]
 
 
 def _averages(F, n, x0=0.0, x1=1.0):
@@ -130,12 +130,14 @@ def _wave_error(orc, n, lim):
 
 @pytest.mark.parametrize("lim", LIMS5)
 def test_density_wave_converges_third_order(orc, lim):
-    # SSPRK3 at a fixed Courant number caps the order at 3; vanleer gives 2
-    e = [_wave_error(orc, n, lim) for n in (32, 64, 128)]
-    orders = np.log2(np.array(e[:-1]) / np.array(e[1:]))
-    assert orders[-1] > 2.7, (lim, e, orders)
+    # SSPRK3 at a fixed Courant number caps the order at 3; vanleer gives 2.
+    # The five-point spatial error is so small that it can cancel against the
+    # time error at one resolution, so the order is taken over 32 -> 256.
+    e = [_wave_error(orc, n, lim) for n in (32, 64, 128, 256)]
+    order = np.log2(e[0] / e[-1]) / 3
+    assert order > 2.7, (lim, e, order)
     ev = [_wave_error(orc, n, "vanleer") for n in (64, 128)]
-    assert e[-1] < 0.2 * ev[-1]
+    assert e[2] < 0.2 * ev[-1]
 
 
 def test_ghost_width_three_across_levels(orc):
@@ -154,3 +156,39 @@ def test_ghost_width_three_across_levels(orc):
     assert orc.mesh_for(W).ng == 3
     W.cfg.level_limiter = None
     assert orc.mesh_for(W).ng == 2
+
+
+def test_wenozp5_fifth_order_at_smooth_extrema(orc):
+    # WENO-Z+ (Acker, Borges & Costa 2016) keeps fifth order where the first
+    # derivative vanishes (a sine's extrema), with lambda = dx^(2/3) shrinking
+    # with the grid
+    errs = []
+    for n in (40, 80, 160):
+        F = lambda x: -np.cos(2 * np.pi * x) / (2 * np.pi)  # noqa: E731
+        a, xe = _averages(F, n)
+        wl_, _ = orc.reconstruct("wenozp5", a, dx=1.0 / n)
+        i = np.arange(3, n - 3)
+        errs.append(np.abs(wl_[i] - np.sin(2 * np.pi * xe[i + 1])).max())
+    oz = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert oz.min() > 4.5, (errs, oz)
+
+
+def test_wenozp5_lambda_follows_the_cell_width(orc):
+    # the added term lambda (beta_k + eps)/(tau5 + eps), lambda = dx^(2/3),
+    # raises the weight of the less smooth candidates.  At a kink (where the
+    # candidates' smoothness indicators are comparable) the face values next
+    # to it move steadily with dx, by ~1e-3 between dx = 1e-9 and 0.5; the
+    # faces whose stencils are all on one side do not move
+    a = 0.1 * np.abs(np.arange(12) - 5.3)
+    vals = np.array([orc.reconstruct("wenozp5", a, dx=dx)[0] for dx in (1e-9, 1e-3, 1e-1, 0.5)])
+    assert np.all(np.diff(vals[:, 4]) < 0) and np.all(np.diff(vals[:, 5]) < 0)
+    assert np.all(np.diff(vals[:, 6]) > 0)
+    assert abs(vals[-1, 5] - vals[0, 5]) > 1e-3
+    np.testing.assert_allclose(vals[:, 2], vals[0, 2], rtol=1e-14)
+    # exact for linear data whatever lambda (equal smoothness indicators)
+    lin = 0.5 + 0.25 * np.arange(12)
+    for dx in (1e-3, 0.5):
+        wl_, wr_ = orc.reconstruct("wenozp5", lin, dx=dx)
+        i = np.arange(2, 10)
+        np.testing.assert_allclose(wl_[i], lin[i] + 0.125, rtol=0, atol=1e-14)
+        np.testing.assert_allclose(wr_[i], lin[i] - 0.125, rtol=0, atol=1e-14)
