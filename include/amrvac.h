@@ -83,11 +83,16 @@ typedef enum {
 /* limiters of the limiter table (Sect. 3.1.1).  Two ghost cells: minmod, van
  * Leer 1974, Koren 1993 (third order), superbee (Roe 1985), woodward
  * (monotonized central, van Leer 1977), mcbeta (beta = 1.4), van Albada 1982
- * (TVD form).  Three ghost cells (five-point, fifth order on smooth data): mp5
+ * (TVD form), cada3 (the compact third-order limiter function of Cada &
+ * Torrilhon 2009: phi(theta) = max(0, min(phi3, max(-theta/2, min(2 theta,
+ * phi3, 1.6)))), phi3 = (2 + theta)/3, theta = dm/dp; it keeps a slope at
+ * extrema).  Three ghost cells (five-point, fifth order on smooth data): mp5
  * (Suresh & Huynh 1997), weno5 (Jiang & Shu 1996, eps = 1e-6), wenoz5 (Borges
- * et al. 2008, exponent 1); these run on the PLAIN kernels only (AUTO picks
- * PLAIN, FUSED is rejected) whenever the limiter or a level's limiter is one
- * of them. */
+ * et al. 2008, exponent 1), wenozp5 (WENO-Z+ of Acker, Borges & Costa 2016:
+ * the Z weights with exponent 2 plus lambda (beta_k + eps)/(tau5 + eps),
+ * lambda = dx^(2/3) of the block's level along the reconstruction); these run
+ * on the PLAIN kernels only (AUTO picks PLAIN, FUSED is rejected) whenever the
+ * limiter or a level's limiter is one of them. */
 typedef enum {
   AMRVAC_LIM_MINMOD = 0,
   AMRVAC_LIM_VANLEER = 1,
@@ -98,7 +103,9 @@ typedef enum {
   AMRVAC_LIM_ALBADA = 6,
   AMRVAC_LIM_MP5 = 7,
   AMRVAC_LIM_WENO5 = 8,
-  AMRVAC_LIM_WENOZ5 = 9
+  AMRVAC_LIM_WENOZ5 = 9,
+  AMRVAC_LIM_CADA3 = 10,
+  AMRVAC_LIM_WENOZP5 = 11
 } amrvac_limiter;
 /* time-integration table of Sect. 3: SSPRK(2,2), SSPRK(3,3) (Gottlieb 2005),
  * SSPRK(4,3) and SSPRK(5,4) (Spiteri & Ruuth 2002) */
@@ -236,6 +243,18 @@ amrvac_status amrvac_set_conserved(amrvac_state* s, int32_t buffer, const void* 
                                    int32_t src_is_device, int32_t src_precision);
 amrvac_status amrvac_get_conserved(amrvac_state* s, int32_t buffer, void* dst,
                                    int32_t dst_is_device, int32_t dst_precision);
+
+/*
+ * Primitive variables of buffer (the paper's snapshots can hold primitive
+ * instead of conserved variables, Sect. 7.5): (rho, v_x, v_y, v_z, p, B_x,
+ * B_y, B_z, psi) of every interior cell into d_dst (device memory of the
+ * caller, the state's precision, the conserved layout [var][block][cell]), with
+ * p = (gamma - 1)(e - m.v/2 - B^2/2) recovered exactly as the stage kernels
+ * recover it: in double for FP64 states; for FP32-bulk states in float-float
+ * (AMRVAC_PRESSURE_FF) or with the subtraction in double (AMRVAC_PRESSURE_FP64),
+ * the kinetic part formed in float.  Asynchronous on the state's stream.
+ */
+amrvac_status amrvac_get_primitives(amrvac_state* s, int32_t buffer, void* d_dst);
 
 /* Per-instance clock: t (host array [ninst]) and t_end.  Marks dt invalid. */
 amrvac_status amrvac_set_time(amrvac_state* s, const double* h_t, const double* h_t_end);

@@ -24,7 +24,8 @@ FP64, FP32 = 0, 1
 
 # every symbol include/amrvac.h declares
 SYMBOLS = ("amrvac_workspace_bytes", "amrvac_state_create", "amrvac_state_destroy",
-           "amrvac_set_conserved", "amrvac_get_conserved", "amrvac_set_time",
+           "amrvac_set_conserved", "amrvac_get_conserved", "amrvac_get_primitives",
+           "amrvac_set_time",
            "amrvac_fill_ghosts", "amrvac_cfl_dt", "amrvac_set_dt", "amrvac_stage",
            "amrvac_step", "amrvac_get_diag", "amrvac_clear_error", "amrvac_launch_count",
            "amrvac_error_string", "amrvac_cfl_dt_noalloc", "amrvac_state_save",
@@ -90,6 +91,7 @@ def load(path: str = LIB_PATH):
     L.amrvac_state_destroy.argtypes = [vp]
     L.amrvac_set_conserved.argtypes = [vp, i32, vp, i32, i32]
     L.amrvac_get_conserved.argtypes = [vp, i32, vp, i32, i32]
+    L.amrvac_get_primitives.argtypes = [vp, i32, vp]
     L.amrvac_set_time.argtypes = [vp, vp, vp]
     L.amrvac_fill_ghosts.argtypes = [vp, i32, vp]
     L.amrvac_cfl_dt.argtypes = [vp, i32, vp]
@@ -276,9 +278,20 @@ class State:
     def ng(self):
         """Ghost cells per block face of the ghost export: 3 when the limiter
         or a level's limiter is a five-point one (mp5, weno5, wenoz5), else 2."""
-        five = {"mp5", "weno5", "wenoz5"}
+        five = {"mp5", "weno5", "wenoz5", "wenozp5"}
         lims = {self.cfg.limiter} | set((self.cfg.level_limiter or {}).values())
         return 3 if lims & five else 2
+
+    def get_primitives(self, buffer=0):
+        """Primitive variables (rho, v, p, B, psi) of buffer, as the stage
+        kernels recover them, returned as a numpy array in the state's
+        precision."""
+        out = self.torch.empty(self.shape, dtype=self.dtype, device=self.device)
+        self.stream.wait_stream(self.torch.cuda.current_stream(self.device))
+        _check(load().amrvac_get_primitives(self._h, buffer, out.data_ptr()),
+               "amrvac_get_primitives")
+        self.stream.synchronize()
+        return out.cpu().numpy()
 
     def fill_ghosts(self, buffer=0):
         P = 1

@@ -41,13 +41,13 @@ bool config_ok(const amrvac_config* c, std::string& err) {
   }
   if (cells > AMRVAC_MAX_BLOCK_CELLS) return err = "block larger than AMRVAC_MAX_BLOCK_CELLS", false;
   if (c->flux < AMRVAC_FLUX_HLL || c->flux > AMRVAC_FLUX_HLLC) return err = "bad flux", false;
-  if (c->limiter < AMRVAC_LIM_MINMOD || c->limiter > AMRVAC_LIM_WENOZ5)
+  if (c->limiter < AMRVAC_LIM_MINMOD || c->limiter > AMRVAC_LIM_WENOZP5)
     return err = "bad limiter", false;
   if (c->reflux != 0 && c->reflux != 1) return err = "bad reflux", false;
   for (int L = 0; L < AMRVAC_MAX_LEVELS; L++) {
     if (c->level_flux[L] < 0 || c->level_flux[L] > AMRVAC_FLUX_HLLC + 1)
       return err = "bad level_flux", false;
-    if (c->level_limiter[L] < 0 || c->level_limiter[L] > AMRVAC_LIM_WENOZ5 + 1)
+    if (c->level_limiter[L] < 0 || c->level_limiter[L] > AMRVAC_LIM_WENOZP5 + 1)
       return err = "bad level_limiter", false;
   }
   if (c->fix_small_values < AMRVAC_FIX_OFF || c->fix_small_values > AMRVAC_FIX_AVERAGE)
@@ -78,9 +78,9 @@ int nx_of(const amrvac_config* c, int d) { return d < c->ndim ? c->block_nx[d] :
 // ghost cells per block face of the plain path: 3 when the limiter or a
 // level's limiter is a five-point one, else 2
 int ghost_width(const amrvac_config* c) {
-  int g = c->limiter >= AMRVAC_LIM_MP5 ? NG5 : NG;
+  int g = five_point_limiter(c->limiter) ? NG5 : NG;
   for (int L = 0; L < AMRVAC_MAX_LEVELS; L++)
-    if (c->level_limiter[L] - 1 >= AMRVAC_LIM_MP5) g = NG5;
+    if (c->level_limiter[L] > 0 && five_point_limiter(c->level_limiter[L] - 1)) g = NG5;
   return g;
 }
 
@@ -131,6 +131,11 @@ bool build_tables(const amrvac_config* c, int ninst, const amrvac_instance_desc*
       if (total > (size_t)1 << 30) return T.err = "block maps too large", false;
     }
   }
+  // the wenozp5 lambda = dx^(2/3) of every (instance, level, dimension), kept
+  // after the cell sizes in the same table
+  const size_t ndx = T.dx.size();
+  T.dx.resize(2 * ndx);
+  for (size_t i = 0; i < ndx; i++) T.dx[ndx + i] = std::pow(T.dx[i], 2.0 / 3.0);
   T.lmap.assign(total, MAP_COARSER);
   auto pos = [&](int q, int L, long i, long j, long k) -> int& {
     const int* nb = &T.lnb[(q * MAXLEV + L) * 3];
@@ -475,6 +480,7 @@ amrvac_status amrvac_state_create(const amrvac_config* cfg, int32_t ninst,
   M.lnb = at<int>(s, L.lnb);
   M.gamma = at<double>(s, L.gamma);
   M.dx = at<double>(s, L.dx);
+  M.wzlam = M.dx + (size_t)ninst * MAXLEV * 3;
   M.inst_start = at<int>(s, L.istart);
   M.inst_blocks = at<int>(s, L.iblocks);
   M.rt = at<InstRT>(s, L.rt);
@@ -679,6 +685,11 @@ amrvac_status amrvac_get_conserved(amrvac_state* s, int32_t buffer, void* dst,
     for (size_t i = 0; i < n; i++) d[i] = tmp[i];
   }
   return cuda_status(e);
+}
+
+amrvac_status amrvac_get_primitives(amrvac_state* s, int32_t buffer, void* d_dst) {
+  if (!s || !d_dst || !buffer_ok(buffer)) return AMRVAC_E_INVALID;
+  return check_launch(s, launch_to_primitive(s, buffer, d_dst));
 }
 
 static amrvac_status read_rt(amrvac_state* s, std::vector<InstRT>& rt) {

@@ -15,6 +15,12 @@ constexpr int NG = 2;       // ghost cells per face of the two-ghost-cell limite
 constexpr int NG5 = 3;      // ghost cells per face of the five-point limiters (plain path)
 constexpr int MAXLEV = AMRVAC_MAX_LEVELS;
 constexpr int NPART = 12;   // per-block partials: smax, chmax, sums[9], pad
+
+// the limiters that reconstruct from five cells (three ghost layers)
+__host__ __device__ inline bool five_point_limiter(int lim) {
+  return lim == AMRVAC_LIM_MP5 || lim == AMRVAC_LIM_WENO5 || lim == AMRVAC_LIM_WENOZ5 ||
+         lim == AMRVAC_LIM_WENOZP5;
+}
 // per-(instance, level) stage constants of the fused kernels, refreshed from
 // InstRT before every fused stage: c dt (the stage's Euler step), ch, psi
 // damping factor over c dt, dx[3], 1/dx[3], finished flag (dt == 0), gamma,
@@ -57,6 +63,7 @@ struct DevMesh {
   const int* lnb;         // [ninst][MAXLEV][3] blocks per dimension at a level
   const double* gamma;    // [ninst]
   const double* dx;       // [ninst][MAXLEV][3] cell size
+  const double* wzlam;    // [ninst][MAXLEV][3] dx^(2/3), the wenozp5 lambda
   const int* inst_start;  // [ninst + 1] CSR of blocks per instance
   const int* inst_blocks; // [nblocks]
   InstRT* rt;             // [ninst]

@@ -149,9 +149,24 @@ template <class T> __device__ __forceinline__ T sym_slope(int lim, T dm, T dp) {
   return dm * dp * (dm + dp) / (dm * dm + dp * dp);
 }
 
+// cada3 (Cada & Torrilhon 2009, the compact third-order limiter function):
+// half the limited slope phi(theta) dp / 2, theta = dm/dp, with
+// phi = max(0, min(phi3, max(-theta/2, min(2 theta, phi3, 1.6)))) and
+// phi3 = (2 + theta)/3, written without the division: s = sgn(dp), a = |dp|,
+// t = s dm (= theta a), phi a = max(0, min(p3, max(-t/2, min(2t, p3, 1.6 a))))
+// with p3 = (2a + t)/3; 0 where dp = 0 (the limit of phi dp)
+template <class T> __device__ __forceinline__ T cada3_half(T dm, T dp) {
+  const T s = sgnT(dp), a = fabs(dp), t = s * dm;
+  const T p3 = (T(2) * a + t) / T(3);
+  const T inner = fmin(fmin(T(2) * t, p3), T(1.6) * a);
+  const T pa = fmax(T(0), fmin(p3, fmax(T(-0.5) * t, inner)));
+  return T(0.5) * s * pa;
+}
+
 // face value at i+1/2 from the cell with values (a, b, c) = (w_{i-1}, w_i, w_{i+1})
 template <class T> __device__ __forceinline__ T recon_plus(int lim, T a, T b, T c) {
   T dm = b - a, dp = c - b;
+  if (lim == AMRVAC_LIM_CADA3) return b + cada3_half(dm, dp);  // keeps a slope at extrema
   if (!(dm * dp > T(0))) return b;
   if (lim >= AMRVAC_LIM_SUPERBEE) return b + T(0.5) * sym_slope(lim, dm, dp);
   if (lim == AMRVAC_LIM_MINMOD) return b + T(0.5) * minmod2(dm, dp);
@@ -164,6 +179,7 @@ template <class T> __device__ __forceinline__ T recon_plus(int lim, T a, T b, T 
 // face value at i-1/2 from the cell with values (a, b, c)
 template <class T> __device__ __forceinline__ T recon_minus(int lim, T a, T b, T c) {
   T dm = b - a, dp = c - b;
+  if (lim == AMRVAC_LIM_CADA3) return b + cada3_half(-dp, -dm);  // the mirrored stencil
   if (!(dm * dp > T(0))) return b;
   if (lim >= AMRVAC_LIM_SUPERBEE) return b - T(0.5) * sym_slope(lim, dm, dp);
   if (lim == AMRVAC_LIM_MINMOD) return b - T(0.5) * minmod2(dm, dp);
@@ -184,6 +200,9 @@ template <class T> __device__ __forceinline__ T recon_minus(int lim, T a, T b, T
 //     (1e-6 + beta_k)^2.
 //   wenoz5 (Borges et al. 2008): alpha_k = d_k (1 + tau5 / (beta_k + eps)),
 //     tau5 = |beta_0 - beta_2|, eps = 1e-40 (double) / 1e-36 (float).
+//   wenozp5 (WENO-Z+, Acker, Borges & Costa 2016): alpha_k = d_k (1 +
+//     (tau5 / (beta_k + eps))^2 + lam (beta_k + eps) / (tau5 + eps)),
+//     lam = dx^(2/3) of the level along the reconstruction.
 template <class T> __device__ __forceinline__ T minmod4g(T w, T x, T y, T z) {
   if (w > T(0) && x > T(0) && y > T(0) && z > T(0)) return fmin(fmin(w, x), fmin(y, z));
   if (w < T(0) && x < T(0) && y < T(0) && z < T(0)) return fmax(fmax(w, x), fmax(y, z));
@@ -206,8 +225,9 @@ template <class T> __device__ __forceinline__ T mp5_face(T vm2, T vm1, T v0, T v
   return vor + minmod2(vmin - vor, vmax - vor);
 }
 
+// kind: 0 weno5, 1 wenoz5, 2 wenozp5 (lam its lambda)
 template <class T>
-__device__ __forceinline__ T weno5_face(bool z, T vm2, T vm1, T v0, T vp1, T vp2) {
+__device__ __forceinline__ T weno5_face(int kind, T vm2, T vm1, T v0, T vp1, T vp2, T lam) {
   const T c13 = T(13) / T(12);
   const T t0 = vm2 - T(2) * vm1 + v0, u0 = vm2 - T(4) * vm1 + T(3) * v0;
   const T t1 = vm1 - T(2) * v0 + vp1, u1 = vm1 - vp1;
@@ -219,7 +239,32 @@ __device__ __forceinline__ T weno5_face(bool z, T vm2, T vm1, T v0, T vp1, T vp2
   const T q1 = (-vm1 + T(5) * v0 + T(2) * vp1) / T(6);
   const T q2 = (T(2) * v0 + T(5) * vp1 - vp2) / T(6);
   T a0, a1, a2;
-  if (z) {
+  if (kind == 2) {
+    const T eps = sizeof(T) == 8 ? T(1e-40) : T(1e-36), tau = fabs(b0 - b2);
+    if constexpr (sizeof(T) == 8) {
+      const T r0 = tau / (b0 + eps), r1 = tau / (b1 + eps), r2 = tau / (b2 + eps);
+      a0 = T(0.1) * (T(1) + r0 * r0 + lam * (b0 + eps) / (tau + eps));
+      a1 = T(0.6) * (T(1) + r1 * r1 + lam * (b1 + eps) / (tau + eps));
+      a2 = T(0.3) * (T(1) + r2 * r2 + lam * (b2 + eps) / (tau + eps));
+    } else {
+      // float: the same weights in a form that cannot overflow.  The lambda
+      // term is written L (beta_k + eps)/(beta_max + eps) with
+      // L = lam (beta_max + eps)/(tau5 + eps); tau5/(beta_k + eps) is capped at
+      // 1e18 and L at 1e36.  While no cap binds this is the definition; a cap
+      // binds only where one group of candidates outweighs the rest by more
+      // than 1e18 (their weights then keep their ratios) and the sum of the
+      // weights stays below 3e36
+      const T bm = fmax(fmax(b0, b1), b2) + eps;
+      const T L = fmin(lam * bm / (tau + eps), T(1e36));
+      const T x0 = fmin(tau / (b0 + eps), T(1e18)), x1 = fmin(tau / (b1 + eps), T(1e18));
+      const T x2 = fmin(tau / (b2 + eps), T(1e18));
+      a0 = T(0.1) * (T(1) + x0 * x0 + L * ((b0 + eps) / bm));
+      a1 = T(0.6) * (T(1) + x1 * x1 + L * ((b1 + eps) / bm));
+      a2 = T(0.3) * (T(1) + x2 * x2 + L * ((b2 + eps) / bm));
+      const T inv = T(1) / (a0 + a1 + a2);
+      return (a0 * inv) * q0 + (a1 * inv) * q1 + (a2 * inv) * q2;
+    }
+  } else if (kind == 1) {
     const T eps = sizeof(T) == 8 ? T(1e-40) : T(1e-36), tau = fabs(b0 - b2);
     a0 = T(0.1) * (T(1) + tau / (b0 + eps));
     a1 = T(0.6) * (T(1) + tau / (b1 + eps));
@@ -233,16 +278,21 @@ __device__ __forceinline__ T weno5_face(bool z, T vm2, T vm1, T v0, T vp1, T vp2
   return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
 }
 
-// left state at i+1/2 of cell i, v = (v_{i-2}, ..., v_{i+2})
-template <class T> __device__ __forceinline__ T recon5_plus(int lim, const T* v) {
+__device__ __forceinline__ int weno_kind(int lim) {
+  return lim == AMRVAC_LIM_WENOZ5 ? 1 : (lim == AMRVAC_LIM_WENOZP5 ? 2 : 0);
+}
+
+// left state at i+1/2 of cell i, v = (v_{i-2}, ..., v_{i+2}); lam: the wenozp5
+// lambda of the level and direction
+template <class T> __device__ __forceinline__ T recon5_plus(int lim, const T* v, T lam) {
   return lim == AMRVAC_LIM_MP5 ? mp5_face(v[0], v[1], v[2], v[3], v[4])
-                               : weno5_face(lim == AMRVAC_LIM_WENOZ5, v[0], v[1], v[2], v[3], v[4]);
+                               : weno5_face(weno_kind(lim), v[0], v[1], v[2], v[3], v[4], lam);
 }
 
 // right state at i-1/2 of cell i, v = (v_{i-2}, ..., v_{i+2})
-template <class T> __device__ __forceinline__ T recon5_minus(int lim, const T* v) {
+template <class T> __device__ __forceinline__ T recon5_minus(int lim, const T* v, T lam) {
   return lim == AMRVAC_LIM_MP5 ? mp5_face(v[4], v[3], v[2], v[1], v[0])
-                               : weno5_face(lim == AMRVAC_LIM_WENOZ5, v[4], v[3], v[2], v[1], v[0]);
+                               : weno5_face(weno_kind(lim), v[4], v[3], v[2], v[1], v[0], lam);
 }
 
 // ---------------------------------------------------------------- Riemann

@@ -255,6 +255,24 @@ __device__ __forceinline__ float2 sym_pair(float a, float b, float c, float e, f
   return make_float2(prod.x > 0.f ? v.x : b, prod.y > 0.f ? v.y : c);
 }
 
+// cada3 (see cada3_half) for both face states of the face between cells b and
+// c: x = left state from cell b with (dm, dp) = (b - a, c - b); y = right state
+// from cell c, the mirrored rule with (dm, dp) = (c - e, b - c)
+__device__ __forceinline__ float2 cada3_pair(float a, float b, float c, float e) {
+  const float2 X = make_float2(b, c);
+  const float2 dm = sub2(X, make_float2(a, e));
+  const float2 dp = sub2(make_float2(c, b), X);
+  const float s0 = sgnT(dp.x), s1 = sgnT(dp.y);
+  const float2 A = make_float2(fabsf(dp.x), fabsf(dp.y));
+  const float2 t = mul2(make_float2(s0, s1), dm);
+  const float2 p3 = mul2(fma2(sp2(2.f), A, t), sp2(1.f / 3.f));
+  const float2 tt = mul2(sp2(2.f), t), ca = mul2(sp2(1.6f), A), ht = mul2(sp2(-0.5f), t);
+  const float i0 = fminf(fminf(tt.x, p3.x), ca.x), i1 = fminf(fminf(tt.y, p3.y), ca.y);
+  const float pa0 = fmaxf(0.f, fminf(p3.x, fmaxf(ht.x, i0)));
+  const float pa1 = fmaxf(0.f, fminf(p3.y, fmaxf(ht.y, i1)));
+  return fma2(mul2(sp2(0.5f), make_float2(s0, s1)), make_float2(pa0, pa1), X);
+}
+
 // Face flux along D from the 4-cell stencils of the 9 primitive variables:
 // st(v, t) for cells f-2, f-1, f, f+1.  Positivity fallback and glm as in
 // face_flux_d.
@@ -278,6 +296,9 @@ __device__ __forceinline__ void stencil_flux_f2(Acc st, int glm, float g, float 
     } else if (lim == AMRVAC_LIM_ALBADA) {
 #pragma unroll
       for (int v = 0; v < NV; v++) w[v] = sym_pair<2>(st(v, 0), st(v, 1), st(v, 2), st(v, 3), 0.f);
+    } else if (lim == AMRVAC_LIM_CADA3) {
+#pragma unroll
+      for (int v = 0; v < NV; v++) w[v] = cada3_pair(st(v, 0), st(v, 1), st(v, 2), st(v, 3));
     } else {
       const float beta = lim == AMRVAC_LIM_WOODWARD ? 2.f : 1.4f;
 #pragma unroll

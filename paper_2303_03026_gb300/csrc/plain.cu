@@ -79,15 +79,16 @@ __global__ void __launch_bounds__(256) k_flux(DevMesh M, const T* __restrict__ W
     int pc = ((k + g2) * P1 + (j + g1)) * P0 + (i + g0);
     const T* src = W + (size_t)b * NV * np + pc;
     T wl[NV], wr[NV], w0[NV], w1[NV];
-    if (lim >= AMRVAC_LIM_MP5) {
+    if (five_point_limiter(lim)) {
       // five-point limiters: cells f-3 .. f+2 (three ghost layers)
+      const T lam = (T)M.wzlam[(q * MAXLEV + lev) * 3 + d];
 #pragma unroll
       for (int v = 0; v < NV; v++) {
         const T* s = src + (size_t)v * np;
         const T c[6] = {s[-3 * stride], s[-2 * stride], s[-stride], s[0], s[stride],
                         s[2 * stride]};
-        wl[v] = recon5_plus(lim, c);
-        wr[v] = recon5_minus(lim, c + 1);
+        wl[v] = recon5_plus(lim, c, lam);
+        wr[v] = recon5_minus(lim, c + 1, lam);
         w0[v] = c[2];
         w1[v] = c[3];
       }
@@ -364,6 +365,26 @@ __global__ void k_fill_ghosts(DevMesh M, const T* __restrict__ U, T* __restrict_
   }
 }
 
+// primitive variables (rho, v, p, B, psi) of every interior cell of U into dst
+// (same [var][block][cell] layout), with the state's pressure recovery: ff = 1
+// the float-float form of FP32-bulk states, else the double subtraction
+template <class T>
+__global__ void __launch_bounds__(256) k_to_primitive(DevMesh M, const T* __restrict__ U,
+                                                      T* __restrict__ dst, int ff) {
+  const size_t vs = (size_t)M.nblocks * M.ncell;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < vs;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(t / M.ncell);
+    const double gamma = M.gamma[M.blk[b * 5]];
+    T u[NV], w[NV];
+#pragma unroll
+    for (int v = 0; v < NV; v++) u[v] = U[(size_t)v * vs + t];
+    cons2prim(gamma, u, w, ff != 0, (float)(gamma - 1.0));
+#pragma unroll
+    for (int v = 0; v < NV; v++) dst[(size_t)v * vs + t] = w[v];
+  }
+}
+
 template <class S, class D>
 __global__ void k_convert(const S* __restrict__ src, D* __restrict__ dst, size_t n) {
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
@@ -517,6 +538,18 @@ int launch_fill_ghosts(amrvac_state* s, int buffer, void* out) {
   else
     k_fill_ghosts<float><<<grid_for(work, 256), 256, 0, s->stream>>>(
         s->mesh, (const float*)s->U[buffer], (float*)out, s->P[0], s->P[1], s->P[2]);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_to_primitive(amrvac_state* s, int buffer, void* dst) {
+  const size_t n = (size_t)s->nblocks * s->ncell;
+  const int ff = s->cfg.precision == AMRVAC_FP32_BULK && s->cfg.pressure == AMRVAC_PRESSURE_FF;
+  if (s->cfg.precision == AMRVAC_FP64)
+    k_to_primitive<double><<<grid_for(n, 256), 256, 0, s->stream>>>(
+        s->mesh, (const double*)s->U[buffer], (double*)dst, 0);
+  else
+    k_to_primitive<float><<<grid_for(n, 256), 256, 0, s->stream>>>(
+        s->mesh, (const float*)s->U[buffer], (float*)dst, ff);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 

@@ -149,6 +149,7 @@ int launch_level_consts(amrvac_state* s, int k);
 int launch_fix_small(amrvac_state* s, int buffer);
 int launch_reflux(amrvac_state* s, int k);
 int launch_fill_ghosts(amrvac_state* s, int buffer, void* out);
+int launch_to_primitive(amrvac_state* s, int buffer, void* dst);
 int launch_convert(amrvac_state* s, const void* src, int src_prec, void* dst, int dst_prec,
                    size_t n);
 int launch_fused_stage(amrvac_state* s, int k, int epilogue);

@@ -40,7 +40,7 @@ VAR_NAMES = ("rho", "m_x", "m_y", "m_z", "e", "B_x", "B_y", "B_z", "psi")
 # option values shared by the C ABI (include/amrvac.h) and the oracle
 FLUX = {"hll": 0, "hlld": 1, "tvdlf": 2, "hllc": 3}
 LIMITER = {"minmod": 0, "vanleer": 1, "koren": 2, "superbee": 3, "woodward": 4, "mcbeta": 5,
-           "albada": 6, "mp5": 7, "weno5": 8, "wenoz5": 9}
+           "albada": 6, "mp5": 7, "weno5": 8, "wenoz5": 9, "cada3": 10, "wenozp5": 11}
 TIME = {"ssprk2": 0, "ssprk3": 1, "ssprk43": 2, "ssprk54": 3}
 PRECISION = {"fp64": 0, "fp32": 1}
 BC = {"periodic": 0, "outflow": 1, "symmetric": 2}
@@ -359,16 +359,18 @@ def solenoidal_velocity(n: int, seed: int, kmin: int = 1, kmax: int = 16) -> np.
 
 
 def c3_turbulence(n: int = 256, bnx: int = 16, seed: int = 3, precision: str = "fp32",
-                  beta: float = 0.01, flux="hlld", limiter="vanleer") -> Workload:
-    """3D periodic box, rho = 1, p = 1/gamma (c_s = 1), Mach-1 rms velocity,
-    uniform B0 along z with plasma beta 2p/B0^2 = beta, psi = 0."""
+                  beta: float = 0.01, flux="hlld", limiter="vanleer",
+                  mach: float = 1.0) -> Workload:
+    """3D periodic box, rho = 1, p = 1/gamma (c_s = 1), rms velocity ``mach``
+    (Mach 1 by default), uniform B0 along z with plasma beta 2p/B0^2 = beta,
+    psi = 0."""
     gamma = 5.0 / 3.0
     nb = n // bnx
     cfg = Config(ndim=3, block_nx=(bnx, bnx, bnx), flux=flux, limiter=limiter,
                  time="ssprk3", precision=precision, glm=True, courant=0.8)
     inst = Instance(base_blocks=(nb, nb, nb), gamma=gamma)
     meta = uniform_meta((nb, nb, nb))
-    v = solenoidal_velocity(n, seed, 1, min(16, n // 4))
+    v = solenoidal_velocity(n, seed, 1, min(16, n // 4)) * mach
     p0 = 1.0 / gamma
     b0 = math.sqrt(2.0 * p0 / beta)
     # scatter the global fields into blocks ([var][block][cell])
@@ -381,7 +383,7 @@ def c3_turbulence(n: int = 256, bnx: int = 16, seed: int = 3, precision: str = "
     U[:] = conserved_from_primitive(gamma, one, vb[0], vb[1], vb[2], p0 * one, zero, zero,
                                     b0 * one)
     return Workload("c3_turbulence", cfg, [inst], meta, U,
-                    {"seed": seed, "beta": beta, "B0": b0})
+                    {"seed": seed, "beta": beta, "B0": b0, "mach": mach})
 
 
 # ----------------------------------------------------------------------------

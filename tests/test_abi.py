@@ -97,15 +97,16 @@ def test_scheme_options_validated(lib):
     for flux, time, lim in (("tvdlf", "ssprk43", "superbee"), ("hllc", "ssprk54", "albada"),
                             ("hlld", "ssprk3", "mcbeta"), ("hlld", "ssprk2", "woodward"),
                             ("hll", "ssprk3", "mp5"), ("hlld", "ssprk3", "weno5"),
-                            ("hllc", "ssprk43", "wenoz5")):
+                            ("hllc", "ssprk43", "wenoz5"), ("hlld", "ssprk3", "cada3"),
+                            ("hllc", "ssprk54", "wenozp5")):
         W = wl.small_amr_2d()
         W.cfg.flux, W.cfg.time, W.cfg.limiter = flux, time, lim
         assert _bytes(lib, W)[0] == 0, (flux, time, lim)
     from paper_2303_03026_gb300 import amrvac
     W = wl.small_amr_2d()
-    for field, value in (("flux", 4), ("time", 4), ("limiter", 10), ("limiter", -1),
+    for field, value in (("flux", 4), ("time", 4), ("limiter", 12), ("limiter", -1),
                          ("reflux", 2), ("fix_small_values", 3), ("level_flux", 5),
-                         ("level_limiter", 11), ("level_flux", -1)):
+                         ("level_limiter", 13), ("level_flux", -1)):
         c = amrvac.make_config(W.cfg)
         if field.startswith("level_"):
             getattr(c, field)[2] = value
@@ -132,6 +133,12 @@ def test_five_point_limiters_widen_the_plain_scratch(lib):
     W.cfg.limiter = "vanleer"
     W.cfg.level_limiter = {0: "mp5"}
     assert _bytes(lib, W, kernel="fused")[0] == 1
+    W.cfg.level_limiter = {0: "wenozp5"}
+    assert _bytes(lib, W, kernel="fused")[0] == 1
+    # cada3 needs two ghost layers: the fused kernels take it
+    W.cfg.level_limiter = None
+    W.cfg.limiter = "cada3"
+    assert _bytes(lib, W, kernel="fused")[0] == 0
 
 
 def test_fix_and_reflux_need_their_workspace(lib):

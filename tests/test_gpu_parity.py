@@ -376,10 +376,10 @@ def test_fp32_low_beta_pressure_recovery(amr, orc, kernel, pressure, beta):
 # full-size workloads: sampled blocks against the oracle
 # ----------------------------------------------------------------------------
 
-def _sampled_full(amr, orc, W, kernel, nsample, tol):
+def _sampled_full(amr, orc, W, kernel, nsample, tol, stages=(0, 1)):
     rng = np.random.Generator(np.random.PCG64(7))
     blocks = np.sort(rng.choice(W.nblocks, size=min(nsample, W.nblocks), replace=False))
-    return _stage_parity(amr, orc, W, kernel, stages=[0, 1], tol=tol, blocks=blocks)
+    return _stage_parity(amr, orc, W, kernel, stages=list(stages), tol=tol, blocks=blocks)
 
 
 def test_full_c2_sampled(amr, orc):
@@ -392,8 +392,9 @@ def test_full_c3_sampled(amr, orc):
 
 def test_full_c4_sampled(amr, orc):
     W = wl.c4_blast_amr(base=6)
-    # sample from every level, including blocks next to level changes
-    _sampled_full(amr, orc, W, "auto", 16, 1e-3)
+    # sample from every level, including blocks next to level changes; all
+    # three stages, the last one with its CFL epilogue
+    _sampled_full(amr, orc, W, "auto", 16, 1e-3, stages=(0, 1, 2))
 
 
 def test_full_c5_sampled(amr, orc):

@@ -176,7 +176,7 @@ def test_full_steps_match_oracle_run(amr, orc, kernel, time, flux):
     S.close()
 
 
-NEW_LIMITERS = ["superbee", "woodward", "mcbeta", "albada"]
+NEW_LIMITERS = ["superbee", "woodward", "mcbeta", "albada", "cada3"]
 
 
 @pytest.mark.parametrize("kernel", ["plain", "auto"])
@@ -305,10 +305,11 @@ def test_hllc_stage_parity_fp32(amr, orc):
 
 
 # ----------------------------------------------------------------------------
-# five-point limiters (mp5, weno5, wenoz5: three ghost cells, plain kernels)
+# five-point limiters (mp5, weno5, wenoz5, wenozp5: three ghost cells, plain
+# kernels)
 # ----------------------------------------------------------------------------
 
-FIVE_POINT = ["mp5", "weno5", "wenoz5"]
+FIVE_POINT = ["mp5", "weno5", "wenoz5", "wenozp5"]
 
 
 @pytest.mark.parametrize("limiter", FIVE_POINT)
@@ -329,7 +330,7 @@ def test_five_point_stage_parity_fp32(amr, orc, limiter):
 def test_five_point_on_one_level_and_ghost_export(amr, orc):
     # a five-point limiter on one AMR level widens every block's ghost layers
     W = wl.small_amr_2d(bnx=8)
-    W.cfg.level_limiter = {1: "wenoz5", 2: "mp5"}
+    W.cfg.level_limiter = {1: "wenozp5", 2: "mp5"}
     _scheme_stage_parity(amr, orc, W, "auto", 1e-12)
     S = amr.State.from_workload(W, kernel="auto")
     S.set_conserved(W.U)

@@ -61,7 +61,7 @@ def test_noalloc_cfl_matches_workspace_entry_point_and_oracle(amr, orc):
     assert W2.nblocks >= W1.nblocks
     res = []
     for W, t in ((W1, 0.0), (W2, 0.0), (W3, 0.0)):
-        got, ref, orac = _reference_and_noalloc(amr, W, t)
+        got, ref, orac = _reference_and_noalloc(amr, orc, W, t)
         assert abs(got[0] - ref[0]) <= TOL * abs(ref[0]), (W.name, got, ref)
         assert abs(got[1] - ref[1]) <= TOL * abs(ref[1]), (W.name, got, ref)
         otol = TOL if W.cfg.precision == "fp64" else 1e-5
