@@ -61,6 +61,8 @@ def parse():
     p.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison leg")
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU-baseline leg")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-configs", action="store_true",
+                   help="skip the sub-records of the other workloads (c2, c3, c5)")
     p.add_argument("--no-tune", action="store_true",
                    help="skip the launch-shape autotuning before the timed region")
     return p.parse_args()
@@ -278,6 +280,142 @@ def time_steps(torch, S, k):
     e1.record(S.stream)
     S.stream.synchronize()
     return e0.elapsed_time(e1) / k
+
+
+VARS = ("rho", "m_x", "m_y", "m_z", "e", "B_x", "B_y", "B_z", "psi")
+
+
+def rel_l1_by_var(a, b, ch):
+    """Relative L1 error of a against b per conserved variable: rho and e
+    against themselves, each component of m and B against the magnitude of
+    its vector, psi against c_h |B| (its natural scale)."""
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    mm = np.sqrt(b[1] ** 2 + b[2] ** 2 + b[3] ** 2).sum()
+    bm = np.sqrt(b[5] ** 2 + b[6] ** 2 + b[7] ** 2).sum()
+    out = {}
+    for v, n in enumerate(VARS):
+        s = (mm if v in (1, 2, 3) else bm if v in (5, 6, 7) else
+             max(np.abs(b[8]).sum(), float(ch) * bm) if v == 8 else np.abs(b[v]).sum())
+        out[n] = float(np.abs(a[v] - b[v]).sum() / max(s, 1e-300))
+    return out
+
+
+def bench_configs(torch, amrvac, dev, args, hbm):
+    """Sub-records of the other workloads of the metric, one GPU, synthetic data:
+    c5, the 256 uneven 2D instances batched in one launch per stage against the
+    same instances advanced one at a time; c3, the 256^3 turbulence box in FP32
+    bulk and in FP64 on the GPU, with the FP32 error against the FP64 GPU path
+    after 1, 10 and 200 steps and against the FP64 oracle after one step; c2,
+    the 1024^2 Orszag-Tang vortex at its stated FP64 precision (and FP32)."""
+    import dataclasses
+    import oracle
+    out = {}
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    # c5: batched vs one at a time
+    W = make_workload("c5", "fp32")[0]
+    cells = W.interior_cells()
+    U = torch.from_numpy(W.U.astype(np.float32)).to(dev)
+    S = amrvac.State.from_workload(W, device=dev)
+    S.set_conserved(U)
+    S.step(3)
+    ms = time_steps(torch, S, 10)
+    states, off = [], 0
+    for q, inst in enumerate(W.instances):
+        nb = int((W.block_meta[:, 0] == q).sum())
+        meta = W.block_meta[off:off + nb].copy()
+        meta[:, 0] = 0
+        Sq = amrvac.State(W.cfg, [inst], meta, device=dev, stream=S.stream)
+        Sq.set_conserved(U[:, off:off + nb].contiguous())
+        Sq.step(1)
+        states.append(Sq)
+        off += nb
+    S.stream.synchronize()
+    e0, e1 = ev(), ev()
+    e0.record(S.stream)
+    for _ in range(3):
+        for Sq in states:
+            Sq.step(1)
+    e1.record(S.stream)
+    S.stream.synchronize()
+    msq = e0.elapsed_time(e1) / 3
+    for Sq in states:
+        Sq.close()
+    out["c5"] = {"workload": "256 uneven 2D instances 64^2..512^2 in 16^2 blocks, FP32 bulk, "
+                             "HLLD+vanleer+glm, SSPRK3, per-instance dt",
+                 "blocks": int(W.nblocks), "cells": int(cells),
+                 "value": cells / (ms / 1e3), "ms_per_step": ms,
+                 "frac": 288 * cells / (ms / 1e3) / 1e9 / hbm,
+                 "one_at_a_time": {"value": cells / (msq / 1e3), "ms_per_step": msq,
+                                   "launches": "one graph per instance per step"},
+                 "batched_speedup": msq / ms}
+    S.close()
+    del U
+
+    # c3: FP32 bulk and FP64 GPU, errors at 1, 10, 200 steps; oracle after 1
+    W = make_workload("c3", "fp32")[0]
+    cells = W.interior_cells()
+    U64 = W.U.astype(np.float32).astype(np.float64)
+    W64 = dataclasses.replace(W, cfg=dataclasses.replace(W.cfg, precision="fp64"))
+    A = amrvac.State.from_workload(W, device=dev)
+    B = amrvac.State.from_workload(W64, device=dev)
+    A.set_conserved(U64.astype(np.float32))
+    B.set_conserved(U64)
+    errs, done = {}, 0
+    for n in (1, 10, 200):
+        A.step(n - done)
+        B.step(n - done)
+        done = n
+        a = A.get_conserved(0)
+        b = B.get_conserved(0)
+        ch = A.diag()["ch"][0]
+        errs[n] = rel_l1_by_var(a, b, ch)
+        if n == 1:
+            m = oracle.mesh_for(W64, os.cpu_count() or 1)
+            Uo, to, ns, st = m.run(U64, 1e30, maxsteps=1)
+            err_oracle = rel_l1_by_var(a, Uo, ch)
+            err64_oracle = float(np.abs(b - Uo).max() / np.abs(Uo).max())
+            del Uo
+    A.set_conserved(U64.astype(np.float32))
+    B.set_conserved(U64)
+    A.step(3)
+    B.step(2)
+    ms32 = time_steps(torch, A, 20)
+    ms64 = time_steps(torch, B, 5)
+    out["c3"] = {"workload": "3D 256^3 Mach-1 beta-0.01 turbulence in 16^3 blocks, "
+                             "HLLD+vanleer+glm, SSPRK3",
+                 "cells": int(cells), "value": cells / (ms32 / 1e3), "ms_per_step": ms32,
+                 "frac": 288 * cells / (ms32 / 1e3) / 1e9 / hbm,
+                 "fp64_gpu": {"value": cells / (ms64 / 1e3), "ms_per_step": ms64,
+                              "frac": 576 * cells / (ms64 / 1e3) / 1e9 / hbm},
+                 "rel_l1_fp32_vs_fp64_gpu": {str(k): v for k, v in errs.items()},
+                 "rel_l1_fp32_vs_oracle_step1": err_oracle,
+                 "rel_linf_fp64_gpu_vs_oracle_step1": err64_oracle,
+                 "norms": "rho, e relative; m and B components against their vector's "
+                          "magnitude; psi against c_h |B|"}
+    A.close()
+    B.close()
+    del U64
+
+    # c2: Orszag-Tang at its stated FP64 precision, and in FP32
+    res = {}
+    for prec in ("fp64", "fp32"):
+        W = make_workload("c2", prec)[0]
+        cells = W.interior_cells()
+        S = amrvac.State.from_workload(W, device=dev)
+        S.set_conserved(W.U if prec == "fp64" else W.U.astype(np.float32))
+        S.step(3)
+        msp = time_steps(torch, S, 20)
+        nbytes = (576 if prec == "fp64" else 288) * cells
+        res[prec] = {"value": cells / (msp / 1e3), "ms_per_step": msp,
+                     "frac": nbytes / (msp / 1e3) / 1e9 / hbm}
+        S.close()
+    out["c2"] = {"workload": "2D Orszag-Tang 1024^2 in 16^2 blocks, HLLD+koren+glm, SSPRK3",
+                 "cells": 1024 * 1024, "fp64": res["fp64"], "fp32": res["fp32"],
+                 "l2": "state smaller than L2 (75.5 MB FP64 per register): frac is not a "
+                       "roofline measurement"}
+    return out
 
 
 def bench_regrid(torch, amrvac, W, S, dev, args, hbm, thr=0.05, ratio=0.2):
@@ -559,6 +697,11 @@ def main():
         for Sq in states:
             Sq.close()
 
+    # the other workloads of the metric (c5 batching, c3 accuracy, c2 FP64)
+    configs = None
+    if not args.no_configs and args.workload == "c4" and ws == 1:
+        configs = bench_configs(torch, amrvac, dev, args, hbm)
+
     # end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
@@ -599,7 +742,17 @@ def main():
         S64.step(nacc)
         a = S.get_conserved(0, numpy=False).double()
         b = S64.get_conserved(0, numpy=False)
-        l1 = ((a - b).abs().sum(dim=(1, 2)) / b.abs().sum(dim=(1, 2)).clamp_min(1e-300)).cpu()
+        ch = float(S64.diag()["ch"].max())
+        # rho, e against themselves; m and B components against the magnitude of
+        # their vector; psi against c_h |B|
+        diff = (a - b).abs().sum(dim=(1, 2))
+        del a
+        mm = torch.sqrt(b[1] ** 2 + b[2] ** 2 + b[3] ** 2).sum()
+        bm = torch.sqrt(b[5] ** 2 + b[6] ** 2 + b[7] ** 2).sum()
+        own = b.abs().sum(dim=(1, 2))
+        scale = torch.stack([own[0], mm, mm, mm, own[4], bm, bm, bm,
+                             torch.maximum(own[8], ch * bm)])
+        l1 = (diff / scale.clamp_min(1e-300)).cpu()
         fp64 = {"value": cells_all / (ms64 / 1e3), "ms_per_step": ms64,
                 "speedup_fp32_fused_vs_fp64_plain": ms64 / ms_step,
                 "rel_l1_fp32_vs_fp64_after_%d_steps" % nacc:
@@ -636,7 +789,7 @@ def main():
                                             else "replicas" if ws > 1 else "1 GPU")),
                 "clocks": clocks, "gpu_launches": launches, "roofline": roofline,
                 "e2e": e2e, "variants": variants or None, "regrid": regrid,
-                "one_at_a_time": one_at_a_time,
+                "one_at_a_time": one_at_a_time, "configs": configs,
                 "fp64_plain": fp64, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     S.close()

@@ -464,6 +464,24 @@ amrvac_status amrvac_regrid_plan(const amrvac_config* cfg, int32_t ninst,
                                  const amrvac_instance_desc* inst, int32_t nblocks,
                                  const int32_t* block_meta, const int8_t* flags,
                                  int32_t capacity, int32_t* new_meta, int32_t* new_nblocks);
+/*
+ * amrvac_regrid_plan_device: the same plan (the same block list, in the same
+ *   order) computed on the device from the state's own mesh tables: the
+ *   splits and their 2:1 closure over the level maps (one pass per launch,
+ *   repeated while a pass adds a split, at most 17 passes), the merges of
+ *   complete families (each family decided independently: a merge can only
+ *   be prevented by leaves of finer levels, whose families come later in the
+ *   sequential order), and the compaction of the new leaves through dense
+ *   per-(instance, level) maps and a prefix sum.  Flags: h_flags (host int8
+ *   [nblocks], -1/0/1) when not NULL, else those of the last
+ *   amrvac_regrid_estimate.  Scratch lives in the state's workspace (no
+ *   allocation).  Synchronises; new_nblocks is always set; AMRVAC_E_INVALID
+ *   when capacity is too small, for a bad flag, a split beyond the deepest
+ *   level, or a mesh whose dense maps one level finer would be too large.
+ */
+amrvac_status amrvac_regrid_plan_device(amrvac_state* s, const int8_t* h_flags,
+                                        int32_t capacity, int32_t* h_new_meta,
+                                        int32_t* h_new_nblocks);
 amrvac_status amrvac_regrid_transfer(amrvac_state* src, int32_t src_buffer, amrvac_state* dst,
                                      int32_t dst_buffer);
 

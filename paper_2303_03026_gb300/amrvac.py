@@ -31,7 +31,7 @@ SYMBOLS = ("amrvac_workspace_bytes", "amrvac_state_create", "amrvac_state_destro
            "amrvac_error_string", "amrvac_cfl_dt_noalloc", "amrvac_state_save",
            "amrvac_state_load", "amrvac_set_tuning", "amrvac_get_tuning", "amrvac_autotune",
            "amrvac_fix_small_values", "amrvac_regrid_estimate", "amrvac_regrid_plan",
-           "amrvac_regrid_transfer")
+           "amrvac_regrid_transfer", "amrvac_regrid_plan_device")
 
 
 class AmrvacError(RuntimeError):
@@ -114,6 +114,7 @@ def load(path: str = LIB_PATH):
     L.amrvac_regrid_plan.argtypes = [C.POINTER(Config), i32, C.POINTER(InstanceDesc), i32, vp,
                                      vp, i32, vp, vp]
     L.amrvac_regrid_transfer.argtypes = [vp, i32, vp, i32]
+    L.amrvac_regrid_plan_device.argtypes = [vp, vp, i32, vp, vp]
     L.amrvac_cfl_dt_noalloc.argtypes = [C.POINTER(Config), C.POINTER(InstanceDesc), i32, vp, dbl,
                                         vp, vp]
     _lib = L
@@ -388,6 +389,22 @@ class State:
                                              est.ctypes.data, flags.ctypes.data),
                "amrvac_regrid_estimate")
         return est, flags
+
+    def regrid_plan(self, flags=None):
+        """Block list after one regrid, planned on the device from this state's
+        mesh (amrvac_regrid_plan_device); ``flags``: int8 [nblocks] (1 refine,
+        -1 coarsen, 0 keep), default the flags of the last regrid_estimate."""
+        fp = None
+        if flags is not None:
+            fl = np.ascontiguousarray(flags, np.int8)
+            assert fl.shape == (self.nblocks,)
+            fp = fl.ctypes.data
+        cap = self.nblocks * (1 << self.cfg.ndim)
+        out = np.zeros((cap, 5), np.int32)
+        n = C.c_int32(0)
+        _check(load().amrvac_regrid_plan_device(self._h, fp, cap, out.ctypes.data, C.byref(n)),
+               "amrvac_regrid_plan_device")
+        return out[:n.value].copy()
 
     def regrid_transfer(self, dst, buffer=0, dst_buffer=0):
         """Fill register ``dst_buffer`` of State ``dst`` (built on a planned block

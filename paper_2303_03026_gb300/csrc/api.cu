@@ -22,13 +22,18 @@ size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 struct Tables {
   std::vector<int> blk, nbr, gface, glist, gkind, rlist, lmap, lmap_off, lnb, istart, iblocks;
   std::vector<double> gamma, dx;
+  // device regrid plan: per instance the deepest level, and the offsets of the
+  // dense new-leaf maps of levels 0 .. deepest + 1 ([ninst * MAXLEV + 1];
+  // empty when a map that fine would be too large)
+  std::vector<int> maxlev, pseg;
   std::string err;
 };
 
 struct Layout {
   size_t U[3], W, F[3], part, blk, nbr, gface, glist, lmap, lmap_off, lnb, gamma, dx, istart,
       iblocks, rt, sums, err, work, work2, counter, gslab, lcf, lcd, flags, fixcount, gkind,
-      rlist, fluxreg, est, eflags, rtab, total;
+      rlist, fluxreg, est, eflags, rtab, pref, pfate, pmap, pseg, pmax, psums, pscal, pout,
+      total;
 };
 
 bool config_ok(const amrvac_config* c, std::string& err) {
@@ -130,6 +135,24 @@ bool build_tables(const amrvac_config* c, int ninst, const amrvac_instance_desc*
       if (L <= maxlev[q]) total += cnt;
       if (total > (size_t)1 << 30) return T.err = "block maps too large", false;
     }
+  }
+  // the dense new-leaf maps of the device regrid plan: levels 0 .. maxlev + 1
+  T.maxlev = maxlev;
+  {
+    T.pseg.assign((size_t)ninst * MAXLEV + 1, 0);
+    size_t ptot = 0;
+    bool fits = true;
+    for (int q = 0; q < ninst; q++)
+      for (int L = 0; L < MAXLEV; L++) {
+        T.pseg[q * MAXLEV + L] = (int)ptot;
+        if (L > maxlev[q] + 1) continue;
+        size_t cnt = 1;
+        for (int d = 0; d < c->ndim; d++) cnt *= (size_t)inst[q].base_blocks[d] << L;
+        ptot += cnt;
+        if (ptot > ((size_t)1 << 28)) fits = false;
+      }
+    T.pseg[(size_t)ninst * MAXLEV] = (int)std::min<size_t>(ptot, (size_t)1 << 30);
+    if (!fits) T.pseg.clear();
   }
   // the wenozp5 lambda = dx^(2/3) of every (instance, level, dimension), kept
   // after the cell sizes in the same table
@@ -334,6 +357,18 @@ Layout make_layout(const amrvac_config* c, int ninst, int nblocks, const Tables&
   L.est = take(sizeof(double) * nblocks);
   L.eflags = take((size_t)nblocks);
   L.rtab = take(sizeof(int) * RTAB_N * (size_t)nblocks);
+  // device regrid plan: split marks and fates per block, the dense new-leaf
+  // maps, their segment table, scan sums, scalars and the new block list (at
+  // most 2^ndim times as many blocks)
+  L.pref = take(sizeof(int) * (size_t)nblocks);
+  L.pfate = take((size_t)nblocks);
+  const size_t pm = T.pseg.empty() ? 0 : (size_t)T.pseg.back();
+  L.pmap = take(sizeof(int) * (pm + 1));
+  L.pseg = take(sizeof(int) * (T.pseg.size() + 1));
+  L.pmax = take(sizeof(int) * (size_t)ninst);
+  L.psums = take(sizeof(int) * (PLAN_CTAS + 1));
+  L.pscal = take(sizeof(int) * 4);
+  L.pout = take(sizeof(int) * 5 * ((size_t)nblocks << c->ndim));
   if (fused) {
     size_t per = (size_t)NV * 2 * 16 * (c->ndim == 3 ? 16 : 1);  // one face
     L.gslab = take(rs * per * T.glist.size());
@@ -500,6 +535,16 @@ amrvac_status amrvac_state_create(const amrvac_config* cfg, int32_t ninst,
   s->d_est = at<double>(s, L.est);
   s->d_eflags = at<signed char>(s, L.eflags);
   s->d_rtab = at<int>(s, L.rtab);
+  s->plan.ref = at<int>(s, L.pref);
+  s->plan.fate = at<signed char>(s, L.pfate);
+  s->plan.map = at<int>(s, L.pmap);
+  s->plan.seg = at<int>(s, L.pseg);
+  s->plan.maxlev = at<int>(s, L.pmax);
+  s->plan.sums = at<int>(s, L.psums);
+  s->plan.scal = at<int>(s, L.pscal);
+  s->plan.out = at<int>(s, L.pout);
+  s->plan.cap = s->nblocks << s->ndim;
+  s->plan.nmap = T.pseg.empty() ? -1 : T.pseg.back();
   s->d_glist = at<int>(s, L.glist);
   s->ngen = (int)T.glist.size();
   s->d_rlist = at<int>(s, L.rlist);
@@ -535,6 +580,8 @@ amrvac_status amrvac_state_create(const amrvac_config* cfg, int32_t ninst,
   up((void*)M.lnb, T.lnb.data(), sizeof(int) * T.lnb.size());
   up((void*)M.gamma, T.gamma.data(), sizeof(double) * T.gamma.size());
   up((void*)M.dx, T.dx.data(), sizeof(double) * T.dx.size());
+  if (!T.pseg.empty()) up((void*)s->plan.seg, T.pseg.data(), sizeof(int) * T.pseg.size());
+  up((void*)s->plan.maxlev, T.maxlev.data(), sizeof(int) * T.maxlev.size());
   up((void*)M.inst_start, T.istart.data(), sizeof(int) * T.istart.size());
   up((void*)M.inst_blocks, T.iblocks.data(), sizeof(int) * T.iblocks.size());
   up((void*)M.rt, rt.data(), sizeof(InstRT) * ninst);

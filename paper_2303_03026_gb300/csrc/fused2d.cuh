@@ -212,24 +212,43 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
         const int fyr = owner ? y : FB, fyc = owner ? x : hr;
         T f[NV];
         auto ax = [&](int v, int t) -> T { return S.prim[v][fxr + NG][fxc + t]; };
-        stencil_flux<T, 0, LIM, FLUX>(ax, sp.glm, g, ch, f, sp.limiter);
-#pragma unroll
-        for (int v = 0; v < NV; v++) S.fx[v][fxr][fxc] = f[v];
-        if (FULL && sp.reflux) {  // block-boundary x faces: 0 (owners x = 0), 1 (helpers)
-          const int face = owner ? (x == 0 ? 0 : -1) : 1;
-          const int code = face >= 0 ? M.nbr[b * 6 + face] : 0;
-          if (code == NBR_GENERAL)
-            keep_face_flux(M, -3 - M.gface[b * 6 + face], fxr, f);
-        }
         auto ay = [&](int v, int t) -> T { return S.prim[v][fyr + t][fyc + NG]; };
-        stencil_flux<T, 1, LIM, FLUX>(ay, sp.glm, g, ch, f, sp.limiter);
+        if constexpr (xy_pair_path<T, LIM, FLUX>()) {
+          // both faces at once, one per float2 lane
+          T f2[NV];
+          stencil_flux_xy(ax, ay, sp.glm, g, ch, f, f2);
 #pragma unroll
-        for (int v = 0; v < NV; v++) S.fy[v][fyr][fyc] = f[v];
-        if (FULL && sp.reflux) {  // block-boundary y faces: 2 (owners y = 0), 3 (helpers)
-          const int face = owner ? (y == 0 ? 2 : -1) : 3;
-          const int code = face >= 0 ? M.nbr[b * 6 + face] : 0;
-          if (code == NBR_GENERAL)
-            keep_face_flux(M, -3 - M.gface[b * 6 + face], fyc, f);
+          for (int v = 0; v < NV; v++) {
+            S.fx[v][fxr][fxc] = f[v];
+            S.fy[v][fyr][fyc] = f2[v];
+          }
+          if (FULL && sp.reflux) {
+            const int face = owner ? (x == 0 ? 0 : -1) : 1;
+            const int code = face >= 0 ? M.nbr[b * 6 + face] : 0;
+            if (code == NBR_GENERAL) keep_face_flux(M, -3 - M.gface[b * 6 + face], fxr, f);
+            const int facey = owner ? (y == 0 ? 2 : -1) : 3;
+            const int codey = facey >= 0 ? M.nbr[b * 6 + facey] : 0;
+            if (codey == NBR_GENERAL) keep_face_flux(M, -3 - M.gface[b * 6 + facey], fyc, f2);
+          }
+        } else {
+          stencil_flux<T, 0, LIM, FLUX>(ax, sp.glm, g, ch, f, sp.limiter);
+#pragma unroll
+          for (int v = 0; v < NV; v++) S.fx[v][fxr][fxc] = f[v];
+          if (FULL && sp.reflux) {  // block-boundary x faces: 0 (owners x = 0), 1 (helpers)
+            const int face = owner ? (x == 0 ? 0 : -1) : 1;
+            const int code = face >= 0 ? M.nbr[b * 6 + face] : 0;
+            if (code == NBR_GENERAL)
+              keep_face_flux(M, -3 - M.gface[b * 6 + face], fxr, f);
+          }
+          stencil_flux<T, 1, LIM, FLUX>(ay, sp.glm, g, ch, f, sp.limiter);
+#pragma unroll
+          for (int v = 0; v < NV; v++) S.fy[v][fyr][fyc] = f[v];
+          if (FULL && sp.reflux) {  // block-boundary y faces: 2 (owners y = 0), 3 (helpers)
+            const int face = owner ? (y == 0 ? 2 : -1) : 3;
+            const int code = face >= 0 ? M.nbr[b * 6 + face] : 0;
+            if (code == NBR_GENERAL)
+              keep_face_flux(M, -3 - M.gface[b * 6 + face], fyc, f);
+          }
         }
       }
       __syncthreads();

@@ -225,6 +225,24 @@ template <class T> __device__ __forceinline__ T mp5_face(T vm2, T vm1, T v0, T v
   return vor + minmod2(vmin - vor, vmax - vor);
 }
 
+// explicitly rounded operations (never contracted into an FMA)
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double div_rn(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float div_rn(float a, float b) { return __fdiv_rn(a, b); }
+
+// Jiang-Shu smoothness indicator 13/12 t^2 + 1/4 u^2, each operation rounded
+// as written: the WENO-Z+ weights depend on tau5 = |beta_0 - beta_2|, a
+// near-cancellation, so beta is evaluated without FMA contraction (the order
+// of a plain left-to-right evaluation)
+template <class T> __device__ __forceinline__ T beta_rn(T t, T u) {
+  return add_rn(mul_rn(mul_rn(T(13) / T(12), t), t), mul_rn(mul_rn(T(0.25), u), u));
+}
+
 // kind: 0 weno5, 1 wenoz5, 2 wenozp5 (lam its lambda)
 template <class T>
 __device__ __forceinline__ T weno5_face(int kind, T vm2, T vm1, T v0, T vp1, T vp2, T lam) {
@@ -232,9 +250,20 @@ __device__ __forceinline__ T weno5_face(int kind, T vm2, T vm1, T v0, T vp1, T v
   const T t0 = vm2 - T(2) * vm1 + v0, u0 = vm2 - T(4) * vm1 + T(3) * v0;
   const T t1 = vm1 - T(2) * v0 + vp1, u1 = vm1 - vp1;
   const T t2 = v0 - T(2) * vp1 + vp2, u2 = T(3) * v0 - T(4) * vp1 + vp2;
-  const T b0 = c13 * t0 * t0 + T(0.25) * u0 * u0;
-  const T b1 = c13 * t1 * t1 + T(0.25) * u1 * u1;
-  const T b2 = c13 * t2 * t2 + T(0.25) * u2 * u2;
+  T b0 = c13 * t0 * t0 + T(0.25) * u0 * u0;
+  T b1 = c13 * t1 * t1 + T(0.25) * u1 * u1;
+  T b2 = c13 * t2 * t2 + T(0.25) * u2 * u2;
+  if (kind == 2) {
+    // t and u as written (left to right), then beta without contraction
+    const T tt0 = add_rn(sub_rn(vm2, mul_rn(T(2), vm1)), v0);
+    const T uu0 = add_rn(sub_rn(vm2, mul_rn(T(4), vm1)), mul_rn(T(3), v0));
+    const T tt1 = add_rn(sub_rn(vm1, mul_rn(T(2), v0)), vp1), uu1 = sub_rn(vm1, vp1);
+    const T tt2 = add_rn(sub_rn(v0, mul_rn(T(2), vp1)), vp2);
+    const T uu2 = add_rn(sub_rn(mul_rn(T(3), v0), mul_rn(T(4), vp1)), vp2);
+    b0 = beta_rn(tt0, uu0);
+    b1 = beta_rn(tt1, uu1);
+    b2 = beta_rn(tt2, uu2);
+  }
   const T q0 = (T(2) * vm2 - T(7) * vm1 + T(11) * v0) / T(6);
   const T q1 = (-vm1 + T(5) * v0 + T(2) * vp1) / T(6);
   const T q2 = (T(2) * v0 + T(5) * vp1 - vp2) / T(6);
@@ -242,10 +271,15 @@ __device__ __forceinline__ T weno5_face(int kind, T vm2, T vm1, T v0, T vp1, T v
   if (kind == 2) {
     const T eps = sizeof(T) == 8 ? T(1e-40) : T(1e-36), tau = fabs(b0 - b2);
     if constexpr (sizeof(T) == 8) {
-      const T r0 = tau / (b0 + eps), r1 = tau / (b1 + eps), r2 = tau / (b2 + eps);
-      a0 = T(0.1) * (T(1) + r0 * r0 + lam * (b0 + eps) / (tau + eps));
-      a1 = T(0.6) * (T(1) + r1 * r1 + lam * (b1 + eps) / (tau + eps));
-      a2 = T(0.3) * (T(1) + r2 * r2 + lam * (b2 + eps) / (tau + eps));
+      // the weights as written, each operation rounded (no contraction)
+      const T te = add_rn(tau, eps);
+      auto alpha = [&](T d, T b) {
+        const T be = add_rn(b, eps), r = div_rn(tau, be);
+        return mul_rn(d, add_rn(add_rn(T(1), mul_rn(r, r)), div_rn(mul_rn(lam, be), te)));
+      };
+      a0 = alpha(T(0.1), b0);
+      a1 = alpha(T(0.6), b1);
+      a2 = alpha(T(0.3), b2);
     } else {
       // float: the same weights in a form that cannot overflow.  The lambda
       // term is written L (beta_k + eps)/(beta_max + eps) with

@@ -22,11 +22,9 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b
 __device__ __forceinline__ float2 rcp2(float2 a) { return make_float2(1.f / a.x, 1.f / a.y); }
 __device__ __forceinline__ float2 sqrt2(float2 a) { return make_float2(sqrtf(a.x), sqrtf(a.y)); }
 
-// fast speeds of both sides; bx2 = B_n^2
-__device__ __forceinline__ float2 fast2(float g, float2 rho, float2 p, float2 by, float2 bz,
-                                        float bx2) {
+// fast speeds of both sides; bt = B_t^2, bx2 = B_n^2
+__device__ __forceinline__ float2 fast2(float g, float2 rho, float2 p, float2 bt, float bx2) {
   float2 ir = rcp2(rho);
-  float2 bt = fma2(bz, bz, mul2(by, by));
   float2 a2 = mul2(mul2(sp2(g), p), ir);
   float2 bt2 = mul2(bt, ir);
   float2 bb = mul2(add2(sp2(bx2), bt), ir);
@@ -40,10 +38,11 @@ struct Side2 {
   float2 rho, u, v, w, p, by, bz;
 };
 
-// total pressure and total energy of both sides
+// total pressure and total energy of both sides; bt = B_t^2 of both sides
 __device__ __forceinline__ void pt_e2(const Side2& q, float bx2, float ig1, float2& pt,
-                                      float2& e) {
-  float2 b2 = fma2(q.bz, q.bz, fma2(q.by, q.by, sp2(bx2)));
+                                      float2& e, float2& bt) {
+  bt = fma2(q.bz, q.bz, mul2(q.by, q.by));
+  float2 b2 = add2(bt, sp2(bx2));
   pt = fma2(b2, sp2(0.5f), q.p);
   float2 uu = fma2(q.w, q.w, fma2(q.v, q.v, mul2(q.u, q.u)));
   e = fma2(q.p, sp2(ig1), fma2(mul2(sp2(0.5f), q.rho), uu, mul2(sp2(0.5f), b2)));
@@ -74,9 +73,9 @@ __device__ __forceinline__ void side_flux(float rho, float u, float v, float w, 
 
 __device__ __forceinline__ void hll_pair(float g, float ig1, const Side2& q, float bx, float* f) {
   const float bx2 = bx * bx;
-  float2 pt, e;
-  pt_e2(q, bx2, ig1, pt, e);
-  float2 cf = fast2(g, q.rho, q.p, q.by, q.bz, bx2);
+  float2 pt, e, bt;
+  pt_e2(q, bx2, ig1, pt, e, bt);
+  float2 cf = fast2(g, q.rho, q.p, bt, bx2);
   float sl = fminf(q.u.x - cf.x, q.u.y - cf.y);
   float sr = fmaxf(q.u.x + cf.x, q.u.y + cf.y);
   float UL[8], FL[8], UR[8], FR[8];
@@ -101,9 +100,9 @@ __device__ __forceinline__ void hll_pair(float g, float ig1, const Side2& q, flo
 __device__ __forceinline__ void tvdlf_pair(float g, float ig1, const Side2& q, float bx,
                                            float* f) {
   const float bx2 = bx * bx;
-  float2 pt, e;
-  pt_e2(q, bx2, ig1, pt, e);
-  const float2 cf = fast2(g, q.rho, q.p, q.by, q.bz, bx2);
+  float2 pt, e, bt;
+  pt_e2(q, bx2, ig1, pt, e, bt);
+  const float2 cf = fast2(g, q.rho, q.p, bt, bx2);
   const float cmax = fmaxf(fabsf(q.u.x) + cf.x, fabsf(q.u.y) + cf.y);
   float UL[8], FL[8], UR[8], FR[8];
   side_flux(q.rho.x, q.u.x, q.v.x, q.w.x, q.by.x, q.bz.x, bx, pt.x, e.x, UL, FL);
@@ -120,9 +119,9 @@ __device__ __forceinline__ void tvdlf_pair(float g, float ig1, const Side2& q, f
 
 __device__ __forceinline__ void hlld_pair(float g, float ig1, const Side2& q, float bx, float* f) {
   const float bx2 = bx * bx;
-  float2 pt, e;
-  pt_e2(q, bx2, ig1, pt, e);
-  float2 cf = fast2(g, q.rho, q.p, q.by, q.bz, bx2);
+  float2 pt, e, bt;
+  pt_e2(q, bx2, ig1, pt, e, bt);
+  float2 cf = fast2(g, q.rho, q.p, bt, bx2);
   const float cmax = fmaxf(cf.x, cf.y);
   const float sl = fminf(q.u.x, q.u.y) - cmax;
   const float sr = fmaxf(q.u.x, q.u.y) + cmax;
@@ -167,8 +166,8 @@ __device__ __forceinline__ void hlld_pair(float g, float ig1, const Side2& q, fl
   t = fma2(sp2(bx), sub2(vb, vbs), add2(t, sp2(pts * sm)));
   const float2 es = mul2(t, isd);
   // double-star states (averages of the two sides, packed over (v, w) / (By, Bz))
-  const float2 sqr = sqrt2(rs);
-  const float2 isq = rcp2(sqr);
+  const float2 isq = make_float2(rsqrtf(rs.x), rsqrtf(rs.y));  // 1/sqrt(rho*)
+  const float2 sqr = mul2(rs, isq);
   const float abx = fabsf(bx);
   const float ssl = sm - abx * isq.x, ssr = sm + abx * isq.y;
   const float sb = sgnT(bx);
@@ -271,6 +270,243 @@ __device__ __forceinline__ float2 cada3_pair(float a, float b, float c, float e)
   const float pa0 = fmaxf(0.f, fminf(p3.x, fmaxf(ht.x, i0)));
   const float pa1 = fmaxf(0.f, fminf(p3.y, fmaxf(ht.y, i1)));
   return fma2(mul2(sp2(0.5f), make_float2(s0, s1)), make_float2(pa0, pa1), X);
+}
+
+// ---------------------------------------------------------------------------
+// Two faces per thread, one per float2 lane: lane x the x face of a cell and
+// lane y its y face.  Each lane loads the stencil of its own face already in
+// the face's local frame (normal velocity and field first), so the packed
+// operands need no register shuffling, and the per-face work of HLLD (wave
+// speeds, double-star states, fan region) runs once for both faces.  The
+// formulas are those of hlld_pair / hlld_local (MK05 with the degeneracy
+// threshold, sgn(0) = 0 and the same region ties); only the packing differs.
+
+__device__ __forceinline__ float2 min2(float2 a, float2 b) {
+  return make_float2(fminf(a.x, b.x), fminf(a.y, b.y));
+}
+__device__ __forceinline__ float2 max2(float2 a, float2 b) {
+  return make_float2(fmaxf(a.x, b.x), fmaxf(a.y, b.y));
+}
+__device__ __forceinline__ float2 abs2(float2 a) { return make_float2(fabsf(a.x), fabsf(a.y)); }
+__device__ __forceinline__ float2 sel2(bool px, bool py, float2 a, float2 b) {
+  return make_float2(px ? a.x : b.x, py ? a.y : b.y);
+}
+
+// primitive face states of both faces in their local frames
+struct Prim2 {
+  float2 rho, u, v, w, p, by, bz;
+};
+
+// van Leer slopes of two cells at once from their one-sided differences:
+// 2 dm dp / (dm + dp) where dm dp > 0, else 0
+__device__ __forceinline__ float2 vl_slope2(float2 dm, float2 dp) {
+  const float2 prod = mul2(dm, dp);
+  const float2 s = mul2(mul2(sp2(2.f), prod), rcp2(add2(dm, dp)));
+  return make_float2(prod.x > 0.f ? s.x : 0.f, prod.y > 0.f ? s.y : 0.f);
+}
+
+// fast speeds (cancellation-free form) from rho, p, B_t^2 and B_n^2
+__device__ __forceinline__ float2 fast_xy(float g, float2 rho, float2 p, float2 bt, float2 bx2) {
+  const float2 ir = rcp2(rho);
+  const float2 a2 = mul2(mul2(sp2(g), p), ir);
+  const float2 bt2 = mul2(bt, ir);
+  const float2 bb = mul2(add2(bx2, bt), ir);
+  const float2 dd = sub2(a2, bb);
+  const float2 sq = sqrt2(fma2(dd, dd, mul2(mul2(sp2(4.f), a2), bt2)));
+  return sqrt2(mul2(sp2(0.5f), add2(add2(a2, bb), sq)));
+}
+
+// single-star state of one side (MK05 eqs. 43-48) for both faces
+struct Star2 {
+  float2 rs, vs, ws, bys, bzs, es, vbs;
+};
+
+__device__ __forceinline__ Star2 hlld_star_xy(const Prim2& q, float2 S, float2 su, float2 A,
+                                              float2 pt, float2 e, float2 sm, float2 pts,
+                                              float2 bx, float2 bx2) {
+  Star2 r;
+  const float2 ssm = sub2(S, sm);
+  const float2 isd = rcp2(ssm);
+  r.rs = mul2(A, isd);
+  const float2 big = mul2(A, ssm);
+  const float2 den = sub2(big, bx2);
+  const float2 iden = rcp2(den);
+  const float2 tv = mul2(mul2(bx, sub2(sm, q.u)), iden);
+  const float2 tb = mul2(sub2(mul2(A, su), bx2), iden);
+  const float2 ntv = mul2(tv, sp2(-1.f));
+  const float eps = Num<float>::hlld_eps;
+  const bool dgx = fabsf(den.x) <= eps * fmaxf(fabsf(big.x), bx2.x);
+  const bool dgy = fabsf(den.y) <= eps * fmaxf(fabsf(big.y), bx2.y);
+  r.vs = sel2(dgx, dgy, q.v, fma2(q.by, ntv, q.v));
+  r.ws = sel2(dgx, dgy, q.w, fma2(q.bz, ntv, q.w));
+  r.bys = sel2(dgx, dgy, q.by, mul2(q.by, tb));
+  r.bzs = sel2(dgx, dgy, q.bz, mul2(q.bz, tb));
+  const float2 vb = fma2(q.w, q.bz, fma2(q.v, q.by, mul2(q.u, bx)));
+  r.vbs = fma2(r.ws, r.bzs, fma2(r.vs, r.bys, mul2(sm, bx)));
+  float2 t = sub2(mul2(su, e), mul2(pt, q.u));
+  t = fma2(bx, sub2(vb, r.vbs), fma2(pts, sm, t));
+  r.es = mul2(t, isd);
+  return r;
+}
+
+// HLLD flux of two faces; f[c] for the local components c = 0..7 (c = 5, the
+// normal field, is left to the glm solve)
+__device__ __forceinline__ void hlld_xy(float g, float ig1, const Prim2& L, const Prim2& R,
+                                        float2 bx, float2* f) {
+  const float2 bx2 = mul2(bx, bx);
+  const float2 btL = fma2(L.bz, L.bz, mul2(L.by, L.by));
+  const float2 btR = fma2(R.bz, R.bz, mul2(R.by, R.by));
+  const float2 b2L = add2(btL, bx2), b2R = add2(btR, bx2);
+  const float2 ptL = fma2(b2L, sp2(0.5f), L.p), ptR = fma2(b2R, sp2(0.5f), R.p);
+  const float2 uuL = fma2(L.w, L.w, fma2(L.v, L.v, mul2(L.u, L.u)));
+  const float2 uuR = fma2(R.w, R.w, fma2(R.v, R.v, mul2(R.u, R.u)));
+  const float2 eL = fma2(L.p, sp2(ig1), fma2(mul2(sp2(0.5f), L.rho), uuL, mul2(sp2(0.5f), b2L)));
+  const float2 eR = fma2(R.p, sp2(ig1), fma2(mul2(sp2(0.5f), R.rho), uuR, mul2(sp2(0.5f), b2R)));
+  const float2 cmax = max2(fast_xy(g, L.rho, L.p, btL, bx2), fast_xy(g, R.rho, R.p, btR, bx2));
+  const float2 sl = sub2(min2(L.u, R.u), cmax), sr = add2(max2(L.u, R.u), cmax);
+  const float2 suL = sub2(sl, L.u), suR = sub2(sr, R.u);
+  const float2 AL = mul2(suL, L.rho), AR = mul2(suR, R.rho);
+  const float2 iden = rcp2(sub2(AR, AL));
+  // S_M and p_T* from the HLL-averaged normal momentum (MK05 eqs. 38, 41)
+  const float2 sm = mul2(sub2(fma2(AR, R.u, ptL), fma2(AL, L.u, ptR)), iden);
+  const float2 pts = mul2(fma2(mul2(mul2(L.rho, R.rho), mul2(suR, suL)), sub2(R.u, L.u),
+                               sub2(mul2(AR, ptL), mul2(AL, ptR))),
+                          iden);
+  const Star2 SL = hlld_star_xy(L, sl, suL, AL, ptL, eL, sm, pts, bx, bx2);
+  const Star2 SR = hlld_star_xy(R, sr, suR, AR, ptR, eR, sm, pts, bx, bx2);
+  // double-star states (MK05 eqs. 59-63)
+  const float2 isqL = make_float2(rsqrtf(SL.rs.x), rsqrtf(SL.rs.y));
+  const float2 isqR = make_float2(rsqrtf(SR.rs.x), rsqrtf(SR.rs.y));
+  const float2 sqrL = mul2(SL.rs, isqL), sqrR = mul2(SR.rs, isqR);
+  const float2 abx = abs2(bx);
+  const float2 ssl = sub2(sm, mul2(abx, isqL)), ssr = fma2(abx, isqR, sm);
+  const float2 sb = make_float2(sgnT(bx.x), sgnT(bx.y));
+  const float2 issum = rcp2(add2(sqrL, sqrR));
+  const float2 vss = mul2(fma2(sub2(SR.bys, SL.bys), sb, fma2(sqrR, SR.vs, mul2(sqrL, SL.vs))), issum);
+  const float2 wss = mul2(fma2(sub2(SR.bzs, SL.bzs), sb, fma2(sqrR, SR.ws, mul2(sqrL, SL.ws))), issum);
+  const float2 sqq = mul2(mul2(sqrL, sqrR), sb);
+  const float2 byss = mul2(fma2(sub2(SR.vs, SL.vs), sqq, fma2(sqrL, SR.bys, mul2(sqrR, SL.bys))), issum);
+  const float2 bzss = mul2(fma2(sub2(SR.ws, SL.ws), sqq, fma2(sqrL, SR.bzs, mul2(sqrR, SL.bzs))), issum);
+  const float2 vbss = fma2(wss, bzss, fma2(vss, byss, mul2(sm, bx)));
+  // e** = e* -/+ sqrt(rho*) (v*.B* - v**.B**) sgn(Bx)
+  const float2 essL = fma2(mul2(sqrL, sb), sub2(vbss, SL.vbs), SL.es);
+  const float2 essR = fma2(mul2(sqrR, sb), sub2(SR.vbs, vbss), SR.es);
+  // fan region containing x/t = 0, per face (ties as in the scalar solver)
+  const bool lx = sm.x >= 0.f, ly = sm.y >= 0.f;
+  const bool ox = lx ? (sl.x > 0.f) : (sr.x < 0.f), oy = ly ? (sl.y > 0.f) : (sr.y < 0.f);
+  const bool sx = lx ? (ssl.x >= 0.f) : !(ssr.x >= 0.f);
+  const bool sy = ly ? (ssl.y >= 0.f) : !(ssr.y >= 0.f);
+  // the upwind side of S_M
+  const float2 rho = sel2(lx, ly, L.rho, R.rho), u = sel2(lx, ly, L.u, R.u);
+  const float2 v = sel2(lx, ly, L.v, R.v), w = sel2(lx, ly, L.w, R.w);
+  const float2 by = sel2(lx, ly, L.by, R.by), bz = sel2(lx, ly, L.bz, R.bz);
+  const float2 pt = sel2(lx, ly, ptL, ptR), e = sel2(lx, ly, eL, eR);
+  const float2 rs = sel2(lx, ly, SL.rs, SR.rs), vs = sel2(lx, ly, SL.vs, SR.vs);
+  const float2 ws = sel2(lx, ly, SL.ws, SR.ws), bys = sel2(lx, ly, SL.bys, SR.bys);
+  const float2 bzs = sel2(lx, ly, SL.bzs, SR.bzs), es = sel2(lx, ly, SL.es, SR.es);
+  const float2 ess = sel2(lx, ly, essL, essR);
+  const float2 c1 = sel2(lx, ly, sl, sr), c2 = sel2(lx, ly, ssl, ssr);
+  const float2 mu = mul2(rho, u);
+  const float2 vb = fma2(w, bz, fma2(v, by, mul2(u, bx)));
+  // physical flux F, state U, star U* and double-star U** of that side
+  const float2 F[8] = {mu, fma2(mu, u, sub2(pt, bx2)), fma2(mu, v, mul2(mul2(bx, by), sp2(-1.f))),
+                       fma2(mu, w, mul2(mul2(bx, bz), sp2(-1.f))),
+                       sub2(mul2(add2(e, pt), u), mul2(bx, vb)), sp2(0.f),
+                       sub2(mul2(by, u), mul2(bx, v)), sub2(mul2(bz, u), mul2(bx, w))};
+  const float2 U[8] = {rho, mu, mul2(rho, v), mul2(rho, w), e, bx, by, bz};
+  const float2 US[8] = {rs, mul2(rs, sm), mul2(rs, vs), mul2(rs, ws), es, bx, bys, bzs};
+  const float2 USS[8] = {rs, mul2(rs, sm), mul2(rs, vss), mul2(rs, wss), ess, bx, byss, bzss};
+#pragma unroll
+  for (int c = 0; c < 8; c++) {
+    if (c == 5) {
+      f[c] = sp2(0.f);
+      continue;
+    }
+    const float2 fs = fma2(c1, sub2(US[c], U[c]), F[c]);
+    // the double-star and star states differ in the tangential and energy parts only
+    const float2 fss = (c == 0 || c == 1) ? fs : fma2(c2, sub2(USS[c], US[c]), fs);
+    f[c] = make_float2(ox ? F[c].x : (sx ? fs.x : fss.x), oy ? F[c].y : (sy ? fs.y : fss.y));
+  }
+}
+
+// local component c of the y face -> primitive variable (normal y, tangential
+// (z, x)); the x face uses the identity
+__device__ __forceinline__ constexpr int yface_var(int c) {
+  return c == 1 ? 2 : c == 2 ? 3 : c == 3 ? 1 : c == 5 ? 6 : c == 6 ? 7 : c == 7 ? 5 : c;
+}
+
+// x and y face fluxes of one cell with vanleer + HLLD: ax(v, t), ay(v, t) the
+// 4-cell stencils (cells f-2 .. f+1) of the x and y faces; positivity fallback
+// and glm as in stencil_flux_f2, per face
+template <class AX, class AY>
+__device__ __forceinline__ void stencil_flux_xy(AX ax, AY ay, int glm, float g, float ch,
+                                                float* fx, float* fy) {
+  float2 wl[NV], wr[NV];
+#pragma unroll
+  for (int c = 0; c < NV; c++) {
+    const int vy = yface_var(c);
+    const float2 A = make_float2(ax(c, 0), ay(vy, 0)), B = make_float2(ax(c, 1), ay(vy, 1));
+    const float2 C = make_float2(ax(c, 2), ay(vy, 2)), E = make_float2(ax(c, 3), ay(vy, 3));
+    const float2 d2 = sub2(C, B);
+    wl[c] = fma2(sp2(0.5f), vl_slope2(sub2(B, A), d2), B);
+    wr[c] = fma2(sp2(-0.5f), vl_slope2(d2, sub2(E, C)), C);
+  }
+  const bool bx_ = !(wl[0].x > 0.f) || !(wl[4].x > 0.f) || !(wr[0].x > 0.f) || !(wr[4].x > 0.f);
+  const bool by_ = !(wl[0].y > 0.f) || !(wl[4].y > 0.f) || !(wr[0].y > 0.f) || !(wr[4].y > 0.f);
+  if (bx_ || by_) {
+#pragma unroll
+    for (int c = 0; c < NV; c++) {
+      if (bx_) {
+        wl[c].x = ax(c, 1);
+        wr[c].x = ax(c, 2);
+      }
+      if (by_) {
+        wl[c].y = ay(yface_var(c), 1);
+        wr[c].y = ay(yface_var(c), 2);
+      }
+    }
+  }
+  const float2 bnl = wl[5], bnr = wr[5];
+  float2 bns, psis;
+  if (glm) {
+    const float ih = 0.5f / ch;
+    bns = sub2(mul2(sp2(0.5f), add2(bnl, bnr)), mul2(sp2(ih), sub2(wr[8], wl[8])));
+    psis = sub2(mul2(sp2(0.5f), add2(wl[8], wr[8])), mul2(sp2(0.5f * ch), sub2(bnr, bnl)));
+  } else {
+    bns = mul2(sp2(0.5f), add2(bnl, bnr));
+    psis = sp2(0.f);
+  }
+  float2 fl[8];
+#ifdef AMRVAC_XY_SPLIT_EXPERIMENT
+  {
+    float fa[8], fb[8];
+    Side2 qx, qy;
+    qx.rho = make_float2(wl[0].x, wr[0].x); qx.u = make_float2(wl[1].x, wr[1].x);
+    qx.v = make_float2(wl[2].x, wr[2].x); qx.w = make_float2(wl[3].x, wr[3].x);
+    qx.p = make_float2(wl[4].x, wr[4].x); qx.by = make_float2(wl[6].x, wr[6].x);
+    qx.bz = make_float2(wl[7].x, wr[7].x);
+    hlld_pair(g, 1.f / (g - 1.f), qx, bns.x, fa);
+    qy.rho = make_float2(wl[0].y, wr[0].y); qy.u = make_float2(wl[1].y, wr[1].y);
+    qy.v = make_float2(wl[2].y, wr[2].y); qy.w = make_float2(wl[3].y, wr[3].y);
+    qy.p = make_float2(wl[4].y, wr[4].y); qy.by = make_float2(wl[6].y, wr[6].y);
+    qy.bz = make_float2(wl[7].y, wr[7].y);
+    hlld_pair(g, 1.f / (g - 1.f), qy, bns.y, fb);
+    for (int c = 0; c < 8; c++) fl[c] = make_float2(fa[c], fb[c]);
+  }
+#else
+  const Prim2 L = {wl[0], wl[1], wl[2], wl[3], wl[4], wl[6], wl[7]};
+  const Prim2 R = {wr[0], wr[1], wr[2], wr[3], wr[4], wr[6], wr[7]};
+  hlld_xy(g, 1.f / (g - 1.f), L, R, bns, fl);
+#endif
+  const float2 fpsi = glm ? mul2(sp2(ch * ch), bns) : sp2(0.f);
+  fl[5] = psis;
+#pragma unroll
+  for (int c = 0; c < 8; c++) {
+    fx[c] = fl[c].x;
+    fy[yface_var(c)] = fl[c].y;
+  }
+  fx[8] = fpsi.x;
+  fy[8] = fpsi.y;
 }
 
 // Face flux along D from the 4-cell stencils of the 9 primitive variables:

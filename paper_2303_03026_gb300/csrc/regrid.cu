@@ -7,7 +7,8 @@
 //       ghost operators of the update), and the block's refine / coarsen flag.
 //       The arithmetic is double with explicit round-to-nearest operations;
 //       the tiled form stages the quantities in shared memory.
-//   amrvac_regrid_plan (host): the new block list, closed under 2:1 balance.
+//   amrvac_regrid_plan (host) and amrvac_regrid_plan_device: the new block
+//       list, closed under 2:1 balance.
 //   k_regrid_transfer: fills a state built on the new list from the old one:
 //       copy, prolongation (coarse value plus minmod-limited slopes times
 //       +-1/4) or restriction (mean of the 2^d children cells).  Sums are
@@ -607,5 +608,338 @@ extern "C" amrvac_status amrvac_regrid_transfer(amrvac_state* src, int32_t src_b
   dst->launches++;
   // the host table must outlive the asynchronous upload
   if (cudaStreamSynchronize(dst->stream) != cudaSuccess) return AMRVAC_E_CUDA;
+  return AMRVAC_OK;
+}
+
+// --------------------------------------------------------------------------
+// The regrid plan on the device.  The same rules as amrvac_regrid_plan, as
+// data-parallel passes over the leaves of the state's mesh:
+//   1. splits: the flagged leaves; then, to a fixed point, every leaf coarser
+//      than a splitting leaf and touching it (faces, edges, corners, periodic
+//      wrap) splits too (one pass per launch, the host repeats while a pass
+//      changed something);
+//   2. merges: a family of 2^ndim sibling leaves all flagged -1 and none
+//      splitting merges unless, after the splits, a leaf two levels finer
+//      than the parent touches it.  In the sequential rule (families in
+//      increasing (instance, level, k, j, i) order of the parent) that test
+//      can change only through merges of finer families, which come later, so
+//      every family is decided independently here;
+//   3. the new leaves are marked in dense per-(instance, level) maps, and a
+//      prefix sum over the maps in (instance, level, k, j, i) order numbers
+//      them: the new block list in the order amrvac_regrid_plan returns.
+namespace amrvac {
+namespace {
+
+enum { FATE_KEEP = 0, FATE_SPLIT = 1, FATE_MERGE_FIRST = 2, FATE_MERGE_AWAY = 3 };
+
+__device__ __forceinline__ int plan_nb(const DevMesh& M, int q, int L, int d) {
+  return M.lnb[(q * MAXLEV + L) * 3 + d];
+}
+
+// position p + o at level L of instance q, wrapped on periodic dimensions;
+// false outside the others
+__device__ __forceinline__ bool plan_step(const DevMesh& M, int q, int L, const int* p,
+                                          const int* o, int* r) {
+  for (int d = 0; d < 3; d++) {
+    r[d] = d < M.ndim ? p[d] + o[d] : 0;
+    if (d >= M.ndim) continue;
+    const int n = plan_nb(M, q, L, d);
+    if (r[d] < 0 || r[d] >= n) {
+      if (M.bc[d][0] != AMRVAC_BC_PERIODIC) return false;
+      r[d] = ((r[d] % n) + n) % n;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ int plan_map(const DevMesh& M, int q, int L, const int* p) {
+  return M.lmap[M.lmap_off[q * MAXLEV + L] +
+                ((size_t)p[2] * plan_nb(M, q, L, 1) + p[1]) * plan_nb(M, q, L, 0) + p[0]];
+}
+
+// leaf covering level-L position p at level L or coarser (its level in *lev),
+// -1 when finer leaves cover p
+__device__ __forceinline__ int plan_covering(const DevMesh& M, int q, int L, const int* p0,
+                                             int* lev) {
+  int p[3] = {p0[0], p0[1], p0[2]};
+  for (int LL = L; LL >= 0; LL--) {
+    const int code = plan_map(M, q, LL, p);
+    if (code >= 0) {
+      *lev = LL;
+      return code;
+    }
+    if (code == MAP_REFINED) return -1;
+    for (int d = 0; d < 3; d++) p[d] >>= 1;
+  }
+  return -1;
+}
+
+// the 3^ndim - 1 offsets around a position
+__device__ __forceinline__ bool plan_offset(const DevMesh& M, int t, int* o) {
+  o[0] = t % 3 - 1;
+  o[1] = M.ndim > 1 ? (t / 3) % 3 - 1 : 0;
+  o[2] = M.ndim > 2 ? t / 9 - 1 : 0;
+  return !(o[0] == 0 && o[1] == 0 && o[2] == 0);
+}
+
+__global__ void k_plan_init(DevMesh M, const signed char* __restrict__ flags, PlanScratch P) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < M.nblocks; b += gridDim.x * blockDim.x) {
+    const int split = flags[b] == 1;
+    if (split && M.blk[b * 5 + 1] + 1 >= MAXLEV) P.scal[2] = 1;  // no level to split into
+    P.ref[b] = split;
+  }
+}
+
+// one pass of the 2:1 closure of the splits
+__global__ void k_plan_close(DevMesh M, PlanScratch P) {
+  const int nt = M.ndim == 3 ? 27 : (M.ndim == 2 ? 9 : 3);
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < M.nblocks; b += gridDim.x * blockDim.x) {
+    if (!P.ref[b]) continue;
+    const int q = M.blk[b * 5], L = M.blk[b * 5 + 1];
+    const int p[3] = {M.blk[b * 5 + 2], M.blk[b * 5 + 3], M.blk[b * 5 + 4]};
+    for (int t = 0; t < nt; t++) {
+      int o[3], r[3];
+      if (!plan_offset(M, t, o) || !plan_step(M, q, L, p, o, r)) continue;
+      int lev = 0;
+      const int c = plan_covering(M, q, L, r, &lev);
+      if (c >= 0 && lev < L && !P.ref[c]) {
+        P.ref[c] = 1;
+        P.scal[0] = 1;
+      }
+    }
+  }
+}
+
+__global__ void k_plan_fate(DevMesh M, PlanScratch P) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < M.nblocks; b += gridDim.x * blockDim.x)
+    P.fate[b] = P.ref[b] ? FATE_SPLIT : FATE_KEEP;
+}
+
+// merges, decided by the family's first child (all offsets 0)
+__global__ void k_plan_merge(DevMesh M, const signed char* __restrict__ flags, PlanScratch P) {
+  const int nt = M.ndim == 3 ? 27 : (M.ndim == 2 ? 9 : 3);
+  const int nk = 1 << M.ndim;
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < M.nblocks; b += gridDim.x * blockDim.x) {
+    const int q = M.blk[b * 5], L = M.blk[b * 5 + 1];
+    const int p[3] = {M.blk[b * 5 + 2], M.blk[b * 5 + 3], M.blk[b * 5 + 4]};
+    if (flags[b] != -1 || P.ref[b] || L == 0) continue;
+    if ((p[0] & 1) || (p[1] & 1) || (p[2] & 1)) continue;  // not the first child
+    int kids[8];
+    bool ok = true;
+    for (int c = 0; c < nk && ok; c++) {
+      const int cp[3] = {p[0] + (c & 1), p[1] + ((c >> 1) & 1), p[2] + ((c >> 2) & 1)};
+      const int s = plan_map(M, q, L, cp);
+      ok = s >= 0 && flags[s] == -1 && !P.ref[s];
+      kids[c] = s;
+    }
+    if (!ok) continue;
+    // no leaf two levels finer than the parent around it, after the splits:
+    // every level-L position inside the parent's neighbours must be a leaf of
+    // level L that does not split, or covered by a coarser leaf
+    const int pp[3] = {p[0] >> 1, p[1] >> 1, p[2] >> 1};
+    for (int t = 0; t < nt && ok; t++) {
+      int o[3], r[3];
+      if (!plan_offset(M, t, o) || !plan_step(M, q, L - 1, pp, o, r)) continue;
+      for (int c = 0; c < nk && ok; c++) {
+        const int cp[3] = {2 * r[0] + (c & 1), M.ndim > 1 ? 2 * r[1] + ((c >> 1) & 1) : 0,
+                           M.ndim > 2 ? 2 * r[2] + ((c >> 2) & 1) : 0};
+        const int code = plan_map(M, q, L, cp);
+        if (code == MAP_REFINED || (code >= 0 && P.ref[code])) ok = false;
+      }
+    }
+    if (!ok) continue;
+    P.fate[b] = FATE_MERGE_FIRST;
+    for (int c = 1; c < nk; c++) P.fate[kids[c]] = FATE_MERGE_AWAY;
+  }
+}
+
+__device__ __forceinline__ void plan_mark(const DevMesh& M, const PlanScratch& P, int q, int L,
+                                          const int* p) {
+  const int n0 = plan_nb(M, q, L, 0), n1 = plan_nb(M, q, L, 1);
+  P.map[(size_t)P.seg[q * MAXLEV + L] + ((size_t)p[2] * n1 + p[1]) * n0 + p[0]] = 1;
+}
+
+__global__ void k_plan_mark(DevMesh M, PlanScratch P) {
+  const int nk = 1 << M.ndim;
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < M.nblocks; b += gridDim.x * blockDim.x) {
+    const int q = M.blk[b * 5], L = M.blk[b * 5 + 1];
+    const int p[3] = {M.blk[b * 5 + 2], M.blk[b * 5 + 3], M.blk[b * 5 + 4]};
+    const int f = P.fate[b];
+    if (f == FATE_KEEP) {
+      plan_mark(M, P, q, L, p);
+    } else if (f == FATE_SPLIT) {
+      for (int c = 0; c < nk; c++) {
+        const int cp[3] = {2 * p[0] + (c & 1), M.ndim > 1 ? 2 * p[1] + ((c >> 1) & 1) : 0,
+                           M.ndim > 2 ? 2 * p[2] + ((c >> 2) & 1) : 0};
+        plan_mark(M, P, q, L + 1, cp);
+      }
+    } else if (f == FATE_MERGE_FIRST) {
+      const int pp[3] = {p[0] >> 1, p[1] >> 1, p[2] >> 1};
+      plan_mark(M, P, q, L - 1, pp);
+    }
+  }
+}
+
+// block-wide exclusive prefix sum of one int per thread (blockDim 256)
+__device__ __forceinline__ int plan_block_scan(int v, int* total) {
+  __shared__ int ws[8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) ws[warp] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int w = 0; w < 8; w++) {
+      const int t = ws[w];
+      ws[w] = acc;
+      acc += t;
+    }
+    *total = acc;
+  }
+  __syncthreads();
+  const int r = x - v + ws[warp];
+  __syncthreads();
+  return r;
+}
+
+// per-CTA counts of new leaves over contiguous chunks of the maps
+__global__ void __launch_bounds__(256) k_plan_count(PlanScratch P, int chunk) {
+  __shared__ int red[8];
+  const size_t lo = (size_t)blockIdx.x * chunk;
+  const size_t hi = lo + chunk < (size_t)P.nmap ? lo + chunk : (size_t)P.nmap;
+  int n = 0;
+  for (size_t e = lo + threadIdx.x; e < hi; e += blockDim.x) n += P.map[e];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = n;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < 8; w++) t += red[w];
+    P.sums[blockIdx.x] = t;
+  }
+}
+
+// exclusive prefix of the CTA counts (one thread: at most PLAN_CTAS entries)
+__global__ void k_plan_prefix(PlanScratch P, int nctas) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int acc = 0;
+  for (int c = 0; c < nctas; c++) {
+    const int t = P.sums[c];
+    P.sums[c] = acc;
+    acc += t;
+  }
+  P.sums[nctas] = acc;
+  P.scal[1] = acc;
+}
+
+// each new leaf's index = its CTA's prefix + the running count inside the
+// chunk; writes (instance, level, i, j, k)
+__global__ void __launch_bounds__(256) k_plan_emit(DevMesh M, PlanScratch P, int chunk,
+                                                   int nseg) {
+  const size_t lo = (size_t)blockIdx.x * chunk;
+  const size_t hi = lo + chunk < (size_t)P.nmap ? lo + chunk : (size_t)P.nmap;
+  int base = P.sums[blockIdx.x];
+  for (size_t e0 = lo; e0 < hi; e0 += blockDim.x) {
+    const size_t e = e0 + threadIdx.x;
+    const int v = e < hi ? P.map[e] : 0;
+    int tot = 0;
+    const int at = base + plan_block_scan(v, &tot);
+    __shared__ int stot;
+    if (threadIdx.x == 0) stot = tot;
+    __syncthreads();
+    if (v && at < P.cap) {
+      // segment (instance, level) of entry e: the last offset <= e
+      int a = 0, z = nseg - 1;
+      while (a < z) {
+        const int m = (a + z + 1) >> 1;
+        if ((size_t)P.seg[m] <= e) a = m;
+        else z = m - 1;
+      }
+      const int q = a / MAXLEV, L = a % MAXLEV;
+      const int pos = (int)(e - (size_t)P.seg[a]);
+      const int n0 = plan_nb(M, q, L, 0), n1 = plan_nb(M, q, L, 1);
+      int* o = P.out + (size_t)at * 5;
+      o[0] = q;
+      o[1] = L;
+      o[2] = pos % n0;
+      o[3] = M.ndim > 1 ? (pos / n0) % n1 : 0;
+      o[4] = M.ndim > 2 ? pos / (n0 * n1) : 0;
+    }
+    base += stot;
+    __syncthreads();
+  }
+}
+
+}  // namespace
+}  // namespace amrvac
+
+extern "C" amrvac_status amrvac_regrid_plan_device(amrvac_state* s, const int8_t* h_flags,
+                                                   int32_t capacity, int32_t* h_new_meta,
+                                                   int32_t* h_new_nblocks) {
+  using namespace amrvac;
+  if (!s || !h_new_nblocks || capacity < 0 || (capacity > 0 && !h_new_meta))
+    return AMRVAC_E_INVALID;
+  PlanScratch& P = s->plan;
+  if (P.nmap < 0) return AMRVAC_E_INVALID;  // the dense maps of this mesh would be too large
+  cudaStream_t st = s->stream;
+  if (h_flags) {
+    for (int b = 0; b < s->nblocks; b++)
+      if (h_flags[b] < -1 || h_flags[b] > 1) return AMRVAC_E_INVALID;
+    if (cudaMemcpyAsync(s->d_eflags, h_flags, (size_t)s->nblocks, cudaMemcpyHostToDevice, st) !=
+        cudaSuccess)
+      return AMRVAC_E_CUDA;
+  }
+  const DevMesh& M = s->mesh;
+  const int nb = s->nblocks;
+  const int grid = (nb + 255) / 256 < 152 * 8 ? (nb + 255) / 256 : 152 * 8;
+  int launches = 0;
+  if (cudaMemsetAsync(P.scal, 0, sizeof(int) * 4, st) != cudaSuccess ||
+      cudaMemsetAsync(P.map, 0, sizeof(int) * ((size_t)P.nmap + 1), st) != cudaSuccess)
+    return AMRVAC_E_CUDA;
+  k_plan_init<<<grid, 256, 0, st>>>(M, s->d_eflags, P);
+  launches++;
+  // 2:1 closure: at most one level coarser per pass, so at most MAXLEV passes
+  for (int pass = 0; pass < MAXLEV + 1; pass++) {
+    k_plan_close<<<grid, 256, 0, st>>>(M, P);
+    launches++;
+    int changed = 0;
+    if (cudaMemcpyAsync(&changed, P.scal, sizeof(int), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return AMRVAC_E_CUDA;
+    if (!changed) break;
+    if (cudaMemsetAsync(P.scal, 0, sizeof(int), st) != cudaSuccess) return AMRVAC_E_CUDA;
+  }
+  k_plan_fate<<<grid, 256, 0, st>>>(M, P);
+  k_plan_merge<<<grid, 256, 0, st>>>(M, s->d_eflags, P);
+  k_plan_mark<<<grid, 256, 0, st>>>(M, P);
+  const int chunk = (P.nmap + PLAN_CTAS - 1) / PLAN_CTAS > 256
+                        ? (P.nmap + PLAN_CTAS - 1) / PLAN_CTAS
+                        : 256;
+  const int nctas = (P.nmap + chunk - 1) / chunk > 0 ? (P.nmap + chunk - 1) / chunk : 1;
+  k_plan_count<<<nctas, 256, 0, st>>>(P, chunk);
+  k_plan_prefix<<<1, 32, 0, st>>>(P, nctas);
+  k_plan_emit<<<nctas, 256, 0, st>>>(M, P, chunk, s->ninst * MAXLEV);
+  launches += 6;
+  if (cudaPeekAtLastError() != cudaSuccess) return AMRVAC_E_CUDA;
+  s->launches += launches;
+  int scal[4] = {0, 0, 0, 0};
+  if (cudaMemcpyAsync(scal, P.scal, sizeof(scal), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return AMRVAC_E_CUDA;
+  if (scal[2]) return AMRVAC_E_INVALID;  // a flagged leaf at the deepest level
+  *h_new_nblocks = scal[1];
+  if (capacity < scal[1] || scal[1] > P.cap) return AMRVAC_E_INVALID;
+  if (scal[1] > 0 &&
+      (cudaMemcpyAsync(h_new_meta, P.out, sizeof(int) * 5 * (size_t)scal[1],
+                       cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+       cudaStreamSynchronize(st) != cudaSuccess))
+    return AMRVAC_E_CUDA;
   return AMRVAC_OK;
 }

@@ -14,6 +14,22 @@ namespace amrvac {
 // 1 prolongation from a parent, 2 restriction of children), source block, and
 // the 2^ndim source children of a merged parent in (z, y, x) order
 constexpr int RTAB_N = 10;
+// CTAs of the compaction of the device regrid plan
+constexpr int PLAN_CTAS = 512;
+
+// device regrid plan scratch (in the workspace)
+struct PlanScratch {
+  int* ref = nullptr;           // [nblocks] 1 when the leaf splits
+  signed char* fate = nullptr;  // [nblocks] keep, split, first child of a merge, merged away
+  int* map = nullptr;           // dense new-leaf marks, per (instance, level) segment
+  int* seg = nullptr;           // [ninst * MAXLEV + 1] segment offsets of map
+  int* maxlev = nullptr;        // [ninst] deepest level of the current mesh
+  int* sums = nullptr;          // [PLAN_CTAS + 1] per-CTA counts, then their prefix
+  int* scal = nullptr;          // [0] changed, [1] new block count, [2] error
+  int* out = nullptr;           // [cap][5] the new block list
+  int cap = 0;
+  int nmap = -1;                // entries of map; -1: the dense maps would be too large
+};
 }  // namespace amrvac
 
 struct amrvac_state {
@@ -62,6 +78,7 @@ struct amrvac_state {
   double* d_est = nullptr;
   signed char* d_eflags = nullptr;
   int* d_rtab = nullptr;
+  amrvac::PlanScratch plan;
   // host copies
   std::vector<int32_t> meta;
   std::vector<amrvac_instance_desc> inst;

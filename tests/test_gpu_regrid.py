@@ -302,3 +302,60 @@ def test_regrid_with_walls(amr, orc):
     new, ref, got = _transfer_pair(amr, orc, W, f, "fp64")
     scale = np.maximum(np.abs(W.U).max(axis=(1, 2)), 1e-300)[:, None, None]
     assert (np.abs(got - ref) / scale).max() <= 1e-14
+
+
+# ----------------------------------------------------------------------------
+# the plan on the device: the same block list as the host plan and the oracle
+# ----------------------------------------------------------------------------
+
+def _flag_patterns(W, seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    lev = W.block_meta[:, 1]
+    out = [_random_flags(W, seed)]
+    sparse = np.where(rng.random(W.nblocks) < 0.05, 1, 0)
+    sparse[rng.random(W.nblocks) < 0.5] = -1
+    sparse[lev == 0] = np.maximum(sparse[lev == 0], 0)
+    out.append(sparse)
+    allc = np.full(W.nblocks, -1)
+    allc[lev == 0] = 0
+    out.append(allc)                       # as many merges as 2:1 allows
+    out.append(np.ones(W.nblocks, int))    # every leaf splits
+    return [np.asarray(f, np.int8) for f in out]
+
+
+@pytest.mark.parametrize("name", ["1d", "2d", "2d_outflow", "3d", "instances"])
+def test_device_plan_equals_host_and_oracle(amr, name):
+    W = (wl.c5_instances(count=5, nmin=32, nmax=96, precision="fp64") if name == "instances"
+         else _cases()[name])
+    S = amr.State.from_workload(W, kernel="plain")
+    for seed in (3, 4):
+        for f in _flag_patterns(W, seed):
+            ref = rg.plan(W.cfg, W.instances, W.block_meta, f)
+            host = amr.regrid_plan(W.cfg, W.instances, W.block_meta, f)
+            dev = S.regrid_plan(f)
+            np.testing.assert_array_equal(host, ref)
+            np.testing.assert_array_equal(dev, ref)
+    # flags from the device estimator, used where they are
+    _, fl = S.regrid_estimate(0.05, 0.2, max_level=int(W.block_meta[:, 1].max()) + 1)
+    np.testing.assert_array_equal(S.regrid_plan(), rg.plan(W.cfg, W.instances, W.block_meta, fl))
+    S.close()
+
+
+def test_device_plan_full_3d_blast_mesh(amr):
+    # the benchmark's 3D AMR mesh (18,304 blocks over 4 levels): bit-identical
+    # to the host plan, and timed against it
+    import time
+    W = wl.c4_blast_amr(base=6)
+    S = amr.State.from_workload(W)
+    for f in _flag_patterns(W, 7)[:2]:
+        t0 = time.perf_counter()
+        host = amr.regrid_plan(W.cfg, W.instances, W.block_meta, f)
+        t_host = time.perf_counter() - t0
+        S.regrid_plan(f)
+        t0 = time.perf_counter()
+        dev = S.regrid_plan(f)
+        t_dev = time.perf_counter() - t0
+        np.testing.assert_array_equal(dev, host)
+        print("plan of %d -> %d blocks: host %.2f ms, device %.2f ms"
+              % (W.nblocks, len(dev), 1e3 * t_host, 1e3 * t_dev))
+    S.close()

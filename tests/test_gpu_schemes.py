@@ -358,7 +358,18 @@ def test_five_point_full_run(amr, orc, limiter):
     S.close()
     assert d["status"] == 0 and abs(d["t"][0] - t[0]) < 1e-14
     sc = np.maximum(np.abs(Uo).max(axis=(1, 2), keepdims=True), 1e-300)
-    assert (np.abs(got - Uo) / sc).max() < 1e-10
+    tol = 1e-10
+    if limiter == "wenozp5":
+        # the WENO-Z+ weights amplify rounding over a run: the oracle itself,
+        # fed its input perturbed by 1e-15, ends up this far from its own run;
+        # the GPU (a different rounding order) must stay within a few times it
+        rng = np.random.Generator(np.random.PCG64(1))
+        Up = W.U * (1 + 1e-15 * rng.standard_normal(W.U.shape))
+        Uq, *_ = orc.mesh_for(W).run(Up, 0.1)
+        sens = (np.abs(Uq - Uo) / sc).max()
+        assert sens > 1e-8  # the sensitivity is real (weno5 stays at ~1e-14)
+        tol = 10 * sens
+    assert (np.abs(got - Uo) / sc).max() < tol
 
 
 def test_fused_rejects_five_point(amr):
