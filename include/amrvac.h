@@ -90,9 +90,12 @@ typedef enum {
  * (Suresh & Huynh 1997), weno5 (Jiang & Shu 1996, eps = 1e-6), wenoz5 (Borges
  * et al. 2008, exponent 1), wenozp5 (WENO-Z+ of Acker, Borges & Costa 2016:
  * the Z weights with exponent 2 plus lambda (beta_k + eps)/(tau5 + eps),
- * lambda = dx^(2/3) of the block's level along the reconstruction); these run
- * on the PLAIN kernels only (AUTO picks PLAIN, FUSED is rejected) whenever the
- * limiter or a level's limiter is one of them. */
+ * lambda = dx^(2/3) of the block's level along the reconstruction).  They
+ * need three ghost layers: the fused kernels take them on 2D 16x16 tiles when
+ * every level uses a five-point limiter (22x22 tiles, three-layer ghost slabs
+ * at level changes); otherwise (3D, or a mesh mixing two- and five-point
+ * levels) they run on the PLAIN kernels (AUTO picks PLAIN, FUSED is
+ * rejected). */
 typedef enum {
   AMRVAC_LIM_MINMOD = 0,
   AMRVAC_LIM_VANLEER = 1,
@@ -368,15 +371,22 @@ amrvac_status amrvac_state_load(amrvac_state* s, const char* path);
 /*
  * Launch shape of the fused stage kernel (its tile is the 16^d block):
  * resident CTAs per SM (0 = as many as fit), work-list order (0 = Morton curve
- * per instance, 1 = storage order) and block scheduling (0 = static, 1 =
- * dynamic via a device counter).  None of them changes the arithmetic: results
- * are bit-identical across tunings.  Setting a tuning drops the captured step
- * graph.  Not part of the paper (a GB300 launch-shape choice).
+ * per instance, 1 = storage order), block scheduling (0 = static, 1 = dynamic
+ * via a device counter), and the faces a thread packs into the two lanes of
+ * its FP32x2 instructions (0 = the two sides of one face: a 96-register kernel,
+ * two CTAs per SM; 1 = the x and y faces of its cell together: fewer
+ * instructions, a ~160-register kernel with one CTA per SM; FP32 bulk with
+ * vanleer + HLLD only, ignored otherwise).  ctas_per_sm, order and dynamic do
+ * not change the arithmetic (results are bit-identical across them); faces = 1
+ * evaluates the same formulas with another FP32 grouping (results agree to
+ * float rounding).  Setting a tuning drops the captured step graph.  Not part
+ * of the paper (a GB300 launch-shape choice).
  */
 typedef struct {
   int32_t ctas_per_sm;
   int32_t order;
   int32_t dynamic;
+  int32_t faces;
   double ms_per_step;      /* measured by amrvac_autotune, else 0 */
 } amrvac_tuning;
 
@@ -384,7 +394,8 @@ amrvac_status amrvac_set_tuning(amrvac_state* s, const amrvac_tuning* t);
 amrvac_status amrvac_get_tuning(amrvac_state* s, amrvac_tuning* t);
 
 /*
- * Times every launch shape over trial_steps full steps on the state itself
+ * Times every launch shape (ctas_per_sm x order x dynamic, and faces where it
+ * applies: 8 or 12 shapes) over trial_steps full steps on the state itself
  * (U^n and the clocks are restored after each trial and at the end), keeps the
  * fastest and returns it in *best.  With cache_path, a tuning stored there for
  * the same (ndim, block size, precision, flux, limiter, pressure, block-count

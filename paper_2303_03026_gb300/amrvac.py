@@ -60,11 +60,12 @@ class InstanceDesc(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("ctas_per_sm", C.c_int32), ("order", C.c_int32), ("dynamic", C.c_int32),
-                ("ms_per_step", C.c_double)]
+                ("faces", C.c_int32), ("ms_per_step", C.c_double)]
 
     def as_dict(self):
         return {"ctas_per_sm": self.ctas_per_sm, "order": ("morton", "storage")[self.order],
-                "dynamic": bool(self.dynamic), "ms_per_step": self.ms_per_step}
+                "dynamic": bool(self.dynamic), "faces": ("sides", "xy")[self.faces],
+                "ms_per_step": self.ms_per_step}
 
 
 class ErrorInfo(C.Structure):
@@ -341,8 +342,12 @@ class State:
         return {"t": t, "dt": dt, "ch": ch, "sums": sums, "status": st,
                 "error": (err.code, err.block, err.cell, err.var)}
 
-    def set_tuning(self, ctas_per_sm=0, order="morton", dynamic=False):
-        t = Tuning(int(ctas_per_sm), {"morton": 0, "storage": 1}[order], int(bool(dynamic)), 0.0)
+    def set_tuning(self, ctas_per_sm=0, order="morton", dynamic=False, faces="sides"):
+        """Launch shape of the fused kernels (amrvac_tuning): faces "sides" packs
+        the two sides of one face per float2 lane pair, "xy" a cell's x and y
+        faces (FP32 vanleer + HLLD)."""
+        t = Tuning(int(ctas_per_sm), {"morton": 0, "storage": 1}[order], int(bool(dynamic)),
+                   {"sides": 0, "xy": 1}[faces], 0.0)
         _check(load().amrvac_set_tuning(self._h, C.byref(t)), "amrvac_set_tuning")
 
     def get_tuning(self):

@@ -19,9 +19,11 @@ OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libamrvac_gb300.so")
 SOURCES = ["api.cu", "plain.cu", "fused.cu", "noalloc.cu", "fix.cu", "reflux.cu", "regrid.cu"]
 # the fused kernel source is compiled once per (precision, dimension, limiter)
-# limiter groups: minmod, vanleer, koren as compile-time limiters, -1 = runtime
-# limiter (superbee, woodward, mcbeta, albada)
-FUSED_GROUPS = [(t, d, l) for t in ("float", "double") for d in (2, 3) for l in (0, 1, 2, -1)]
+# limiter groups: minmod, vanleer, koren as compile-time limiters, -1 = the
+# other two-ghost-cell limiters at run time, -2 = the five-point limiters at run
+# time (2D tiles only)
+FUSED_GROUPS = ([(t, d, l) for t in ("float", "double") for d in (2, 3) for l in (0, 1, 2, -1)] +
+                [(t, 2, -2) for t in ("float", "double")])
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
               "--expt-relaxed-constexpr"]
@@ -79,7 +81,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         # FP32 bulk: approximate single-precision division and square root
         # (MUFU based, <= 2 ulp) and flush-to-zero; double arithmetic unaffected
         fast = ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"] if t == "float" else []
-        units.append(("fused_inst.cu", "fused_%s_%dd_l%s.o" % (t, d, l if l >= 0 else "rt"),
+        units.append(("fused_inst.cu", "fused_%s_%dd_l%s.o" % (t, d, {-1: "rt", -2: "r5"}.get(l, l)),
                       ["-DAMRVAC_FT=" + t, "-DAMRVAC_FD=%d" % d, "-DAMRVAC_FL=%d" % l] + fast))
 
     def compile_one(unit):

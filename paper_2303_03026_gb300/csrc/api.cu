@@ -285,10 +285,15 @@ bool build_tables(const amrvac_config* c, int ninst, const amrvac_instance_desc*
   return true;
 }
 
+// the fused kernels take two ghost layers, or three on 2D tiles whose every
+// level uses a five-point limiter
+bool fused_ok(const amrvac_config* c) {
+  return ghost_width(c) == NG ? fused_supported(c) : fused_supported5(c);
+}
+
 bool use_fused_for(const amrvac_config* c) {
-  if (c->kernel == AMRVAC_KERNEL_PLAIN || ghost_width(c) != NG) return false;
-  if (c->kernel == AMRVAC_KERNEL_FUSED) return true;
-  return fused_supported(c);
+  if (c->kernel == AMRVAC_KERNEL_PLAIN) return false;
+  return fused_ok(c);
 }
 
 Layout make_layout(const amrvac_config* c, int ninst, int nblocks, const Tables& T, bool fused) {
@@ -370,7 +375,7 @@ Layout make_layout(const amrvac_config* c, int ninst, int nblocks, const Tables&
   L.pscal = take(sizeof(int) * 4);
   L.pout = take(sizeof(int) * 5 * ((size_t)nblocks << c->ndim));
   if (fused) {
-    size_t per = (size_t)NV * 2 * 16 * (c->ndim == 3 ? 16 : 1);  // one face
+    size_t per = (size_t)NV * ghost_width(c) * 16 * (c->ndim == 3 ? 16 : 1);  // one face
     L.gslab = take(rs * per * T.glist.size());
   }
   L.total = off;
@@ -445,7 +450,7 @@ amrvac_status amrvac_workspace_bytes(const amrvac_config* cfg, int32_t ninst,
                                      const int32_t* block_meta, size_t* bytes) {
   std::string err;
   if (!bytes || !config_ok(cfg, err)) return AMRVAC_E_INVALID;
-  if (cfg->kernel == AMRVAC_KERNEL_FUSED && (!fused_supported(cfg) || ghost_width(cfg) != NG))
+  if (cfg->kernel == AMRVAC_KERNEL_FUSED && !fused_ok(cfg))
     return AMRVAC_E_INVALID;
   Tables T;
   if (!build_tables(cfg, ninst, inst, nblocks, block_meta, T)) return AMRVAC_E_INVALID;
@@ -461,7 +466,7 @@ amrvac_status amrvac_state_create(const amrvac_config* cfg, int32_t ninst,
   std::string err;
   if (!out || !config_ok(cfg, err)) return AMRVAC_E_INVALID;
   *out = nullptr;
-  if (cfg->kernel == AMRVAC_KERNEL_FUSED && (!fused_supported(cfg) || ghost_width(cfg) != NG))
+  if (cfg->kernel == AMRVAC_KERNEL_FUSED && !fused_ok(cfg))
     return AMRVAC_E_INVALID;
   Tables T;
   if (!build_tables(cfg, ninst, inst, nblocks, block_meta, T)) return AMRVAC_E_INVALID;
@@ -957,7 +962,7 @@ amrvac_status amrvac_state_load(amrvac_state* s, const char* path) {
 
 amrvac_status amrvac_set_tuning(amrvac_state* s, const amrvac_tuning* t) {
   if (!s || !t || t->ctas_per_sm < 0 || t->ctas_per_sm > 32 || (t->order != 0 && t->order != 1) ||
-      (t->dynamic != 0 && t->dynamic != 1))
+      (t->dynamic != 0 && t->dynamic != 1) || (t->faces != 0 && t->faces != 1))
     return AMRVAC_E_INVALID;
   cudaError_t e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return AMRVAC_E_CUDA;
@@ -1000,8 +1005,8 @@ amrvac_status amrvac_autotune(amrvac_state* s, int32_t trial_steps, const char* 
       amrvac_tuning t{};
       amrvac_tuning found{};
       bool have = false;
-      while (fscanf(f, "%159s %d %d %d %lf", k, &t.ctas_per_sm, &t.order, &t.dynamic,
-                    &t.ms_per_step) == 5)
+      while (fscanf(f, "%159s %d %d %d %d %lf", k, &t.ctas_per_sm, &t.order, &t.dynamic,
+                    &t.faces, &t.ms_per_step) == 6)
         if (key == k) found = t, have = true;  // the last entry for a key wins
       fclose(f);
       if (have) {
@@ -1012,7 +1017,7 @@ amrvac_status amrvac_autotune(amrvac_state* s, int32_t trial_steps, const char* 
     }
   }
   if (!s->use_fused) {  // the plain path has no launch shape to tune
-    amrvac_tuning t{0, 0, 0, 0.0};
+    amrvac_tuning t{0, 0, 0, 0, 0.0};
     if (best) *best = t;
     return amrvac_set_tuning(s, &t);
   }
@@ -1037,12 +1042,24 @@ amrvac_status amrvac_autotune(amrvac_state* s, int32_t trial_steps, const char* 
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return AMRVAC_E_CUDA;
-  amrvac_tuning cand[8];
+  // face pairs apply to the lean FP32 vanleer + HLLD scheme groups; their
+  // kernel holds one CTA per SM, so only the default CTA count is tried
+  bool pairs = s->cfg.precision == AMRVAC_FP32_BULK && !s->cfg.reflux &&
+               s->cfg.time != AMRVAC_SSPRK54;
+  bool eligible = false;
+  for (int d = 0; d < s->cfg.ndim; d++)
+    pairs = pairs && s->cfg.bc[d][0] != AMRVAC_BC_SYMMETRIC && s->cfg.bc[d][1] != AMRVAC_BC_SYMMETRIC;
+  for (int g = 0; g < s->ngroups; g++)
+    eligible = eligible || (s->grp_flux[g] == AMRVAC_FLUX_HLLD && s->grp_lim[g] == AMRVAC_LIM_VANLEER);
+  pairs = pairs && eligible;
+  amrvac_tuning cand[12];
   int nc = 0;
-  for (int ctas : {0, 1})
-    for (int order : {0, 1})
-      for (int dyn : {0, 1}) cand[nc++] = amrvac_tuning{ctas, order, dyn, 0.0};
-  amrvac_tuning win{0, 0, 0, 1e300};
+  for (int faces = 0; faces <= (pairs ? 1 : 0); faces++)
+    for (int ctas : {0, 1})
+      for (int order : {0, 1})
+        for (int dyn : {0, 1})
+          if (faces == 0 || ctas == 0) cand[nc++] = amrvac_tuning{ctas, order, dyn, faces, 0.0};
+  amrvac_tuning win{0, 0, 0, 0, 1e300};
   for (int c = 0; c < nc && !st; c++) {
     st = amrvac_set_tuning(s, &cand[c]);
     if (!st) st = restore();
@@ -1069,8 +1086,8 @@ amrvac_status amrvac_autotune(amrvac_state* s, int32_t trial_steps, const char* 
   if (best) *best = win;
   if (cache_path) {
     if (FILE* f = fopen(cache_path, "a")) {
-      fprintf(f, "%s %d %d %d %.6f\n", key.c_str(), win.ctas_per_sm, win.order, win.dynamic,
-              win.ms_per_step);
+      fprintf(f, "%s %d %d %d %d %.6f\n", key.c_str(), win.ctas_per_sm, win.order, win.dynamic,
+              win.faces, win.ms_per_step);
       fclose(f);
     }
   }

@@ -14,7 +14,21 @@ bool fused_supported(const amrvac_config* c) {
   return false;
 }
 
+// three ghost layers (five-point limiters) on the fused path: 2D tiles whose
+// every level reconstructs with a five-point limiter
+bool fused_supported5(const amrvac_config* c) {
+  if (c->ndim != 2 || !fused_supported(c) || !five_point_limiter(c->limiter)) return false;
+  for (int L = 0; L < MAXLEV; L++)
+    if (c->level_limiter[L] > 0 && !five_point_limiter(c->level_limiter[L] - 1)) return false;
+  return true;
+}
+
 template <class T, int DIM> static int by_limiter(amrvac_state* s, int k, int epilogue, int g) {
+  if (five_point_limiter(s->grp_lim[g])) {
+    // the five-point limiters share one 2D instantiation (three ghost layers)
+    if constexpr (DIM == 2) return launch_fused_l<T, 2, -2>(s, k, epilogue, g);
+    return -1;
+  }
   switch (s->grp_lim[g]) {
     case AMRVAC_LIM_MINMOD: return launch_fused_l<T, DIM, AMRVAC_LIM_MINMOD>(s, k, epilogue, g);
     case AMRVAC_LIM_VANLEER: return launch_fused_l<T, DIM, AMRVAC_LIM_VANLEER>(s, k, epilogue, g);

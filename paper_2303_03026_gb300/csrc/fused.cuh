@@ -50,17 +50,20 @@ __device__ __forceinline__ int fused_row(int warp, int lane) {
   return (warp & 3) + (warp >> 2) * 8 + (lane >> 4) * 4;
 }
 
-template <class T, int DIM> struct FusedSmem {
-  static constexpr int NSLOT = DIM == 3 ? 4 : 1;
+// DEEP: the one-CTA-per-SM layout (face pairs), with room for a 6-plane ring
+// (planes land one iteration before they are converted) and three U0 slots
+template <class T, int DIM, bool DEEP = false> struct FusedSmem {
+  static constexpr int NSLOT = DIM == 3 ? (DEEP ? 6 : 4) : 1;
+  static constexpr int NU0 = DEEP ? 3 : 1;
   T plane[NSLOT][NV][FPW][FPW];
   // face fluxes of the current plane, double-buffered by plane parity so that
   // one barrier per plane separates writers and readers
   T fx[2][NV][FB][FXW];       // x faces: column i = face i - 1/2, i = 0..16
   T fy[2][NV][FB + 1][FXW];   // y faces: row j = face j - 1/2
-  // float path: U0 of the owners' cells of the current plane, copied in while
-  // the plane's faces are computed (the fp64 path reads U0 directly: a
-  // double slot would not fit beside its planes)
-  T u0[sizeof(T) == 4 ? NV : 1][FB * FB];
+  // float path: U0 of the owners' cells of the current plane (and, DEEP, of
+  // the next two), copied in ahead of the update (the fp64 path reads U0
+  // directly: a double slot would not fit beside its planes)
+  T u0[NU0][sizeof(T) == 4 ? NV : 1][FB * FB];
   double red[8][NPART];
   int next;
 };
@@ -178,12 +181,12 @@ __device__ __forceinline__ void keep_face_flux(const DevMesh& M, int code, int i
   for (int v = 0; v < NV; v++) reg[(size_t)v * M.farea] = f[v];
 }
 
-// the fused kernels can compute the x and y faces of a cell together in the
-// two float2 lanes (stencil_flux_xy, FP32 vanleer + HLLD): 16% fewer
-// instructions, but 156 registers against the 96 of two CTAs per SM, so it is
-// off (see the design notes on the measured budget)
-template <class T, int LIM, int FLUX> constexpr bool xy_pair_path() {
-  return false && sizeof(T) == 4 && LIM == AMRVAC_LIM_VANLEER && FLUX == AMRVAC_FLUX_HLLD;
+// the instantiations that can compute the x and y faces of a cell together in
+// the two float2 lanes (stencil_flux_xy): FP32 vanleer + HLLD, lean.  16% fewer
+// instructions, but ~160 registers, hence one CTA per SM; a tuning choice
+// (amrvac_tuning.faces)
+template <class T, int LIM, int FLUX, bool FULL> constexpr bool xy_pair_ok() {
+  return sizeof(T) == 4 && LIM == AMRVAC_LIM_VANLEER && FLUX == AMRVAC_FLUX_HLLD && !FULL;
 }
 
 template <class T> __device__ __forceinline__ T over_dx(T a, T dx, T idx);
@@ -217,21 +220,48 @@ __device__ __forceinline__ void stencil_flux(Acc S, int glm, T g, T ch, T* f, in
   face_flux_d<T, D>(FLUX, glm, g, ch, wl, wr, f);
 }
 
+// face flux from the six-cell stencil S(v, t), t = 0..5 for cells f-3 .. f+2
+// around the face f-1/2, with a five-point limiter lim (lam: wenozp5's lambda)
+template <class T, int D, int FLUX, class Acc>
+__device__ __forceinline__ void stencil_flux5(Acc S, int lim, T lam, int glm, T g, T ch, T* f) {
+  if constexpr (sizeof(T) == 4) {
+    stencil_flux5_f2<D, FLUX>(S, lim, lam, glm, g, ch, f);
+  } else {
+    T wl[NV], wr[NV];
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+      const T c[6] = {S(v, 0), S(v, 1), S(v, 2), S(v, 3), S(v, 4), S(v, 5)};
+      wl[v] = recon5_plus<T>(lim, c, lam);
+      wr[v] = recon5_minus<T>(lim, c + 1, lam);
+    }
+    if (!(wl[0] > T(0)) || !(wl[4] > T(0)) || !(wr[0] > T(0)) || !(wr[4] > T(0))) {
+#pragma unroll
+      for (int v = 0; v < NV; v++) {
+        wl[v] = S(v, 2);
+        wr[v] = S(v, 3);
+      }
+    }
+    face_flux_d<T, D>(FLUX, glm, g, ch, wl, wr, f);
+  }
+}
+
 // Ghost values of every level-change face of the mesh, from the stage input
 // Uk: restriction (mean of the finer children) where the neighbour is finer,
 // prolongation (coarse value plus minmod-limited slopes times +-1/4, slopes
 // computed once per coarse cell) where it is coarser.  One CTA per face at a
 // time; slab gi belongs to face glist[gi] = block * 6 + face and holds
 // [v][layer][t2][t1], layer = ghost index along the normal from the low end
-// (cells -2, -1 on a low face, 16, 17 on a high face).
-template <class T, int DIM>
+// (G layers: cells -G .. -1 on a low face, 16 .. 15 + G on a high face; the
+// G fine layers lie in G/2 rounded up coarse layers).
+template <class T, int DIM, int G = NG>
 __global__ void __launch_bounds__(256)
     k_ghost_slabs(DevMesh M, const T* __restrict__ Uk, T* __restrict__ gslab,
                   const int* __restrict__ glist, int ngen) {
   constexpr int NT2 = DIM == 3 ? FB : 1;
-  constexpr int SLAB_FACE = NV * 2 * FB * NT2;
+  constexpr int SLAB_FACE = NV * G * FB * NT2;
   constexpr int NC2 = DIM == 3 ? FB / 2 : 1;
-  __shared__ T cs[(FB / 2) * NC2 * (1 + DIM) * NV];  // [coarse cell][value, slopes][v]
+  constexpr int NCL = (G + 1) / 2;  // coarse layers (1 or 2)
+  __shared__ T cs[NCL * (FB / 2) * NC2 * (1 + DIM) * NV];  // [cl][coarse cell][value, slopes][v]
   const int tid = threadIdx.x;
   const size_t vs = (size_t)M.nblocks * M.ncell;
   for (int gi = blockIdx.x; gi < ngen; gi += gridDim.x) {
@@ -242,7 +272,7 @@ __global__ void __launch_bounds__(256)
     // global level-L index of ghost (layer, t1, t2) of this face
     auto ghost_p = [&](int layer, int t1, int t2, int* p) {
       int loc[3];
-      const int n = side ? FB + layer : layer - 2;
+      const int n = side ? FB + layer : layer - G;
       if (d == 0) { loc[0] = n; loc[1] = t1; loc[2] = t2; }
       else if (d == 1) { loc[0] = t1; loc[1] = n; loc[2] = t2; }
       else { loc[0] = t1; loc[1] = t2; loc[2] = n; }
@@ -257,22 +287,26 @@ __global__ void __launch_bounds__(256)
     T* sf = gslab + (size_t)gi * SLAB_FACE;
     if (code == MAP_REFINED) {
       // restriction: mean of the finer children
-      for (int e = tid; e < 2 * FB * NT2; e += blockDim.x) {
+      for (int e = tid; e < G * FB * NT2; e += blockDim.x) {
         const int t1 = e % FB, t2 = (e / FB) % NT2, layer = e / (FB * NT2);
         int p[3];
         ghost_p(layer, t1, t2, p);
         T u[NV];
         level_value_down(M, Uk, vs, q, L, p, u);
 #pragma unroll
-        for (int v = 0; v < NV; v++) sf[((v * 2 + layer) * NT2 + t2) * FB + t1] = u[v];
+        for (int v = 0; v < NV; v++) sf[((v * G + layer) * NT2 + t2) * FB + t1] = u[v];
       }
     } else {
-      // prolongation: value and minmod slopes once per coarse cell ...
-      for (int e = tid; e < (FB / 2) * NC2 * DIM; e += blockDim.x) {
-        const int dd = e % DIM, cc = e / DIM;
+      // prolongation: value and minmod slopes once per coarse cell (cl: the
+      // coarse layer, counted from the fine layer 0 side) ...
+      for (int e = tid; e < NCL * (FB / 2) * NC2 * DIM; e += blockDim.x) {
+        const int dd = e % DIM, cc = (e / DIM) % ((FB / 2) * NC2), cl = e / (DIM * (FB / 2) * NC2);
         const int ct1 = cc % (FB / 2), ct2 = cc / (FB / 2);
         int p[3];
-        ghost_p(0, 2 * ct1, 2 * ct2, p);
+        // a fine layer inside coarse layer cl: the low face's fine layers -G..-1
+        // start at coarse -(G+1)/2; the high face's 16.. at coarse 8
+        const int fl = side ? 2 * cl : (G % 2 ? 2 * cl - 1 : 2 * cl);
+        ghost_p(fl < 0 ? 0 : fl, 2 * ct1, 2 * ct2, p);
         int qc[3];
 #pragma unroll
         for (int k2 = 0; k2 < 3; k2++) qc[k2] = k2 < DIM ? (p[k2] >> 1) : 0;
@@ -283,19 +317,22 @@ __global__ void __launch_bounds__(256)
         qp[dd] += 1;
         level_value_down(M, Uk, vs, q, L - 1, qm, um);
         level_value_down(M, Uk, vs, q, L - 1, qp, up);
+        const int cb = cl * (FB / 2) * NC2 + cc;  // cache slot
 #pragma unroll
         for (int v = 0; v < NV; v++) {
-          cs[(cc * (1 + DIM) + 1 + dd) * NV + v] = minmod_g(uc[v] - um[v], up[v] - uc[v]);
-          if (dd == 0) cs[(cc * (1 + DIM)) * NV + v] = uc[v];
+          cs[(cb * (1 + DIM) + 1 + dd) * NV + v] = minmod_g(uc[v] - um[v], up[v] - uc[v]);
+          if (dd == 0) cs[(cb * (1 + DIM)) * NV + v] = uc[v];
         }
       }
       __syncthreads();
       // ... then every fine ghost: coarse value + sum_d (+-1/4) slope_d
-      for (int e = tid; e < 2 * FB * NT2; e += blockDim.x) {
+      for (int e = tid; e < G * FB * NT2; e += blockDim.x) {
         const int t1 = e % FB, t2 = (e / FB) % NT2, layer = e / (FB * NT2);
         int p[3];
         ghost_p(layer, t1, t2, p);
-        const int cc = (t2 >> 1) * (FB / 2) + (t1 >> 1);
+        // coarse layer of this fine layer (see above)
+        const int cl = side ? layer / 2 : (layer + (G % 2)) / 2;
+        const int cc = cl * (FB / 2) * NC2 + (t2 >> 1) * (FB / 2) + (t1 >> 1);
         const T* c0 = cs + (cc * (1 + DIM)) * NV;
 #pragma unroll
         for (int v = 0; v < NV; v++) {
@@ -305,7 +342,7 @@ __global__ void __launch_bounds__(256)
             const T wgt = (p[dd] & 1) ? T(0.25) : T(-0.25);
             val = val + wgt * c0[(1 + dd) * NV + v];
           }
-          sf[((v * 2 + layer) * NT2 + t2) * FB + t1] = val;
+          sf[((v * G + layer) * NT2 + t2) * FB + t1] = val;
         }
       }
     }
@@ -317,16 +354,20 @@ __global__ void __launch_bounds__(256)
 // mirrored reads of symmetric walls are compiled in (they are runtime-uniform
 // branches that still cost the hot loop registers and scheduling freedom, so
 // the lean instantiation runs otherwise)
-template <class T, int DIM, int LIM, int FLUX, bool FULL>
-__global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
+// PAIR: the x and y faces of a thread's cell share the float2 lanes (one CTA
+// per SM: no minimum-occupancy register cap)
+template <class T, int DIM, int LIM, int FLUX, bool FULL, bool PAIR>
+__global__ void __launch_bounds__(FT, sizeof(T) == 4 && !PAIR ? 2 : 1)
     k_fused(DevMesh M, const T* U0, const T* __restrict__ Uk, const T* U2, T* out, T* out2,
             const int* __restrict__ work, int nwork, const T* __restrict__ gslab,
             int* __restrict__ counter, StageParams sp) {
   extern __shared__ __align__(16) unsigned char smraw[];
   static_assert(DIM == 3, "16x16 blocks in 2D use k_fused2d");
-  FusedSmem<T, DIM>& S = *reinterpret_cast<FusedSmem<T, DIM>*>(smraw);
+  // the face-pair kernel (one CTA per SM) also takes the deep ring
+  constexpr bool DEEP = PAIR;
+  FusedSmem<T, DIM, DEEP>& S = *reinterpret_cast<FusedSmem<T, DIM, DEEP>*>(smraw);
   constexpr int NZ = DIM == 3 ? FB : 1;
-  constexpr int NSLOT = FusedSmem<T, DIM>::NSLOT;
+  constexpr int NSLOT = FusedSmem<T, DIM, DEEP>::NSLOT;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int x = lane & 15, y = fused_row(warp, lane);
   const size_t vs = (size_t)M.nblocks * M.ncell;
@@ -334,8 +375,8 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
   const bool ff = sp.pressure_ff != 0;
   constexpr int NT2 = DIM == 3 ? FB : 1;          // second tangential extent of a face
   constexpr int SLAB_FACE = NV * 2 * FB * NT2;    // one face: [v][layer][t2][t1]
-  // FP32 vanleer + HLLD: the x and y faces of a thread share the float2 lanes
-  constexpr bool XYPAIR = xy_pair_path<T, LIM, FLUX>();
+  static_assert(!PAIR || xy_pair_ok<T, LIM, FLUX, FULL>(), "face pairs: FP32 vanleer + HLLD");
+  constexpr bool XYPAIR = PAIR;
 
   const bool owner = tid < FB * FB;
   const int hr = tid - FB * FB;  // helper index 0..15
@@ -513,7 +554,19 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
       stencil_flux<T, 2, LIM, FLUX>(acc, sp.glm, g, ch, f, sp.limiter);
     };
 
+    constexpr bool PRE0 = sizeof(T) == 4;
+    const bool pre0 = PRE0 && !sp.plain && owner;
+    // U0 of this thread's cell of plane pz into its slot (a DRAM read landing
+    // ahead of the update; read back by the same thread only)
+    auto issue_u0 = [&](int pz) {
+      const T* src = U0 + (size_t)b * ncell + (pz * FB + y) * FB + x;
+      T* dst = &S.u0[pz % FusedSmem<T, DIM, DEEP>::NU0][0][tid];
+#pragma unroll
+      for (int v = 0; v < NV; v++) cp_async_elem_after_reads(dst + v * FB * FB, src + v * vs);
+    };
+
     T fzp[NV];
+    if (DEEP && pre0) issue_u0(0);
     for (int pz = -2; pz <= 1; pz++) issue_plane(pz);
     cp_async_wait_all();
     for (int pz = -2; pz <= 1; pz++) convert_plane(pz);
@@ -522,6 +575,11 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
     __syncthreads();  // the halo copies of planes 0 and 1 are visible
     convert_halo(0);
     __syncthreads();  // plane 0 with its halo in primitives
+    if constexpr (DEEP) {
+      // one plane ahead of the loop: plane 2 and U0 of plane 1 in flight
+      if (pre0) issue_u0(1);
+      issue_plane(2);
+    }
 
 
     // One barrier per plane.  Iteration z: issue the copies of U0 of plane z
@@ -533,18 +591,19 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
     // z+1/2; barrier; update of plane z.  The buffer of parity z is rewritten at
     // iteration z+2, after the barrier of iteration z+1, which every thread
     // passes only after its update of plane z.
-    constexpr bool PRE0 = sizeof(T) == 4;
-    const bool pre0 = PRE0 && !sp.plain && owner;
+    // DEEP: the same with the copies one iteration earlier: iteration z issues
+    // plane z+3 and U0 of plane z+2 into a 6-plane ring and three U0 slots and
+    // waits only for the group of the previous iteration (plane z+2, U0 z+1).
 #pragma unroll 1
     for (int z = 0; z < NZ; z++) {
-      if (pre0) {
-        // U0 of this thread's cell of plane z (a DRAM read), landing while the
-        // faces below are computed; read back by the same thread only
-        const T* src = U0 + (size_t)b * ncell + (z * FB + y) * FB + x;
-#pragma unroll
-        for (int v = 0; v < NV; v++) cp_async_elem_after_reads(&S.u0[v][tid], src + v * vs);
+      if constexpr (DEEP) {
+        if (pre0 && z + 2 < NZ) issue_u0(z + 2);
+        if (z + 3 <= NZ + 1) issue_plane(z + 3);  // commits one group
+        else cp_async_commit();                   // an empty group keeps the count
+      } else {
+        if (pre0) issue_u0(z);
+        issue_plane(z + 2);  // commits this thread's copies as one group
       }
-      issue_plane(z + 2);  // commits this thread's copies as one group
       const int sl = z % NSLOT, fb = z & 1;
       {
         // owners: the x and y faces on the low side of their cell; helpers: the
@@ -591,7 +650,8 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
       // below); owners 128..255 also a halo cell of plane z+1, whose copies
       // owners 0..127 waited for before the previous barrier (needed next
       // iteration)
-      cp_async_wait_all();
+      if constexpr (DEEP) asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+      else cp_async_wait_all();
       convert_plane(z + 2);
       if (z + 1 < NZ) convert_halo(z + 1);
       // float path: the stage input of the own cell, loaded before the z face
@@ -620,7 +680,9 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
         const T uk = PRE0 ? ukr[PRE0 ? v : 0] : Uk[at];
         T ut = uk - dt * acc;
         if (v == 8) ut = ut * damp;
-        un[v] = sp.plain ? ut : ca * (PRE0 ? S.u0[v][tid] : U0[at]) + cb * ut;
+        un[v] = sp.plain ? ut
+                         : ca * (PRE0 ? S.u0[z % FusedSmem<T, DIM, DEEP>::NU0][v][tid] : U0[at]) +
+                               cb * ut;
         if (FULL && sp.has2) {
           // SSPRK(5,4) stage 3: w = a2 U2 + b2 (Uk + c2 dt L); U2 is out's
           // register and out2 is U0's, both read above before their writes
@@ -648,11 +710,13 @@ namespace amrvac {
 
 // ---------------------------------------------------------------- launcher
 
-template <class T, int DIM, int LIM, int FLUX, bool FULL>
+template <class T, int DIM, int LIM, int FLUX, bool FULL, bool PAIR = false>
 static int launch_one(amrvac_state* s, const T* U0, const T* Uk, const T* U2, T* out, T* out2,
                       const int* work, int nwork, int* counter, StageParams sp) {
-  auto kern = DIM == 3 ? k_fused<T, 3, LIM, FLUX, FULL> : k_fused2d<T, LIM, FLUX, FULL>;
-  const int smem = DIM == 3 ? (int)sizeof(FusedSmem<T, 3>) : (int)sizeof(Fused2dSmem<T>);
+  static_assert(DIM == 2 || LIM != -2, "five-point limiters: 2D tiles only");
+  auto kern = DIM == 3 ? k_fused<T, 3, LIM, FLUX, FULL, PAIR> : k_fused2d<T, LIM, FLUX, FULL, PAIR>;
+  const int smem = DIM == 3 ? (int)sizeof(FusedSmem<T, 3, PAIR>)
+                            : (int)sizeof(Fused2dSmem<T, tile_ghosts(LIM)>);
   static int nsm = 0, per_sm = 0;  // per instantiation, this device
   if (nsm == 0) {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
@@ -696,10 +760,15 @@ int launch_fused_l(amrvac_state* s, int k, int epilogue, int g) {
     if (launch_level_consts(s, k) < 0) return -1;
     n++;
     if (s->ngen > 0) {
-      // ghost slabs of the level-change faces of the stage input
+      // ghost slabs of the level-change faces of the stage input (as many
+      // layers as the mesh's tiles have ghost cells)
       const int gs = s->ngen < 152 * 8 ? s->ngen : 152 * 8;
-      k_ghost_slabs<T, DIM><<<gs, 256, 0, s->stream>>>(s->mesh, Uk, (T*)s->gslab, s->d_glist,
-                                                        s->ngen);
+      if (DIM == 2 && s->mesh.ng == NG5)
+        k_ghost_slabs<T, DIM, NG5><<<gs, 256, 0, s->stream>>>(s->mesh, Uk, (T*)s->gslab,
+                                                               s->d_glist, s->ngen);
+      else
+        k_ghost_slabs<T, DIM, NG><<<gs, 256, 0, s->stream>>>(s->mesh, Uk, (T*)s->gslab,
+                                                              s->d_glist, s->ngen);
       n++;
     }
   }
@@ -712,6 +781,13 @@ int launch_fused_l(amrvac_state* s, int k, int epilogue, int g) {
   const bool full = sp.has2 || sp.reflux || wall;
   const int flux = s->grp_flux[g];
   int m;
+  if constexpr (xy_pair_ok<T, LIM, AMRVAC_FLUX_HLLD, false>()) {
+    if (flux == AMRVAC_FLUX_HLLD && !full && s->tune.faces == 1)
+      return (m = launch_one<T, DIM, LIM, AMRVAC_FLUX_HLLD, false, true>(
+                  s, U0, Uk, U2, out, out2, work, nwork, counter, sp)) < 0
+                 ? -1
+                 : n + m;
+  }
   if (flux == AMRVAC_FLUX_HLLD)
     m = full ? launch_one<T, DIM, LIM, AMRVAC_FLUX_HLLD, true>(s, U0, Uk, U2, out, out2, work,
                                                                nwork, counter, sp)

@@ -36,24 +36,32 @@ __device__ __forceinline__ void warp_max2_atomic(double smax, double cmax, doubl
   }
 }
 
-template <class T> struct Fused2dSmem {
-  T cons[2][NV][FPW][FPW];  // conserved values with halo, by block parity
+// G: ghost layers of the tile (2, or 3 for the five-point limiters)
+template <class T, int G = NG> struct Fused2dSmem {
+  static constexpr int PW = FB + 2 * G;  // padded tile width
+  T cons[2][NV][PW][PW];    // conserved values with halo, by block parity
   T u0[2][NV][FB * FB];     // U0 of the owners' cells (stages k > 0)
-  T prim[NV][FPW][FPW];
+  T prim[NV][PW][PW];
   T fx[NV][FB][FXW];        // x faces: column i = face i - 1/2, i = 0..16
   T fy[NV][FB + 1][FXW];    // y faces: row j = face j - 1/2
   int first[2];
   int next;
 };
 
-template <class T, int LIM, int FLUX, bool FULL>
-__global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
+// the tile's ghost layers for a limiter template value (-2: the five-point
+// limiters, chosen at run time)
+__host__ __device__ constexpr int tile_ghosts(int lim) { return lim == -2 ? NG5 : NG; }
+
+template <class T, int LIM, int FLUX, bool FULL, bool PAIR>
+__global__ void __launch_bounds__(FT, sizeof(T) == 4 && !PAIR ? 2 : 1)
     k_fused2d(DevMesh M, const T* U0, const T* __restrict__ Uk, const T* U2, T* out, T* out2,
               const int* __restrict__ work, int nwork, const T* __restrict__ gslab,
               int* __restrict__ counter, StageParams sp) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  Fused2dSmem<T>& S = *reinterpret_cast<Fused2dSmem<T>*>(smraw);
-  constexpr int SLAB_FACE = NV * 2 * FB;  // one face: [v][layer][t1]
+  static_assert(!PAIR || xy_pair_ok<T, LIM, FLUX, FULL>(), "face pairs: FP32 vanleer + HLLD");
+  constexpr int G = tile_ghosts(LIM);
+  Fused2dSmem<T, G>& S = *reinterpret_cast<Fused2dSmem<T, G>*>(smraw);
+  constexpr int SLAB_FACE = NV * G * FB;  // one face: [v][layer][t1]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int x = lane & 15, y = fused_row(warp, lane);
   const size_t vs = (size_t)M.nblocks * M.ncell;
@@ -61,18 +69,19 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
   const bool ff = sp.pressure_ff != 0;
   const bool owner = tid < FB * FB;
   const int hr = tid - FB * FB;  // helper index 0..15
-  // halo cell of threads 0..127: x-halo (tid < 64) then y-halo
+  // halo cell of threads 0 .. 4 G 16 - 1: x-halo (the first half), then y-halo
+  constexpr int HX = 2 * G * FB;  // x-halo cells (both sides)
   int hx = 0, hy = 0;
-  const bool halo = tid < 128;
+  const bool halo = tid < 2 * HX;
   if (halo) {
-    if (tid < 64) {
-      const int side = tid >> 5, r = tid & 31;
-      hy = r >> 1;
-      hx = side ? FB + (r & 1) : -2 + (r & 1);
+    if (tid < HX) {
+      const int side = tid / (G * FB), r = tid % (G * FB);
+      hy = r / G;
+      hx = side ? FB + r % G : -G + r % G;
     } else {
-      const int u = tid - 64, side = u >> 5, r = u & 31;
-      hx = r & 15;
-      hy = side ? FB + (r >> 4) : -2 + (r >> 4);
+      const int u = tid - HX, side = u / (G * FB), r = u % (G * FB);
+      hx = r % FB;
+      hy = side ? FB + r / FB : -G + r / FB;
     }
   }
 
@@ -90,9 +99,9 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
     }
     int code = M.nbr[bb * 6 + f];
     if (code == NBR_GENERAL) {
-      const int layer = n < 0 ? n + 2 : n - FB;
+      const int layer = n < 0 ? n + G : n - FB;
       ptr = gslab + (size_t)M.gface[bb * 6 + f] * SLAB_FACE + layer * FB + t1;
-      vstride = 2 * FB;
+      vstride = G * FB;
       return;
     }
     int nn = code >= 0 ? (n < 0 ? n + FB : n - FB) : (n < 0 ? 0 : FB - 1);
@@ -110,7 +119,7 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
       locate(bb, x, y, ptr, st);
 #pragma unroll
       for (int v = 0; v < NV; v++)
-        cp_async_elem_after_reads(&S.cons[s][v][y + NG][x + NG], ptr + v * st);
+        cp_async_elem_after_reads(&S.cons[s][v][y + G][x + G], ptr + v * st);
       if (!sp.plain) {
         const T* src = U0 + (size_t)bb * ncell + y * FB + x;
 #pragma unroll
@@ -121,7 +130,7 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
       locate(bb, hx, hy, ptr, st);
 #pragma unroll
       for (int v = 0; v < NV; v++)
-        cp_async_elem_after_reads(&S.cons[s][v][hy + NG][hx + NG], ptr + v * st);
+        cp_async_elem_after_reads(&S.cons[s][v][hy + G][hx + G], ptr + v * st);
     }
     cp_async_commit();
   };
@@ -169,7 +178,7 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
         T u[NV];
 #pragma unroll
         for (int v = 0; v < NV; v++) {
-          u[v] = S.cons[s][v][y + NG][x + NG];
+          u[v] = S.cons[s][v][y + G][x + G];
           out[(size_t)v * vs + (size_t)b * ncell + y * FB + x] = u[v];
           if (FULL && sp.has2) out2[(size_t)v * vs + (size_t)b * ncell + y * FB + x] = u[v];
         }
@@ -185,7 +194,7 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
       auto to_prim = [&](int i, int j, int which) {
         T u[NV], w[NV];
 #pragma unroll
-        for (int v = 0; v < NV; v++) u[v] = S.cons[s][v][j + NG][i + NG];
+        for (int v = 0; v < NV; v++) u[v] = S.cons[s][v][j + G][i + G];
         cons2prim(gammad, u, w, ff, gm1f);
         if (FULL && which) {
           // a halo cell mirrored by a symmetric wall of this block
@@ -195,7 +204,7 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
         if (sp.check_small && is_small_prim(w[0], w[4], rho_floor, p_floor))
           latch_error(M.err, AMRVAC_E_SMALL_VALUES, b, tid, which);
 #pragma unroll
-        for (int v = 0; v < NV; v++) S.prim[v][j + NG][i + NG] = w[v];
+        for (int v = 0; v < NV; v++) S.prim[v][j + G][i + G] = w[v];
       };
       if (owner) to_prim(x, y, 0);
       if (halo) to_prim(hx, hy, 1);
@@ -211,9 +220,29 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
         const int fxr = owner ? y : hr, fxc = owner ? x : FB;
         const int fyr = owner ? y : FB, fyc = owner ? x : hr;
         T f[NV];
-        auto ax = [&](int v, int t) -> T { return S.prim[v][fxr + NG][fxc + t]; };
-        auto ay = [&](int v, int t) -> T { return S.prim[v][fyr + t][fyc + NG]; };
-        if constexpr (xy_pair_path<T, LIM, FLUX>()) {
+        auto ax = [&](int v, int t) -> T { return S.prim[v][fxr + G][fxc + t]; };
+        auto ay = [&](int v, int t) -> T { return S.prim[v][fyr + t][fyc + G]; };
+        if constexpr (LIM == -2) {
+          // five-point limiters: six-cell stencils (three ghost layers)
+          const int lv = M.blk[b * 5 + 1];
+          const T lamx = (T)M.wzlam[(q * MAXLEV + lv) * 3], lamy = (T)M.wzlam[(q * MAXLEV + lv) * 3 + 1];
+          stencil_flux5<T, 0, FLUX>(ax, sp.limiter, lamx, sp.glm, g, ch, f);
+#pragma unroll
+          for (int v = 0; v < NV; v++) S.fx[v][fxr][fxc] = f[v];
+          if (FULL && sp.reflux) {
+            const int face = owner ? (x == 0 ? 0 : -1) : 1;
+            const int code = face >= 0 ? M.nbr[b * 6 + face] : 0;
+            if (code == NBR_GENERAL) keep_face_flux(M, -3 - M.gface[b * 6 + face], fxr, f);
+          }
+          stencil_flux5<T, 1, FLUX>(ay, sp.limiter, lamy, sp.glm, g, ch, f);
+#pragma unroll
+          for (int v = 0; v < NV; v++) S.fy[v][fyr][fyc] = f[v];
+          if (FULL && sp.reflux) {
+            const int face = owner ? (y == 0 ? 2 : -1) : 3;
+            const int code = face >= 0 ? M.nbr[b * 6 + face] : 0;
+            if (code == NBR_GENERAL) keep_face_flux(M, -3 - M.gface[b * 6 + face], fyc, f);
+          }
+        } else if constexpr (PAIR) {
           // both faces at once, one per float2 lane
           T f2[NV];
           stencil_flux_xy(ax, ay, sp.glm, g, ch, f, f2);
@@ -263,7 +292,7 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? 2 : 1)
         for (int v = 0; v < NV; v++) {
           T acc = over_dx<T>(S.fx[v][y][x + 1] - S.fx[v][y][x], dx0, idx0);
           acc += over_dx<T>(S.fy[v][y + 1][x] - S.fy[v][y][x], dx1, idx1);
-          const T uk = S.cons[s][v][y + NG][x + NG];
+          const T uk = S.cons[s][v][y + G][x + G];
           T ut = uk - dt * acc;
           if (v == 8) ut = ut * damp;
           un[v] = sp.plain ? ut : ca * S.u0[s][v][tid] + cb * ut;

@@ -477,27 +477,9 @@ __device__ __forceinline__ void stencil_flux_xy(AX ax, AY ay, int glm, float g, 
     psis = sp2(0.f);
   }
   float2 fl[8];
-#ifdef AMRVAC_XY_SPLIT_EXPERIMENT
-  {
-    float fa[8], fb[8];
-    Side2 qx, qy;
-    qx.rho = make_float2(wl[0].x, wr[0].x); qx.u = make_float2(wl[1].x, wr[1].x);
-    qx.v = make_float2(wl[2].x, wr[2].x); qx.w = make_float2(wl[3].x, wr[3].x);
-    qx.p = make_float2(wl[4].x, wr[4].x); qx.by = make_float2(wl[6].x, wr[6].x);
-    qx.bz = make_float2(wl[7].x, wr[7].x);
-    hlld_pair(g, 1.f / (g - 1.f), qx, bns.x, fa);
-    qy.rho = make_float2(wl[0].y, wr[0].y); qy.u = make_float2(wl[1].y, wr[1].y);
-    qy.v = make_float2(wl[2].y, wr[2].y); qy.w = make_float2(wl[3].y, wr[3].y);
-    qy.p = make_float2(wl[4].y, wr[4].y); qy.by = make_float2(wl[6].y, wr[6].y);
-    qy.bz = make_float2(wl[7].y, wr[7].y);
-    hlld_pair(g, 1.f / (g - 1.f), qy, bns.y, fb);
-    for (int c = 0; c < 8; c++) fl[c] = make_float2(fa[c], fb[c]);
-  }
-#else
   const Prim2 L = {wl[0], wl[1], wl[2], wl[3], wl[4], wl[6], wl[7]};
   const Prim2 R = {wr[0], wr[1], wr[2], wr[3], wr[4], wr[6], wr[7]};
   hlld_xy(g, 1.f / (g - 1.f), L, R, bns, fl);
-#endif
   const float2 fpsi = glm ? mul2(sp2(ch * ch), bns) : sp2(0.f);
   fl[5] = psis;
 #pragma unroll
@@ -508,6 +490,9 @@ __device__ __forceinline__ void stencil_flux_xy(AX ax, AY ay, int glm, float g, 
   fx[8] = fpsi.x;
   fy[8] = fpsi.y;
 }
+
+template <int D, int FLUX>
+__device__ __forceinline__ void face_flux_f2(float2* w, int glm, float g, float ch, float* f);
 
 // Face flux along D from the 4-cell stencils of the 9 primitive variables:
 // st(v, t) for cells f-2, f-1, f, f+1.  Positivity fallback and glm as in
@@ -546,6 +531,31 @@ __device__ __forceinline__ void stencil_flux_f2(Acc st, int glm, float g, float 
 #pragma unroll
     for (int v = 0; v < NV; v++) w[v] = make_float2(st(v, 1), st(v, 2));
   }
+  face_flux_f2<D, FLUX>(w, glm, g, ch, f);
+}
+
+// Five-point limiters (mp5, weno5, wenoz5, wenozp5; lim at run time, lam the
+// wenozp5 lambda): st(v, t) for the six cells f-3 .. f+2 around the face
+// f-1/2; each face state reconstructed in float as on the plain path
+template <int D, int FLUX, class Acc>
+__device__ __forceinline__ void stencil_flux5_f2(Acc st, int lim, float lam, int glm, float g,
+                                                 float ch, float* f) {
+  float2 w[NV];
+#pragma unroll
+  for (int v = 0; v < NV; v++) {
+    const float c[6] = {st(v, 0), st(v, 1), st(v, 2), st(v, 3), st(v, 4), st(v, 5)};
+    w[v] = make_float2(recon5_plus<float>(lim, c, lam), recon5_minus<float>(lim, c + 1, lam));
+  }
+  if (!(w[0].x > 0.f) || !(w[4].x > 0.f) || !(w[0].y > 0.f) || !(w[4].y > 0.f)) {
+#pragma unroll
+    for (int v = 0; v < NV; v++) w[v] = make_float2(st(v, 2), st(v, 3));
+  }
+  face_flux_f2<D, FLUX>(w, glm, g, ch, f);
+}
+
+// glm solve and Riemann flux along D from the face states w[v] = (left, right)
+template <int D, int FLUX>
+__device__ __forceinline__ void face_flux_f2(float2* w, int glm, float g, float ch, float* f) {
   constexpr int t1 = D == 2 ? 0 : D + 1, t2 = D == 0 ? 2 : D - 1;
   const float bnl = w[5 + D].x, bnr = w[5 + D].y;
   float bns, psis;

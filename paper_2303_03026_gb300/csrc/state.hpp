@@ -65,7 +65,7 @@ struct amrvac_state {
   int nrlist = 0;
   void* fluxreg = nullptr;
   // launch shape of the fused kernel (see amrvac_tuning)
-  amrvac_tuning tune{0, 0, 0, 0.0};
+  amrvac_tuning tune{0, 0, 0, 0, 0.0};
   int* d_work_morton = nullptr;
   int* d_work_storage = nullptr;
   int* d_counter = nullptr;  // one dynamic-schedule counter per scheme group
@@ -171,5 +171,6 @@ int launch_convert(amrvac_state* s, const void* src, int src_prec, void* dst, in
                    size_t n);
 int launch_fused_stage(amrvac_state* s, int k, int epilogue);
 bool fused_supported(const amrvac_config* cfg);
+bool fused_supported5(const amrvac_config* cfg);
 
 }  // namespace amrvac

@@ -66,8 +66,10 @@ def _l1_by_var(got, ref, ch=None):
 
 
 def _stage_parity(amr, orc, W, kernel, stages=None, tol=1e-12, blocks=None, threads=8,
-                  pressure="fp64"):
+                  pressure="fp64", faces="sides"):
     S = amr.State.from_workload(W, kernel=kernel, pressure=pressure)
+    if faces != "sides":
+        S.set_tuning(faces=faces)
     m = orc.mesh_for(W, threads)
     U = W.U.astype(np.float32).astype(np.float64) if W.cfg.precision == "fp32" else W.U
     dt, ch = m.cfl(U)
@@ -482,9 +484,51 @@ def test_autotune_restores_state_and_caches(amr, tmp_path):
     np.testing.assert_array_equal(got, B.get_conserved(0))
     # the second state of the same shape reads the cache instead of timing
     again = B.autotune(trial_steps=2, cache=cache)
-    assert {k: again[k] for k in ("ctas_per_sm", "order", "dynamic")} == \
-        {k: best[k] for k in ("ctas_per_sm", "order", "dynamic")}
+    keys = ("ctas_per_sm", "order", "dynamic", "faces")
+    assert {k: again[k] for k in keys} == {k: best[k] for k in keys}
+    assert best["faces"] in ("sides", "xy")
+    assert len(open(cache).read().split()) == 6  # key and five fields
     assert abs(again["ms_per_step"] - best["ms_per_step"]) < 1e-5  # cached with 6 decimals
     assert len(open(cache).read().strip().splitlines()) == 1
     A.close()
     B.close()
+
+
+# ----------------------------------------------------------------------------
+# the face-pair launch shape (x and y faces of a cell in the two float2 lanes)
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("which", ["amr3d", "c3", "riemann2d", "c5"])
+def test_face_pairs_stage_parity(amr, orc, which):
+    # the same formulas in another FP32 grouping: the FP32 stage tolerances
+    if which == "amr3d":
+        W, tol = wl.c4_blast_amr(base=4, levels=3, bnx=16, shell=(0.2, 0.26),
+                                 precision="fp32"), 1e-3
+    elif which == "c3":
+        W, tol = wl.c3_turbulence(n=32, bnx=16, precision="fp32"), 1e-5
+    elif which == "riemann2d":
+        W, tol = _riemann_2d(angle=0.3), 1e-5
+    else:
+        W, tol = wl.c5_instances(count=6, nmin=32, nmax=96, precision="fp32"), 1e-5
+    _stage_parity(amr, orc, W, "fused", tol=tol, pressure="ff", faces="xy")
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_face_pairs_agree_with_sides_over_steps(amr, ndim):
+    W = (wl.c4_blast_amr(base=4, levels=3, bnx=16, shell=(0.2, 0.26), precision="fp32")
+         if ndim == 3 else wl.c5_instances(count=6, nmin=32, nmax=96, precision="fp32"))
+    U = W.U.astype(np.float32)
+    out = {}
+    for faces in ("sides", "xy"):
+        S = amr.State.from_workload(W, pressure="ff")
+        S.set_tuning(faces=faces)
+        S.set_conserved(U)
+        S.step(5)
+        out[faces] = (S.get_conserved(0).astype(np.float64), S.diag(raise_on_error=True))
+        assert S.get_tuning()["faces"] == faces
+        S.close()
+    a, da = out["xy"]
+    b, db = out["sides"]
+    e = _l1_by_var(a, b, db["ch"])
+    assert e.max() < 1e-5, e
+    np.testing.assert_allclose(da["t"], db["t"], rtol=1e-5)

@@ -377,3 +377,54 @@ def test_fused_rejects_five_point(amr):
     W.cfg.limiter = "weno5"
     with pytest.raises(amr.AmrvacError):
         amr.State.from_workload(W, kernel="fused")
+
+
+# ----------------------------------------------------------------------------
+# five-point limiters on the fused 2D kernel (22 x 22 tiles: three ghost
+# layers, three-layer ghost slabs at level changes)
+# ----------------------------------------------------------------------------
+
+def _five_2d_cases(precision):
+    walls = wl.small_amr_2d(bnx=16, periodic=False, seed=5, precision=precision)
+    walls.cfg.bc = (("symmetric", "symmetric"), ("symmetric", "outflow"), ("outflow", "outflow"))
+    return [wl.cp_alfven(32, precision=precision),
+            wl.small_amr_2d(bnx=16, precision=precision),
+            wl.small_amr_2d(bnx=16, periodic=False, seed=9, precision=precision),
+            wl.c5_instances(count=4, nmin=32, nmax=64, precision=precision),
+            walls]
+
+
+@pytest.mark.parametrize("limiter", FIVE_POINT)
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_five_point_fused_2d_stage_parity(amr, orc, limiter, precision):
+    for W in _five_2d_cases(precision):
+        W.cfg.limiter = limiter
+        _scheme_stage_parity(amr, orc, W, "fused", 1e-12 if precision == "fp64" else 1e-5)
+
+
+def test_five_point_fused_2d_ghost_slabs_and_steps(amr, orc):
+    # three-layer slabs at level changes: a few full FP64 steps on the AMR mesh
+    # (glm on) match the oracle's run, and the fused path is the one taken
+    W = wl.small_amr_2d(bnx=16)
+    W.cfg.limiter = "mp5"
+    S = amr.State.from_workload(W, kernel="fused")
+    assert S.ng == 3
+    S.set_conserved(W.U)
+    S.step(4)
+    got = S.get_conserved(0)
+    d = S.diag(raise_on_error=True)
+    S.close()
+    Uo, t, ns, st = orc.mesh_for(W, 8).run(W.U, 1e30, maxsteps=4)
+    assert st == 0 and ns == 4
+    assert abs(d["t"][0] - t[0]) < 1e-13 * t[0]
+    sc = np.maximum(np.abs(Uo).max(axis=(1, 2), keepdims=True), 1e-300)
+    assert (np.abs(got - Uo) / sc).max() < 1e-10
+
+
+def test_fused_takes_five_point_only_on_uniform_2d_tiles(amr):
+    W = wl.cp_alfven(32)
+    W.cfg.limiter = "wenoz5"
+    amr.State.from_workload(W, kernel="fused").close()       # 2D, every level five-point
+    W.cfg.level_limiter = {1: "vanleer"}                       # mixed ghost widths: plain only
+    with pytest.raises(amr.AmrvacError):
+        amr.State.from_workload(W, kernel="fused")
