@@ -91,11 +91,12 @@ typedef enum {
  * et al. 2008, exponent 1), wenozp5 (WENO-Z+ of Acker, Borges & Costa 2016:
  * the Z weights with exponent 2 plus lambda (beta_k + eps)/(tau5 + eps),
  * lambda = dx^(2/3) of the block's level along the reconstruction).  They
- * need three ghost layers: the fused kernels take them on 2D 16x16 tiles when
- * every level uses a five-point limiter (22x22 tiles, three-layer ghost slabs
- * at level changes); otherwise (3D, or a mesh mixing two- and five-point
- * levels) they run on the PLAIN kernels (AUTO picks PLAIN, FUSED is
- * rejected). */
+ * need three ghost layers: the fused kernels take them when every level uses a
+ * five-point limiter, on 2D 16x16 tiles (22x22 tiles) and on 3D 16^3 blocks in
+ * FP32 bulk (a ring of six 22x22 planes, one CTA per SM), with three-layer
+ * ghost slabs at level changes; otherwise (3D in FP64, or a mesh mixing two-
+ * and five-point levels) they run on the PLAIN kernels (AUTO picks PLAIN,
+ * FUSED is rejected). */
 typedef enum {
   AMRVAC_LIM_MINMOD = 0,
   AMRVAC_LIM_VANLEER = 1,

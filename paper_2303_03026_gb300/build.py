@@ -23,7 +23,7 @@ SOURCES = ["api.cu", "plain.cu", "fused.cu", "noalloc.cu", "fix.cu", "reflux.cu"
 # other two-ghost-cell limiters at run time, -2 = the five-point limiters at run
 # time (2D tiles only)
 FUSED_GROUPS = ([(t, d, l) for t in ("float", "double") for d in (2, 3) for l in (0, 1, 2, -1)] +
-                [(t, 2, -2) for t in ("float", "double")])
+                [(t, 2, -2) for t in ("float", "double")] + [("float", 3, -2)])
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
               "--expt-relaxed-constexpr"]

@@ -14,10 +14,12 @@ bool fused_supported(const amrvac_config* c) {
   return false;
 }
 
-// three ghost layers (five-point limiters) on the fused path: 2D tiles whose
-// every level reconstructs with a five-point limiter
+// three ghost layers (five-point limiters) on the fused path: 2D tiles, and
+// 3D blocks in FP32 bulk, whose every level reconstructs with a five-point
+// limiter
 bool fused_supported5(const amrvac_config* c) {
-  if (c->ndim != 2 || !fused_supported(c) || !five_point_limiter(c->limiter)) return false;
+  if (c->ndim == 3 && c->precision == AMRVAC_FP64) return false;
+  if (c->ndim < 2 || !fused_supported(c) || !five_point_limiter(c->limiter)) return false;
   for (int L = 0; L < MAXLEV; L++)
     if (c->level_limiter[L] > 0 && !five_point_limiter(c->level_limiter[L] - 1)) return false;
   return true;
@@ -25,8 +27,9 @@ bool fused_supported5(const amrvac_config* c) {
 
 template <class T, int DIM> static int by_limiter(amrvac_state* s, int k, int epilogue, int g) {
   if (five_point_limiter(s->grp_lim[g])) {
-    // the five-point limiters share one 2D instantiation (three ghost layers)
-    if constexpr (DIM == 2) return launch_fused_l<T, 2, -2>(s, k, epilogue, g);
+    // the five-point limiters share one instantiation (three ghost layers;
+    // 3D in FP32 bulk only)
+    if constexpr (DIM == 2 || sizeof(T) == 4) return launch_fused_l<T, DIM, -2>(s, k, epilogue, g);
     return -1;
   }
   switch (s->grp_lim[g]) {

@@ -41,8 +41,11 @@ constexpr int FB = 16;          // block edge handled by the fused kernel
 // helpers (the 32 faces on the +x/+y block boundary).  The 2D kernel uses the
 // same roles with threads 0..127 copying and converting the halo.
 constexpr int FT = FB * FB + FB;
-constexpr int FPW = FB + 2 * NG;  // padded plane width (row stride 20 floats)
 constexpr int FXW = 20;           // row stride of the face-flux arrays
+
+// ghost layers of a tile for a limiter template value (-2: the five-point
+// limiters, chosen at run time)
+__host__ __device__ constexpr int tile_ghosts(int lim) { return lim == -2 ? NG5 : NG; }
 
 // Thread (x, y) of a warp: lanes 0-15 take row r, lanes 16-31 row r + 4, so the
 // two half-warps of a row-stride-20 array fall on disjoint banks (4*20 = 16 mod 32).
@@ -51,11 +54,15 @@ __device__ __forceinline__ int fused_row(int warp, int lane) {
 }
 
 // DEEP: the one-CTA-per-SM layout (face pairs), with room for a 6-plane ring
-// (planes land one iteration before they are converted) and three U0 slots
-template <class T, int DIM, bool DEEP = false> struct FusedSmem {
-  static constexpr int NSLOT = DIM == 3 ? (DEEP ? 6 : 4) : 1;
+// (planes land one iteration before they are converted) and three U0 slots.
+// G: ghost layers; a plane is (16 + 2G)^2 (row stride 20 or 22) and the ring
+// holds the 2G planes of a z stencil
+template <class T, int DIM, bool DEEP = false, int G = NG> struct FusedSmem {
+  static_assert(!DEEP || G == NG, "the deep ring takes two ghost layers");
+  static constexpr int PW = FB + 2 * G;
+  static constexpr int NSLOT = DIM == 3 ? (DEEP ? 6 : 2 * G) : 1;
   static constexpr int NU0 = DEEP ? 3 : 1;
-  T plane[NSLOT][NV][FPW][FPW];
+  T plane[NSLOT][NV][PW][PW];
   // face fluxes of the current plane, double-buffered by plane parity so that
   // one barrier per plane separates writers and readers
   T fx[2][NV][FB][FXW];       // x faces: column i = face i - 1/2, i = 0..16
@@ -356,8 +363,10 @@ __global__ void __launch_bounds__(256)
 // the lean instantiation runs otherwise)
 // PAIR: the x and y faces of a thread's cell share the float2 lanes (one CTA
 // per SM: no minimum-occupancy register cap)
+// LIM -2: the five-point limiters (runtime limiter, three ghost layers: a
+// 6-plane ring of 22 x 22 planes and 192 halo cells a plane, one CTA per SM)
 template <class T, int DIM, int LIM, int FLUX, bool FULL, bool PAIR>
-__global__ void __launch_bounds__(FT, sizeof(T) == 4 && !PAIR ? 2 : 1)
+__global__ void __launch_bounds__(FT, sizeof(T) == 4 && !PAIR && LIM != -2 ? 2 : 1)
     k_fused(DevMesh M, const T* U0, const T* __restrict__ Uk, const T* U2, T* out, T* out2,
             const int* __restrict__ work, int nwork, const T* __restrict__ gslab,
             int* __restrict__ counter, StageParams sp) {
@@ -365,31 +374,36 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 && !PAIR ? 2 : 1)
   static_assert(DIM == 3, "16x16 blocks in 2D use k_fused2d");
   // the face-pair kernel (one CTA per SM) also takes the deep ring
   constexpr bool DEEP = PAIR;
-  FusedSmem<T, DIM, DEEP>& S = *reinterpret_cast<FusedSmem<T, DIM, DEEP>*>(smraw);
+  constexpr int G = tile_ghosts(LIM);
+  using Smem = FusedSmem<T, DIM, DEEP, G>;
+  Smem& S = *reinterpret_cast<Smem*>(smraw);
   constexpr int NZ = DIM == 3 ? FB : 1;
-  constexpr int NSLOT = FusedSmem<T, DIM, DEEP>::NSLOT;
+  constexpr int NSLOT = Smem::NSLOT;
+  constexpr int PW = Smem::PW;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int x = lane & 15, y = fused_row(warp, lane);
   const size_t vs = (size_t)M.nblocks * M.ncell;
   const int ncell = M.ncell;
   const bool ff = sp.pressure_ff != 0;
   constexpr int NT2 = DIM == 3 ? FB : 1;          // second tangential extent of a face
-  constexpr int SLAB_FACE = NV * 2 * FB * NT2;    // one face: [v][layer][t2][t1]
+  constexpr int SLAB_FACE = NV * G * FB * NT2;    // one face: [v][layer][t2][t1]
   static_assert(!PAIR || xy_pair_ok<T, LIM, FLUX, FULL>(), "face pairs: FP32 vanleer + HLLD");
   constexpr bool XYPAIR = PAIR;
 
   const bool owner = tid < FB * FB;
   const int hr = tid - FB * FB;  // helper index 0..15
-  // halo cell h (0..127) of a plane: x-halo (h < 64) then y-halo
+  // halo cell h (0 .. NH-1) of a plane: x-halo (h < NH/2) then y-halo; owners
+  // 0 .. NH-1 copy one each, owners 256-NH .. 255 convert one each
+  constexpr int NH = 4 * G * FB;  // 128 or 192
   auto halo_xy = [](int h, int& hx, int& hy) {
-    if (h < 64) {
-      int side = h >> 5, r = h & 31;
-      hy = r >> 1;
-      hx = side ? FB + (r & 1) : -2 + (r & 1);
+    if (h < NH / 2) {
+      const int side = h / (G * FB), r = h % (G * FB);
+      hy = r / G;
+      hx = side ? FB + r % G : -G + r % G;
     } else {
-      int u = h - 64, side = u >> 5, r = u & 31;
-      hx = r & 15;
-      hy = side ? FB + (r >> 4) : -2 + (r >> 4);
+      const int u = h - NH / 2, side = u / (G * FB), r = u % (G * FB);
+      hx = r % FB;
+      hy = side ? FB + r / FB : -G + r / FB;
     }
   };
 
@@ -469,9 +483,9 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 && !PAIR ? 2 : 1)
       }
       const int code = nb[f];
       if (code <= -3) {
-        const int layer = n < 0 ? n + 2 : n - FB;
+        const int layer = n < 0 ? n + G : n - FB;
         ptr = gslab + (size_t)(-3 - code) * SLAB_FACE + (layer * NT2 + t2) * FB + t1;
-        vstride = 2 * NT2 * FB;
+        vstride = G * NT2 * FB;
         return;
       }
       int nn = code >= 0 ? (n < 0 ? n + FB : n - FB) : (n < 0 ? 0 : FB - 1);
@@ -485,21 +499,21 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 && !PAIR ? 2 : 1)
     };
 
     auto to_prim = [&](T* cell, int which, int flip) {
-      // cell: the 9 values of one cell in a plane slot (stride FPW*FPW), in
+      // cell: the 9 values of one cell in a plane slot (stride PW*PW), in
       // place; flip: (FULL) dimensions whose wall mirrored this cell
       T u[NV], w[NV];
 #pragma unroll
-      for (int v = 0; v < NV; v++) u[v] = cell[v * FPW * FPW];
+      for (int v = 0; v < NV; v++) u[v] = cell[v * PW * PW];
       cons2prim(gammad, u, w, ff, gm1f);
       if (FULL && flip) wall_flip(flip, w);
       if (sp.check_small && is_small_prim(w[0], w[4], rho_floor, p_floor))
         latch_error(M.err, AMRVAC_E_SMALL_VALUES, b, tid, which);
 #pragma unroll
-      for (int v = 0; v < NV; v++) cell[v * FPW * FPW] = w[v];
+      for (int v = 0; v < NV; v++) cell[v * PW * PW] = w[v];
     };
 
     // asynchronous copy of plane pz's conserved values into its ring slot
-    // (own column; threads 0..127 also their halo cell of interior planes) ...
+    // (own column; threads 0..NH-1 also their halo cell of interior planes) ...
     auto issue_plane = [&](int pz) {
       const int slot = ((pz % NSLOT) + NSLOT) % NSLOT;
       const T* ptr;
@@ -508,14 +522,14 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 && !PAIR ? 2 : 1)
         locate(x, y, pz, ptr, st);
 #pragma unroll
         for (int v = 0; v < NV; v++)
-          cp_async_elem(&S.plane[slot][v][y + NG][x + NG], ptr + v * st);
-        if (tid < 128 && pz >= 0 && pz < NZ) {
+          cp_async_elem(&S.plane[slot][v][y + G][x + G], ptr + v * st);
+        if (tid < NH && pz >= 0 && pz < NZ) {
           int hx, hy;
           halo_xy(tid, hx, hy);
           locate(hx, hy, pz, ptr, st);
 #pragma unroll
           for (int v = 0; v < NV; v++)
-            cp_async_elem(&S.plane[slot][v][hy + NG][hx + NG], ptr + v * st);
+            cp_async_elem(&S.plane[slot][v][hy + G][hx + G], ptr + v * st);
         }
       }
       cp_async_commit();
@@ -525,33 +539,46 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 && !PAIR ? 2 : 1)
     auto convert_plane = [&](int pz) {
       const int slot = ((pz % NSLOT) + NSLOT) % NSLOT;
       const int flip = FULL && ((pz < 0 && (wmask & 16)) || (pz >= NZ && (wmask & 32))) ? 4 : 0;
-      if (owner) to_prim(&S.plane[slot][0][y + NG][x + NG], 0, flip);
+      if (owner) to_prim(&S.plane[slot][0][y + G][x + G], 0, flip);
     };
     // ... and, one barrier after their copies landed, the conversion of the
-    // halo cells of plane pz by owners 128..255 (one cell each)
+    // halo cells of plane pz by owners 256-NH..255 (one cell each)
     auto convert_halo = [&](int pz) {
       const int slot = ((pz % NSLOT) + NSLOT) % NSLOT;
-      if (tid >= 128 && tid < 256) {
+      if (tid >= FB * FB - NH && tid < FB * FB) {
         int hx, hy;
-        halo_xy(tid - 128, hx, hy);
+        halo_xy(tid - (FB * FB - NH), hx, hy);
         int flip = 0;
         if (FULL) {
           if ((hx < 0 && (wmask & 1)) || (hx >= FB && (wmask & 2))) flip |= 1;
           if ((hy < 0 && (wmask & 4)) || (hy >= FB && (wmask & 8))) flip |= 2;
         }
-        to_prim(&S.plane[slot][0][hy + NG][hx + NG], 1, flip);
+        to_prim(&S.plane[slot][0][hy + G][hx + G], 1, flip);
       }
     };
 
+    // five-point limiters: WENO-Z+ lambda of the block's level per direction
+    const T lam[3] = {G == NG ? T(0) : (T)M.wzlam[(q * MAXLEV + L) * 3],
+                      G == NG ? T(0) : (T)M.wzlam[(q * MAXLEV + L) * 3 + 1],
+                      G == NG ? T(0) : (T)M.wzlam[(q * MAXLEV + L) * 3 + 2]};
     auto zflux = [&](int zc, T* f) {
       // z face between planes zc-1 and zc of the thread's own column
-      int s0 = (zc - 2 + 2 * NSLOT) % NSLOT, s1 = (zc - 1 + 2 * NSLOT) % NSLOT;
-      int s2 = (zc + 2 * NSLOT) % NSLOT, s3 = (zc + 1 + 2 * NSLOT) % NSLOT;
-      auto acc = [&](int v, int t) -> T {
-        int s = t == 0 ? s0 : (t == 1 ? s1 : (t == 2 ? s2 : s3));
-        return S.plane[s][v][y + NG][x + NG];
-      };
-      stencil_flux<T, 2, LIM, FLUX>(acc, sp.glm, g, ch, f, sp.limiter);
+      if constexpr (G == NG) {
+        int s0 = (zc - 2 + 2 * NSLOT) % NSLOT, s1 = (zc - 1 + 2 * NSLOT) % NSLOT;
+        int s2 = (zc + 2 * NSLOT) % NSLOT, s3 = (zc + 1 + 2 * NSLOT) % NSLOT;
+        auto acc = [&](int v, int t) -> T {
+          int s = t == 0 ? s0 : (t == 1 ? s1 : (t == 2 ? s2 : s3));
+          return S.plane[s][v][y + NG][x + NG];
+        };
+        stencil_flux<T, 2, LIM, FLUX>(acc, sp.glm, g, ch, f, sp.limiter);
+      } else {
+        // planes zc-3 .. zc+2 (the ring holds exactly these six)
+        int sl6[6];
+#pragma unroll
+        for (int t = 0; t < 6; t++) sl6[t] = (zc - 3 + t + 2 * NSLOT) % NSLOT;
+        auto acc = [&](int v, int t) -> T { return S.plane[sl6[t]][v][y + G][x + G]; };
+        stencil_flux5<T, 2, FLUX>(acc, sp.limiter, lam[2], sp.glm, g, ch, f);
+      }
     };
 
     constexpr bool PRE0 = sizeof(T) == 4;
@@ -560,16 +587,16 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 && !PAIR ? 2 : 1)
     // ahead of the update; read back by the same thread only)
     auto issue_u0 = [&](int pz) {
       const T* src = U0 + (size_t)b * ncell + (pz * FB + y) * FB + x;
-      T* dst = &S.u0[pz % FusedSmem<T, DIM, DEEP>::NU0][0][tid];
+      T* dst = &S.u0[pz % Smem::NU0][0][tid];
 #pragma unroll
       for (int v = 0; v < NV; v++) cp_async_elem_after_reads(dst + v * FB * FB, src + v * vs);
     };
 
     T fzp[NV];
     if (DEEP && pre0) issue_u0(0);
-    for (int pz = -2; pz <= 1; pz++) issue_plane(pz);
+    for (int pz = -G; pz < G; pz++) issue_plane(pz);
     cp_async_wait_all();
-    for (int pz = -2; pz <= 1; pz++) convert_plane(pz);
+    for (int pz = -G; pz < G; pz++) convert_plane(pz);
     if (owner) zflux(0, fzp);  // own column only
     if (FULL && sp.reflux && owner && nb[4] <= -3) keep_face_flux(M, nb[4], y * FB + x, fzp);
     __syncthreads();  // the halo copies of planes 0 and 1 are visible
@@ -583,12 +610,12 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 && !PAIR ? 2 : 1)
 
 
     // One barrier per plane.  Iteration z: issue the copies of U0 of plane z
-    // (stages k > 0) and of plane z+2 into the slot of plane z-2 (its last
-    // readers were the faces of plane z-2 and this thread's own z face of
+    // (stages k > 0) and of plane z+G into the slot of plane z-G (its last
+    // readers were the faces of plane z-G and this thread's own z face of
     // iteration z-1); x/y faces of plane z into the flux buffer of parity z;
-    // wait for and convert the own cells of plane z+2, convert the halo of
-    // plane z+1 (owners 128..255); load U_k of the own cell of plane z; z face
-    // z+1/2; barrier; update of plane z.  The buffer of parity z is rewritten at
+    // wait for and convert the own cells of plane z+G, convert the halo of
+    // plane z+1 (owners 256-NH..255); load U_k of the own cell of plane z; z
+    // face z+1/2 (planes z+1-G .. z+G); barrier; update of plane z.  The buffer of parity z is rewritten at
     // iteration z+2, after the barrier of iteration z+1, which every thread
     // passes only after its update of plane z.
     // DEEP: the same with the copies one iteration earlier: iteration z issues
@@ -602,7 +629,7 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 && !PAIR ? 2 : 1)
         else cp_async_commit();                   // an empty group keeps the count
       } else {
         if (pre0) issue_u0(z);
-        issue_plane(z + 2);  // commits this thread's copies as one group
+        issue_plane(z + G);  // commits this thread's copies as one group
       }
       const int sl = z % NSLOT, fb = z & 1;
       {
@@ -612,9 +639,25 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 && !PAIR ? 2 : 1)
         const int fxr = owner ? y : hr, fxc = owner ? x : FB;
         const int fyr = owner ? y : FB, fyc = owner ? x : hr;
         T f[NV];
-        auto ax = [&](int v, int t) -> T { return S.plane[sl][v][fxr + NG][fxc + t]; };
-        auto ay = [&](int v, int t) -> T { return S.plane[sl][v][fyr + t][fyc + NG]; };
-        if constexpr (XYPAIR) {
+        auto ax = [&](int v, int t) -> T { return S.plane[sl][v][fxr + G][fxc + t]; };
+        auto ay = [&](int v, int t) -> T { return S.plane[sl][v][fyr + t][fyc + G]; };
+        if constexpr (G == NG5) {
+          // five-point limiters: six-cell stencils
+          stencil_flux5<T, 0, FLUX>(ax, sp.limiter, lam[0], sp.glm, g, ch, f);
+#pragma unroll
+          for (int v = 0; v < NV; v++) S.fx[fb][v][fxr][fxc] = f[v];
+          if (FULL && sp.reflux) {
+            const int face = owner ? (x == 0 ? 0 : -1) : 1;
+            if (face >= 0 && nb[face] <= -3) keep_face_flux(M, nb[face], z * FB + fxr, f);
+          }
+          stencil_flux5<T, 1, FLUX>(ay, sp.limiter, lam[1], sp.glm, g, ch, f);
+#pragma unroll
+          for (int v = 0; v < NV; v++) S.fy[fb][v][fyr][fyc] = f[v];
+          if (FULL && sp.reflux) {
+            const int face = owner ? (y == 0 ? 2 : -1) : 3;
+            if (face >= 0 && nb[face] <= -3) keep_face_flux(M, nb[face], z * FB + fyc, f);
+          }
+        } else if constexpr (XYPAIR) {
           // both faces at once, one per float2 lane
           T f2[NV];
           stencil_flux_xy(ax, ay, sp.glm, g, ch, f, f2);
@@ -646,13 +689,13 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 && !PAIR ? 2 : 1)
           }
         }
       }
-      // owners: own cell of plane z+2 -> primitives (needed by the z face
-      // below); owners 128..255 also a halo cell of plane z+1, whose copies
-      // owners 0..127 waited for before the previous barrier (needed next
+      // owners: own cell of plane z+G -> primitives (needed by the z face
+      // below); owners 256-NH..255 also a halo cell of plane z+1, whose copies
+      // owners 0..NH-1 waited for before the previous barrier (needed next
       // iteration)
       if constexpr (DEEP) asm volatile("cp.async.wait_group 1;\n" ::: "memory");
       else cp_async_wait_all();
-      convert_plane(z + 2);
+      convert_plane(z + G);
       if (z + 1 < NZ) convert_halo(z + 1);
       // float path: the stage input of the own cell, loaded before the z face
       // and the barrier so that its L2 latency overlaps them (the double path
@@ -681,7 +724,7 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 && !PAIR ? 2 : 1)
         T ut = uk - dt * acc;
         if (v == 8) ut = ut * damp;
         un[v] = sp.plain ? ut
-                         : ca * (PRE0 ? S.u0[z % FusedSmem<T, DIM, DEEP>::NU0][v][tid] : U0[at]) +
+                         : ca * (PRE0 ? S.u0[z % Smem::NU0][v][tid] : U0[at]) +
                                cb * ut;
         if (FULL && sp.has2) {
           // SSPRK(5,4) stage 3: w = a2 U2 + b2 (Uk + c2 dt L); U2 is out's
@@ -713,9 +756,10 @@ namespace amrvac {
 template <class T, int DIM, int LIM, int FLUX, bool FULL, bool PAIR = false>
 static int launch_one(amrvac_state* s, const T* U0, const T* Uk, const T* U2, T* out, T* out2,
                       const int* work, int nwork, int* counter, StageParams sp) {
-  static_assert(DIM == 2 || LIM != -2, "five-point limiters: 2D tiles only");
+  static_assert(DIM == 2 || LIM != -2 || sizeof(T) == 4,
+                "five-point limiters in 3D: FP32 bulk only (a double 6-plane ring does not fit)");
   auto kern = DIM == 3 ? k_fused<T, 3, LIM, FLUX, FULL, PAIR> : k_fused2d<T, LIM, FLUX, FULL, PAIR>;
-  const int smem = DIM == 3 ? (int)sizeof(FusedSmem<T, 3, PAIR>)
+  const int smem = DIM == 3 ? (int)sizeof(FusedSmem<T, 3, PAIR, tile_ghosts(LIM)>)
                             : (int)sizeof(Fused2dSmem<T, tile_ghosts(LIM)>);
   static int nsm = 0, per_sm = 0;  // per instantiation, this device
   if (nsm == 0) {
@@ -763,7 +807,7 @@ int launch_fused_l(amrvac_state* s, int k, int epilogue, int g) {
       // ghost slabs of the level-change faces of the stage input (as many
       // layers as the mesh's tiles have ghost cells)
       const int gs = s->ngen < 152 * 8 ? s->ngen : 152 * 8;
-      if (DIM == 2 && s->mesh.ng == NG5)
+      if (s->mesh.ng == NG5)
         k_ghost_slabs<T, DIM, NG5><<<gs, 256, 0, s->stream>>>(s->mesh, Uk, (T*)s->gslab,
                                                                s->d_glist, s->ngen);
       else

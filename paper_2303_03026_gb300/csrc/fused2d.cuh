@@ -48,9 +48,6 @@ template <class T, int G = NG> struct Fused2dSmem {
   int next;
 };
 
-// the tile's ghost layers for a limiter template value (-2: the five-point
-// limiters, chosen at run time)
-__host__ __device__ constexpr int tile_ghosts(int lim) { return lim == -2 ? NG5 : NG; }
 
 template <class T, int LIM, int FLUX, bool FULL, bool PAIR>
 __global__ void __launch_bounds__(FT, sizeof(T) == 4 && !PAIR ? 2 : 1)

@@ -300,9 +300,21 @@ __device__ __forceinline__ T weno5_face(int kind, T vm2, T vm1, T v0, T vp1, T v
     }
   } else if (kind == 1) {
     const T eps = sizeof(T) == 8 ? T(1e-40) : T(1e-36), tau = fabs(b0 - b2);
-    a0 = T(0.1) * (T(1) + tau / (b0 + eps));
-    a1 = T(0.6) * (T(1) + tau / (b1 + eps));
-    a2 = T(0.3) * (T(1) + tau / (b2 + eps));
+    if constexpr (sizeof(T) == 8) {
+      a0 = T(0.1) * (T(1) + tau / (b0 + eps));
+      a1 = T(0.6) * (T(1) + tau / (b1 + eps));
+      a2 = T(0.3) * (T(1) + tau / (b2 + eps));
+    } else {
+      // float: tau5/(beta_k + eps) overflows once a beta_k is 0 and tau5 is
+      // above ~340, so the weights are scaled by the common factor
+      // (beta_min + eps)/(beta_min + eps + tau5): a_k = d_k (beta_min + eps +
+      // r_k tau5)/(beta_min + eps + tau5) with r_k = (beta_min + eps)/(beta_k +
+      // eps) <= 1, so 0 < a_k <= d_k and the normalised weights are unchanged
+      const T bm = fmin(fmin(b0, b1), b2) + eps, den = bm + tau;
+      a0 = T(0.1) * ((bm + (bm / (b0 + eps)) * tau) / den);
+      a1 = T(0.6) * ((bm + (bm / (b1 + eps)) * tau) / den);
+      a2 = T(0.3) * ((bm + (bm / (b2 + eps)) * tau) / den);
+    }
   } else {
     const T eps = T(1e-6);
     a0 = T(0.1) / ((eps + b0) * (eps + b0));

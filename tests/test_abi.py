@@ -121,15 +121,19 @@ def test_scheme_options_validated(lib):
 
 
 def test_five_point_limiters_widen_the_plain_scratch(lib):
-    # three ghost layers in the plain path's padded scratch; the fused kernels
-    # (two ghost layers) are not used for them, and asking for them fails
-    W = wl.c3_turbulence(n=32, bnx=16, precision="fp32")
+    # three ghost layers in the plain path's padded scratch; in 3D the fused
+    # kernel takes them in FP32 bulk only (a double 6-plane ring does not fit),
+    # and never on a mesh mixing two- and five-point levels
+    W = wl.c3_turbulence(n=32, bnx=16, precision="fp64")
     st, n2 = _bytes(lib, W, kernel="plain")
     W.cfg.limiter = "weno5"
     st5, n3 = _bytes(lib, W, kernel="plain")
     assert st == 0 and st5 == 0 and n3 > n2
     assert _bytes(lib, W, kernel="auto") == (0, n3)  # AUTO falls back to PLAIN
     assert _bytes(lib, W, kernel="fused")[0] == 1
+    W.cfg.precision = "fp32"
+    st, nf = _bytes(lib, W, kernel="fused")
+    assert st == 0 and _bytes(lib, W, kernel="auto") == (0, nf)  # AUTO takes FUSED
     W.cfg.limiter = "vanleer"
     W.cfg.level_limiter = {0: "mp5"}
     assert _bytes(lib, W, kernel="fused")[0] == 1

@@ -372,8 +372,9 @@ def test_five_point_full_run(amr, orc, limiter):
     assert (np.abs(got - Uo) / sc).max() < tol
 
 
-def test_fused_rejects_five_point(amr):
-    W = wl.c3_turbulence(n=32, bnx=16, precision="fp32")
+def test_fused_rejects_five_point_in_fp64_3d(amr):
+    # a double 6-plane ring of 22 x 22 planes does not fit in shared memory
+    W = wl.c3_turbulence(n=32, bnx=16, precision="fp64")
     W.cfg.limiter = "weno5"
     with pytest.raises(amr.AmrvacError):
         amr.State.from_workload(W, kernel="fused")
@@ -421,10 +422,84 @@ def test_five_point_fused_2d_ghost_slabs_and_steps(amr, orc):
     assert (np.abs(got - Uo) / sc).max() < 1e-10
 
 
-def test_fused_takes_five_point_only_on_uniform_2d_tiles(amr):
+def test_fused_takes_five_point_only_on_uniform_meshes(amr):
     W = wl.cp_alfven(32)
     W.cfg.limiter = "wenoz5"
     amr.State.from_workload(W, kernel="fused").close()       # 2D, every level five-point
     W.cfg.level_limiter = {1: "vanleer"}                       # mixed ghost widths: plain only
     with pytest.raises(amr.AmrvacError):
         amr.State.from_workload(W, kernel="fused")
+    W3 = wl.c3_turbulence(n=32, bnx=16, precision="fp32")
+    W3.cfg.limiter = "mp5"
+    amr.State.from_workload(W3, kernel="fused").close()      # 3D FP32 bulk: the 6-plane ring
+
+
+def _field_jump(W, by=40.0):
+    # a static tangential discontinuity: at rest, rho = 1, B = (0, by, 0) and
+    # p = 1 on the upper half in x, B = 0 and p = 1 + by^2 / 2 below (total
+    # pressure balanced).  Flat runs (zero smoothness indicators) meet a jump
+    # whose indicator difference is ~1e3, beyond float range for tau5 / eps
+    U = np.zeros_like(W.U)
+    for b in range(W.nblocks):
+        x, y, z = wl.cell_centres(W.cfg, W.instances[int(W.block_meta[b, 0])], W.block_meta[b])
+        one, zero = np.ones_like(x), np.zeros_like(x)
+        up = x > 0.5
+        U[:, b, :] = wl.conserved_from_primitive(W.instances[0].gamma, one, zero, zero, zero,
+                                                 np.where(up, 1.0, 1.0 + 0.5 * by * by), zero,
+                                                 np.where(up, by, 0.0), zero).reshape(9, -1)
+    W.U = U
+    return W
+
+
+def _five_3d_cases():
+    walls = wl.c3_turbulence(n=32, bnx=16, precision="fp32")
+    walls.cfg.bc = (("symmetric", "symmetric"), ("periodic", "periodic"), ("symmetric", "outflow"))
+    rk54 = wl.c3_turbulence(n=32, bnx=16, seed=8, precision="fp32")
+    rk54.cfg.time = "ssprk54"
+    return [(wl.c3_turbulence(n=32, bnx=16, precision="fp32"), 1e-5), (walls, 1e-5),
+            (rk54, 1e-5), (_field_jump(wl.c3_turbulence(n=32, bnx=16, precision="fp32")), 1e-5),
+            (wl.c4_blast_amr(base=4, levels=3, bnx=16, shell=(0.2, 0.26), precision="fp32"),
+             1e-3)]
+
+
+@pytest.mark.parametrize("limiter", FIVE_POINT)
+def test_five_point_fused_3d_stage_parity(amr, orc, limiter):
+    # the 6-plane ring with three-layer halos and slabs (FP32 bulk): every stage
+    # of uniform, walled (FULL kernel), SSPRK(5,4) and AMR meshes against the
+    # oracle at the FP32 stage tolerances of the two-ghost-cell kernels
+    for W, tol in _five_3d_cases():
+        W.cfg.limiter = limiter
+        S = amr.State.from_workload(W, kernel="fused")
+        assert S.ng == 3
+        S.close()
+        _scheme_stage_parity(amr, orc, W, "fused", tol)
+
+
+def test_five_point_fused_3d_steps_and_reflux(amr, orc):
+    # whole steps on the AMR mesh (slabs from the pre-pass, the CFL epilogue):
+    # the FP32 bulk run against the oracle's FP64 run from the same rounded
+    # state, and with refluxing the fused and plain FP32 paths agree
+    W = wl.c4_blast_amr(base=4, levels=3, bnx=16, shell=(0.2, 0.26), precision="fp32")
+    W.cfg.limiter = "mp5"
+    U32 = W.U.astype(np.float32)
+    S = amr.State.from_workload(W, kernel="fused", pressure="fp64")
+    S.set_conserved(U32)
+    S.step(3)
+    got = S.get_conserved(0, precision=0)
+    d = S.diag(raise_on_error=True)
+    S.close()
+    Uo, t, ns, st = orc.mesh_for(W, 8).run(U32.astype(np.float64), 1e30, maxsteps=3)
+    assert st == 0 and ns == 3
+    assert abs(d["t"][0] - t[0]) < 1e-5 * t[0]
+    e = _err(got, Uo, True, d["ch"])
+    assert e.max() < 1e-4, e
+    W.cfg.reflux = True
+    out = {}
+    for kernel in ("fused", "plain"):
+        S = amr.State.from_workload(W, kernel=kernel, pressure="fp64")
+        S.set_conserved(U32)
+        S.step(2)
+        out[kernel] = (S.get_conserved(0, precision=0), S.diag(raise_on_error=True))
+        S.close()
+    e = _err(out["fused"][0], out["plain"][0], True, out["plain"][1]["ch"])
+    assert e.max() < 1e-5, e
