@@ -436,16 +436,17 @@ def test_fused_takes_five_point_only_on_uniform_meshes(amr):
 
 def _field_jump(W, by=40.0):
     # a static tangential discontinuity: at rest, rho = 1, B = (0, by, 0) and
-    # p = 1 on the upper half in x, B = 0 and p = 1 + by^2 / 2 below (total
-    # pressure balanced).  Flat runs (zero smoothness indicators) meet a jump
-    # whose indicator difference is ~1e3, beyond float range for tau5 / eps
+    # p = 100 on the upper half in x, B = 0 and p = 100 + by^2 / 2 below (total
+    # pressure balanced; beta 1/8, so that the stage tests' 1e-3 perturbations
+    # keep p > 0).  Flat runs (zero smoothness indicators) meet jumps whose
+    # indicator differences are ~1e3 and more, beyond float range for tau5 / eps
     U = np.zeros_like(W.U)
     for b in range(W.nblocks):
         x, y, z = wl.cell_centres(W.cfg, W.instances[int(W.block_meta[b, 0])], W.block_meta[b])
         one, zero = np.ones_like(x), np.zeros_like(x)
         up = x > 0.5
         U[:, b, :] = wl.conserved_from_primitive(W.instances[0].gamma, one, zero, zero, zero,
-                                                 np.where(up, 1.0, 1.0 + 0.5 * by * by), zero,
+                                                 np.where(up, 100.0, 100.0 + 0.5 * by * by), zero,
                                                  np.where(up, by, 0.0), zero).reshape(9, -1)
     W.U = U
     return W
