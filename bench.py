@@ -788,12 +788,39 @@ def main():
         barrier()
         el = time.perf_counter() - t0
         nbytes = h_in.numel() * 4
+
+        # the host link alone: one upload, one download, then both at once
+        def link(do_up, do_down):
+            torch.cuda.synchronize(dev)
+            t = time.perf_counter()
+            if do_up:
+                with torch.cuda.stream(up):
+                    d_in[0].copy_(h_in, non_blocking=True)
+            if do_down:
+                with torch.cuda.stream(down):
+                    h_out[0].copy_(d_out[0], non_blocking=True)
+            up.synchronize()
+            down.synchronize()
+            return time.perf_counter() - t
+        link(True, True)
+        t_up = min(link(True, False) for _ in range(2))
+        t_down = min(link(False, True) for _ in range(2))
+        t_both = min(link(True, True) for _ in range(2))
+        # per step the link must carry one input and one result; with the copies
+        # hidden behind the steps the pipeline is bound by the slower of the
+        # two: the step on the device and the link's concurrent transfer
+        bound_s = max(ms_step / 1e3, t_both)
         e2e = {"value": cells_all * n_e2e / max_over_ranks(el, dev), "unit": "cell-updates/s",
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                "steps": n_e2e,
                "method": "pinned host input uploaded and result downloaded every step on "
                          "their own streams through double-buffered device staging, "
-                         "overlapping the steps; wall clock incl. pipeline fill and drain"}
+                         "overlapping the steps; wall clock incl. pipeline fill and drain",
+               "link": {"h2d_gbs": nbytes / t_up / 1e9, "d2h_gbs": nbytes / t_down / 1e9,
+                        "both_gbs": 2 * nbytes / t_both / 1e9,
+                        "bound_value": cells_all / bound_s,
+                        "frac_of_bound": cells_all * n_e2e / max_over_ranks(el, dev) /
+                        (cells_all / bound_s)}}
         del d_in, d_out, h_out
 
     # plain FP64 per-block path on the same workload, and the FP32 error
