@@ -510,19 +510,21 @@ __device__ __forceinline__ void stencil_flux_f2(Acc st, int glm, float g, float 
       else w[v] = make_float2(recon_plus<float>(LIM, a, b, c), recon_minus<float>(LIM, b, c, e));
     }
   } else {
-    // runtime limiter: one switch per face, the variable loop inside
+    // runtime limiter: one switch per face, the variable loop inside (not
+    // unrolled: four limiters inlined at three faces would otherwise crowd the
+    // instruction cache)
     if (lim == AMRVAC_LIM_SUPERBEE) {
-#pragma unroll
+#pragma unroll 1
       for (int v = 0; v < NV; v++) w[v] = sym_pair<1>(st(v, 0), st(v, 1), st(v, 2), st(v, 3), 0.f);
     } else if (lim == AMRVAC_LIM_ALBADA) {
-#pragma unroll
+#pragma unroll 1
       for (int v = 0; v < NV; v++) w[v] = sym_pair<2>(st(v, 0), st(v, 1), st(v, 2), st(v, 3), 0.f);
     } else if (lim == AMRVAC_LIM_CADA3) {
-#pragma unroll
+#pragma unroll 1
       for (int v = 0; v < NV; v++) w[v] = cada3_pair(st(v, 0), st(v, 1), st(v, 2), st(v, 3));
     } else {
       const float beta = lim == AMRVAC_LIM_WOODWARD ? 2.f : 1.4f;
-#pragma unroll
+#pragma unroll 1
       for (int v = 0; v < NV; v++)
         w[v] = sym_pair<0>(st(v, 0), st(v, 1), st(v, 2), st(v, 3), beta);
     }
@@ -541,7 +543,10 @@ template <int D, int FLUX, class Acc>
 __device__ __forceinline__ void stencil_flux5_f2(Acc st, int lim, float lam, int glm, float g,
                                                  float ch, float* f) {
   float2 w[NV];
-#pragma unroll
+  // one copy of the reconstruction for the nine variables (not unrolled): the
+  // limiters' code, four of them behind the runtime switch and inlined at the
+  // three faces, otherwise overflows the instruction cache
+#pragma unroll 1
   for (int v = 0; v < NV; v++) {
     const float c[6] = {st(v, 0), st(v, 1), st(v, 2), st(v, 3), st(v, 4), st(v, 5)};
     w[v] = make_float2(recon5_plus<float>(lim, c, lam), recon5_minus<float>(lim, c + 1, lam));
