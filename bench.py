@@ -319,6 +319,7 @@ def bench_configs(torch, amrvac, dev, args, hbm):
     U = torch.from_numpy(W.U.astype(np.float32)).to(dev)
     S = amrvac.State.from_workload(W, device=dev)
     S.set_conserved(U)
+    tune5 = None if args.no_tune else S.autotune(trial_steps=3)
     S.step(3)
     ms = time_steps(torch, S, 10)
     states, off = [], 0
@@ -327,6 +328,8 @@ def bench_configs(torch, amrvac, dev, args, hbm):
         meta = W.block_meta[off:off + nb].copy()
         meta[:, 0] = 0
         Sq = amrvac.State(W.cfg, [inst], meta, device=dev, stream=S.stream)
+        if tune5 is not None:  # the batched state's launch shape
+            Sq.set_tuning(tune5["ctas_per_sm"], tune5["order"], tune5["dynamic"], tune5["faces"])
         Sq.set_conserved(U[:, off:off + nb].contiguous())
         Sq.step(1)
         states.append(Sq)
@@ -345,7 +348,7 @@ def bench_configs(torch, amrvac, dev, args, hbm):
     out["c5"] = {"workload": "256 uneven 2D instances 64^2..512^2 in 16^2 blocks, FP32 bulk, "
                              "HLLD+vanleer+glm, SSPRK3, per-instance dt",
                  "blocks": int(W.nblocks), "cells": int(cells),
-                 "value": cells / (ms / 1e3), "ms_per_step": ms,
+                 "value": cells / (ms / 1e3), "ms_per_step": ms, "tuning": tune5,
                  "frac": 288 * cells / (ms / 1e3) / 1e9 / hbm,
                  "one_at_a_time": {"value": cells / (msq / 1e3), "ms_per_step": msq,
                                    "launches": "one graph per instance per step"},
@@ -358,6 +361,8 @@ def bench_configs(torch, amrvac, dev, args, hbm):
     W.cfg.limiter = "wenozp5"
     for kern in ("fused", "plain"):
         Sf = amrvac.State.from_workload(W, device=dev, kernel=kern)
+        if kern == "fused" and tune5 is not None:
+            Sf.set_tuning(tune5["ctas_per_sm"], tune5["order"], tune5["dynamic"], "sides")
         Sf.set_conserved(U)
         Sf.step(2)
         msf = time_steps(torch, Sf, 5)
