@@ -302,7 +302,8 @@ def rel_l1_by_var(a, b, ch):
 
 
 def bench_configs(torch, amrvac, dev, args, hbm):
-    """Sub-records of the other workloads of the metric, one GPU, synthetic data:
+    """Sub-records of the other workloads of the metric, one GPU, synthetic data
+    (FP32 bulk with the headline's pressure recovery, --pressure):
     c5, the 256 uneven 2D instances batched in one launch per stage against the
     same instances advanced one at a time; c3, the 256^3 turbulence box in FP32
     bulk and in FP64 on the GPU, with the FP32 error against the FP64 GPU path
@@ -317,7 +318,7 @@ def bench_configs(torch, amrvac, dev, args, hbm):
     W = make_workload("c5", "fp32")[0]
     cells = W.interior_cells()
     U = torch.from_numpy(W.U.astype(np.float32)).to(dev)
-    S = amrvac.State.from_workload(W, device=dev)
+    S = amrvac.State.from_workload(W, device=dev, pressure=args.pressure)
     S.set_conserved(U)
     tune5 = None if args.no_tune else S.autotune(trial_steps=3)
     S.step(3)
@@ -327,9 +328,10 @@ def bench_configs(torch, amrvac, dev, args, hbm):
         nb = int((W.block_meta[:, 0] == q).sum())
         meta = W.block_meta[off:off + nb].copy()
         meta[:, 0] = 0
-        Sq = amrvac.State(W.cfg, [inst], meta, device=dev, stream=S.stream)
-        if tune5 is not None:  # the batched state's launch shape
-            Sq.set_tuning(tune5["ctas_per_sm"], tune5["order"], tune5["dynamic"], tune5["faces"])
+        # the default launch shape: the batched state's dynamic schedule would
+        # add a counter reset to every one of these small launches
+        Sq = amrvac.State(W.cfg, [inst], meta, device=dev, stream=S.stream,
+                          pressure=args.pressure)
         Sq.set_conserved(U[:, off:off + nb].contiguous())
         Sq.step(1)
         states.append(Sq)
@@ -349,6 +351,7 @@ def bench_configs(torch, amrvac, dev, args, hbm):
                              "HLLD+vanleer+glm, SSPRK3, per-instance dt",
                  "blocks": int(W.nblocks), "cells": int(cells),
                  "value": cells / (ms / 1e3), "ms_per_step": ms, "tuning": tune5,
+                 "pressure": args.pressure,
                  "frac": 288 * cells / (ms / 1e3) / 1e9 / hbm,
                  "one_at_a_time": {"value": cells / (msq / 1e3), "ms_per_step": msq,
                                    "launches": "one graph per instance per step"},
@@ -360,7 +363,7 @@ def bench_configs(torch, amrvac, dev, args, hbm):
     five = {}
     W.cfg.limiter = "wenozp5"
     for kern in ("fused", "plain"):
-        Sf = amrvac.State.from_workload(W, device=dev, kernel=kern)
+        Sf = amrvac.State.from_workload(W, device=dev, kernel=kern, pressure=args.pressure)
         if kern == "fused" and tune5 is not None:
             Sf.set_tuning(tune5["ctas_per_sm"], tune5["order"], tune5["dynamic"], "sides")
         Sf.set_conserved(U)
@@ -378,7 +381,7 @@ def bench_configs(torch, amrvac, dev, args, hbm):
     cells = W.interior_cells()
     U64 = W.U.astype(np.float32).astype(np.float64)
     W64 = dataclasses.replace(W, cfg=dataclasses.replace(W.cfg, precision="fp64"))
-    A = amrvac.State.from_workload(W, device=dev)
+    A = amrvac.State.from_workload(W, device=dev, pressure=args.pressure)
     B = amrvac.State.from_workload(W64, device=dev)
     A.set_conserved(U64.astype(np.float32))
     B.set_conserved(U64)
@@ -406,6 +409,7 @@ def bench_configs(torch, amrvac, dev, args, hbm):
     out["c3"] = {"workload": "3D 256^3 Mach-1 beta-0.01 turbulence in 16^3 blocks, "
                              "HLLD+vanleer+glm, SSPRK3",
                  "cells": int(cells), "value": cells / (ms32 / 1e3), "ms_per_step": ms32,
+                 "pressure": args.pressure,
                  "frac": 288 * cells / (ms32 / 1e3) / 1e9 / hbm,
                  "fp64_gpu": {"value": cells / (ms64 / 1e3), "ms_per_step": ms64,
                               "frac": 576 * cells / (ms64 / 1e3) / 1e9 / hbm},
@@ -423,7 +427,7 @@ def bench_configs(torch, amrvac, dev, args, hbm):
     for prec in ("fp64", "fp32"):
         W = make_workload("c2", prec)[0]
         cells = W.interior_cells()
-        S = amrvac.State.from_workload(W, device=dev)
+        S = amrvac.State.from_workload(W, device=dev, pressure=args.pressure)
         S.set_conserved(W.U if prec == "fp64" else W.U.astype(np.float32))
         S.step(3)
         msp = time_steps(torch, S, 20)
@@ -433,6 +437,7 @@ def bench_configs(torch, amrvac, dev, args, hbm):
         S.close()
     out["c2"] = {"workload": "2D Orszag-Tang 1024^2 in 16^2 blocks, HLLD+koren+glm, SSPRK3",
                  "cells": 1024 * 1024, "fp64": res["fp64"], "fp32": res["fp32"],
+                 "pressure_fp32": args.pressure,
                  "l2": "state smaller than L2 (75.5 MB FP64 per register): frac is not a "
                        "roofline measurement"}
     return out
