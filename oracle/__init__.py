@@ -101,7 +101,8 @@ def lib():
 
 _FLUX = {"hll": 0, "hlld": 1, "tvdlf": 2, "hllc": 3}
 _LIM = {"minmod": 0, "vanleer": 1, "koren": 2, "superbee": 3, "woodward": 4, "mcbeta": 5,
-        "albada": 6, "mp5": 7, "weno5": 8, "wenoz5": 9, "cada3": 10, "wenozp5": 11}
+        "albada": 6, "mp5": 7, "weno5": 8, "wenoz5": 9, "cada3": 10, "wenozp5": 11,
+        "venk": 12}
 _FIVE = (7, 8, 9, 11)
 _TIME = {"ssprk2": 0, "ssprk3": 1, "ssprk43": 2, "ssprk54": 3}
 _BC = {"periodic": 0, "outflow": 1, "symmetric": 2}

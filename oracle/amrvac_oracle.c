@@ -18,7 +18,8 @@
  *    `superbee`, `woodward`, `mcbeta` (beta = 1.4) and `albada` of the limiter
  *    table (order 3 for koren, 2 for the others); albada in its TVD form
  *    (zero slope at extrema, like the others); `cada3` (Cada & Torrilhon
- *    2009, third order, two ghost cells, see cada3_phi); and the
+ *    2009, third order, two ghost cells, see cada3_phi); `venk`
+ *    (Venkatakrishnan 1995, see venk_phi; smoothing constant 0); and the
  *    three-ghost-cell five-point `mp5`, `weno5`, `wenoz5` and `wenozp5` (see
  *    mp5_plus, weno5_plus).
  *  - a face whose reconstructed density or pressure is not positive falls back
@@ -238,10 +239,35 @@ static double cada3_face(double dm, double dp) {
   return 0.5 * cada3_phi(dm / dp) * dp;
 }
 
+/* 12 venk (Venkatakrishnan 1995), on the 1D stencil (a, b, c) of a cell: the
+ * unlimited increment from the cell centre to its faces is the central
+ * difference d2 = +-(c - a)/4; a face whose increment d2 has the sign of
+ * D = max(a, b, c) - b (d2 > 0) or D = min(a, b, c) - b (d2 < 0) is limited by
+ *   phi(y) = (y^2 + 2 y)/(y^2 + y + 2),  y = D/d2 >= 0,
+ * written (D^2 + 2 D d2)/(D^2 + 2 d2^2 + D d2), the smooth replacement of
+ * min(1, y); the cell takes the smaller of its two faces' factors, and its
+ * face values are b +- phi d2.  The smoothing constant eps^2 = (K dx)^3 of the
+ * original is taken as 0 (the paper gives no K). */
+static double venk_phi(double D, double d2) {
+  return (D * D + 2.0 * D * d2) / (D * D + 2.0 * d2 * d2 + D * d2);
+}
+
+/* the limited increment phi d2 from b to its right face (the left face gets
+ * the opposite) */
+static double venk_increment(double a, double b, double c) {
+  const double d2 = 0.25 * (c - a);
+  if (d2 == 0.0) return 0.0;
+  const double up = dmax(dmax(a, b), c) - b, dn = dmin(dmin(a, b), c) - b;
+  const double phr = venk_phi(d2 > 0.0 ? up : dn, d2);   /* right face: +d2 */
+  const double phl = venk_phi(d2 > 0.0 ? dn : up, -d2);  /* left face: -d2 */
+  return dmin(phr, phl) * d2;
+}
+
 /* left state at the right face (i+1/2) of the cell with values (a, b, c) */
 static double recon_plus(int lim, double a, double b, double c) {
   double dm = b - a, dp = c - b;
   if (lim == 10) return b + cada3_face(dm, dp);
+  if (lim == 12) return b + venk_increment(a, b, c);
   if (!(dm * dp > 0.0)) return b;
   if (lim >= 3) return b + 0.5 * sym_slope(lim, dm, dp);
   switch (lim) {
@@ -261,6 +287,7 @@ static double recon_minus(int lim, double a, double b, double c) {
   double dm = b - a, dp = c - b;
   /* cada3: the same rule on the mirrored stencil (c, b, a) */
   if (lim == 10) return b + cada3_face(-dp, -dm);
+  if (lim == 12) return b - venk_increment(a, b, c);
   if (!(dm * dp > 0.0)) return b;
   if (lim >= 3) return b - 0.5 * sym_slope(lim, dm, dp);
   switch (lim) {
@@ -826,13 +853,13 @@ orc_mesh* orc_create(const orc_config* cfg, int ninst, const orc_instance* inst,
   m->nblocks = nblocks;
   m->nthreads = 1;
   if (cfg->ndim < 1 || cfg->ndim > 3) FAIL("ndim must be 1..3");
-  if (cfg->limiter < 0 || cfg->limiter > 11) FAIL("limiter must be 0..11");
+  if (cfg->limiter < 0 || cfg->limiter > 12) FAIL("limiter must be 0..12");
   for (int d = 0; d < cfg->ndim; d++)
     for (int side = 0; side < 2; side++)
       if (cfg->bc[d][side] < 0 || cfg->bc[d][side] > 2) FAIL("bc must be 0..2");
   m->ng = five_point(cfg->limiter) ? NG5 : NG;
   for (int L = 0; L < 16; L++) {
-    if (cfg->level_limiter[L] > 11) FAIL("level_limiter must be -1..11");
+    if (cfg->level_limiter[L] > 12) FAIL("level_limiter must be -1..12");
     if (cfg->level_limiter[L] >= 0 && five_point(cfg->level_limiter[L])) m->ng = NG5;
   }
   for (int d = 0; d < 3; d++) {

@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
-SYMMETRIC = ["minmod", "vanleer", "superbee", "woodward", "mcbeta", "albada"]
+SYMMETRIC = ["minmod", "vanleer", "superbee", "woodward", "mcbeta", "albada", "venk"]
 ALL = SYMMETRIC + ["koren"]
 
 
@@ -48,7 +48,7 @@ def test_second_order_tvd_region(orc):
     # Sweby: second-order TVD limiters lie between minmod and superbee
     for r in np.linspace(0.02, 6.0, 300):
         lo, hi = _phi(orc, "minmod", r), _phi(orc, "superbee", r)
-        for lim in ("vanleer", "woodward", "mcbeta", "albada"):
+        for lim in ("vanleer", "woodward", "mcbeta", "albada", "venk"):
             p = _phi(orc, lim, r)
             assert lo - 1e-15 <= p <= hi + 1e-15, (lim, r, p, lo, hi)
             assert p <= min(2 * r, 2) + 1e-15  # TVD bound
@@ -91,7 +91,7 @@ def _cp_err(orc, lim, n):
     return rel_l1(U[7], Ue[7])
 
 
-@pytest.mark.parametrize("lim", ["woodward", "mcbeta", "albada"])
+@pytest.mark.parametrize("lim", ["woodward", "mcbeta", "albada", "venk"])
 def test_new_limiters_second_order_on_cp_wave(orc, lim):
     import math
     e32, e64 = _cp_err(orc, lim, 32), _cp_err(orc, lim, 64)
