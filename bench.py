@@ -52,7 +52,7 @@ def parse():
                    help="override the workload's flux scheme")
     p.add_argument("--limiter", default=None,
                    choices=["minmod", "vanleer", "koren", "superbee", "woodward", "mcbeta",
-                            "albada", "cada3", "mp5", "weno5", "wenoz5", "wenozp5"],
+                            "albada", "cada3", "venk", "mp5", "weno5", "wenoz5", "wenozp5"],
                    help="override the workload's limiter")
     p.add_argument("--no-variants", action="store_true",
                    help="skip the HLL and FP64-pressure variant timings")

@@ -86,7 +86,11 @@ typedef enum {
  * (TVD form), cada3 (the compact third-order limiter function of Cada &
  * Torrilhon 2009: phi(theta) = max(0, min(phi3, max(-theta/2, min(2 theta,
  * phi3, 1.6)))), phi3 = (2 + theta)/3, theta = dm/dp; it keeps a slope at
- * extrema).  Three ghost cells (five-point, fifth order on smooth data): mp5
+ * extrema), venk (Venkatakrishnan 1995 in 1D form: the central increment
+ * (c - a)/4 to each face times the smooth factor (D^2 + 2 D d)/(D^2 + 2 d^2 +
+ * D d), d the face's increment and D the stencil's range beyond the cell value
+ * on d's side, the smaller of the cell's two factors; no smoothing constant).
+ * Three ghost cells (five-point, fifth order on smooth data): mp5
  * (Suresh & Huynh 1997), weno5 (Jiang & Shu 1996, eps = 1e-6), wenoz5 (Borges
  * et al. 2008, exponent 1), wenozp5 (WENO-Z+ of Acker, Borges & Costa 2016:
  * the Z weights with exponent 2 plus lambda (beta_k + eps)/(tau5 + eps),
@@ -109,7 +113,8 @@ typedef enum {
   AMRVAC_LIM_WENO5 = 8,
   AMRVAC_LIM_WENOZ5 = 9,
   AMRVAC_LIM_CADA3 = 10,
-  AMRVAC_LIM_WENOZP5 = 11
+  AMRVAC_LIM_WENOZP5 = 11,
+  AMRVAC_LIM_VENK = 12
 } amrvac_limiter;
 /* time-integration table of Sect. 3: SSPRK(2,2), SSPRK(3,3) (Gottlieb 2005),
  * SSPRK(4,3) and SSPRK(5,4) (Spiteri & Ruuth 2002) */

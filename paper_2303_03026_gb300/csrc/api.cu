@@ -46,13 +46,13 @@ bool config_ok(const amrvac_config* c, std::string& err) {
   }
   if (cells > AMRVAC_MAX_BLOCK_CELLS) return err = "block larger than AMRVAC_MAX_BLOCK_CELLS", false;
   if (c->flux < AMRVAC_FLUX_HLL || c->flux > AMRVAC_FLUX_HLLC) return err = "bad flux", false;
-  if (c->limiter < AMRVAC_LIM_MINMOD || c->limiter > AMRVAC_LIM_WENOZP5)
+  if (c->limiter < AMRVAC_LIM_MINMOD || c->limiter > AMRVAC_LIM_VENK)
     return err = "bad limiter", false;
   if (c->reflux != 0 && c->reflux != 1) return err = "bad reflux", false;
   for (int L = 0; L < AMRVAC_MAX_LEVELS; L++) {
     if (c->level_flux[L] < 0 || c->level_flux[L] > AMRVAC_FLUX_HLLC + 1)
       return err = "bad level_flux", false;
-    if (c->level_limiter[L] < 0 || c->level_limiter[L] > AMRVAC_LIM_WENOZP5 + 1)
+    if (c->level_limiter[L] < 0 || c->level_limiter[L] > AMRVAC_LIM_VENK + 1)
       return err = "bad level_limiter", false;
   }
   if (c->fix_small_values < AMRVAC_FIX_OFF || c->fix_small_values > AMRVAC_FIX_AVERAGE)

@@ -163,9 +163,32 @@ template <class T> __device__ __forceinline__ T cada3_half(T dm, T dp) {
   return T(0.5) * s * pa;
 }
 
+// venk (Venkatakrishnan 1995) in 1D: the central increment d = (c - a)/4 from
+// the centre of the cell (a, b, c) to its right face (the left face gets -d),
+// times phi = (D^2 + 2 D e)/(D^2 + 2 e^2 + D e) per face, e the face's
+// increment and D the range of the stencil beyond b on e's side; the cell
+// takes the smaller factor of its two faces (smoothing constant 0).  D and e
+// are scaled by max(|D|, |e|) first: the denominator is then at least 1, so
+// no square underflows into a 0/0 (D has e's sign or is 0)
+template <class T> __device__ __forceinline__ T venk_phi(T D, T e) {
+  const T m = fmax(fabs(D), fabs(e));
+  const T x = D / m, y = e / m;
+  return (x * x + T(2) * x * y) / (x * x + T(2) * y * y + x * y);
+}
+
+template <class T> __device__ __forceinline__ T venk_increment(T a, T b, T c) {
+  const T d = T(0.25) * (c - a);
+  if (d == T(0)) return T(0);
+  const T up = fmax(fmax(a, b), c) - b, dn = fmin(fmin(a, b), c) - b;
+  const T pr = venk_phi(d > T(0) ? up : dn, d);   // right face: +d
+  const T pl = venk_phi(d > T(0) ? dn : up, -d);  // left face: -d
+  return fmin(pr, pl) * d;
+}
+
 // face value at i+1/2 from the cell with values (a, b, c) = (w_{i-1}, w_i, w_{i+1})
 template <class T> __device__ __forceinline__ T recon_plus(int lim, T a, T b, T c) {
   T dm = b - a, dp = c - b;
+  if (lim == AMRVAC_LIM_VENK) return b + venk_increment(a, b, c);
   if (lim == AMRVAC_LIM_CADA3) return b + cada3_half(dm, dp);  // keeps a slope at extrema
   if (!(dm * dp > T(0))) return b;
   if (lim >= AMRVAC_LIM_SUPERBEE) return b + T(0.5) * sym_slope(lim, dm, dp);
@@ -179,6 +202,7 @@ template <class T> __device__ __forceinline__ T recon_plus(int lim, T a, T b, T 
 // face value at i-1/2 from the cell with values (a, b, c)
 template <class T> __device__ __forceinline__ T recon_minus(int lim, T a, T b, T c) {
   T dm = b - a, dp = c - b;
+  if (lim == AMRVAC_LIM_VENK) return b - venk_increment(a, b, c);
   if (lim == AMRVAC_LIM_CADA3) return b + cada3_half(-dp, -dm);  // the mirrored stencil
   if (!(dm * dp > T(0))) return b;
   if (lim >= AMRVAC_LIM_SUPERBEE) return b - T(0.5) * sym_slope(lim, dm, dp);

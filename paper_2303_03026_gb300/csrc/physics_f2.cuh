@@ -522,6 +522,12 @@ __device__ __forceinline__ void stencil_flux_f2(Acc st, int glm, float g, float 
     } else if (lim == AMRVAC_LIM_CADA3) {
 #pragma unroll 1
       for (int v = 0; v < NV; v++) w[v] = cada3_pair(st(v, 0), st(v, 1), st(v, 2), st(v, 3));
+    } else if (lim == AMRVAC_LIM_VENK) {
+#pragma unroll 1
+      for (int v = 0; v < NV; v++) {
+        const float a = st(v, 0), b = st(v, 1), c = st(v, 2), e = st(v, 3);
+        w[v] = make_float2(b + venk_increment(a, b, c), c - venk_increment(b, c, e));
+      }
     } else {
       const float beta = lim == AMRVAC_LIM_WOODWARD ? 2.f : 1.4f;
 #pragma unroll 1

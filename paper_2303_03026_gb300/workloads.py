@@ -40,7 +40,8 @@ VAR_NAMES = ("rho", "m_x", "m_y", "m_z", "e", "B_x", "B_y", "B_z", "psi")
 # option values shared by the C ABI (include/amrvac.h) and the oracle
 FLUX = {"hll": 0, "hlld": 1, "tvdlf": 2, "hllc": 3}
 LIMITER = {"minmod": 0, "vanleer": 1, "koren": 2, "superbee": 3, "woodward": 4, "mcbeta": 5,
-           "albada": 6, "mp5": 7, "weno5": 8, "wenoz5": 9, "cada3": 10, "wenozp5": 11}
+           "albada": 6, "mp5": 7, "weno5": 8, "wenoz5": 9, "cada3": 10, "wenozp5": 11,
+           "venk": 12}
 TIME = {"ssprk2": 0, "ssprk3": 1, "ssprk43": 2, "ssprk54": 3}
 PRECISION = {"fp64": 0, "fp32": 1}
 BC = {"periodic": 0, "outflow": 1, "symmetric": 2}

@@ -98,15 +98,15 @@ def test_scheme_options_validated(lib):
                             ("hlld", "ssprk3", "mcbeta"), ("hlld", "ssprk2", "woodward"),
                             ("hll", "ssprk3", "mp5"), ("hlld", "ssprk3", "weno5"),
                             ("hllc", "ssprk43", "wenoz5"), ("hlld", "ssprk3", "cada3"),
-                            ("hllc", "ssprk54", "wenozp5")):
+                            ("hllc", "ssprk54", "wenozp5"), ("hll", "ssprk43", "venk")):
         W = wl.small_amr_2d()
         W.cfg.flux, W.cfg.time, W.cfg.limiter = flux, time, lim
         assert _bytes(lib, W)[0] == 0, (flux, time, lim)
     from paper_2303_03026_gb300 import amrvac
     W = wl.small_amr_2d()
-    for field, value in (("flux", 4), ("time", 4), ("limiter", 12), ("limiter", -1),
+    for field, value in (("flux", 4), ("time", 4), ("limiter", 13), ("limiter", -1),
                          ("reflux", 2), ("fix_small_values", 3), ("level_flux", 5),
-                         ("level_limiter", 13), ("level_flux", -1)):
+                         ("level_limiter", 14), ("level_flux", -1)):
         c = amrvac.make_config(W.cfg)
         if field.startswith("level_"):
             getattr(c, field)[2] = value

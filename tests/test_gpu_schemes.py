@@ -176,7 +176,7 @@ def test_full_steps_match_oracle_run(amr, orc, kernel, time, flux):
     S.close()
 
 
-NEW_LIMITERS = ["superbee", "woodward", "mcbeta", "albada", "cada3"]
+NEW_LIMITERS = ["superbee", "woodward", "mcbeta", "albada", "cada3", "venk"]
 
 
 @pytest.mark.parametrize("kernel", ["plain", "auto"])
