@@ -4,18 +4,20 @@
 // One CTA of 272 threads owns one block at a time and loops over the work
 // list (grid = resident CTAs).  Thread (x, y) < 256 owns a column of the block;
 // 16 helper threads take the 32 faces on the +x/+y block boundary.
-//   3D: march over z with a ring of 4 primitive planes in shared memory, each
-//       with its 2-cell x/y halo.  Iteration z:
-//         cp.async copies of plane z+2 (own column; threads 0..127: one x/y
-//           halo cell each):
+//   3D: march over z with a ring of 2G primitive planes in shared memory,
+//       each with its G-cell x/y halo (G = 2 ghost layers: 4 planes of 20 x
+//       20, 128 halo cells a plane; G = 3 for the five-point limiters: 6
+//       planes of 22 x 22, 192 halo cells).  Iteration z:
+//         cp.async copies of plane z+G (own column; threads 0 .. 64G-1: one
+//           x/y halo cell each):
 //           same-level neighbour, outflow clamp or the ghost slab of a
 //           level-change face (built before the launch by k_ghost_slabs);
 //           for stages k > 0 also U0 of the owner's cell of plane z;
 //         x- and y-face fluxes of plane z into shared memory (double-buffered
 //           by plane parity);
 //         wait for the copies, conserved -> primitive in place of the own
-//           cells of plane z+2 and (owners 128..255, one cell each) of the
-//           halo of plane z+1 (float-float or fp64 pressure for FP32 bulk);
+//           cells of plane z+G and (owners 256-64G .. 255, one cell each) of
+//           the halo of plane z+1 (float-float or fp64 pressure for FP32 bulk);
 //         the z-face z+1/2 flux of the thread's own column (registers);
 //         one barrier; update of cell (x, y, z): flux divergence with the
 //           z-face flux carried from the previous plane, psi damping, SSPRK
@@ -36,10 +38,11 @@ namespace amrvac {
 
 constexpr int FB = 16;          // block edge handled by the fused kernel
 // threads per CTA: 256 column owners (x- and y-face of their cell, z-face of
-// their column, their cell's update; owners 0..127 also copy in and owners
-// 128..255 convert one of the 128 x/y halo cells of each plane) and 16
-// helpers (the 32 faces on the +x/+y block boundary).  The 2D kernel uses the
-// same roles with threads 0..127 copying and converting the halo.
+// their column, their cell's update; with two ghost layers owners 0..127 also
+// copy in and owners 128..255 convert one of the 128 x/y halo cells of each
+// plane, with three owners 0..191 and 64..255 share the 192) and 16 helpers
+// (the 32 faces on the +x/+y block boundary).  The 2D kernel uses the same
+// roles with threads 0 .. 64G-1 copying and converting the halo.
 constexpr int FT = FB * FB + FB;
 constexpr int FXW = 20;           // row stride of the face-flux arrays
 
@@ -48,7 +51,8 @@ constexpr int FXW = 20;           // row stride of the face-flux arrays
 __host__ __device__ constexpr int tile_ghosts(int lim) { return lim == -2 ? NG5 : NG; }
 
 // Thread (x, y) of a warp: lanes 0-15 take row r, lanes 16-31 row r + 4, so the
-// two half-warps of a row-stride-20 array fall on disjoint banks (4*20 = 16 mod 32).
+// two half-warps of a row-stride-20 array fall on disjoint banks (4*20 = 16 mod 32;
+// the 22-wide planes of the five-point ring overlap in 8 banks).
 __device__ __forceinline__ int fused_row(int warp, int lane) {
   return (warp & 3) + (warp >> 2) * 8 + (lane >> 4) * 4;
 }

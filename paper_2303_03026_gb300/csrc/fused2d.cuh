@@ -2,12 +2,13 @@
 //
 // A 2D block is a single plane, so the z-march that hides the loads of the 3D
 // kernel does not exist here.  Instead the CTA copies the NEXT block of its
-// work list (conserved values with the 2-cell halo, and U0 for stages k > 0)
+// work list (conserved values with the G-cell halo, and U0 for stages k > 0)
 // into the other of two shared-memory slots with cp.async while it computes
 // the current one.  Per block:
 //   issue the copies of the next block into slot s^1;
 //   wait for this thread's copies of the current block (slot s);
-//   conserved -> primitive: owners their cell, threads 0..127 one halo cell;
+//   conserved -> primitive: owners their cell, threads 0 .. 64G-1 one halo
+//   cell (G = 2, or 3 for the five-point limiters with a 22 x 22 tile);
 //   barrier; x and y faces (owners the low faces of their cell, the 16 helper
 //   threads the +x / +y block-boundary faces);
 //   barrier; update of the owner's cell from the conserved values in slot s.

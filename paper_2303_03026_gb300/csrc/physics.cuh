@@ -8,9 +8,12 @@
 //    formed in float;
 //  - fast magnetosonic speed in the cancellation-free form
 //    c_f^2 = (a^2 + b^2 + sqrt((a^2 - b^2)^2 + 4 a^2 b_t^2)) / 2;
-//  - minmod / vanleer / koren face values (limiter table of Sect. 3.1.1);
+//  - face values of the limiter table of Sect. 3.1.1: minmod, vanleer, koren,
+//    superbee, woodward, mcbeta, albada, cada3 and venk on three cells, mp5,
+//    weno5, wenoz5 and wenozp5 on five;
 //  - glm interface solve of the (B_n, psi) pair (Dedner et al. 2002);
-//  - HLL (Harten 1983) and HLLD (Miyoshi & Kusano 2005) fluxes.
+//  - HLL (Harten 1983), HLLD (Miyoshi & Kusano 2005), TVDLF and HLLC (Li
+//    2005) fluxes.
 #pragma once
 
 #include <math.h>
