@@ -9,17 +9,18 @@
 //       the tiled form stages the quantities in shared memory.
 //   amrvac_regrid_plan (host) and amrvac_regrid_plan_device: the new block
 //       list, closed under 2:1 balance.
-//   k_regrid_transfer: fills a state built on the new list from the old one:
-//       copy, prolongation (coarse value plus minmod-limited slopes times
-//       +-1/4) or restriction (mean of the 2^d children cells).  Sums are
-//       formed in double in a fixed order and rounded once to the state's
-//       precision.
+//   k_regrid_copy, k_regrid_restrict, k_regrid_transfer: fill a state built
+//       on the new list from the old one: copy (kept blocks, wide elements),
+//       restriction (mean of the 2^d children cells) or prolongation (coarse
+//       value plus minmod-limited slopes times +-1/4).  Sums are formed in double in a fixed order
+//       and rounded once to the state's precision.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <array>
 #include <cmath>
 #include <map>
+#include <unordered_map>
 #include <unordered_set>
 #include <vector>
 
@@ -128,7 +129,21 @@ __global__ void __launch_bounds__(256) k_regrid_estimate(DevMesh M, const T* __r
 // not once per stencil use), the cells' estimates accumulate in shared memory
 // over the chunks in ascending variable order, then the block maximum is
 // taken.  Every value and every operation order equals k_regrid_estimate's.
+// A block whose every stencil cell (its cells and their face neighbours)
+// holds bit for bit the conserved values of its first cell is recorded with
+// the estimate 0 without the double arithmetic: equal inputs give equal
+// primitives, every second difference is then exactly 0, so num = 0 and every
+// cell's estimate is +0 (also where den is 0 or the values are not finite,
+// which the quotient's guard turns into 0).
 constexpr int EST_TILED_THREADS = 512;
+
+template <class T> __device__ __forceinline__ bool same_bits(T a, T b);
+template <> __device__ __forceinline__ bool same_bits<float>(float a, float b) {
+  return __float_as_uint(a) == __float_as_uint(b);
+}
+template <> __device__ __forceinline__ bool same_bits<double>(double a, double b) {
+  return __double_as_longlong(a) == __double_as_longlong(b);
+}
 
 template <class T>
 __global__ void __launch_bounds__(EST_TILED_THREADS)
@@ -148,6 +163,28 @@ __global__ void __launch_bounds__(EST_TILED_THREADS)
   const int stride[3] = {1, P0, P0 * P1};
   for (int b = blockIdx.x; b < M.nblocks; b += gridDim.x) {
     const double g = M.gamma[M.blk[b * 5]];
+    // uniform block: every stencil cell equal to the first cell, bit for bit
+    T ref[NV];
+    read_cell(M, U, vs, b, 0, ref);
+    int same = 1;
+    for (int t = threadIdx.x; t < np && same; t += blockDim.x) {
+      const int i = t % P0 - 1, j = (t / P0) % P1 - h1, k = t / (P0 * P1) - h2;
+      const int outside =
+          (i < 0 || i >= M.nx[0]) + (j < 0 || j >= M.nx[1]) + (k < 0 || k >= M.nx[2]);
+      if (outside > 1) continue;
+      T u[NV];
+      block_cell_value(M, U, vs, b, i, j, k, u);
+#pragma unroll
+      for (int v = 0; v < NV; v++) same = same && same_bits(u[v], ref[v]);
+    }
+    if (__syncthreads_and(same)) {
+      if (threadIdx.x == 0) {
+        const int L = M.blk[b * 5 + 1];
+        est[b] = 0.0;
+        flags[b] = (0.0 > thr && L < maxlev) ? 1 : ((0.0 < dthr && L > 0) ? -1 : 0);
+      }
+      continue;  // uniform across the CTA
+    }
     for (int c = threadIdx.x; c < M.ncell; c += blockDim.x) ecell[c] = 0.0;
     for (int c0 = 0; c0 < nw; c0 += nch) {
       const int cn = nw - c0 < nch ? nw - c0 : nch;
@@ -249,68 +286,105 @@ __global__ void __launch_bounds__(256) k_regrid_transfer(DevMesh Ms, const T* __
   for (int b = blockIdx.x; b < Md.nblocks; b += gridDim.x) {
     const int* t = tab + (size_t)b * RTAB_N;
     const int kind = t[0], sb = t[1];
+    if (kind != 1) continue;  // kept blocks: k_regrid_copy; merged parents: k_regrid_restrict
     const int idx[3] = {Md.blk[b * 5 + 2], Md.blk[b * 5 + 3], Md.blk[b * 5 + 4]};
     for (int c = threadIdx.x; c < Md.ncell; c += blockDim.x) {
       const size_t dst = (size_t)b * Md.ncell + c;
-      if (kind == 0) {
-        const size_t src = (size_t)sb * Ms.ncell + c;
-#pragma unroll
-        for (int v = 0; v < NV; v++) Ud[(size_t)v * vsd + dst] = Us[(size_t)v * vss + src];
-        continue;
-      }
       const int ci[3] = {c % nx[0], (c / nx[0]) % nx[1], c / (nx[0] * nx[1])};
       double out[NV];
-      if (kind == 1) {
-        // child cell ci lies in parent cell pc of the split block sb
-        int pc[3];
+      // child cell ci lies in parent cell pc of the split block sb
+      int pc[3];
 #pragma unroll
-        for (int d = 0; d < 3; d++) pc[d] = d < nd ? (idx[d] & 1) * h[d] + ci[d] / 2 : 0;
-        T ub[NV];
-        read_cell(Ms, Us, vss, sb, (pc[2] * nx[1] + pc[1]) * nx[0] + pc[0], ub);
-        double base[NV];
+      for (int d = 0; d < 3; d++) pc[d] = d < nd ? (idx[d] & 1) * h[d] + ci[d] / 2 : 0;
+      T ub[NV];
+      read_cell(Ms, Us, vss, sb, (pc[2] * nx[1] + pc[1]) * nx[0] + pc[0], ub);
+      double base[NV];
 #pragma unroll
-        for (int v = 0; v < NV; v++) out[v] = base[v] = (double)ub[v];
-        for (int d = 0; d < nd; d++) {
-          int p[3] = {pc[0], pc[1], pc[2]}, m[3] = {pc[0], pc[1], pc[2]};
-          p[d] += 1;
-          m[d] -= 1;
-          T up[NV], um[NV];
-          block_cell_value(Ms, Us, vss, sb, p[0], p[1], p[2], up);
-          block_cell_value(Ms, Us, vss, sb, m[0], m[1], m[2], um);
-          const double w = (ci[d] & 1) ? 0.25 : -0.25;
+      for (int v = 0; v < NV; v++) out[v] = base[v] = (double)ub[v];
+      for (int d = 0; d < nd; d++) {
+        int p[3] = {pc[0], pc[1], pc[2]}, m[3] = {pc[0], pc[1], pc[2]};
+        p[d] += 1;
+        m[d] -= 1;
+        T up[NV], um[NV];
+        block_cell_value(Ms, Us, vss, sb, p[0], p[1], p[2], up);
+        block_cell_value(Ms, Us, vss, sb, m[0], m[1], m[2], um);
+        const double w = (ci[d] & 1) ? 0.25 : -0.25;
 #pragma unroll
-          for (int v = 0; v < NV; v++) {
-            const double a = base[v] - (double)um[v], bb = (double)up[v] - base[v];
-            const double sl = a * bb > 0.0 ? (a > 0.0 ? fmin(a, bb) : fmax(a, bb)) : 0.0;
-            out[v] = out[v] + w * sl;
-          }
+        for (int v = 0; v < NV; v++) {
+          const double a = base[v] - (double)um[v], bb = (double)up[v] - base[v];
+          const double sl = a * bb > 0.0 ? (a > 0.0 ? fmin(a, bb) : fmax(a, bb)) : 0.0;
+          out[v] = out[v] + w * sl;
         }
-      } else {
-        // merged parent: its cell ci covers 2^d cells of one child
-        int o[3], f0[3];
-#pragma unroll
-        for (int d = 0; d < 3; d++) {
-          o[d] = d < nd ? ci[d] / h[d] : 0;
-          f0[d] = d < nd ? 2 * ci[d] - o[d] * nx[d] : 0;
-        }
-        const int cb = t[2 + (o[2] * 2 + o[1]) * 2 + o[0]];
-#pragma unroll
-        for (int v = 0; v < NV; v++) out[v] = 0.0;
-        for (int fz = 0; fz < (nd > 2 ? 2 : 1); fz++)
-          for (int fy = 0; fy < (nd > 1 ? 2 : 1); fy++)
-            for (int fx = 0; fx < 2; fx++) {
-              const size_t src = (size_t)cb * Ms.ncell +
-                                 ((size_t)(f0[2] + fz) * nx[1] + (f0[1] + fy)) * nx[0] + f0[0] + fx;
-#pragma unroll
-              for (int v = 0; v < NV; v++) out[v] += (double)Us[(size_t)v * vss + src];
-            }
-        const double inv = nd == 3 ? 0.125 : (nd == 2 ? 0.25 : 0.5);  // exact
-#pragma unroll
-        for (int v = 0; v < NV; v++) out[v] *= inv;
       }
 #pragma unroll
       for (int v = 0; v < NV; v++) Ud[(size_t)v * vsd + dst] = (T)out[v];
     }
+  }
+}
+
+// merged parents of a transfer (kind 2 in the table): each cell the mean of
+// the 2^d cells of one child it covers, summed in double in a fixed order and
+// rounded once; a kernel of its own, so that the register-heavy prolongation
+// does not limit its occupancy
+template <class T>
+__global__ void __launch_bounds__(256) k_regrid_restrict(DevMesh Ms, const T* __restrict__ Us,
+                                                         DevMesh Md, T* __restrict__ Ud,
+                                                         const int* __restrict__ tab) {
+  const size_t vss = (size_t)Ms.nblocks * Ms.ncell, vsd = (size_t)Md.nblocks * Md.ncell;
+  const int nd = Md.ndim;
+  const int nx[3] = {Md.nx[0], Md.nx[1], Md.nx[2]};
+  const int h[3] = {nx[0] / 2, nd > 1 ? nx[1] / 2 : 1, nd > 2 ? nx[2] / 2 : 1};
+  for (int b = blockIdx.x; b < Md.nblocks; b += gridDim.x) {
+    const int* t = tab + (size_t)b * RTAB_N;
+    if (t[0] != 2) continue;
+    for (int c = threadIdx.x; c < Md.ncell; c += blockDim.x) {
+      const size_t dst = (size_t)b * Md.ncell + c;
+      const int ci[3] = {c % nx[0], (c / nx[0]) % nx[1], c / (nx[0] * nx[1])};
+      double out[NV];
+      // merged parent: its cell ci covers 2^d cells of one child
+      int o[3], f0[3];
+#pragma unroll
+      for (int d = 0; d < 3; d++) {
+        o[d] = d < nd ? ci[d] / h[d] : 0;
+        f0[d] = d < nd ? 2 * ci[d] - o[d] * nx[d] : 0;
+      }
+      const int cb = t[2 + (o[2] * 2 + o[1]) * 2 + o[0]];
+#pragma unroll
+      for (int v = 0; v < NV; v++) out[v] = 0.0;
+      for (int fz = 0; fz < (nd > 2 ? 2 : 1); fz++)
+        for (int fy = 0; fy < (nd > 1 ? 2 : 1); fy++)
+          for (int fx = 0; fx < 2; fx++) {
+            const size_t src = (size_t)cb * Ms.ncell +
+                               ((size_t)(f0[2] + fz) * nx[1] + (f0[1] + fy)) * nx[0] + f0[0] + fx;
+#pragma unroll
+            for (int v = 0; v < NV; v++) out[v] += (double)Us[(size_t)v * vss + src];
+          }
+      const double inv = nd == 3 ? 0.125 : (nd == 2 ? 0.25 : 0.5);  // exact
+#pragma unroll
+      for (int v = 0; v < NV; v++) out[v] *= inv;
+#pragma unroll
+      for (int v = 0; v < NV; v++) Ud[(size_t)v * vsd + dst] = (T)out[v];
+    }
+  }
+}
+
+// the kept blocks of a transfer (kind 0 in the table): each variable's run of
+// cells copied from the source block, W-wide elements (the run length in W
+// units is nw), every other block skipped; a lean kernel at full occupancy
+// beside the register-heavy prolongation of k_regrid_transfer
+template <class W>
+__global__ void __launch_bounds__(256) k_regrid_copy(const W* __restrict__ Us, W* __restrict__ Ud,
+                                                     const int* __restrict__ tab, int nblocks_dst,
+                                                     size_t vss, size_t vsd, int nw) {
+  const size_t total = (size_t)nblocks_dst * NV * nw;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int x = (int)(e % nw);
+    const size_t r = e / nw;
+    const int v = (int)(r % NV), b = (int)(r / NV);
+    const int* t = tab + (size_t)b * RTAB_N;
+    if (t[0] != 0) continue;
+    Ud[(size_t)v * vsd + (size_t)b * nw + x] = Us[(size_t)v * vss + (size_t)t[1] * nw + x];
   }
 }
 
@@ -550,7 +624,10 @@ extern "C" amrvac_status amrvac_regrid_transfer(amrvac_state* src, int32_t src_b
   for (int q = 0; q < src->ninst; q++)
     for (int d = 0; d < nd; d++)
       if (src->inst[q].base_blocks[d] != dst->inst[q].base_blocks[d]) return AMRVAC_E_INVALID;
-  std::map<Key, int> old;
+  // the source blocks by key (hashed: the table is built on the host for every
+  // transfer, tens of thousands of lookups for a C4-size mesh)
+  std::unordered_map<Key, int, KeyHash> old;
+  old.reserve(2 * (size_t)src->nblocks);
   for (int b = 0; b < src->nblocks; b++) {
     const int32_t* r = &src->meta[5 * b];
     old[Key{r[0], r[1], r[2], nd > 1 ? r[3] : 0, nd > 2 ? r[4] : 0}] = b;
@@ -596,16 +673,44 @@ extern "C" amrvac_status amrvac_regrid_transfer(amrvac_state* src, int32_t src_b
                       dst->stream) != cudaSuccess)
     return AMRVAC_E_CUDA;
   const int g = grid_for(dst->nblocks);
-  if (c.precision == AMRVAC_FP64)
+  // kept blocks: 16-byte elements where every run of cells starts on a
+  // 16-byte boundary (the registers are 256-byte aligned), else scalars
+  const size_t rs = c.precision == AMRVAC_FP64 ? 8 : 4;
+  const size_t run = (size_t)dst->ncell * rs;
+  const int gc = 152 * 8;
+  const void* us = src->U[src_buffer];
+  void* ud = dst->U[dst_buffer];
+  if (run % 16 == 0 && ((uintptr_t)us % 16) == 0 && ((uintptr_t)ud % 16) == 0) {
+    const int nw = (int)(run / 16);
+    k_regrid_copy<float4><<<gc, 256, 0, dst->stream>>>(
+        (const float4*)us, (float4*)ud, dst->d_rtab, dst->nblocks, (size_t)src->nblocks * nw,
+        (size_t)dst->nblocks * nw, nw);
+  } else if (c.precision == AMRVAC_FP64) {
+    k_regrid_copy<double><<<gc, 256, 0, dst->stream>>>(
+        (const double*)us, (double*)ud, dst->d_rtab, dst->nblocks,
+        (size_t)src->nblocks * src->ncell, (size_t)dst->nblocks * dst->ncell, dst->ncell);
+  } else {
+    k_regrid_copy<float><<<gc, 256, 0, dst->stream>>>(
+        (const float*)us, (float*)ud, dst->d_rtab, dst->nblocks,
+        (size_t)src->nblocks * src->ncell, (size_t)dst->nblocks * dst->ncell, dst->ncell);
+  }
+  if (c.precision == AMRVAC_FP64) {
+    k_regrid_restrict<double><<<g, 256, 0, dst->stream>>>(
+        src->mesh, (const double*)src->U[src_buffer], dst->mesh, (double*)dst->U[dst_buffer],
+        dst->d_rtab);
     k_regrid_transfer<double><<<g, 256, 0, dst->stream>>>(
         src->mesh, (const double*)src->U[src_buffer], dst->mesh, (double*)dst->U[dst_buffer],
         dst->d_rtab);
-  else
+  } else {
+    k_regrid_restrict<float><<<g, 256, 0, dst->stream>>>(
+        src->mesh, (const float*)src->U[src_buffer], dst->mesh, (float*)dst->U[dst_buffer],
+        dst->d_rtab);
     k_regrid_transfer<float><<<g, 256, 0, dst->stream>>>(
         src->mesh, (const float*)src->U[src_buffer], dst->mesh, (float*)dst->U[dst_buffer],
         dst->d_rtab);
+  }
   if (cudaPeekAtLastError() != cudaSuccess) return AMRVAC_E_CUDA;
-  dst->launches++;
+  dst->launches += 3;
   // the host table must outlive the asynchronous upload
   if (cudaStreamSynchronize(dst->stream) != cudaSuccess) return AMRVAC_E_CUDA;
   return AMRVAC_OK;
