@@ -322,6 +322,10 @@ __global__ void __launch_bounds__(256) k_regrid_transfer(DevMesh Ms, const T* __
   }
 }
 
+template <class T> struct Pair;
+template <> struct Pair<float> { using type = float2; };
+template <> struct Pair<double> { using type = double2; };
+
 // merged parents of a transfer (kind 2 in the table): each cell the mean of
 // the 2^d cells of one child it covers, summed in double in a fixed order and
 // rounded once; a kernel of its own, so that the register-heavy prolongation
@@ -351,14 +355,21 @@ __global__ void __launch_bounds__(256) k_regrid_restrict(DevMesh Ms, const T* __
       const int cb = t[2 + (o[2] * 2 + o[1]) * 2 + o[0]];
 #pragma unroll
       for (int v = 0; v < NV; v++) out[v] = 0.0;
+      // the two x-neighbours of a child pair in one aligned 2-wide load (the
+      // pair starts at an even cell of an even-width row), summed in the
+      // order (fz, fy, fx)
       for (int fz = 0; fz < (nd > 2 ? 2 : 1); fz++)
-        for (int fy = 0; fy < (nd > 1 ? 2 : 1); fy++)
-          for (int fx = 0; fx < 2; fx++) {
-            const size_t src = (size_t)cb * Ms.ncell +
-                               ((size_t)(f0[2] + fz) * nx[1] + (f0[1] + fy)) * nx[0] + f0[0] + fx;
+        for (int fy = 0; fy < (nd > 1 ? 2 : 1); fy++) {
+          const size_t src = (size_t)cb * Ms.ncell +
+                             ((size_t)(f0[2] + fz) * nx[1] + (f0[1] + fy)) * nx[0] + f0[0];
 #pragma unroll
-            for (int v = 0; v < NV; v++) out[v] += (double)Us[(size_t)v * vss + src];
+          for (int v = 0; v < NV; v++) {
+            const auto pr = *reinterpret_cast<const typename Pair<T>::type*>(
+                Us + (size_t)v * vss + src);
+            out[v] += (double)pr.x;
+            out[v] += (double)pr.y;
           }
+        }
       const double inv = nd == 3 ? 0.125 : (nd == 2 ? 0.25 : 0.5);  // exact
 #pragma unroll
       for (int v = 0; v < NV; v++) out[v] *= inv;
