@@ -146,7 +146,7 @@ template <> __device__ __forceinline__ bool same_bits<double>(double a, double b
 }
 
 template <class T>
-__global__ void __launch_bounds__(EST_TILED_THREADS)
+__global__ void __launch_bounds__(EST_TILED_THREADS, 1)
     k_regrid_estimate_tiled(DevMesh M, const T* __restrict__ U, EstWeights ew, int nch,
                             double thr, double dthr, int maxlev, double* est,
                             signed char* flags) {
@@ -196,7 +196,15 @@ __global__ void __launch_bounds__(EST_TILED_THREADS)
         if (outside > 1) continue;  // edge and corner cells are never read
         double q[NV];
         est_cell(M, U, vs, b, i, j, k, ew, g, q);
-        for (int cc = 0; cc < cn; cc++) tile[(size_t)cc * np + t] = q[vars[c0 + cc]];
+        // the chunk's weighted quantities, q indexed by constants only (a
+        // runtime index would put q in local memory)
+        int rank = 0;
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+          if (v >= (ew.prim ? NV : 1) || ew.w[v] == 0.0) continue;
+          if (rank >= c0 && rank < c0 + cn) tile[(size_t)(rank - c0) * np + t] = q[v];
+          rank++;
+        }
       }
       __syncthreads();
       for (int c = threadIdx.x; c < M.ncell; c += blockDim.x) {
