@@ -283,6 +283,11 @@ int launch_estimate(amrvac_state* s, const T* U, const EstWeights& ew, double th
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
+// children of split blocks (kind 1 in the table): one thread per cell of the
+// parent covered by the child's octant computes that cell's minmod slopes once
+// and writes its 2^d child cells, each the coarse value plus the slopes times
+// +-1/4 summed in the order of the dimensions (the arithmetic of one cell does
+// not depend on which thread does it)
 template <class T>
 __global__ void __launch_bounds__(256) k_regrid_transfer(DevMesh Ms, const T* __restrict__ Us,
                                                          DevMesh Md, T* __restrict__ Ud,
@@ -291,24 +296,23 @@ __global__ void __launch_bounds__(256) k_regrid_transfer(DevMesh Ms, const T* __
   const int nd = Md.ndim;
   const int nx[3] = {Md.nx[0], Md.nx[1], Md.nx[2]};
   const int h[3] = {nx[0] / 2, nd > 1 ? nx[1] / 2 : 1, nd > 2 ? nx[2] / 2 : 1};
+  const int nh = h[0] * h[1] * h[2];  // parent cells under one child block
   for (int b = blockIdx.x; b < Md.nblocks; b += gridDim.x) {
     const int* t = tab + (size_t)b * RTAB_N;
     const int kind = t[0], sb = t[1];
     if (kind != 1) continue;  // kept blocks: k_regrid_copy; merged parents: k_regrid_restrict
     const int idx[3] = {Md.blk[b * 5 + 2], Md.blk[b * 5 + 3], Md.blk[b * 5 + 4]};
-    for (int c = threadIdx.x; c < Md.ncell; c += blockDim.x) {
-      const size_t dst = (size_t)b * Md.ncell + c;
-      const int ci[3] = {c % nx[0], (c / nx[0]) % nx[1], c / (nx[0] * nx[1])};
-      double out[NV];
-      // child cell ci lies in parent cell pc of the split block sb
+    for (int e = threadIdx.x; e < nh; e += blockDim.x) {
+      // parent cell pc of the split block sb, local cell lc of the octant
+      const int lc[3] = {e % h[0], (e / h[0]) % h[1], e / (h[0] * h[1])};
       int pc[3];
 #pragma unroll
-      for (int d = 0; d < 3; d++) pc[d] = d < nd ? (idx[d] & 1) * h[d] + ci[d] / 2 : 0;
+      for (int d = 0; d < 3; d++) pc[d] = d < nd ? (idx[d] & 1) * h[d] + lc[d] : 0;
       T ub[NV];
       read_cell(Ms, Us, vss, sb, (pc[2] * nx[1] + pc[1]) * nx[0] + pc[0], ub);
-      double base[NV];
+      double base[NV], sl[3][NV];
 #pragma unroll
-      for (int v = 0; v < NV; v++) out[v] = base[v] = (double)ub[v];
+      for (int v = 0; v < NV; v++) base[v] = (double)ub[v];
       for (int d = 0; d < nd; d++) {
         int p[3] = {pc[0], pc[1], pc[2]}, m[3] = {pc[0], pc[1], pc[2]};
         p[d] += 1;
@@ -316,16 +320,26 @@ __global__ void __launch_bounds__(256) k_regrid_transfer(DevMesh Ms, const T* __
         T up[NV], um[NV];
         block_cell_value(Ms, Us, vss, sb, p[0], p[1], p[2], up);
         block_cell_value(Ms, Us, vss, sb, m[0], m[1], m[2], um);
-        const double w = (ci[d] & 1) ? 0.25 : -0.25;
 #pragma unroll
         for (int v = 0; v < NV; v++) {
           const double a = base[v] - (double)um[v], bb = (double)up[v] - base[v];
-          const double sl = a * bb > 0.0 ? (a > 0.0 ? fmin(a, bb) : fmax(a, bb)) : 0.0;
-          out[v] = out[v] + w * sl;
+          sl[d][v] = a * bb > 0.0 ? (a > 0.0 ? fmin(a, bb) : fmax(a, bb)) : 0.0;
         }
       }
+      for (int cz = 0; cz < (nd > 2 ? 2 : 1); cz++)
+        for (int cy = 0; cy < (nd > 1 ? 2 : 1); cy++)
+          for (int cx = 0; cx < 2; cx++) {
+            const int co[3] = {cx, cy, cz};
+            const size_t dst = (size_t)b * Md.ncell +
+                               ((size_t)(2 * lc[2] + cz) * nx[1] + (2 * lc[1] + cy)) * nx[0] +
+                               2 * lc[0] + cx;
 #pragma unroll
-      for (int v = 0; v < NV; v++) Ud[(size_t)v * vsd + dst] = (T)out[v];
+            for (int v = 0; v < NV; v++) {
+              double out = base[v];
+              for (int d = 0; d < nd; d++) out = out + (co[d] ? 0.25 : -0.25) * sl[d][v];
+              Ud[(size_t)v * vsd + dst] = (T)out;
+            }
+          }
     }
   }
 }
