@@ -192,3 +192,20 @@ def test_wenozp5_lambda_follows_the_cell_width(orc):
         i = np.arange(2, 10)
         np.testing.assert_allclose(wl_[i], lin[i] + 0.125, rtol=0, atol=1e-14)
         np.testing.assert_allclose(wr_[i], lin[i] - 0.125, rtol=0, atol=1e-14)
+
+
+def test_wenozp5_exponent_two_at_a_jump(orc):
+    # Next to a jump the stencil crossing it has tau5 ~ beta_2 ~ O(jump^2)
+    # while the smooth ones have beta ~ (h p')^2: WENO-Z+ gives the crossing
+    # candidate a weight ~ (beta_smooth / tau5)^2 relative to the smooth ones,
+    # so the face value on the smooth side keeps the smooth (exact for
+    # quadratics) reconstruction to ~1e-9 at h = 0.01; with the exponent 1 of
+    # WENO-Z the weight is ~ beta_smooth / tau5 and the face is ~1e-5 off
+    h, n, i = 0.01, 12, 6
+    xe = 0.5 + h * np.arange(n + 1)
+    a = (xe[1:] ** 3 - xe[:-1] ** 3) / (3 * h)  # cell averages of x^2
+    a[i + 2:] += 1.0                              # a jump between cells i+1 and i+2
+    wl_, _ = orc.reconstruct("wenozp5", a, dx=h)
+    assert abs(wl_[i] - xe[i + 1] ** 2) < 1e-7
+    wz, _ = orc.reconstruct("wenoz5", a, dx=h)
+    assert abs(wz[i] - xe[i + 1] ** 2) > 1e-6  # the exponent-1 weights do not get there
