@@ -99,3 +99,20 @@ def test_density_wave_converges(orc):
     ek = _wave_error(orc, 128, "koren")
     ev = _wave_error(orc, 128, "vanleer")
     assert e[-1] < 1.5 * ek and e[-1] < 0.5 * ev, (e, ek, ev)
+
+
+def test_saturation_for_steep_ratios(orc):
+    # Cada & Torrilhon's LimO3 caps the limiter function at 1.6: for slope
+    # ratios theta = dm/dp above 2.8 (where the third-order phi3 = (2 + theta)/3
+    # passes 1.6) the face increment no longer grows with dm, it stays
+    # 1.6 dp / 2; just below 2.8 it still follows phi3 (continuous at 2.8)
+    for theta in (3.0, 5.0, 10.0, 100.0):
+        for dp in (1.0, -0.5):
+            wl_, _ = orc.reconstruct("cada3", np.array([-theta * dp, 0.0, dp]))
+            assert abs(wl_[1] - 0.8 * dp) < 1e-14 * abs(dp), (theta, dp, wl_[1])
+    for theta in (2.0, 2.7):
+        wl_, _ = orc.reconstruct("cada3", np.array([-theta, 0.0, 1.0]))
+        assert abs(wl_[1] - (2.0 + theta) / 6.0) < 1e-14, (theta, wl_[1])
+    lo, _ = orc.reconstruct("cada3", np.array([-2.8 * (1 - 1e-9), 0.0, 1.0]))
+    hi, _ = orc.reconstruct("cada3", np.array([-2.8 * (1 + 1e-9), 0.0, 1.0]))
+    assert abs(lo[1] - hi[1]) < 1e-9
